@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark: QBX layer-potential targets/s of GIGAQBX on one GB300 per rank.
+
+Workload: 16 x 16 grid of starfish curves (64 panels x 16 nodes each,
+262,144 base nodes, 1,048,576 quadrature nodes, 524,288 QBX centres),
+1,048,576 off-surface targets uniform in the bounding box + 1,048,576
+on-surface targets (the quadrature nodes, two-sided), p_qbx = 8, p_fmm = 15,
+n_max = 32, single-layer potential S in FP64.
+
+One step = the whole hot path for one geometry and density: centres, target
+association, root, keys, quadtree, the six interaction lists (gq_build) and
+upsampling, Stages 2-8 and the final QBX evaluation (gq_eval).  Inputs are
+resident in device memory when the timed region starts; an L2 flush (256 MB
+write) separates timed steps.  `e2e` repeats the step through the same C ABI
+from pinned host buffers, host<->device copies included.
+
+Multi-GPU: one independent replica per rank (the method has no exchange
+step between independent problems); value = all ranks' targets / max time.
+`--impl reference` times the CPU FP64 oracle (plain serial C) on a bounded
+sample of the workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QBX layer-potential targets/sec at stated rel. error vs FP64 oracle; % roofline"
+UNIT = "targets/s"
+NOMINAL_FP64_TFLOPS = 1.25   # GB300 nominal FP64, used only if the probe fails
+SAMPLE_GRID = (8, 6)         # CPU baseline: 48 of the 256 curves, same per-curve sizes
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gigaqbx", choices=["gigaqbx", "reference"])
+    ap.add_argument("--kernel", default="S", choices=["S", "D"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n_off=1 << 20, grid=(16, 16)):
+    import workloads
+    return workloads.starfish_grid(grid[0], grid[1], 64, n_off=n_off, on_surface="up", seed=1)
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_init(args):
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        if args.impl == "gigaqbx":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic work model
+def work_model(geo, p, q):
+    """Units per launch of each stage (pairs), from the exported lists.  Flop
+    weights: direct to centres 14q + 20 per (source, centre) pair, direct to
+    points 10 per pair, M2L 8(p+1)^2 per List 2 pair, List 3 far to centres
+    8(p+1)(q+1) per (box, centre)."""
+    bx = geo.boxes()
+    L = geo.lists()
+    nsrc, nctr, ntgt = bx["nsrc"].astype(np.int64), bx["nctr"].astype(np.int64), bx["ntgt"].astype(np.int64)
+
+    def per_box_sum(name):
+        off, idx = L[name]
+        v = np.zeros(len(off) - 1, np.int64)
+        box = np.repeat(np.arange(len(off) - 1), np.diff(off))
+        np.add.at(v, box, nsrc[idx])
+        return v
+
+    near = per_box_sum("U") + per_box_sum("WC") + per_box_sum("XC")
+    wf = np.diff(L["WF"][0]).astype(np.int64)
+    pairs_ctr = int((near * nctr).sum())
+    pairs_pt = int((near * ntgt).sum())
+    v_pairs = int(len(L["V"][1]))
+    wf_ctr = int((wf * nctr).sum())
+    return {
+        5: dict(name="k_near_centres", units=pairs_ctr, flops_per_unit=14 * q + 20, unit="(source, centre) pair"),
+        6: dict(name="k_near_points", units=pairs_pt, flops_per_unit=10, unit="(source, point) pair"),
+        2: dict(name="k_m2l", units=v_pairs, flops_per_unit=8 * (p + 1) ** 2, unit="List 2 pair"),
+        7: dict(name="k_w_centres", units=wf_ctr, flops_per_unit=8 * (p + 1) * (q + 1), unit="(List 3 far box, centre)"),
+    }
+
+
+STAGE_NAMES = ["upsample", "p2m_m2m", "m2l", "p2l", "l2l", "near_centres", "near_points", "wfar_centres",
+               "wfar_points", "l2qbxl_l2p", "final"]
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(kernel, reps=1):
+    """The CPU oracle (serial C, FP64) on an 8 x 6 sub-grid of the workload:
+    same per-curve discretisation, density recipe and target density (3/16 of
+    the curves and of the off-surface targets).  Build + evaluation timed."""
+    import oracle
+    n_off = (1 << 20) * SAMPLE_GRID[0] * SAMPLE_GRID[1] // 256
+    g = workload(n_off=n_off, grid=SAMPLE_GRID)
+    times = []
+    vals = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        o = oracle.Oracle(g, oracle.default_params(g))
+        vals = o.eval(kernel, g["density"])
+        times.append(time.perf_counter() - t0)
+    nt = len(g["tgt_xy"])
+    return g, vals, nt, times
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(args.kernel)
+    g, _, nt, times = oracle_sample(args.kernel, reps=args.steps)
+    tot = sum(times)
+    value = nt * args.steps / tot
+    sample = (f"oracle build + {args.kernel} evaluation of a {SAMPLE_GRID[0]}x{SAMPLE_GRID[1]} sub-grid "
+              f"({nt} targets, {len(g['up_w'])} quadrature nodes) per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "starfish-grid16x16x64x16-p8-15 (sub-grid sample)",
+                                             "kernel": args.kernel, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local):
+    import torch
+
+    from paper_1801_04070_gb300 import Geometry, lib, params_default
+    from paper_1801_04070_gb300._lib import GeometryDesc, Stats, TreeInfo, _ptr
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = lib()
+    g = workload()
+    nt = len(g["tgt_xy"])
+    P, Q = int(g["p_fmm"]), int(g["p_qbx"])
+    prm = params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"]))
+    stream = torch.cuda.current_stream(dev)
+
+    # device-resident inputs
+    keys = ("ref_b", "ref_u", "base_xy", "base_n", "up_xy", "up_n", "up_w", "panel_len")
+    dg = {k: torch.tensor(np.ascontiguousarray(g[k], np.float64), device=dev) for k in keys}
+    d_txy = torch.tensor(g["tgt_xy"], dtype=torch.float64, device=dev)
+    d_ton = torch.tensor(g["tgt_onsurf"], dtype=torch.int32, device=dev)
+    d_mu = torch.tensor(g["density"], dtype=torch.float64, device=dev)
+    d_out = torch.empty(nt, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    ctx = C.c_void_p()
+    assert L.gq_create(local, C.c_void_p(stream.cuda_stream), C.byref(ctx)) == 0
+    desc = GeometryDesc(int(g["npanels"]), int(g["nb"]), int(g["nu"]), *[dg[k].data_ptr() for k in keys])
+    geom = C.c_void_p()
+
+    def chk(s):
+        if s != 0:
+            raise RuntimeError(L.gq_last_error(ctx).decode())
+
+    chk(L.gq_geometry_create(ctx, C.byref(desc), C.byref(prm), C.byref(geom)))
+    kern = 0 if args.kernel == "S" else 1
+    st = Stats()
+
+    def step():
+        chk(L.gq_targets_set(geom, nt, d_txy.data_ptr(), d_ton.data_ptr()))
+        chk(L.gq_build(geom))
+        chk(L.gq_eval(geom, kern, d_mu.data_ptr(), d_out.data_ptr(), C.byref(st)))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n0 = C.c_int64()
+    chk(L.gq_context_launches(ctx, C.byref(n0)))
+    step_ms, eval_ms, stage_ms = [], [], np.zeros(11)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            eval_ms.append(st.ms_total)
+            stage_ms += np.array(st.ms_stage[:11])
+    torch.cuda.synchronize()
+    barrier(world)
+    n1 = C.c_int64()
+    chk(L.gq_context_launches(ctx, C.byref(n1)))
+    launches = int(n1.value - n0.value)
+    tot_ms = max_over_ranks(sum(step_ms), world, dev)
+    ms_step = tot_ms / args.steps
+    value = world * nt * args.steps / (tot_ms * 1e-3)
+    stage_ms /= args.steps
+
+    # ---- roofline of the dominant kernel (longest stage), FP64 ALU bound
+    wrap = Geometry.__new__(Geometry)
+    wrap.L, wrap._ctx, wrap._geom, wrap.nt = L, ctx, geom, nt
+    info = TreeInfo()
+    chk(L.gq_tree_info_get(geom, C.byref(info)))
+    wrap.info, wrap.nbox, wrap.nc, wrap.npt, wrap.nsrc = info, info.nbox, info.ncentres, info.npoint_targets, info.nsources
+    model = work_model(wrap, P, Q)
+    dom = int(np.argmax(stage_ms))
+    peak = C.c_double()
+    peak_src = "measured (FP64 FMA probe, gq_probe_fma_peak)"
+    if L.gq_probe_fma_peak(ctx, 0, C.byref(peak)) != 0 or not peak.value > 0:
+        peak.value, peak_src = NOMINAL_FP64_TFLOPS, "nominal GB300 FP64"
+    roof = None
+    if dom in model:
+        m = model[dom]
+        flops = m["units"] * m["flops_per_unit"]
+        achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tf):
+            traffic = json.load(open(tf)).get(m["name"])
+        roof = {"bound": "alu", "kernel": m["name"], "achieved": achieved, "peak": peak.value,
+                "unit": "TFLOP/s", "frac": achieved / peak.value, "traffic": traffic,
+                "peak_source": peak_src, "units_per_launch": m["units"], "unit_of_work": m["unit"],
+                "flops_per_unit": m["flops_per_unit"], "ms_per_launch": stage_ms[dom]}
+    stage_report = {STAGE_NAMES[i]: round(float(stage_ms[i]), 4) for i in range(11)}
+    for i, m in model.items():
+        stage_report[STAGE_NAMES[i] + "_tflops"] = m["units"] * m["flops_per_unit"] / (stage_ms[i] * 1e-3) / 1e12
+
+    # ---- end to end through the same ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.tensor(np.ascontiguousarray(g[k], np.float64)).pin_memory() for k in keys}
+        h_txy = torch.tensor(g["tgt_xy"], dtype=torch.float64).pin_memory()
+        h_ton = torch.tensor(g["tgt_onsurf"], dtype=torch.int32).pin_memory()
+        h_mu = torch.tensor(g["density"], dtype=torch.float64).pin_memory()
+        h_out = torch.empty(nt, dtype=torch.float64).pin_memory()
+        hdesc = GeometryDesc(int(g["npanels"]), int(g["nb"]), int(g["nu"]), *[pin[k].data_ptr() for k in keys])
+        h2d = sum(pin[k].numel() * 8 for k in keys) + h_txy.numel() * 8 + h_ton.numel() * 4 + h_mu.numel() * 8
+        d2h = h_out.numel() * 8
+
+        def step_e2e():
+            hg = C.c_void_p()
+            chk(L.gq_geometry_create(ctx, C.byref(hdesc), C.byref(prm), C.byref(hg)))
+            chk(L.gq_targets_set(hg, nt, h_txy.data_ptr(), h_ton.data_ptr()))
+            chk(L.gq_build(hg))
+            chk(L.gq_eval(hg, kern, h_mu.data_ptr(), h_out.data_ptr(), None))
+            L.gq_geometry_destroy(hg)
+
+        step_e2e()
+        torch.cuda.synchronize()
+        barrier(world)
+        t = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_e2e()
+            torch.cuda.synchronize()
+            t.append(time.perf_counter() - t0)
+        tot = max_over_ranks(sum(t), world, dev)
+        e2e = {"value": world * nt * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * tot / args.steps}
+
+    # ---- CPU oracle baseline and accuracy on the same sample (rank 0, N = 1)
+    cpu = None
+    rel_err = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gs, ref, nts, times = oracle_sample(args.kernel)
+        sgeo = Geometry(gs, params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"])), device=local)
+        sgeo.build()
+        v = sgeo.eval(args.kernel, gs["density"])
+        rel_err = float(np.abs(v - ref).max() / np.abs(ref).max())
+        sgeo.close()
+        cpu = {"value": nts / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"serial C oracle, build + {args.kernel} evaluation of a {SAMPLE_GRID[0]}x{SAMPLE_GRID[1]} "
+                          f"sub-grid of the workload ({nts} targets), {times[0]:.1f} s")}
+
+    L.gq_geometry_destroy(geom)
+    L.gq_destroy(ctx)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": g["name"], "kernel": args.kernel, "targets": nt,
+                   "quadrature_nodes": int(len(g["up_w"])), "centres": int(info.ncentres),
+                   "point_targets": int(info.npoint_targets), "boxes": int(info.nbox),
+                   "p_qbx": Q, "p_fmm": P, "n_max": int(g["n_max"]), "t_f": 0.9,
+                   "step": "gq_targets_set + gq_build + gq_eval", "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "eval_only": {"value": world * nt / (statistics.mean(eval_ms) * 1e-3), "unit": UNIT,
+                      "ms": statistics.mean(eval_ms)},
+        "stages_ms": stage_report,
+        "rel_err_vs_oracle": rel_err,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * gigaqbx.h -- C ABI of the GB300 (sm_103a) GIGAQBX library.
+ *
+ * GIGAQBX evaluates the 2D Laplace single- and double-layer potentials
+ *     S mu(x) = -(1/2pi) int_Gamma mu(y) log|y - x| ds(y)             (Sec. 1, eq. slp)
+ *     D mu(x) = -(1/2pi) int_Gamma mu(y) n(y) . grad_y log|y - x| ds(y) (Sec. 1, eq. dlp)
+ * on, near and away from a curve Gamma by Quadrature by Expansion
+ * (Sec. 2.1, eq. qbx) accelerated by the modified FMM of Sec. 4 (target
+ * confinement regions, 2-away separation, Lists 1, 2, 3 close/far and
+ * 4 close/far; Algorithm, Stages 1-8).
+ *
+ * Inputs follow the problem statement at the start of Sec. 4: (a) a curve
+ * cut into panels carrying a Gauss-Legendre rule, (b) orders chosen from an
+ * accuracy, (c) a density at the panel nodes, (d) target points.
+ *
+ * Conventions for every call
+ *  - Status: 0 (GQ_OK) or a negative GQ_ERR_* code; calls never abort.
+ *    gq_last_error() returns a message for the context's last failure.
+ *  - Pointers marked "host or device" may point to either; the library
+ *    checks with cudaPointerGetAttributes and copies as needed.  The caller
+ *    keeps ownership of every array it passes; the library copies what it
+ *    keeps.  Handles are owned by the library and released by *_destroy.
+ *  - All device work is ordered on the stream given to gq_create.  Outputs
+ *    written to device memory are complete when that stream reaches the
+ *    point after the call; host outputs are complete when the call returns.
+ *  - Arrays of points are interleaved (x0, y0, x1, y1, ...) doubles.
+ *  - Complex coefficients are interleaved (re, im) doubles.
+ */
+#ifndef GIGAQBX_H
+#define GIGAQBX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gq_status;
+#define GQ_OK 0
+#define GQ_ERR_INVALID (-1)     /* bad argument (null, size, order out of range) */
+#define GQ_ERR_NOMEM (-2)       /* device or host allocation failed */
+#define GQ_ERR_CUDA (-3)        /* a CUDA runtime call or kernel failed */
+#define GQ_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define GQ_ERR_UNSUPPORTED (-5) /* degenerate geometry or unsupported parameters */
+#define GQ_ERR_STATE (-6)       /* call out of order (e.g. eval before build) */
+
+typedef struct gq_ctx gq_ctx;
+typedef struct gq_geom gq_geom;
+
+/* Layer potential to evaluate.  GQ_SP is the normal derivative of S at
+ * on-surface targets (Sec. 1, exterior Neumann equation); it is defined for
+ * on-surface (two-sided) targets only, other targets receive NaN. */
+enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
+
+/* Algorithm parameters (Sec. 4.1 and 4.3).
+ *  p_qbx, p_fmm : QBX and FMM orders, 1 <= p_qbx <= 16, 1 <= p_fmm <= 30.
+ *                 0 means "choose from eps": p_fmm = ceil(log2(1/eps)) - 1
+ *                 (FMM error ~ (1/2)^(p_fmm+1), Sec. 4.1, 5.1) and p_qbx by
+ *                 the same rule capped at 16.
+ *  n_max        : subdivide a box owning more than n_max particles eligible
+ *                 for its children (Sec. 4.3, Stage 1).
+ *  tf_num/tf_den: target confinement factor t_f as an exact fraction
+ *                 (0 <= t_f < 1; default 9/10 as in Sec. 5.1).
+ *  w3_demote    : List 3 far boxes with fewer sources are handled directly
+ *                 (Remark 1; Sec. 5.2 uses 15).
+ *  max_level    : deepest tree level (<= 30).
+ *  radius_factor: expansion radius = radius_factor * panel arc length
+ *                 (Sec. 2.2.2 places centres half a panel length off the curve).
+ *  assoc_slack  : an off-surface target is served by the centre minimising
+ *                 |t-c|/r when that ratio is <= assoc_slack (Sec. 2.2.2
+ *                 reports up to 20% slack as harmless); otherwise it is an
+ *                 ordinary FMM point target.
+ */
+typedef struct {
+    int p_qbx, p_fmm, n_max;
+    int tf_num, tf_den;
+    int w3_demote;
+    int max_level;
+    double radius_factor;
+    double assoc_slack;
+    double eps;
+} gq_params;
+
+/* Discretised curve (Sec. 2.1, 2.2.1).  Panel k owns base nodes
+ * [k*nb, (k+1)*nb) and quadrature (upsampled) nodes [k*nu, (k+1)*nu).
+ * ref_b[nb], ref_u[nu]: reference Gauss-Legendre nodes on [-1, 1] of the
+ * base and quadrature rules; the density given at base nodes is carried to
+ * the quadrature nodes by Lagrange interpolation on these nodes.  All
+ * arrays host or device. */
+typedef struct {
+    int npanels, nb, nu;
+    const double *ref_b, *ref_u;
+    const double *base_xy;   /* [npanels*nb][2] base nodes                  */
+    const double *base_n;    /* [npanels*nb][2] unit outward normals         */
+    const double *up_xy;     /* [npanels*nu][2] quadrature nodes             */
+    const double *up_n;      /* [npanels*nu][2] unit outward normals         */
+    const double *up_w;      /* [npanels*nu] quadrature weights (arc length) */
+    const double *panel_len; /* [npanels] panel arc lengths                  */
+} gq_geometry_desc;
+
+/* Per-evaluation statistics (optional output of gq_eval). */
+typedef struct {
+    int64_t kernel_launches;  /* kernels this library launched in the call */
+    double ms_total;          /* device time of the call (CUDA events) */
+    double ms_stage[12];      /* device time per stage group: 0 upsample + strengths,
+                                 1 P2M + M2M, 2 M2L (List 2), 3 P2L (List 4 far),
+                                 4 L2L, 5 direct to centres (Lists 1, 3 close, 4 close),
+                                 6 direct to point targets, 7 List 3 far to centres,
+                                 8 List 3 far to point targets, 9 L2QBXL + L2P,
+                                 10 final QBX evaluation, 11 unused */
+} gq_stats;
+
+/* Tree and list sizes after gq_build. */
+typedef struct {
+    int nbox, nlevels, ncentres, npoint_targets, ntargets, nsources;
+    int64_t list_size[6];     /* U, V, W close, W far, X close, X far */
+} gq_tree_info;
+
+gq_status gq_params_default(gq_params *out);
+
+/* Context on `device`, ordering work on `cuda_stream` (a cudaStream_t; NULL
+ * = the legacy default stream). */
+gq_status gq_create(int device, void *cuda_stream, gq_ctx **out);
+gq_status gq_destroy(gq_ctx *ctx);
+const char *gq_last_error(const gq_ctx *ctx);
+/* Change the stream later calls order their work on. */
+gq_status gq_set_stream(gq_ctx *ctx, void *cuda_stream);
+
+/* Copy a discretised curve to the device and form the QBX centres
+ * (Sec. 2.2.2: two centres per base node at t -/+ r n, r = radius_factor *
+ * panel length; centre 2i on the interior side, 2i+1 on the exterior). */
+gq_status gq_geometry_create(gq_ctx *ctx, const gq_geometry_desc *desc, const gq_params *params,
+                             gq_geom **out);
+gq_status gq_geometry_destroy(gq_geom *g);
+
+/* Set the n targets (host or device).  on_surface_node[i] >= 0 marks an
+ * on-surface target evaluated by the two centres of that base node and
+ * averaged (principal value); -1 marks an off-surface target. */
+gq_status gq_targets_set(gq_geom *g, int n, const double *xy, const int *on_surface_node);
+
+/* Stage 1 and the lists: target association, root box, Morton keys, the
+ * target-confinement quadtree, and Lists 1, 2, 3 close/far, 4 close/far
+ * (Sec. 4.3, Definitions 1-8).  Reused by every later gq_eval. */
+gq_status gq_build(gq_geom *g);
+
+/* Stages 2-8 and the final QBX evaluation (Sec. 4.4 Algorithm; eq. qbx).
+ * density_base: [npanels*nb] density at base nodes (host or device).
+ * out: [ntargets] potential values (host or device).  stats may be NULL. */
+gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *out, gq_stats *stats);
+
+/* Sizes of the built tree. */
+gq_status gq_tree_info_get(gq_geom *g, gq_tree_info *out);
+
+/* Host copies of build results for inspection and bit-exact comparison.
+ * Boxes are numbered level by level, Morton order within a level. */
+gq_status gq_export_root(gq_geom *g, double out[4]); /* lo_x, lo_y, H, u */
+gq_status gq_export_boxes(gq_geom *g, int *level, int64_t *ix, int64_t *iy, int *parent,
+                          int *nsrc, int *nctr, int *ntgt, int *sub_src, int *sub_tgt);
+/* which: 0 U, 1 V, 2 W close, 3 W far, 4 X close, 5 X far.  off[nbox+1], idx[size]. */
+gq_status gq_export_list(gq_geom *g, int which, int *off, int *idx);
+gq_status gq_export_centres(gq_geom *g, double *xy, double *r, int *level);
+/* kind: 0 point target, 1 one-sided QBX target, 2 two-sided; ctr: centre id (two-sided: interior centre) */
+gq_status gq_export_assoc(gq_geom *g, int *kind, int *ctr);
+/* owner box of every source (quadrature node order), centre and target (-1 for QBX targets) */
+gq_status gq_export_owners(gq_geom *g, int *src_owner, int *ctr_owner, int *tgt_owner);
+/* QBX coefficients of the last gq_eval, [ncentres][p_qbx+1] complex, in the
+ * unscaled form of eq. qbx (coefficient of (x - c)^m). */
+gq_status gq_export_qbx(gq_geom *g, double *coeffs);
+
+/* Number of kernels this context has launched so far (all calls). */
+gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out);
+
+/* Measurement helper: throughput of a dependent-chain-free FMA loop on the
+ * context's device, in TFLOP/s (2 flops per FMA).  what = 0: FP64 FMA,
+ * what = 1: FP32 FMA.  Used as the measured peak of the FP64/FP32 roofline;
+ * the paper has no counterpart.  Runs about 0.1 s of device work. */
+gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,243 @@
+"""ctypes binding of include/gigaqbx.h (same function names)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libgigaqbx.so")
+_lock = threading.Lock()
+_lib = None
+
+GQ_S, GQ_D, GQ_SP = 0, 1, 2
+KERNELS = {"S": GQ_S, "D": GQ_D, "SP": GQ_SP}
+LISTS = ("U", "V", "WC", "WF", "XC", "XF")
+
+
+class GigaQBXError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gigaqbx error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("p_qbx", C.c_int), ("p_fmm", C.c_int), ("n_max", C.c_int),
+                ("tf_num", C.c_int), ("tf_den", C.c_int), ("w3_demote", C.c_int),
+                ("max_level", C.c_int), ("radius_factor", C.c_double),
+                ("assoc_slack", C.c_double), ("eps", C.c_double)]
+
+
+class GeometryDesc(C.Structure):
+    _fields_ = [("npanels", C.c_int), ("nb", C.c_int), ("nu", C.c_int),
+                ("ref_b", C.c_void_p), ("ref_u", C.c_void_p), ("base_xy", C.c_void_p),
+                ("base_n", C.c_void_p), ("up_xy", C.c_void_p), ("up_n", C.c_void_p),
+                ("up_w", C.c_void_p), ("panel_len", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("ms_total", C.c_double),
+                ("ms_stage", C.c_double * 12)]
+
+
+class TreeInfo(C.Structure):
+    _fields_ = [("nbox", C.c_int), ("nlevels", C.c_int), ("ncentres", C.c_int),
+                ("npoint_targets", C.c_int), ("ntargets", C.c_int), ("nsources", C.c_int),
+                ("list_size", C.c_int64 * 6)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libgigaqbx.so; raises if it was not built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: run __graft_entry__.build() "
+                              "(or python -m paper_1801_04070_gb300.build)")
+        L = C.CDLL(_LIB_PATH)
+        vp, i32, st = C.c_void_p, C.c_int, C.c_int
+        sig = {
+            "gq_params_default": (st, [C.POINTER(Params)]),
+            "gq_create": (st, [i32, vp, C.POINTER(vp)]),
+            "gq_destroy": (st, [vp]),
+            "gq_last_error": (C.c_char_p, [vp]),
+            "gq_set_stream": (st, [vp, vp]),
+            "gq_geometry_create": (st, [vp, C.POINTER(GeometryDesc), C.POINTER(Params), C.POINTER(vp)]),
+            "gq_geometry_destroy": (st, [vp]),
+            "gq_targets_set": (st, [vp, i32, vp, vp]),
+            "gq_build": (st, [vp]),
+            "gq_eval": (st, [vp, i32, vp, vp, C.POINTER(Stats)]),
+            "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
+            "gq_export_root": (st, [vp, vp]),
+            "gq_export_boxes": (st, [vp] + [vp] * 9),
+            "gq_export_list": (st, [vp, i32, vp, vp]),
+            "gq_export_centres": (st, [vp, vp, vp, vp]),
+            "gq_export_assoc": (st, [vp, vp, vp]),
+            "gq_export_owners": (st, [vp, vp, vp, vp]),
+            "gq_export_qbx": (st, [vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return _lib
+
+
+def params_default(**kw) -> Params:
+    p = Params()
+    lib().gq_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None stays None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _current_stream(device):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Geometry:
+    """One context + discretised curve + targets, built once, evaluated many times."""
+
+    def __init__(self, g: dict, params: Params | None = None, device: int = 0, stream=None):
+        self.L = lib()
+        self._ctx = C.c_void_p()
+        s = stream if stream is not None else _current_stream(device)
+        self._check(self.L.gq_create(device, s, C.byref(self._ctx)), ctx=False)
+        self.params = params or params_default(p_qbx=int(g.get("p_qbx", 5)), p_fmm=int(g.get("p_fmm", 10)),
+                                                n_max=int(g.get("n_max", 32)))
+        keep = {k: np.ascontiguousarray(g[k], np.float64)
+                for k in ("ref_b", "ref_u", "base_xy", "base_n", "up_xy", "up_n", "up_w", "panel_len")}
+        d = GeometryDesc(int(g["npanels"]), int(g["nb"]), int(g["nu"]), _ptr(keep["ref_b"]),
+                         _ptr(keep["ref_u"]), _ptr(keep["base_xy"]), _ptr(keep["base_n"]),
+                         _ptr(keep["up_xy"]), _ptr(keep["up_n"]), _ptr(keep["up_w"]),
+                         _ptr(keep["panel_len"]))
+        self._geom = C.c_void_p()
+        self._check(self.L.gq_geometry_create(self._ctx, C.byref(d), C.byref(self.params), C.byref(self._geom)))
+        self.nbase = int(g["npanels"]) * int(g["nb"])
+        self.nsrc = int(g["npanels"]) * int(g["nu"])
+        self.nt = 0
+        if "tgt_xy" in g:
+            self.set_targets(g["tgt_xy"], g["tgt_onsurf"])
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, status, ctx=True):
+        if status != 0:
+            msg = self.L.gq_last_error(self._ctx).decode() if ctx else "context creation failed"
+            raise GigaQBXError(status, msg)
+
+    def close(self):
+        if getattr(self, "_geom", None):
+            self.L.gq_geometry_destroy(self._geom)
+            self._geom = None
+        if getattr(self, "_ctx", None):
+            self.L.gq_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._check(self.L.gq_set_stream(self._ctx, stream))
+
+    # -------------------------------------------------------------- API
+    def set_targets(self, xy, on_surface_node):
+        xy_a = xy if not isinstance(xy, np.ndarray) else np.ascontiguousarray(xy, np.float64)
+        on_a = on_surface_node if not isinstance(on_surface_node, np.ndarray) else \
+            np.ascontiguousarray(on_surface_node, np.int32)
+        self.nt = int(len(on_a))
+        self._check(self.L.gq_targets_set(self._geom, self.nt, _ptr(xy_a), _ptr(on_a)))
+
+    def build(self):
+        self._check(self.L.gq_build(self._geom))
+        info = TreeInfo()
+        self._check(self.L.gq_tree_info_get(self._geom, C.byref(info)))
+        self.info = info
+        self.nbox = info.nbox
+        self.nc = info.ncentres
+        self.npt = info.npoint_targets
+        return self
+
+    def eval(self, kernel, density, out=None, stats: bool = False):
+        """Evaluate S, D or SP at the targets.  density / out: numpy (host) or
+        torch CUDA tensors (device).  Returns out (allocated on the host when
+        not given) and optionally the library's statistics."""
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        if isinstance(density, np.ndarray):
+            density = np.ascontiguousarray(density, np.float64)
+        if out is None:
+            out = np.empty(self.nt, np.float64)
+        st = Stats()
+        self._check(self.L.gq_eval(self._geom, k, _ptr(density), _ptr(out), C.byref(st)))
+        return (out, st) if stats else out
+
+    # -------------------------------------------------------------- exports
+    def root(self):
+        o = np.zeros(4)
+        self._check(self.L.gq_export_root(self._geom, _ptr(o)))
+        return dict(lo_x=o[0], lo_y=o[1], H=o[2], u=o[3])
+
+    def boxes(self):
+        n = self.nbox
+        d = dict(level=np.zeros(n, np.int32), ix=np.zeros(n, np.int64), iy=np.zeros(n, np.int64),
+                 parent=np.zeros(n, np.int32), nsrc=np.zeros(n, np.int32), nctr=np.zeros(n, np.int32),
+                 ntgt=np.zeros(n, np.int32), sub_src=np.zeros(n, np.int32), sub_tgt=np.zeros(n, np.int32))
+        self._check(self.L.gq_export_boxes(self._geom, *[_ptr(d[k]) for k in
+                                                        ("level", "ix", "iy", "parent", "nsrc", "nctr",
+                                                         "ntgt", "sub_src", "sub_tgt")]))
+        return d
+
+    def lists(self):
+        out = {}
+        for i, name in enumerate(LISTS):
+            n = int(self.info.list_size[i])
+            off = np.zeros(self.nbox + 1, np.int32)
+            idx = np.zeros(max(n, 1), np.int32)
+            self._check(self.L.gq_export_list(self._geom, i, _ptr(off), _ptr(idx)))
+            out[name] = (off, idx[:n])
+        return out
+
+    def centres(self):
+        xy = np.zeros((self.nc, 2)); r = np.zeros(self.nc); lc = np.zeros(self.nc, np.int32)
+        self._check(self.L.gq_export_centres(self._geom, _ptr(xy), _ptr(r), _ptr(lc)))
+        return xy, r, lc
+
+    def association(self):
+        kind = np.zeros(self.nt, np.int32); ctr = np.zeros(self.nt, np.int32)
+        self._check(self.L.gq_export_assoc(self._geom, _ptr(kind), _ptr(ctr)))
+        return kind, ctr
+
+    def owners(self):
+        so = np.zeros(self.nsrc, np.int32); co = np.zeros(self.nc, np.int32); to = np.zeros(self.nt, np.int32)
+        self._check(self.L.gq_export_owners(self._geom, _ptr(so), _ptr(co), _ptr(to)))
+        return so, co, to
+
+    def qbx_coefficients(self):
+        q = np.zeros((self.nc, self.params.p_qbx + 1, 2))
+        self._check(self.L.gq_export_qbx(self._geom, _ptr(q)))
+        return q[..., 0] + 1j * q[..., 1]

@@ -1,0 +1,374 @@
+// gq_api.cu -- the extern "C" boundary declared in include/gigaqbx.h.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "gq_internal.cuh"
+
+void gq_form_centres(gq_geom *g);
+void gq_tables_release(gq_geom *g);
+
+namespace {
+
+gq_status fail(gq_ctx *ctx, const gq_error &e) {
+    if (ctx) ctx->last_error = e.msg;
+    return e.code;
+}
+
+template <class F>
+gq_status guarded(gq_ctx *ctx, F &&f) {
+    try {
+        f();
+        return GQ_OK;
+    } catch (const gq_error &e) {
+        return fail(ctx, e);
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, gq_error{GQ_ERR_NOMEM, "host allocation failed"});
+    } catch (...) {
+        return fail(ctx, gq_error{GQ_ERR_CUDA, "unexpected failure"});
+    }
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+void upload(gq_ctx *ctx, dbuf<T> &dst, const T *src, size_t n) {
+    GQ_REQUIRE(src != nullptr || n == 0, GQ_ERR_INVALID, "null input array");
+    dst.alloc(n);
+    if (n) GQ_CUDA(cudaMemcpyAsync(dst.p, src, sizeof(T) * n, cudaMemcpyDefault, ctx->stream));
+}
+
+// Lagrange interpolation matrix from the nb base reference nodes to the nu
+// quadrature reference nodes of a panel: I[j][i] = prod_{k != i} (u_j - b_k) / (b_i - b_k)
+std::vector<double> lagrange_matrix(const double *rb, int nb, const double *ru, int nu) {
+    std::vector<double> I((size_t)nu * nb);
+    for (int j = 0; j < nu; ++j)
+        for (int i = 0; i < nb; ++i) {
+            double v = 1.0;
+            for (int k = 0; k < nb; ++k)
+                if (k != i) v *= (ru[j] - rb[k]) / (rb[i] - rb[k]);
+            I[(size_t)j * nb + i] = v;
+        }
+    return I;
+}
+
+void resolve_orders(gq_params &p) {
+    if (p.p_fmm <= 0 || p.p_qbx <= 0) {
+        GQ_REQUIRE(p.eps > 0 && p.eps < 1, GQ_ERR_INVALID, "orders of 0 need 0 < eps < 1");
+        int k = (int)ceil(log2(1.0 / p.eps)) - 1;
+        if (p.p_fmm <= 0) p.p_fmm = k < 1 ? 1 : (k > GQ_MAX_PFMM ? GQ_MAX_PFMM : k);
+        if (p.p_qbx <= 0) p.p_qbx = k < 1 ? 1 : (k > GQ_MAX_PQBX ? GQ_MAX_PQBX : k);
+    }
+    GQ_REQUIRE(p.p_qbx >= 1 && p.p_qbx <= GQ_MAX_PQBX, GQ_ERR_INVALID, "p_qbx must be in [1, 16]");
+    GQ_REQUIRE(p.p_fmm >= 1 && p.p_fmm <= GQ_MAX_PFMM, GQ_ERR_INVALID, "p_fmm must be in [1, 30]");
+    GQ_REQUIRE(p.n_max >= 1, GQ_ERR_INVALID, "n_max must be >= 1");
+    GQ_REQUIRE(p.tf_den > 0 && p.tf_num >= 0 && p.tf_num < p.tf_den, GQ_ERR_INVALID, "need 0 <= t_f < 1");
+    GQ_REQUIRE(p.max_level >= 1 && p.max_level <= GQ_KEYBITS, GQ_ERR_INVALID, "max_level must be in [1, 30]");
+    GQ_REQUIRE(p.radius_factor > 0, GQ_ERR_INVALID, "radius_factor must be > 0");
+    GQ_REQUIRE(p.assoc_slack >= 0, GQ_ERR_INVALID, "assoc_slack must be >= 0");
+    GQ_REQUIRE(p.w3_demote >= 1, GQ_ERR_INVALID, "w3_demote must be >= 1");
+}
+
+}  // namespace
+
+extern "C" {
+
+gq_status gq_params_default(gq_params *out) {
+    if (!out) return GQ_ERR_INVALID;
+    memset(out, 0, sizeof(*out));
+    out->p_qbx = 5;
+    out->p_fmm = 10;
+    out->n_max = 32;
+    out->tf_num = 9;
+    out->tf_den = 10;
+    out->w3_demote = 15;
+    out->max_level = 30;
+    out->radius_factor = 0.5;
+    out->assoc_slack = 1.2;
+    out->eps = 0.0;
+    return GQ_OK;
+}
+
+gq_status gq_create(int device, void *cuda_stream, gq_ctx **out) {
+    if (!out) return GQ_ERR_INVALID;
+    *out = nullptr;
+    gq_ctx *ctx = new (std::nothrow) gq_ctx;
+    if (!ctx) return GQ_ERR_NOMEM;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        delete ctx;
+        return GQ_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete ctx;
+        return GQ_ERR_CUDA;
+    }
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    *out = ctx;
+    return GQ_OK;
+}
+
+gq_status gq_destroy(gq_ctx *ctx) {
+    if (!ctx) return GQ_ERR_INVALID;
+    delete ctx;
+    return GQ_OK;
+}
+
+const char *gq_last_error(const gq_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+gq_status gq_set_stream(gq_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return GQ_ERR_INVALID;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return GQ_OK;
+}
+
+gq_status gq_geometry_create(gq_ctx *ctx, const gq_geometry_desc *d, const gq_params *params, gq_geom **out) {
+    if (!ctx || !d || !params || !out) return GQ_ERR_INVALID;
+    *out = nullptr;
+    gq_geom *g = nullptr;
+    gq_status s = guarded(ctx, [&] {
+        GQ_CUDA(cudaSetDevice(ctx->device));
+        GQ_REQUIRE(d->npanels > 0 && d->nb > 0 && d->nu > 0, GQ_ERR_INVALID, "empty geometry");
+        GQ_REQUIRE((long long)d->npanels * d->nu < (1ll << 28), GQ_ERR_UNSUPPORTED, "too many quadrature nodes");
+        g = new gq_geom;
+        g->ctx = ctx;
+        g->prm = *params;
+        resolve_orders(g->prm);
+        g->npanels = d->npanels;
+        g->nb = d->nb;
+        g->nu = d->nu;
+        g->nbase = d->npanels * d->nb;
+        g->nsrc = d->npanels * d->nu;
+        // reference nodes are needed on the host for the interpolation matrix
+        std::vector<double> rb(d->nb), ru(d->nu);
+        GQ_CUDA(cudaMemcpy(rb.data(), d->ref_b, sizeof(double) * d->nb, cudaMemcpyDefault));
+        GQ_CUDA(cudaMemcpy(ru.data(), d->ref_u, sizeof(double) * d->nu, cudaMemcpyDefault));
+        std::vector<double> I = lagrange_matrix(rb.data(), d->nb, ru.data(), d->nu);
+        upload(ctx, g->interp, I.data(), I.size());
+        upload(ctx, g->base_xy, d->base_xy, 2 * (size_t)g->nbase);
+        upload(ctx, g->base_n, d->base_n, 2 * (size_t)g->nbase);
+        upload(ctx, g->up_xy, d->up_xy, 2 * (size_t)g->nsrc);
+        upload(ctx, g->up_n, d->up_n, 2 * (size_t)g->nsrc);
+        upload(ctx, g->up_w, d->up_w, (size_t)g->nsrc);
+        upload(ctx, g->panel_len, d->panel_len, (size_t)g->npanels);
+        gq_form_centres(g);
+        GQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+    if (s != GQ_OK) {
+        delete g;
+        return s;
+    }
+    *out = g;
+    return GQ_OK;
+}
+
+gq_status gq_geometry_destroy(gq_geom *g) {
+    if (!g) return GQ_ERR_INVALID;
+    cudaStreamSynchronize(g->ctx->stream);
+    gq_tables_release(g);
+    delete g;
+    return GQ_OK;
+}
+
+gq_status gq_targets_set(gq_geom *g, int n, const double *xy, const int *on_surface_node) {
+    if (!g || n < 0 || (n > 0 && (!xy || !on_surface_node))) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        std::vector<int> on(n);
+        if (n) GQ_CUDA(cudaMemcpy(on.data(), on_surface_node, sizeof(int) * n, cudaMemcpyDefault));
+        for (int i = 0; i < n; ++i)
+            GQ_REQUIRE(on[i] >= -1 && on[i] < g->nbase, GQ_ERR_INVALID, "on_surface_node out of range");
+        g->nt = n;
+        upload(g->ctx, g->tgt_xy, xy, 2 * (size_t)n);
+        upload(g->ctx, g->tgt_on, on.data(), (size_t)n);
+        GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
+        g->targets_set = true;
+        g->built = false;
+        g->have_eval = false;
+        gq_tables_release(g);
+    });
+}
+
+gq_status gq_build(gq_geom *g) {
+    if (!g) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        GQ_CUDA(cudaSetDevice(g->ctx->device));
+        gq_tables_release(g);
+        gq_form_centres(g);
+        gq_build_all(g);
+        GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
+        g->built = true;
+    });
+}
+
+gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *out, gq_stats *stats) {
+    if (!g || !density_base || (!out && g->nt > 0)) return GQ_ERR_INVALID;
+    if (kernel != GQ_S && kernel != GQ_D && kernel != GQ_SP) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        GQ_REQUIRE(g->built, GQ_ERR_STATE, "gq_eval before gq_build");
+        cudaStream_t st = g->ctx->stream;
+        const double *dens = density_base;
+        if (!is_device_ptr(density_base)) {
+            g->dens_dev.alloc(g->nbase);
+            GQ_CUDA(cudaMemcpyAsync(g->dens_dev.p, density_base, sizeof(double) * g->nbase, cudaMemcpyDefault, st));
+            dens = g->dens_dev.p;
+        }
+        bool out_dev = is_device_ptr(out);
+        double *o = out;
+        if (!out_dev) {
+            g->out_dev.alloc(g->nt);
+            o = g->out_dev.p;
+        }
+        if (stats) memset(stats, 0, sizeof(*stats));
+        gq_eval_all(g, kernel, dens, o, stats);
+        if (!out_dev && g->nt) {
+            GQ_CUDA(cudaMemcpyAsync(out, o, sizeof(double) * g->nt, cudaMemcpyDefault, st));
+            GQ_CUDA(cudaStreamSynchronize(st));
+        }
+    });
+}
+
+gq_status gq_tree_info_get(gq_geom *g, gq_tree_info *out) {
+    if (!g || !out) return GQ_ERR_INVALID;
+    if (!g->built) return GQ_ERR_STATE;
+    out->nbox = g->nbox;
+    out->nlevels = g->nlev;
+    out->ncentres = g->nc;
+    out->npoint_targets = g->npt;
+    out->ntargets = g->nt;
+    out->nsources = g->nsrc;
+    for (int i = 0; i < 6; ++i) out->list_size[i] = g->list_size[i];
+    return GQ_OK;
+}
+
+gq_status gq_export_root(gq_geom *g, double out[4]) {
+    if (!g || !out) return GQ_ERR_INVALID;
+    if (!g->built) return GQ_ERR_STATE;
+    out[0] = g->root.lo_x;
+    out[1] = g->root.lo_y;
+    out[2] = g->root.H;
+    out[3] = g->root.u;
+    return GQ_OK;
+}
+
+gq_status gq_export_boxes(gq_geom *g, int *level, int64_t *ix, int64_t *iy, int *parent, int *nsrc, int *nctr,
+                          int *ntgt, int *sub_src, int *sub_tgt) {
+    if (!g) return GQ_ERR_INVALID;
+    if (!g->built) return GQ_ERR_STATE;
+    return guarded(g->ctx, [&] {
+        int n = g->nbox;
+        std::vector<int> a(n), b(n), c(n), d(n), e(n);
+        auto get = [&](const int *src, int *dst) {
+            if (dst) GQ_CUDA(cudaMemcpy(dst, src, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        };
+        get(g->blev, level);
+        get(g->bparent, parent);
+        get(g->sub_src, sub_src);
+        get(g->sub_tgt, sub_tgt);
+        GQ_CUDA(cudaMemcpy(a.data(), g->bix.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        GQ_CUDA(cudaMemcpy(b.data(), g->biy.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        if (ix) for (int i = 0; i < n; ++i) ix[i] = a[i];
+        if (iy) for (int i = 0; i < n; ++i) iy[i] = b[i];
+        std::vector<int> sb(n), se(n), cb(n), ce(n), pb(n), pe(n);
+        GQ_CUDA(cudaMemcpy(sb.data(), g->src_beg.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        GQ_CUDA(cudaMemcpy(se.data(), g->src_end.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        GQ_CUDA(cudaMemcpy(cb.data(), g->ctr_beg.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        GQ_CUDA(cudaMemcpy(ce.data(), g->ctr_end.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        GQ_CUDA(cudaMemcpy(pb.data(), g->pt_beg.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        GQ_CUDA(cudaMemcpy(pe.data(), g->pt_end.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i) {
+            if (nsrc) nsrc[i] = se[i] - sb[i];
+            if (nctr) nctr[i] = ce[i] - cb[i];
+            if (ntgt) ntgt[i] = pe[i] - pb[i];
+        }
+    });
+}
+
+gq_status gq_export_list(gq_geom *g, int which, int *off, int *idx) {
+    if (!g || which < 0 || which > 5 || !off) return GQ_ERR_INVALID;
+    if (!g->built) return GQ_ERR_STATE;
+    return guarded(g->ctx, [&] {
+        GQ_CUDA(cudaMemcpy(off, g->list_off[which].p, sizeof(int) * (g->nbox + 1), cudaMemcpyDeviceToHost));
+        if (idx && g->list_size[which])
+            GQ_CUDA(cudaMemcpy(idx, g->list_idx[which].p, sizeof(int) * g->list_size[which], cudaMemcpyDeviceToHost));
+    });
+}
+
+gq_status gq_export_centres(gq_geom *g, double *xy, double *r, int *level) {
+    if (!g) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        if (xy) GQ_CUDA(cudaMemcpy(xy, g->c_xy.p, sizeof(double) * 2 * g->nc, cudaMemcpyDeviceToHost));
+        if (r) GQ_CUDA(cudaMemcpy(r, g->c_r.p, sizeof(double) * g->nc, cudaMemcpyDeviceToHost));
+        if (level) {
+            GQ_REQUIRE(g->built, GQ_ERR_STATE, "centre levels need gq_build");
+            GQ_CUDA(cudaMemcpy(level, g->c_lc.p, sizeof(int) * g->nc, cudaMemcpyDeviceToHost));
+        }
+    });
+}
+
+gq_status gq_export_assoc(gq_geom *g, int *kind, int *ctr) {
+    if (!g) return GQ_ERR_INVALID;
+    if (!g->built) return GQ_ERR_STATE;
+    return guarded(g->ctx, [&] {
+        if (kind && g->nt) GQ_CUDA(cudaMemcpy(kind, g->t_kind.p, sizeof(int) * g->nt, cudaMemcpyDeviceToHost));
+        if (ctr && g->nt) GQ_CUDA(cudaMemcpy(ctr, g->t_ctr.p, sizeof(int) * g->nt, cudaMemcpyDeviceToHost));
+    });
+}
+
+gq_status gq_export_owners(gq_geom *g, int *src_owner, int *ctr_owner, int *tgt_owner) {
+    if (!g) return GQ_ERR_INVALID;
+    if (!g->built) return GQ_ERR_STATE;
+    return guarded(g->ctx, [&] {
+        if (src_owner) {
+            std::vector<int> perm(g->nsrc), own(g->nsrc);
+            GQ_CUDA(cudaMemcpy(perm.data(), g->src_perm.p, sizeof(int) * g->nsrc, cudaMemcpyDeviceToHost));
+            GQ_CUDA(cudaMemcpy(own.data(), g->src_owner.p, sizeof(int) * g->nsrc, cudaMemcpyDeviceToHost));
+            for (int j = 0; j < g->nsrc; ++j) src_owner[perm[j]] = own[j];
+        }
+        if (ctr_owner) {
+            std::vector<int> perm(g->nc), own(g->nc);
+            GQ_CUDA(cudaMemcpy(perm.data(), g->ctr_perm.p, sizeof(int) * g->nc, cudaMemcpyDeviceToHost));
+            GQ_CUDA(cudaMemcpy(own.data(), g->ctr_owner.p, sizeof(int) * g->nc, cudaMemcpyDeviceToHost));
+            for (int j = 0; j < g->nc; ++j) ctr_owner[perm[j]] = own[j];
+        }
+        if (tgt_owner) {
+            for (int t = 0; t < g->nt; ++t) tgt_owner[t] = -1;
+            std::vector<int> perm(g->npt), own(g->npt);
+            if (g->npt) {
+                GQ_CUDA(cudaMemcpy(perm.data(), g->pt_perm.p, sizeof(int) * g->npt, cudaMemcpyDeviceToHost));
+                GQ_CUDA(cudaMemcpy(own.data(), g->pt_owner.p, sizeof(int) * g->npt, cudaMemcpyDeviceToHost));
+            }
+            for (int j = 0; j < g->npt; ++j) tgt_owner[perm[j]] = own[j];
+        }
+    });
+}
+
+gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out) {
+    if (!ctx || !out) return GQ_ERR_INVALID;
+    *out = ctx->launches;
+    return GQ_OK;
+}
+
+gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops) {
+    if (!ctx || !tflops || (what != 0 && what != 1)) return GQ_ERR_INVALID;
+    return guarded(ctx, [&] { *tflops = gq_probe_fma(ctx, what); });
+}
+
+gq_status gq_export_qbx(gq_geom *g, double *coeffs) {
+    if (!g || !coeffs) return GQ_ERR_INVALID;
+    if (!g->have_eval) return GQ_ERR_STATE;
+    return guarded(g->ctx, [&] { gq_export_qbx_impl(g, coeffs); });
+}
+
+}  // extern "C"

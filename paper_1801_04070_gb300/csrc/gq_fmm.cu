@@ -1,0 +1,829 @@
+// gq_fmm.cu -- Stages 2-8 of the GIGAQBX Algorithm (Sec. 4.4) and the final
+// QBX evaluation (eq. qbx), in complex-variable form (Sec. 3.1).
+//
+// Complex potential Phi: S mu = -(1/2pi) Re Phi_S with Phi_S(z) = sum q log(z - y),
+// q = w mu; D mu = -(1/2pi) Re Phi_D with Phi_D(z) = sum d / (y - z), d = w mu n.
+//
+// Storage is box-scaled so that translations between same-level boxes do not
+// depend on the level:  a box b of half-width rho keeps
+//   M_b[k] = a_k / rho^k   (multipole about the box centre, eq. multipole)
+//   L_b[m] = beta_m rho^m  (local about the box centre, eq. local)
+// and a QBX centre c of radius r keeps Q_c[m] = beta_m r^m (eq. qbx).
+// Constant terms of S keep their real part (log|.|): imaginary parts of
+// constant terms never feed a real part of any later coefficient or value.
+//
+// Translations used (y = target centre - source centre):
+//   M2M  alpha_m = -a_0 t^m/m + sum_{k<=m} C(m-1,k-1) a_k t^(m-k),  t = -y   (eq. m2m)
+//   M2L  beta_0  = a_0 log y + sum_k a_k / y^k
+//        beta_m  = (-1)^m y^-m [ -a_0/m + sum_k C(m+k-1,k-1) a_k y^-k ]       (eq. m2l,
+//        a_0 term with the sign obtained by expanding log z about y)
+//   L2L  beta_m  = sum_{k>=m} C(k,m) b_k y^(k-m)                             (eq. l2l)
+// M2L is evaluated in that factored form: scale a_k by y^-k, apply the real
+// matrix C(m+k-1,k-1) shared by every pair, scale by (-1)^m y^-m.
+#include <math.h>
+
+#include <map>
+#include <mutex>
+
+#include "gq_internal.cuh"
+
+namespace {
+
+constexpr double kInv2Pi = 0.15915494309189533576888376337251;
+constexpr int kBinN = 64;   // binomial table C(n, k), n, k < 64
+
+struct EvalView {
+    RootInfo R;
+    int P, Q, kernel;
+    const int *blev, *bix, *biy, *bparent;
+    const int4 *bchild;
+    const int *src_beg, *src_end;
+    const int *ctr_beg, *ctr_end, *pt_beg, *pt_end;
+    const int *sub_src, *sub_tgt;
+    const double2 *s_xy;
+    const double2 *str;
+    const double2 *sc_xy;
+    const double *sc_r;
+    const double2 *sp_xy;
+    const int *loff[6];
+    const int *lidx[6];
+    const double *binom;   // [kBinN][kBinN]
+};
+
+__device__ __forceinline__ double box_rho(const RootInfo &R, int l) { return ldexp(R.H, -l); }
+__device__ __forceinline__ double2 box_centre(const RootInfo &R, int l, int ix, int iy) {
+    double h = ldexp(R.H, -l);
+    return make_double2(R.lo_x + (double)(2 * ix + 1) * h, R.lo_y + (double)(2 * iy + 1) * h);
+}
+__device__ __forceinline__ double bin(const EvalView &E, int n, int k) { return E.binom[n * kBinN + k]; }
+
+__device__ __forceinline__ double2 shfl2(double2 v, int src, int width) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src, width), __shfl_sync(0xffffffffu, v.y, src, width));
+}
+__device__ __forceinline__ double2 shfl2_up(double2 v, int d, int width) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, d, width), __shfl_up_sync(0xffffffffu, v.y, d, width));
+}
+__device__ __forceinline__ double2 shfl2_xor(double2 v, int m) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+// lane g of a group of `width` lanes receives u^g
+__device__ __forceinline__ double2 lane_powers(double2 u, int g, int width) {
+    double2 v = g == 0 ? make_double2(1.0, 0.0) : u;
+    for (int o = 1; o < width; o <<= 1) {
+        double2 t = shfl2_up(v, o, width);
+        if (g >= o) v = cmul(v, t);
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------ A1: upsample + strengths
+__global__ void k_strengths(int nsrc, int nu, int nb, const int *__restrict__ src_perm, const double *__restrict__ interp,
+                            const double *__restrict__ dens, const double *__restrict__ s_w,
+                            const double2 *__restrict__ s_n, int kernel, double2 *__restrict__ str) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nsrc) return;
+    int id = src_perm[j];
+    int panel = id / nu, jj = id - panel * nu;
+    const double *row = interp + (size_t)jj * nb;
+    const double *mu_b = dens + (size_t)panel * nb;
+    double mu = 0.0;
+    for (int i = 0; i < nb; ++i) mu += row[i] * mu_b[i];
+    double wm = s_w[j] * mu;
+    str[j] = kernel == GQ_D ? cscale(s_n[j], wm) : make_double2(wm, 0.0);
+}
+
+// ------------------------------------------------------------------ Stage 2: P2M (one warp per leaf, lane = k)
+__global__ void k_p2m(EvalView E, int nwork, const int *__restrict__ work, double2 *__restrict__ M) {
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, k = threadIdx.x & 31;
+    if (wid >= nwork) return;
+    int b = work[wid];
+    int l = E.blev[b];
+    double rho = box_rho(E.R, l), irho = 1.0 / rho;
+    double2 zc = box_centre(E.R, l, E.bix[b], E.biy[b]);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int s = E.src_beg[b]; s < E.src_end[b]; ++s) {
+        double2 y = E.s_xy[s], st = E.str[s];
+        double2 u = make_double2((y.x - zc.x) * irho, (y.y - zc.y) * irho);
+        double2 pk = lane_powers(u, k, 32);           // u^k
+        if (E.kernel == GQ_D) {
+            double2 pkm1 = shfl2_up(pk, 1, 32);        // u^(k-1)
+            if (k >= 1) acc = csub(acc, cscale(cmul(st, pkm1), irho));
+        } else {
+            if (k == 0) acc.x += st.x;
+            else acc = csub(acc, cscale(pk, st.x / k));
+        }
+    }
+    if (k <= E.P) M[(size_t)b * (E.P + 1) + k] = acc;
+}
+
+// ------------------------------------------------------------------ Stage 2: M2M, one thread per (parent, m)
+__global__ void k_m2m(EvalView E, int lstart, int lend, double2 *__restrict__ M) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int P1 = E.P + 1;
+    int b = lstart + (int)(t / P1), m = (int)(t % P1);
+    if (b >= lend) return;
+    int4 c4 = E.bchild[b];
+    int ch[4] = {c4.x, c4.y, c4.z, c4.w};
+    if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;  // leaf
+    if (E.sub_src[b] == 0) return;
+    int l = E.blev[b];
+    double2 zp = box_centre(E.R, l, E.bix[b], E.biy[b]);
+    double rho = box_rho(E.R, l);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int q = 0; q < 4; ++q) {
+        int c = ch[q];
+        if (c < 0 || E.sub_src[c] == 0) continue;
+        double2 zc = box_centre(E.R, l + 1, E.bix[c], E.biy[c]);
+        double2 eta = make_double2((zc.x - zp.x) / rho, (zc.y - zp.y) / rho);
+        const double2 *A = M + (size_t)c * P1;
+        if (m == 0) {
+            acc = cadd(acc, A[0]);
+            continue;
+        }
+        // sum_{k=1}^{m} C(m-1,k-1) A_k 2^-k eta^(m-k), k descending so the power grows
+        double2 pw = make_double2(1.0, 0.0), s = make_double2(0.0, 0.0);
+        for (int k = m; k >= 1; --k) {
+            s = cadd(s, cscale(cmul(A[k], pw), bin(E, m - 1, k - 1) * ldexp(1.0, -k)));
+            pw = cmul(pw, eta);
+        }
+        // pw = eta^m
+        s = csub(s, cscale(pw, A[0].x / m));
+        acc = cadd(acc, s);
+    }
+    M[(size_t)b * P1 + m] = acc;
+}
+
+// ------------------------------------------------------------------ Stage 4: M2L over List 2
+// Groups of G lanes (G = 16 when p_fmm < 16, two boxes per warp); lane g is
+// the order index.  dtab[off][k] = delta^-k for the 11x11 same-level offsets,
+// delta = (z_b - z_d)/rho in units of the half-width.
+template <int G>
+__global__ void k_m2l(EvalView E, int nwork, const int *__restrict__ work, const double2 *__restrict__ M,
+                      const double2 *__restrict__ dtab, const double *__restrict__ logtab, double2 *__restrict__ L) {
+    extern __shared__ double pasc[];   // [P+1][P+1]: C(m+k-1, k-1)
+    int P = E.P, P1 = P + 1;
+    for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) {
+        int m = i / P1, k = i % P1;
+        pasc[i] = k >= 1 ? E.binom[(m + k - 1) * kBinN + (k - 1)] : 0.0;
+    }
+    __syncthreads();
+    int lane = threadIdx.x & 31, g = lane % G;
+    long long grp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    bool act = grp < nwork;
+    int b = act ? work[grp] : 0;
+    int beg = act ? E.loff[1][b] : 0, end = act ? E.loff[1][b + 1] : 0;
+    int n = end - beg, nmax = n;
+    for (int o = G; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    int l = E.blev[b], bx = E.bix[b], by = E.biy[b];
+    double logrho = log(box_rho(E.R, l));
+    double2 acc = make_double2(0.0, 0.0);
+    const double *prow = pasc + (g <= P ? g : 0) * P1;
+    for (int i = 0; i < nmax; ++i) {
+        bool valid = i < n;
+        int d = valid ? E.lidx[1][beg + i] : b;
+        int off = valid ? (by - E.biy[d] + 5) * 11 + (bx - E.bix[d] + 5) : 0;
+        double2 A = (valid && g <= P) ? M[(size_t)d * P1 + g] : make_double2(0.0, 0.0);
+        double2 tk = dtab[off * 32 + g];                       // delta^-g
+        double2 At = g >= 1 ? cmul(A, tk) : make_double2(0.0, 0.0);
+        double A0 = __shfl_sync(0xffffffffu, A.x, 0, G);
+        double2 Gm = make_double2(0.0, 0.0);
+        for (int k = 1; k <= P; ++k) {
+            double2 a = shfl2(At, k, G);
+            double c = prow[k];
+            Gm.x += c * a.x;
+            Gm.y += c * a.y;
+        }
+        if (!valid) continue;
+        if (g == 0) {
+            acc.x += A0 * (logrho + logtab[off]) + Gm.x;
+            acc.y += Gm.y;
+        } else if (g <= P) {
+            double2 t = make_double2(Gm.x - A0 / g, Gm.y);
+            double2 s = (g & 1) ? make_double2(-tk.x, -tk.y) : tk;
+            acc = cadd(acc, cmul(s, t));
+        }
+    }
+    if (act && g <= P) {
+        double2 *dst = L + (size_t)b * P1 + g;
+        *dst = cadd(*dst, acc);
+    }
+}
+
+// ------------------------------------------------------------------ Stage 6b: P2L over List 4 far (warp per box, lane = m)
+__global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, double2 *__restrict__ L) {
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, m = threadIdx.x & 31;
+    if (wid >= nwork) return;
+    int b = work[wid];
+    int beg = E.loff[5][b], end = E.loff[5][b + 1];
+    if (beg == end) return;
+    int l = E.blev[b];
+    double rho = box_rho(E.R, l);
+    double2 zc = box_centre(E.R, l, E.bix[b], E.biy[b]);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = beg; i < end; ++i) {
+        int d = E.lidx[5][i];
+        for (int s = E.src_beg[d]; s < E.src_end[d]; ++s) {
+            double2 y = E.s_xy[s], st = E.str[s];
+            double2 w = make_double2(y.x - zc.x, y.y - zc.y);
+            double n2 = w.x * w.x + w.y * w.y, inv = 1.0 / n2;
+            double2 winv = make_double2(w.x * inv, -w.y * inv);      // 1/w
+            double2 um = lane_powers(cscale(winv, rho), m, 32);      // (rho/w)^m
+            if (E.kernel == GQ_D) {
+                acc = cadd(acc, cmul(cmul(st, winv), um));
+            } else if (m == 0) {
+                acc.x += st.x * 0.5 * log(n2);
+            } else {
+                acc = csub(acc, cscale(um, st.x / m));
+            }
+        }
+    }
+    if (m <= E.P) {
+        double2 *dst = L + (size_t)b * (E.P + 1) + m;
+        *dst = cadd(*dst, acc);
+    }
+}
+
+// ------------------------------------------------------------------ Stage 7: L2L, one thread per (child, m)
+__global__ void k_l2l(EvalView E, int lstart, int lend, double2 *__restrict__ L) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int P1 = E.P + 1;
+    int c = lstart + (int)(t / P1), m = (int)(t % P1);
+    if (c >= lend || E.sub_tgt[c] == 0) return;
+    int p = E.bparent[c];
+    int l = E.blev[c];
+    double rho_p = box_rho(E.R, l - 1);
+    double2 zp = box_centre(E.R, l - 1, E.bix[p], E.biy[p]);
+    double2 zc = box_centre(E.R, l, E.bix[c], E.biy[c]);
+    double2 eta = make_double2((zc.x - zp.x) / rho_p, (zc.y - zp.y) / rho_p);
+    const double2 *B = L + (size_t)p * P1;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = E.P; k >= m; --k) acc = cadd(cmul(acc, eta), cscale(B[k], bin(E, k, m)));
+    double2 *dst = L + (size_t)c * P1 + m;
+    *dst = cadd(*dst, cscale(acc, ldexp(1.0, -m)));
+}
+
+// ------------------------------------------------------------------ Stages 3, 5a, 6a: direct near field
+// One block per target box; the box's List 1, 3 close and 4 close source
+// ranges are flattened into shared memory; each warp takes one target and its
+// lanes stride over the flattened sources.
+constexpr int kNearThreads = 128;
+constexpr int kNearRanges = 256;
+
+struct NearRanges {
+    int beg[kNearRanges];
+    int pre[kNearRanges + 1];
+    int n;
+};
+
+__device__ int block_excl_scan_128(int v, int *wsum) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int off = 0;
+    for (int i = 0; i < w; ++i) off += wsum[i];
+    __syncthreads();
+    return off + x - v;
+}
+
+// load entries [e0, e0 + kNearRanges) of the concatenated lists U, WC, XC of box b
+__device__ void load_ranges(const EvalView &E, int b, int e0, int ne, NearRanges &R, int *wsum) {
+    int n0 = E.loff[0][b + 1] - E.loff[0][b], n2 = E.loff[2][b + 1] - E.loff[2][b];
+    int cnt = min(kNearRanges, ne - e0);
+    int lens[2] = {0, 0};
+    for (int r = 0; r < 2; ++r) {
+        int i = threadIdx.x * 2 + r;
+        if (i < cnt) {
+            int e = e0 + i, d;
+            if (e < n0) d = E.lidx[0][E.loff[0][b] + e];
+            else if (e < n0 + n2) d = E.lidx[2][E.loff[2][b] + e - n0];
+            else d = E.lidx[4][E.loff[4][b] + e - n0 - n2];
+            R.beg[i] = E.src_beg[d];
+            lens[r] = E.src_end[d] - E.src_beg[d];
+        }
+    }
+    int pre = block_excl_scan_128(lens[0] + lens[1], wsum);
+    if (threadIdx.x * 2 < kNearRanges) R.pre[threadIdx.x * 2] = pre;
+    if (threadIdx.x * 2 + 1 < kNearRanges) R.pre[threadIdx.x * 2 + 1] = pre + lens[0];
+    if (threadIdx.x == kNearThreads - 1) R.pre[kNearRanges] = pre + lens[0] + lens[1];
+    if (threadIdx.x == 0) R.n = cnt;
+    __syncthreads();
+}
+
+// QBX coefficients at centres: S: Q_0 = sum q log|w|, Q_m = -(1/m) sum q (r/w)^m;
+// D: Q_m = sum (d/w) (r/w)^m, with w = y - c.
+template <int QQ, int KERNEL>
+__global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int nwork, const int *__restrict__ work,
+                                                                double2 *__restrict__ Qout) {
+    __shared__ NearRanges R;
+    __shared__ int wsum[kNearThreads / 32];
+    int b = work[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
+    int cb = E.ctr_beg[b], ce = E.ctr_end[b];
+    bool single = ne <= kNearRanges;
+    if (single) load_ranges(E, b, 0, ne, R, wsum);
+    for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
+        int c = c0 + w;
+        bool valid = c < ce;
+        double2 cz = valid ? E.sc_xy[c] : make_double2(0.0, 0.0);
+        double rc = valid ? E.sc_r[c] : 1.0;
+        double2 acc[QQ + 1];
+#pragma unroll
+        for (int m = 0; m <= QQ; ++m) acc[m] = make_double2(0.0, 0.0);
+        for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
+            if (!single) {
+                __syncthreads();
+                load_ranges(E, b, e0, ne, R, wsum);
+            }
+            int T = R.pre[R.n];
+            if (valid) {
+                int r = 0;
+                for (int v = lane; v < T; v += 32) {
+                    while (R.pre[r + 1] <= v) ++r;
+                    int s = R.beg[r] + (v - R.pre[r]);
+                    double2 y = E.s_xy[s], st = E.str[s];
+                    double wx = y.x - cz.x, wy = y.y - cz.y;
+                    double n2 = wx * wx + wy * wy;
+                    double inv = 1.0 / n2;
+                    double2 winv = make_double2(wx * inv, -wy * inv);    // 1/w
+                    double2 u = make_double2(rc * winv.x, rc * winv.y);   // r/w
+                    if (KERNEL == GQ_D) {
+                        double2 t = cmul(st, winv);
+                        acc[0] = cadd(acc[0], t);
+#pragma unroll
+                        for (int m = 1; m <= QQ; ++m) {
+                            t = cmul(t, u);
+                            acc[m] = cadd(acc[m], t);
+                        }
+                    } else {
+                        acc[0].x += st.x * (0.5 * log(n2));
+                        double2 t = make_double2(st.x * u.x, st.x * u.y);
+                        acc[1] = cadd(acc[1], t);
+#pragma unroll
+                        for (int m = 2; m <= QQ; ++m) {
+                            t = cmul(t, u);
+                            acc[m] = cadd(acc[m], t);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= QQ; ++m)
+            for (int o = 16; o > 0; o >>= 1) acc[m] = cadd(acc[m], shfl2_xor(acc[m], o));
+        if (valid && lane <= QQ) {
+            double2 v = acc[0];
+#pragma unroll
+            for (int m = 1; m <= QQ; ++m)
+                if (lane == m) v = acc[m];
+            if (KERNEL != GQ_D && lane >= 1) v = cscale(v, -1.0 / lane);
+            Qout[(size_t)c * (QQ + 1) + lane] = v;
+        }
+    }
+}
+
+// potential at point targets: S: sum q log|t - y| (coincident sources skipped), D: Re sum d/(y - t)
+template <int KERNEL>
+__global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nwork, const int *__restrict__ work,
+                                                               double *__restrict__ pot) {
+    __shared__ NearRanges R;
+    __shared__ int wsum[kNearThreads / 32];
+    int b = work[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
+    int tb = E.pt_beg[b], te = E.pt_end[b];
+    bool single = ne <= kNearRanges;
+    if (single) load_ranges(E, b, 0, ne, R, wsum);
+    for (int t0 = tb; t0 < te; t0 += kNearThreads / 32) {
+        int t = t0 + w;
+        bool valid = t < te;
+        double2 tz = valid ? E.sp_xy[t] : make_double2(0.0, 0.0);
+        double acc = 0.0;
+        for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
+            if (!single) {
+                __syncthreads();
+                load_ranges(E, b, e0, ne, R, wsum);
+            }
+            int T = R.pre[R.n];
+            if (valid) {
+                int r = 0;
+                for (int v = lane; v < T; v += 32) {
+                    while (R.pre[r + 1] <= v) ++r;
+                    int s = R.beg[r] + (v - R.pre[r]);
+                    double2 y = E.s_xy[s], st = E.str[s];
+                    double wx = y.x - tz.x, wy = y.y - tz.y;
+                    double n2 = wx * wx + wy * wy;
+                    if (n2 == 0.0) continue;
+                    if (KERNEL == GQ_D) acc += (st.x * wx + st.y * wy) / n2;
+                    else acc += st.x * (0.5 * log(n2));
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (valid && lane == 0) pot[t] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ Stage 5b: List 3 far
+// M2QBXL: warp per centre, loop over the owner box's List 3 far boxes; lane
+// k forms a_k y^-k, lane m <= q applies the M2L matrix row and the (r/y)^m scale.
+__global__ void k_w_centres(EvalView E, int nwork, const int *__restrict__ ctr_box_of,
+                            const double2 *__restrict__ M, double2 *__restrict__ Qout) {
+    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (wid >= nwork) return;
+    int c = (int)wid;
+    int b = ctr_box_of[c];
+    int beg = E.loff[3][b], end = E.loff[3][b + 1];
+    if (beg == end) return;
+    int P = E.P, P1 = P + 1, Qn = E.Q;
+    double2 cz = E.sc_xy[c];
+    double rc = E.sc_r[c];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = beg; i < end; ++i) {
+        int d = E.lidx[3][i];
+        int l = E.blev[d];
+        double rho = box_rho(E.R, l);
+        double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
+        double2 y = make_double2(cz.x - zd.x, cz.y - zd.y);
+        double n2 = y.x * y.x + y.y * y.y, inv = 1.0 / n2;
+        double2 yinv = make_double2(y.x * inv, -y.y * inv);
+        double2 vk = lane_powers(cscale(yinv, rho), lane, 32);   // (rho/y)^k
+        double2 sm = lane_powers(cscale(yinv, rc), lane, 32);    // (r/y)^m
+        double2 A = lane <= P ? M[(size_t)d * P1 + lane] : make_double2(0.0, 0.0);
+        double2 At = lane >= 1 ? cmul(A, vk) : make_double2(0.0, 0.0);
+        double A0 = __shfl_sync(0xffffffffu, A.x, 0);
+        double2 Gm = make_double2(0.0, 0.0);
+        int mrow = lane <= Qn ? lane : 0;
+        for (int k = 1; k <= P; ++k) {
+            double2 a = shfl2(At, k, 32);
+            double cc = E.binom[(mrow + k - 1) * kBinN + (k - 1)];
+            Gm.x += cc * a.x;
+            Gm.y += cc * a.y;
+        }
+        if (lane == 0) {
+            acc.x += A0 * 0.5 * log(n2) + Gm.x;
+            acc.y += Gm.y;
+        } else if (lane <= Qn) {
+            double2 t = make_double2(Gm.x - A0 / lane, Gm.y);
+            double2 s = (lane & 1) ? make_double2(-sm.x, -sm.y) : sm;
+            acc = cadd(acc, cmul(s, t));
+        }
+    }
+    if (lane <= Qn) {
+        double2 *dst = Qout + (size_t)c * (Qn + 1) + lane;
+        *dst = cadd(*dst, acc);
+    }
+}
+
+// M2P: warp per point target, lanes stride over the List 3 far boxes of its box
+__global__ void k_w_points2(EvalView E, int npt, const int *__restrict__ pt_owner, const double2 *__restrict__ M,
+                            double *__restrict__ pot) {
+    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (wid >= npt) return;
+    int t = (int)wid;
+    int b = pt_owner[t];
+    int beg = E.loff[3][b], end = E.loff[3][b + 1];
+    if (beg == end) return;
+    int P = E.P, P1 = P + 1;
+    double2 tz = E.sp_xy[t];
+    double acc = 0.0;
+    for (int i = beg + lane; i < end; i += 32) {
+        int d = E.lidx[3][i];
+        int l = E.blev[d];
+        double rho = box_rho(E.R, l);
+        double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
+        double2 z = make_double2(tz.x - zd.x, tz.y - zd.y);
+        double n2 = z.x * z.x + z.y * z.y, inv = 1.0 / n2;
+        double2 v = make_double2(rho * z.x * inv, -rho * z.y * inv);   // rho / z
+        const double2 *A = M + (size_t)d * P1;
+        double2 h = A[P];
+        for (int k = P - 1; k >= 1; --k) h = cadd(cmul(h, v), A[k]);
+        h = cmul(h, v);
+        acc += h.x + A[0].x * 0.5 * log(n2);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) pot[t] += acc;
+}
+
+// ------------------------------------------------------------------ Stage 8
+// L2QBXL: thread per (centre, m): Q_m += (r/rho)^m sum_{k>=m} C(k,m) L_k eta^(k-m)
+__global__ void k_l2qbxl(EvalView E, int nc, const int *__restrict__ ctr_box_of, const double2 *__restrict__ L,
+                         double2 *__restrict__ Qout) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int Q1 = E.Q + 1;
+    int c = (int)(t / Q1), m = (int)(t % Q1);
+    if (c >= nc) return;
+    int b = ctr_box_of[c];
+    int l = E.blev[b];
+    double rho = box_rho(E.R, l);
+    double2 zb = box_centre(E.R, l, E.bix[b], E.biy[b]);
+    double2 cz = E.sc_xy[c];
+    double2 eta = make_double2((cz.x - zb.x) / rho, (cz.y - zb.y) / rho);
+    const double2 *B = L + (size_t)b * (E.P + 1);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = E.P; k >= m; --k) acc = cadd(cmul(acc, eta), cscale(B[k], bin(E, k, m)));
+    double s = E.sc_r[c] / rho, sm = 1.0;
+    for (int i = 0; i < m; ++i) sm *= s;
+    double2 *dst = Qout + (size_t)c * Q1 + m;
+    *dst = cadd(*dst, cscale(acc, sm));
+}
+
+// L2P: thread per point target
+__global__ void k_l2p(EvalView E, int npt, const int *__restrict__ pt_owner, const double2 *__restrict__ L,
+                      double *__restrict__ pot) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npt) return;
+    int b = pt_owner[t];
+    int l = E.blev[b];
+    double rho = box_rho(E.R, l);
+    double2 zb = box_centre(E.R, l, E.bix[b], E.biy[b]);
+    double2 tz = E.sp_xy[t];
+    double2 zeta = make_double2((tz.x - zb.x) / rho, (tz.y - zb.y) / rho);
+    const double2 *B = L + (size_t)b * (E.P + 1);
+    double2 h = B[E.P];
+    for (int k = E.P - 1; k >= 0; --k) h = cadd(cmul(h, zeta), B[k]);
+    pot[t] += h.x;
+}
+
+// final values at the targets (eq. qbx; two-sided targets average both centres)
+__global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ kind, const int *__restrict__ ctr,
+                        const int *__restrict__ ctr_pos, const int *__restrict__ tgt_ptpos,
+                        const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on,
+                        const double *__restrict__ base_n, const double2 *__restrict__ sc_xy,
+                        const double *__restrict__ sc_r, const double2 *__restrict__ Qc, const double *__restrict__ pot,
+                        double *__restrict__ out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int k = kind[t];
+    if (k == 0) {
+        out[t] = kernel == GQ_SP ? nan("") : -kInv2Pi * pot[tgt_ptpos[t]];
+        return;
+    }
+    double2 tz = make_double2(tgt_xy[2 * t], tgt_xy[2 * t + 1]);
+    int nside = k == 2 ? 2 : 1;
+    double sum = 0.0;
+    for (int sd = 0; sd < nside; ++sd) {
+        int cp = ctr_pos[ctr[t] + sd];
+        double2 cz = sc_xy[cp];
+        double r = sc_r[cp];
+        double2 zeta = make_double2((tz.x - cz.x) / r, (tz.y - cz.y) / r);
+        const double2 *B = Qc + (size_t)cp * (Q + 1);
+        if (kernel == GQ_SP) {
+            int node = tgt_on[t];
+            if (node < 0) { sum = nan(""); break; }
+            double2 h = cscale(B[Q], (double)Q);
+            for (int m = Q - 1; m >= 1; --m) h = cadd(cmul(h, zeta), cscale(B[m], (double)m));
+            double2 n = make_double2(base_n[2 * node], base_n[2 * node + 1]);
+            sum += -kInv2Pi * cmul(n, h).x / r;
+        } else {
+            double2 h = B[Q];
+            for (int m = Q - 1; m >= 0; --m) h = cadd(cmul(h, zeta), B[m]);
+            sum += -kInv2Pi * h.x;
+        }
+    }
+    out[t] = sum / nside;
+}
+
+__global__ void k_export_qbx(int nc, int Q, const int *__restrict__ ctr_perm, const double *__restrict__ sc_r,
+                             const double2 *__restrict__ Qc, double2 *__restrict__ out) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = (int)(t / (Q + 1)), m = (int)(t % (Q + 1));
+    if (c >= nc) return;
+    double r = sc_r[c], s = 1.0;
+    for (int i = 0; i < m; ++i) s /= r;
+    out[(size_t)ctr_perm[c] * (Q + 1) + m] = cscale(Qc[(size_t)c * (Q + 1) + m], s);
+}
+
+template <int QQ>
+void launch_near_centres(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, double2 *Q) {
+    auto kd = k_near_centres<QQ, GQ_D>;
+    auto ks = k_near_centres<QQ, GQ_S>;
+    if (E.kernel == GQ_D)
+        GQ_LAUNCH(ctx, kd, nwork, kNearThreads, 0, E, nwork, work, Q);
+    else
+        GQ_LAUNCH(ctx, ks, nwork, kNearThreads, 0, E, nwork, work, Q);
+}
+
+void dispatch_near_centres(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, double2 *Q) {
+    switch (E.Q) {
+#define GQ_CASE(v) case v: launch_near_centres<v>(ctx, E, nwork, work, Q); break;
+        GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
+        GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
+#undef GQ_CASE
+        default: throw gq_error{GQ_ERR_INVALID, "p_qbx out of range"};
+    }
+}
+
+__global__ void k_tgt_ptpos(int npt, const int *__restrict__ pt_perm, int *__restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < npt) out[pt_perm[j]] = j;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ tables (per geometry)
+struct EvalTables {
+    dbuf<double> binom;      // [64][64]
+    dbuf<double2> dtab;      // [121][32] delta^-k
+    dbuf<double> logtab;     // [121] log|delta|
+    dbuf<int> tgt_ptpos;     // [nt] target -> sorted point index
+};
+
+static void make_tables(gq_geom *g, EvalTables &T) {
+    std::vector<double> bn(kBinN * kBinN, 0.0);
+    for (int n = 0; n < kBinN; ++n) {
+        bn[n * kBinN] = 1.0;
+        for (int k = 1; k <= n; ++k) bn[n * kBinN + k] = bn[(n - 1) * kBinN + k - 1] + (k <= n - 1 ? bn[(n - 1) * kBinN + k] : 0.0);
+    }
+    std::vector<double2> dt(121 * 32);
+    std::vector<double> lt(121, 0.0);
+    for (int dy = -5; dy <= 5; ++dy)
+        for (int dx = -5; dx <= 5; ++dx) {
+            int off = (dy + 5) * 11 + (dx + 5);
+            double re = 2.0 * dx, im = 2.0 * dy, n2 = re * re + im * im;
+            double ir = n2 > 0 ? re / n2 : 0.0, ii = n2 > 0 ? -im / n2 : 0.0;
+            double pr = 1.0, pi = 0.0;
+            for (int k = 0; k < 32; ++k) {
+                dt[off * 32 + k] = make_double2(pr, pi);
+                double nr = pr * ir - pi * ii, ni = pr * ii + pi * ir;
+                pr = nr; pi = ni;
+            }
+            lt[off] = n2 > 0 ? 0.5 * log(n2) : 0.0;
+        }
+    cudaStream_t st = g->ctx->stream;
+    T.binom.alloc(bn.size());
+    T.dtab.alloc(dt.size());
+    T.logtab.alloc(lt.size());
+    GQ_CUDA(cudaMemcpyAsync(T.binom.p, bn.data(), sizeof(double) * bn.size(), cudaMemcpyHostToDevice, st));
+    GQ_CUDA(cudaMemcpyAsync(T.dtab.p, dt.data(), sizeof(double2) * dt.size(), cudaMemcpyHostToDevice, st));
+    GQ_CUDA(cudaMemcpyAsync(T.logtab.p, lt.data(), sizeof(double) * lt.size(), cudaMemcpyHostToDevice, st));
+    T.tgt_ptpos.alloc(g->nt);
+    if (g->npt) GQ_LAUNCH(g->ctx, k_tgt_ptpos, gq_blocks(g->npt, 256), 256, 0, g->npt, (const int *)g->pt_perm.p, T.tgt_ptpos.p);
+    GQ_CUDA(cudaStreamSynchronize(st));
+}
+
+// tables are owned by the geometry through this registry
+static std::mutex g_tab_mu;
+static std::map<gq_geom *, EvalTables *> g_tabs;
+
+void gq_tables_release(gq_geom *g) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto it = g_tabs.find(g);
+    if (it != g_tabs.end()) {
+        delete it->second;
+        g_tabs.erase(it);
+    }
+}
+
+static EvalTables &get_tables(gq_geom *g) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto it = g_tabs.find(g);
+    if (it != g_tabs.end()) return *it->second;
+    EvalTables *T = new EvalTables;
+    make_tables(g, *T);
+    g_tabs[g] = T;
+    return *T;
+}
+
+void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *stt) {
+    gq_ctx *ctx = g->ctx;
+    cudaStream_t st = ctx->stream;
+    EvalTables &T = get_tables(g);
+    int P = g->prm.p_fmm, Qn = g->prm.p_qbx, P1 = P + 1, Q1 = Qn + 1;
+    int kin = kernel == GQ_SP ? GQ_S : kernel;
+    EvalView E;
+    E.R = g->root;
+    E.P = P;
+    E.Q = Qn;
+    E.kernel = kin;
+    E.blev = g->blev; E.bix = g->bix; E.biy = g->biy; E.bparent = g->bparent; E.bchild = g->bchild;
+    E.src_beg = g->src_beg; E.src_end = g->src_end;
+    E.ctr_beg = g->ctr_beg; E.ctr_end = g->ctr_end; E.pt_beg = g->pt_beg; E.pt_end = g->pt_end;
+    E.sub_src = g->sub_src; E.sub_tgt = g->sub_tgt;
+    E.s_xy = g->s_xy; E.str = g->strength; E.sc_xy = g->sc_xy; E.sc_r = g->sc_r; E.sp_xy = g->sp_xy;
+    for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
+    E.binom = T.binom;
+
+    g->strength.alloc(g->nsrc);
+    E.str = g->strength;
+    g->M.alloc((size_t)g->nbox * P1);
+    g->L.alloc((size_t)g->nbox * P1);
+    g->Q.alloc((size_t)g->nc * Q1);
+    g->pot.alloc(g->npt);
+
+    // stage events (recorded only when statistics are requested)
+    const int kStages = 11;
+    cudaEvent_t ev[kStages + 1];
+    bool timed = stt != nullptr;
+    if (timed)
+        for (int i = 0; i <= kStages; ++i) GQ_CUDA(cudaEventCreate(&ev[i]));
+    auto mark = [&](int i) {
+        if (timed) GQ_CUDA(cudaEventRecord(ev[i], st));
+    };
+    mark(0);
+    int64_t l0 = ctx->launches;
+
+    // A1
+    GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
+              (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, g->strength.p);
+    GQ_CUDA(cudaMemsetAsync(g->M.p, 0, sizeof(double2) * g->nbox * P1, st));
+    GQ_CUDA(cudaMemsetAsync(g->L.p, 0, sizeof(double2) * g->nbox * P1, st));
+    mark(1);
+    // Stage 2
+    if (g->n_leaf_src)
+        GQ_LAUNCH(ctx, k_p2m, gq_blocks((long long)g->n_leaf_src * 32, 128), 128, 0, E, g->n_leaf_src,
+                  (const int *)g->leaf_src_boxes, g->M.p);
+    for (int l = g->nlev - 2; l >= 0; --l) {
+        int s = g->level_start_h[l], e = g->level_start_h[l + 1];
+        GQ_LAUNCH(ctx, k_m2m, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->M.p);
+    }
+    mark(2);
+    // Stage 4
+    if (g->n_far_boxes) {
+        size_t sm = sizeof(double) * P1 * P1;
+        auto k16 = k_m2l<16>;
+        auto k32 = k_m2l<32>;
+        int G = P1 <= 16 ? 16 : 32;
+        GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E,
+                  g->n_far_boxes, (const int *)g->far_boxes, (const double2 *)g->M, (const double2 *)T.dtab,
+                  (const double *)T.logtab, g->L.p);
+    }
+    mark(3);
+    if (g->n_far_boxes) {
+        // Stage 6b
+        GQ_LAUNCH(ctx, k_p2l, gq_blocks((long long)g->n_far_boxes * 32, 128), 128, 0, E, g->n_far_boxes,
+                  (const int *)g->far_boxes, g->L.p);
+    }
+    mark(4);
+    // Stage 7
+    for (int l = 1; l < g->nlev; ++l) {
+        int s = g->level_start_h[l], e = g->level_start_h[l + 1];
+        GQ_LAUNCH(ctx, k_l2l, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->L.p);
+    }
+    // Stages 3, 5a, 6a (near field)
+    GQ_CUDA(cudaMemsetAsync(g->Q.p, 0, sizeof(double2) * g->nc * Q1, st));
+    mark(5);
+    if (g->n_ctr_boxes) dispatch_near_centres(ctx, E, g->n_ctr_boxes, g->ctr_boxes, g->Q.p);
+    mark(6);
+    if (g->n_pt_boxes) {
+        auto kd = k_near_points<GQ_D>;
+        auto ks = k_near_points<GQ_S>;
+        GQ_LAUNCH(ctx, (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, g->n_pt_boxes, (const int *)g->pt_boxes,
+                  g->pot.p);
+    }
+    mark(7);
+    // Stage 5b
+    if (g->nc)
+        GQ_LAUNCH(ctx, k_w_centres, gq_blocks((long long)g->nc * 32, 128), 128, 0, E, g->nc, (const int *)g->ctr_owner,
+                  (const double2 *)g->M, g->Q.p);
+    mark(8);
+    if (g->npt)
+        GQ_LAUNCH(ctx, k_w_points2, gq_blocks((long long)g->npt * 32, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,
+                  (const double2 *)g->M, g->pot.p);
+    mark(9);
+    // Stage 8
+    if (g->nc)
+        GQ_LAUNCH(ctx, k_l2qbxl, gq_blocks((long long)g->nc * Q1, 128), 128, 0, E, g->nc, (const int *)g->ctr_owner,
+                  (const double2 *)g->L, g->Q.p);
+    if (g->npt)
+        GQ_LAUNCH(ctx, k_l2p, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner, (const double2 *)g->L,
+                  g->pot.p);
+    mark(10);
+    if (g->nt)
+        GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, (const int *)g->t_kind,
+                  (const int *)g->t_ctr, (const int *)g->ctr_pos, (const int *)T.tgt_ptpos, (const double *)g->tgt_xy,
+                  (const int *)g->tgt_on, (const double *)g->base_n, (const double2 *)g->sc_xy,
+                  (const double *)g->sc_r, (const double2 *)g->Q, (const double *)g->pot, out_dev);
+    mark(kStages);
+    if (timed) {
+        GQ_CUDA(cudaEventSynchronize(ev[kStages]));
+        float ms = 0;
+        GQ_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[kStages]));
+        stt->ms_total = ms;
+        for (int i = 0; i < kStages; ++i) {
+            GQ_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+            stt->ms_stage[i] = ms;
+        }
+        stt->kernel_launches = ctx->launches - l0;
+        for (int i = 0; i <= kStages; ++i) cudaEventDestroy(ev[i]);
+    }
+    g->have_eval = true;
+    g->last_kernel = kernel;
+}
+
+void gq_export_qbx_impl(gq_geom *g, double *host) {
+    int Q1 = g->prm.p_qbx + 1;
+    dbuf<double2> tmp;
+    tmp.alloc((size_t)g->nc * Q1);
+    GQ_LAUNCH(g->ctx, k_export_qbx, gq_blocks((long long)g->nc * Q1, 256), 256, 0, g->nc, g->prm.p_qbx,
+              (const int *)g->ctr_perm, (const double *)g->sc_r, (const double2 *)g->Q, tmp.p);
+    GQ_CUDA(cudaMemcpyAsync(host, tmp.p, sizeof(double2) * g->nc * Q1, cudaMemcpyDeviceToHost, g->ctx->stream));
+    GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
+}

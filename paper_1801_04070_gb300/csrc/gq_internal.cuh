@@ -1,0 +1,196 @@
+// gq_internal.cuh -- shared declarations of the GIGAQBX CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gigaqbx.h"
+
+#define GQ_KEYBITS 30
+#define GQ_MAX_PQBX 16
+#define GQ_MAX_PFMM 30
+
+// ------------------------------------------------------------------ errors
+struct gq_error {
+    gq_status code;
+    std::string msg;
+};
+
+#define GQ_CUDA(call)                                                                         \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw gq_error{GQ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+#define GQ_CHECK_LAUNCH() GQ_CUDA(cudaGetLastError())
+#define GQ_REQUIRE(cond, code, text) \
+    do {                             \
+        if (!(cond)) throw gq_error{code, text}; \
+    } while (0)
+
+// ------------------------------------------------------------------ device buffers
+template <class T>
+struct dbuf {
+    T *p = nullptr;
+    size_t n = 0;
+    dbuf() = default;
+    dbuf(const dbuf &) = delete;
+    dbuf &operator=(const dbuf &) = delete;
+    ~dbuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        if (count <= n && p) return;
+        release();
+        size_t bytes = (count ? count : 1) * sizeof(T);
+        cudaError_t e = cudaMalloc((void **)&p, bytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            throw gq_error{GQ_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+        }
+        n = count;
+    }
+    void swap(dbuf &o) {
+        T *tp = p; p = o.p; o.p = tp;
+        size_t tn = n; n = o.n; o.n = tn;
+    }
+    operator T *() const { return p; }
+};
+
+struct gq_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    int64_t launches = 0;   // kernels launched by this context
+};
+
+// box-centre geometry broadcast to kernels
+struct RootInfo {
+    double lo_x, lo_y, H, u;
+};
+
+struct gq_geom {
+    gq_ctx *ctx = nullptr;
+    gq_params prm{};
+    int npanels = 0, nb = 0, nu = 0, nbase = 0, nsrc = 0, nc = 0, nt = 0;
+    // geometry (device, original order)
+    dbuf<double> base_xy, base_n, up_xy, up_n, up_w, panel_len, interp;  // interp [nu][nb]
+    dbuf<double> c_xy, c_r;
+    dbuf<int> c_lc;
+    // targets
+    dbuf<double> tgt_xy;
+    dbuf<int> tgt_on;
+    bool targets_set = false;
+    // association
+    dbuf<int> t_kind, t_ctr;
+    int npt = 0;
+    dbuf<int> pt_tgt;   // point target k -> target index (ascending)
+    // root
+    RootInfo root{};
+    // tree
+    bool built = false;
+    int nbox = 0, nlev = 0;
+    std::vector<int> level_start_h;  // [nlev+1]
+    dbuf<int> level_start;
+    dbuf<uint64_t> bkey;             // Morton key at the box's level
+    dbuf<int> blev, bix, biy, bparent;
+    dbuf<int4> bchild;
+    dbuf<int> sub_src, sub_tgt, own_tgt;
+    dbuf<int> src_beg, src_end;      // owned sources (leaves) in sorted-source order
+    dbuf<int> ssub_beg, ssub_end;    // subtree sources in sorted-source order
+    dbuf<int> ctr_beg, ctr_end;      // owned centres in sorted-centre order
+    dbuf<int> pt_beg, pt_end;        // owned point targets in sorted-point order
+    // sorted particle data
+    dbuf<int> src_perm;              // sorted source j -> quadrature node id
+    dbuf<double2> s_xy;              // sorted source positions
+    dbuf<double> s_w;                // sorted weights
+    dbuf<double2> s_n;               // sorted normals
+    dbuf<int> src_owner;             // sorted source j -> owner box
+    dbuf<int> ctr_perm;              // sorted centre position -> centre id
+    dbuf<int> ctr_pos;               // centre id -> sorted position
+    dbuf<double2> sc_xy;             // sorted centres
+    dbuf<double> sc_r;
+    dbuf<int> ctr_owner;             // sorted centre -> owner box
+    dbuf<int> pt_perm;               // sorted point target -> target index
+    dbuf<double2> sp_xy;
+    dbuf<int> pt_owner;              // sorted point target -> owner box
+    // lists (CSR over boxes): 0 U, 1 V, 2 WC, 3 WF, 4 XC, 5 XF
+    dbuf<int> list_off[6], list_idx[6];
+    int64_t list_size[6] = {0, 0, 0, 0, 0, 0};
+    // work lists for the evaluation
+    dbuf<int> leaf_src_boxes;  int n_leaf_src = 0;   // leaves owning sources
+    dbuf<int> ctr_boxes;       int n_ctr_boxes = 0;  // boxes owning centres
+    dbuf<int> pt_boxes;        int n_pt_boxes = 0;   // boxes owning point targets
+    dbuf<int> far_boxes;       int n_far_boxes = 0;  // boxes with V or X far entries
+    // evaluation buffers
+    dbuf<double2> strength;          // sorted sources: S -> (q, 0), D -> d
+    dbuf<double2> M, L;              // [nbox][p_fmm+1] box-scaled expansions
+    dbuf<double2> Q;                 // [nc][p_qbx+1] r-scaled QBX coefficients (sorted centres)
+    dbuf<double> pot;                // sorted point targets: Re Phi
+    dbuf<double> out_dev;            // [nt] staging for host outputs
+    dbuf<double> dens_dev;           // [nbase] staging for host inputs
+    int last_kernel = -1;
+    bool have_eval = false;
+};
+
+// ------------------------------------------------------------------ launch helpers
+inline int gq_blocks(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------------------------------ primitives (gq_prims.cu)
+// Exclusive prefix sum of n ints: out[0..n] (out[n] = total).  tmp sized by scan_tmp_size.
+size_t gq_scan_tmp_size(long long n);
+void gq_exclusive_scan(gq_ctx *ctx, const int *in, int *out, long long n, int *tmp);
+// Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  In/out may alias
+// the temporaries: results are returned in keys/vals.
+void gq_radix_sort_pairs(gq_ctx *ctx, uint64_t *keys, int *vals, long long n, int bits);
+void gq_radix_sort_pairs32(gq_ctx *ctx, uint32_t *keys, int *vals, long long n, int bits);
+
+// ------------------------------------------------------------------ stages
+void gq_build_all(gq_geom *g);                 // gq_tree.cu
+void gq_build_lists(gq_geom *g);               // gq_lists.cu
+void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *st);  // gq_fmm.cu
+void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
+double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
+
+#define GQ_LAUNCH(ctx, kern, grid, block, smem, ...)                     \
+    do {                                                                 \
+        kern<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);   \
+        GQ_CHECK_LAUNCH();                                               \
+        (ctx)->launches++;                                               \
+    } while (0)
+
+// ------------------------------------------------------------------ device helpers
+__host__ __device__ inline uint64_t gq_spread_bits(uint64_t x) {
+    // insert a zero bit above each of the low 32 bits
+    x &= 0xffffffffull;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+// Morton key: x bits on even positions, y bits on odd positions
+__host__ __device__ inline uint64_t gq_morton(uint64_t ix, uint64_t iy) {
+    return gq_spread_bits(ix) | (gq_spread_bits(iy) << 1);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cinv(double2 a) {
+    double d = 1.0 / (a.x * a.x + a.y * a.y);
+    return make_double2(a.x * d, -a.y * d);
+}

@@ -1,0 +1,305 @@
+// gq_lists.cu -- interaction lists of Sec. 4.3.2 (Definitions 1-8) for the
+// target-confinement quadtree, as CSR arrays over boxes, built by a count
+// pass, a prefix scan and a fill pass that share one enumeration routine.
+//
+// All relations are integer tests on box coordinates measured in units of
+// half a level-30 box: a level-l box has half-width h = 2^(30-l) and centre
+// (2 ix + 1) h.  With d the l-inf distance of two box centres:
+//   adjacent(a, b)    d <= h_a + h_b        (closed squares intersect; a box
+//                                            is adjacent to itself)
+//   2-colleagues      same level, d <= 4 h
+//   a < TCR(b)        d >= 3 h_a + (1 + t_f) h_b
+//   TCR(a) < b        d >= 3 (1 + t_f) h_a + h_b
+// with t_f = tf_num / tf_den handled exactly by clearing the denominator.
+//
+// Which boxes carry which list: List 1, 3 close/far and 4 close for boxes
+// owning targets (centres or point targets); List 2 and 4 far for boxes
+// with targets anywhere in their subtree.  Only boxes with sources in their
+// subtree are entered.
+#include "gq_internal.cuh"
+
+void gq_build_far_boxes(gq_geom *g);
+
+namespace {
+
+constexpr int kT = 128;
+constexpr int kStack = 128;
+
+struct TreeView {
+    int nlev;
+    const int *level_start;
+    const uint64_t *bkey;
+    const int *blev, *bix, *biy;
+    const int4 *bchild;
+    const int *sub_src, *sub_tgt, *own_tgt;
+    int64_t tn, td;
+    int demote;
+};
+
+struct IBox {
+    int l;
+    int64_t x, y;  // box coordinates at level l
+};
+
+__device__ __forceinline__ int64_t ih(int l) { return (int64_t)1 << (GQ_KEYBITS - l); }
+__device__ __forceinline__ int64_t i64abs(int64_t a) { return a < 0 ? -a : a; }
+__device__ __forceinline__ int64_t dcen(IBox a, IBox b) {
+    int64_t dx = i64abs((2 * a.x + 1) * ih(a.l) - (2 * b.x + 1) * ih(b.l));
+    int64_t dy = i64abs((2 * a.y + 1) * ih(a.l) - (2 * b.y + 1) * ih(b.l));
+    return dx > dy ? dx : dy;
+}
+__device__ __forceinline__ bool adjacent(IBox a, IBox b) { return dcen(a, b) <= ih(a.l) + ih(b.l); }
+__device__ __forceinline__ bool sep_a_tcrb(const TreeView &T, IBox a, IBox b) {
+    return T.td * dcen(a, b) >= 3 * T.td * ih(a.l) + (T.td + T.tn) * ih(b.l);
+}
+__device__ __forceinline__ bool sep_tcra_b(const TreeView &T, IBox a, IBox b) {
+    return T.td * dcen(a, b) >= 3 * (T.td + T.tn) * ih(a.l) + T.td * ih(b.l);
+}
+__device__ __forceinline__ IBox ibox(const TreeView &T, int b) { return IBox{T.blev[b], T.bix[b], T.biy[b]}; }
+__device__ __forceinline__ bool is_leaf(const TreeView &T, int b) {
+    int4 c = T.bchild[b];
+    return c.x < 0 && c.y < 0 && c.z < 0 && c.w < 0;
+}
+
+// box index of (l, x, y) or -1
+__device__ int lookup(const TreeView &T, int l, int64_t x, int64_t y) {
+    if (l < 0 || l >= T.nlev) return -1;
+    int64_t side = (int64_t)1 << l;
+    if (x < 0 || y < 0 || x >= side || y >= side) return -1;
+    uint64_t k = gq_morton((uint64_t)x, (uint64_t)y);
+    int lo = T.level_start[l], hi = T.level_start[l + 1];
+    while (lo < hi) {
+        int m = (lo + hi) >> 1;
+        if (T.bkey[m] < k) lo = m + 1; else hi = m;
+    }
+    return (lo < T.level_start[l + 1] && T.bkey[lo] == k) ? lo : -1;
+}
+
+enum { LU = 0, LV = 1, LWC = 2, LWF = 3, LXC = 4, LXF = 5 };
+// stack modes
+enum { M_OWN = 0, M_COLL = 1, M_FARCLOSE = 2, M_LEAVES_WC = 3 };
+
+struct Emitter {
+    bool fill;
+    int cnt[6];
+    int *dst[6];
+    __device__ void emit(int which, int d) {
+        if (fill) dst[which][cnt[which]] = d;
+        cnt[which]++;
+    }
+};
+
+__device__ void push_children(const TreeView &T, int b, int mode, int *stk, int &sp, int *err) {
+    int4 c = T.bchild[b];
+    int cc[4] = {c.x, c.y, c.z, c.w};
+    for (int q = 3; q >= 0; --q) {
+        if (cc[q] < 0) continue;
+        if (sp >= kStack) { *err = 1; return; }
+        stk[sp++] = (cc[q] << 3) | mode;
+    }
+}
+
+// Depth-first walk of the boxes on the stack.  Modes: M_OWN collects the
+// source leaves of b's subtree (List 1); M_COLL descends a 2-colleague's
+// subtree through boxes adjacent to b (adjacent leaves -> List 1, the first
+// non-adjacent boxes -> List 3, Def. 3); M_FARCLOSE splits a List 3 box into
+// List 3 far (d < TCR(b), Def. 5) or, through its descendants, List 3 close
+// leaves (Def. 4), demoting far boxes with fewer than `demote` sources to
+// their leaves (Remark 1); M_LEAVES_WC emits the leaves of a demoted box.
+__device__ void drain(const TreeView &T, IBox B, int *stk, int &sp, Emitter &E, int *err) {
+    while (sp > 0) {
+        int e = stk[--sp];
+        int d = e >> 3, mode = e & 7;
+        if (T.sub_src[d] == 0) continue;
+        bool leaf = is_leaf(T, d);
+        IBox D = ibox(T, d);
+        if (mode == M_OWN) {
+            if (leaf) E.emit(LU, d);
+            else push_children(T, d, M_OWN, stk, sp, err);
+        } else if (mode == M_COLL) {
+            if (!adjacent(D, B)) {
+                if (sp >= kStack) { *err = 1; return; }
+                stk[sp++] = (d << 3) | M_FARCLOSE;
+            } else if (leaf) {
+                E.emit(LU, d);
+            } else {
+                push_children(T, d, M_COLL, stk, sp, err);
+            }
+        } else if (mode == M_FARCLOSE) {
+            if (sep_a_tcrb(T, D, B)) {
+                if (T.sub_src[d] < T.demote) {
+                    if (sp >= kStack) { *err = 1; return; }
+                    stk[sp++] = (d << 3) | M_LEAVES_WC;
+                } else {
+                    E.emit(LWF, d);
+                }
+            } else if (leaf) {
+                E.emit(LWC, d);
+            } else {
+                push_children(T, d, M_FARCLOSE, stk, sp, err);
+            }
+        } else {
+            if (leaf) E.emit(LWC, d);
+            else push_children(T, d, M_LEAVES_WC, stk, sp, err);
+        }
+        if (*err) return;
+    }
+}
+
+__device__ void enumerate(const TreeView &T, int b, Emitter &E, int *err) {
+    if (T.sub_tgt[b] == 0) return;
+    const bool tb = T.own_tgt[b] > 0;
+    const IBox B = ibox(T, b);
+    const int l = B.l;
+    int stk[kStack];
+    int sp = 0;
+
+    // ---- List 2: children of the 2-colleagues of parent(b), 2-well-separated from b
+    if (l >= 1) {
+        int64_t px = B.x >> 1, py = B.y >> 1;
+        for (int64_t jy = 2 * (py - 2); jy <= 2 * (py + 2) + 1; ++jy)
+            for (int64_t jx = 2 * (px - 2); jx <= 2 * (px + 2) + 1; ++jx) {
+                if (i64abs(jx - B.x) <= 2 && i64abs(jy - B.y) <= 2) continue;
+                int d = lookup(T, l, jx, jy);
+                if (d >= 0 && T.sub_src[d] > 0) E.emit(LV, d);
+            }
+    }
+
+    if (tb) {
+        // ---- List 1 (a): leaves of b's own subtree, b included
+        stk[sp++] = (b << 3) | M_OWN;
+        drain(T, B, stk, sp, E, err);
+        if (*err) return;
+        // ---- List 1 (b): coarser or same-level leaves adjacent to b
+        for (int m = 0; m <= l; ++m) {
+            int64_t ax = B.x >> (l - m), ay = B.y >> (l - m);
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!dx && !dy) continue;
+                    int d = lookup(T, m, ax + dx, ay + dy);
+                    if (d < 0 || !is_leaf(T, d) || T.sub_src[d] == 0) continue;
+                    if (adjacent(ibox(T, d), B)) E.emit(LU, d);
+                }
+        }
+    }
+    // ---- descendants of the 2-colleagues: finer adjacent leaves (List 1) and List 3
+    for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+            if (!dx && !dy) continue;
+            int t = lookup(T, l, B.x + dx, B.y + dy);
+            if (!tb || t < 0 || is_leaf(T, t) || T.sub_src[t] == 0) continue;
+            push_children(T, t, M_COLL, stk, sp, err);
+            drain(T, B, stk, sp, E, err);
+            if (*err) return;
+        }
+
+    // ---- List 4 close / far: source leaves that are 2-colleagues of b or of an ancestor
+    for (int m = 0; m <= l; ++m) {
+        IBox A{m, B.x >> (l - m), B.y >> (l - m)};
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                if (!dx && !dy) continue;
+                int d = lookup(T, m, A.x + dx, A.y + dy);
+                if (d < 0 || !is_leaf(T, d) || T.sub_src[d] == 0) continue;
+                IBox D = ibox(T, d);
+                bool in_upto_l = false, in_upto_lm1 = false, in_b = false;
+                for (int j = m; j <= l; ++j) {
+                    IBox W{j, B.x >> (l - j), B.y >> (l - j)};
+                    bool mem;
+                    if (j == m) {
+                        mem = !adjacent(D, W);                        // Def. 6, first part
+                    } else {
+                        IBox Wp{j - 1, B.x >> (l - j + 1), B.y >> (l - j + 1)};
+                        mem = adjacent(D, Wp) && !adjacent(D, W);   // Def. 6, second part
+                    }
+                    if (mem) {
+                        in_upto_l = true;
+                        if (j <= l - 1) in_upto_lm1 = true;
+                        if (j == l) in_b = true;
+                    }
+                }
+                bool far_b = sep_tcra_b(T, B, D);
+                if (tb && in_upto_l && !far_b) E.emit(LXC, d);      // Def. 7
+                bool close_par = false;
+                if (l >= 1) {
+                    IBox Pb{l - 1, B.x >> 1, B.y >> 1};
+                    close_par = in_upto_lm1 && !sep_tcra_b(T, Pb, D);
+                }
+                if ((in_b || close_par) && far_b) E.emit(LXF, d);   // Def. 8
+            }
+    }
+}
+
+__global__ void k_lists(TreeView T, int nbox, int fill, const int *__restrict__ off0, const int *__restrict__ off1,
+                        const int *__restrict__ off2, const int *__restrict__ off3, const int *__restrict__ off4,
+                        const int *__restrict__ off5, int *idx0, int *idx1, int *idx2, int *idx3, int *idx4, int *idx5,
+                        int *cnt0, int *cnt1, int *cnt2, int *cnt3, int *cnt4, int *cnt5, int *err) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    Emitter E;
+    E.fill = fill != 0;
+    for (int i = 0; i < 6; ++i) E.cnt[i] = 0;
+    if (fill) {
+        E.dst[0] = idx0 + off0[b]; E.dst[1] = idx1 + off1[b]; E.dst[2] = idx2 + off2[b];
+        E.dst[3] = idx3 + off3[b]; E.dst[4] = idx4 + off4[b]; E.dst[5] = idx5 + off5[b];
+    }
+    int e = 0;
+    enumerate(T, b, E, &e);
+    if (e) atomicExch(err, 1);
+    if (!fill) {
+        cnt0[b] = E.cnt[0]; cnt1[b] = E.cnt[1]; cnt2[b] = E.cnt[2];
+        cnt3[b] = E.cnt[3]; cnt4[b] = E.cnt[4]; cnt5[b] = E.cnt[5];
+    }
+}
+
+}  // namespace
+
+void gq_build_lists(gq_geom *g) {
+    gq_ctx *ctx = g->ctx;
+    cudaStream_t st = ctx->stream;
+    TreeView T;
+    T.nlev = g->nlev;
+    T.level_start = g->level_start.p;
+    T.bkey = g->bkey.p;
+    T.blev = g->blev.p;
+    T.bix = g->bix.p;
+    T.biy = g->biy.p;
+    T.bchild = g->bchild.p;
+    T.sub_src = g->sub_src.p;
+    T.sub_tgt = g->sub_tgt.p;
+    T.own_tgt = g->own_tgt.p;
+    T.tn = g->prm.tf_num;
+    T.td = g->prm.tf_den;
+    T.demote = g->prm.w3_demote;
+    int nbox = g->nbox;
+    dbuf<int> cnt[6], err, tmp;
+    for (int i = 0; i < 6; ++i) {
+        cnt[i].alloc(nbox);
+        g->list_off[i].alloc(nbox + 1);
+    }
+    err.alloc(1);
+    GQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    tmp.alloc(gq_scan_tmp_size(nbox));
+    GQ_LAUNCH(ctx, k_lists, gq_blocks(nbox, kT), kT, 0, T, nbox, 0, (const int *)nullptr, (const int *)nullptr,
+              (const int *)nullptr, (const int *)nullptr, (const int *)nullptr, (const int *)nullptr, (int *)nullptr,
+              (int *)nullptr, (int *)nullptr, (int *)nullptr, (int *)nullptr, (int *)nullptr, cnt[0].p, cnt[1].p,
+              cnt[2].p, cnt[3].p, cnt[4].p, cnt[5].p, err.p);
+    for (int i = 0; i < 6; ++i) {
+        gq_exclusive_scan(ctx, cnt[i].p, g->list_off[i].p, nbox, tmp.p);
+        int tot = 0;
+        GQ_CUDA(cudaMemcpyAsync(&tot, g->list_off[i].p + nbox, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GQ_CUDA(cudaStreamSynchronize(st));
+        g->list_size[i] = tot;
+        g->list_idx[i].alloc(tot);
+    }
+    GQ_LAUNCH(ctx, k_lists, gq_blocks(nbox, kT), kT, 0, T, nbox, 1, (const int *)g->list_off[0].p,
+              (const int *)g->list_off[1].p, (const int *)g->list_off[2].p, (const int *)g->list_off[3].p,
+              (const int *)g->list_off[4].p, (const int *)g->list_off[5].p, g->list_idx[0].p, g->list_idx[1].p,
+              g->list_idx[2].p, g->list_idx[3].p, g->list_idx[4].p, g->list_idx[5].p, (int *)nullptr, (int *)nullptr,
+              (int *)nullptr, (int *)nullptr, (int *)nullptr, (int *)nullptr, err.p);
+    int herr = 0;
+    GQ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GQ_CUDA(cudaStreamSynchronize(st));
+    GQ_REQUIRE(herr == 0, GQ_ERR_UNSUPPORTED, "list construction: traversal stack overflow");
+    gq_build_far_boxes(g);
+}

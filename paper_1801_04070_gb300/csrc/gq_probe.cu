@@ -1,0 +1,56 @@
+// gq_probe.cu -- FMA-throughput probe used as the measured FP64 / FP32 peak
+// of the ALU roofline (the measured peaks cover HBM and BF16 only).
+#include "gq_internal.cuh"
+
+namespace {
+
+constexpr int kChains = 8;     // independent FMA chains per thread
+constexpr int kIters = 4096;
+
+template <class T>
+__global__ void k_fma_loop(T *out, T a, T b) {
+    T x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == (T)-1.2345) out[0] = s;   // keeps the loop alive; never true for these inputs
+}
+
+template <class T>
+double run(gq_ctx *ctx) {
+    int dev = ctx->device, sms = 0;
+    GQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    dbuf<T> out;
+    out.alloc(1);
+    const int threads = 256;
+    const int blocks = sms * 8;
+    cudaEvent_t e0, e1;
+    GQ_CUDA(cudaEventCreate(&e0));
+    GQ_CUDA(cudaEventCreate(&e1));
+    GQ_LAUNCH(ctx, k_fma_loop<T>, blocks, threads, 0, out.p, (T)0.999999, (T)1e-7);  // warm-up
+    double best = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+        GQ_CUDA(cudaEventRecord(e0, ctx->stream));
+        GQ_LAUNCH(ctx, k_fma_loop<T>, blocks, threads, 0, out.p, (T)0.999999, (T)1e-7);
+        GQ_CUDA(cudaEventRecord(e1, ctx->stream));
+        GQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        GQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        double flops = 2.0 * kChains * (double)kIters * threads * blocks;
+        double tf = flops / (ms * 1e-3) / 1e12;
+        if (tf > best) best = tf;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+}  // namespace
+
+double gq_probe_fma(gq_ctx *ctx, int what) { return what == 0 ? run<double>(ctx) : run<float>(ctx); }
