@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--kernel", default="S", choices=["S", "D"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--grid", type=int, nargs=2, default=[16, 16],
+                    help="curves per row / column (the benchmark workload is 16 16; smaller grids are "
+                         "profiling cases with the same per-curve sizes)")
     return ap.parse_args()
 
 
@@ -225,7 +228,8 @@ def run_gpu(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     L = lib()
-    g = workload()
+    grid = tuple(args.grid)
+    g = workload(n_off=(1 << 20) * grid[0] * grid[1] // 256, grid=grid)
     nt = len(g["tgt_xy"])
     P, Q = int(g["p_fmm"]), int(g["p_qbx"])
     prm = params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"]))
@@ -295,6 +299,7 @@ def run_gpu(args, rank, world, local):
     chk(L.gq_tree_info_get(geom, C.byref(info)))
     wrap.info, wrap.nbox, wrap.nc, wrap.npt, wrap.nsrc = info, info.nbox, info.ncentres, info.npoint_targets, info.nsources
     model = work_model(wrap, P, Q)
+    wrap._geom = wrap._ctx = None     # borrowed handles: released below, not by the wrapper
     dom = int(np.argmax(stage_ms))
     peak = C.c_double()
     peak_src = "measured (FP64 FMA probe, gq_probe_fma_peak)"

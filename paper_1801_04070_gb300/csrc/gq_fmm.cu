@@ -32,6 +32,11 @@ namespace {
 constexpr double kInv2Pi = 0.15915494309189533576888376337251;
 constexpr int kBinN = 64;   // binomial table C(n, k), n, k < 64
 
+// C(m+k-1, k-1) for m <= GQ_MAX_PQBX, k <= 32: the real matrix of the factored
+// M2L applied at QBX order (List 3 far to centres).  Read with warp-uniform
+// indices, so constant-cache broadcasts serve it.
+__constant__ double c_pascal[GQ_MAX_PQBX + 1][33];
+
 struct EvalView {
     RootInfo R;
     int P, Q, kernel;
@@ -92,28 +97,58 @@ __global__ void k_strengths(int nsrc, int nu, int nb, const int *__restrict__ sr
     str[j] = kernel == GQ_D ? cscale(s_n[j], wm) : make_double2(wm, 0.0);
 }
 
-// ------------------------------------------------------------------ Stage 2: P2M (one warp per leaf, lane = k)
+// ------------------------------------------------------------------ Stage 2: P2M
+// One warp per source leaf; lanes stride over its sources and keep all p+1
+// coefficients in registers (PM >= p, guarded unrolled loops); a warp
+// reduction sums the lanes.  S: A_0 = sum q, A_k = -(1/k) sum q u^k;
+// D: A_k = -(1/rho) sum d u^(k-1), u = (y - z_b)/rho.
+template <int PM>
 __global__ void k_p2m(EvalView E, int nwork, const int *__restrict__ work, double2 *__restrict__ M) {
-    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, k = threadIdx.x & 31;
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (wid >= nwork) return;
     int b = work[wid];
-    int l = E.blev[b];
+    int l = E.blev[b], P = E.P;
     double rho = box_rho(E.R, l), irho = 1.0 / rho;
     double2 zc = box_centre(E.R, l, E.bix[b], E.biy[b]);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int s = E.src_beg[b]; s < E.src_end[b]; ++s) {
+    double2 acc[PM + 1];
+#pragma unroll
+    for (int k = 0; k <= PM; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int s = E.src_beg[b] + lane; s < E.src_end[b]; s += 32) {
         double2 y = E.s_xy[s], st = E.str[s];
         double2 u = make_double2((y.x - zc.x) * irho, (y.y - zc.y) * irho);
-        double2 pk = lane_powers(u, k, 32);           // u^k
         if (E.kernel == GQ_D) {
-            double2 pkm1 = shfl2_up(pk, 1, 32);        // u^(k-1)
-            if (k >= 1) acc = csub(acc, cscale(cmul(st, pkm1), irho));
+            double2 t = cscale(st, irho);
+            acc[1] = cadd(acc[1], t);
+#pragma unroll
+            for (int k = 2; k <= PM; ++k)
+                if (k <= P) {
+                    t = cmul(t, u);
+                    acc[k] = cadd(acc[k], t);
+                }
         } else {
-            if (k == 0) acc.x += st.x;
-            else acc = csub(acc, cscale(pk, st.x / k));
+            acc[0].x += st.x;
+            double2 t = make_double2(st.x * u.x, st.x * u.y);
+            acc[1] = cadd(acc[1], t);
+#pragma unroll
+            for (int k = 2; k <= PM; ++k)
+                if (k <= P) {
+                    t = cmul(t, u);
+                    acc[k] = cadd(acc[k], t);
+                }
         }
     }
-    if (k <= E.P) M[(size_t)b * (E.P + 1) + k] = acc;
+#pragma unroll
+    for (int k = 0; k <= PM; ++k)
+        if (k <= P)
+            for (int o = 16; o > 0; o >>= 1) acc[k] = cadd(acc[k], shfl2_xor(acc[k], o));
+    double2 v = acc[0];
+#pragma unroll
+    for (int k = 1; k <= PM; ++k)
+        if (lane == k) v = acc[k];
+    if (lane <= P) {
+        if (lane >= 1) v = E.kernel == GQ_D ? make_double2(-v.x, -v.y) : cscale(v, -1.0 / lane);
+        M[(size_t)b * (P + 1) + lane] = v;
+    }
 }
 
 // ------------------------------------------------------------------ Stage 2: M2M, one thread per (parent, m)
@@ -430,21 +465,25 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
 }
 
 // ------------------------------------------------------------------ Stage 5b: List 3 far
-// M2QBXL: warp per centre, loop over the owner box's List 3 far boxes; lane
-// k forms a_k y^-k, lane m <= q applies the M2L matrix row and the (r/y)^m scale.
-__global__ void k_w_centres(EvalView E, int nwork, const int *__restrict__ ctr_box_of,
-                            const double2 *__restrict__ M, double2 *__restrict__ Qout) {
-    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (wid >= nwork) return;
-    int c = (int)wid;
+// M2QBXL, one thread per centre (centres of a box share their List 3 far
+// boxes, so a warp reads the same multipoles).  Per far box d, with y = c - z_d,
+// v = rho_d / y, s = r / y and At_k = A_k v^k:
+//   Q_0 += A_0 log|y| + sum_k At_k
+//   Q_m += (-1)^m s^m (sum_k C(m+k-1,k-1) At_k - A_0/m),   1 <= m <= q.
+template <int PM>
+__global__ void k_w_centres(EvalView E, int nc, const int *__restrict__ ctr_box_of, const double2 *__restrict__ M,
+                            double2 *__restrict__ Qout) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
     int b = ctr_box_of[c];
     int beg = E.loff[3][b], end = E.loff[3][b + 1];
     if (beg == end) return;
-    int P = E.P, P1 = P + 1, Qn = E.Q;
+    const int P = E.P, P1 = P + 1, Qn = E.Q;
     double2 cz = E.sc_xy[c];
     double rc = E.sc_r[c];
-    double2 acc = make_double2(0.0, 0.0);
+    double2 acc[GQ_MAX_PQBX + 1];
+#pragma unroll
+    for (int m = 0; m <= GQ_MAX_PQBX; ++m) acc[m] = make_double2(0.0, 0.0);
     for (int i = beg; i < end; ++i) {
         int d = E.lidx[3][i];
         int l = E.blev[d];
@@ -453,63 +492,75 @@ __global__ void k_w_centres(EvalView E, int nwork, const int *__restrict__ ctr_b
         double2 y = make_double2(cz.x - zd.x, cz.y - zd.y);
         double n2 = y.x * y.x + y.y * y.y, inv = 1.0 / n2;
         double2 yinv = make_double2(y.x * inv, -y.y * inv);
-        double2 vk = lane_powers(cscale(yinv, rho), lane, 32);   // (rho/y)^k
-        double2 sm = lane_powers(cscale(yinv, rc), lane, 32);    // (r/y)^m
-        double2 A = lane <= P ? M[(size_t)d * P1 + lane] : make_double2(0.0, 0.0);
-        double2 At = lane >= 1 ? cmul(A, vk) : make_double2(0.0, 0.0);
-        double A0 = __shfl_sync(0xffffffffu, A.x, 0);
-        double2 Gm = make_double2(0.0, 0.0);
-        int mrow = lane <= Qn ? lane : 0;
-        for (int k = 1; k <= P; ++k) {
-            double2 a = shfl2(At, k, 32);
-            double cc = E.binom[(mrow + k - 1) * kBinN + (k - 1)];
-            Gm.x += cc * a.x;
-            Gm.y += cc * a.y;
+        double2 v = cscale(yinv, rho), sv = cscale(yinv, rc);
+        const double2 *A = M + (size_t)d * P1;
+        double A0 = A[0].x;
+        double2 At[PM + 1];
+        double2 vk = v, sum = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int k = 1; k <= PM; ++k) {
+            At[k] = make_double2(0.0, 0.0);
+            if (k <= P) {
+                At[k] = cmul(A[k], vk);
+                sum = cadd(sum, At[k]);
+                vk = cmul(vk, v);
+            }
         }
-        if (lane == 0) {
-            acc.x += A0 * 0.5 * log(n2) + Gm.x;
-            acc.y += Gm.y;
-        } else if (lane <= Qn) {
-            double2 t = make_double2(Gm.x - A0 / lane, Gm.y);
-            double2 s = (lane & 1) ? make_double2(-sm.x, -sm.y) : sm;
-            acc = cadd(acc, cmul(s, t));
+        acc[0].x += A0 * 0.5 * log(n2) + sum.x;
+        acc[0].y += sum.y;
+        double2 sm = make_double2(1.0, 0.0);
+#pragma unroll
+        for (int m = 1; m <= GQ_MAX_PQBX; ++m) {
+            if (m <= Qn) {
+                sm = cmul(sm, sv);
+                double2 G = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int k = 1; k <= PM; ++k)
+                    if (k <= P) {
+                        double cc = c_pascal[m][k];
+                        G.x += cc * At[k].x;
+                        G.y += cc * At[k].y;
+                    }
+                G.x -= A0 / m;
+                double2 t = cmul(sm, G);
+                if (m & 1) acc[m] = csub(acc[m], t);
+                else acc[m] = cadd(acc[m], t);
+            }
         }
     }
-    if (lane <= Qn) {
-        double2 *dst = Qout + (size_t)c * (Qn + 1) + lane;
-        *dst = cadd(*dst, acc);
-    }
+    double2 *dst = Qout + (size_t)c * (Qn + 1);
+#pragma unroll
+    for (int m = 0; m <= GQ_MAX_PQBX; ++m)
+        if (m <= Qn) dst[m] = cadd(dst[m], acc[m]);
 }
 
-// M2P: warp per point target, lanes stride over the List 3 far boxes of its box
-__global__ void k_w_points2(EvalView E, int npt, const int *__restrict__ pt_owner, const double2 *__restrict__ M,
-                            double *__restrict__ pot) {
-    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (wid >= npt) return;
-    int t = (int)wid;
+// M2P, one thread per point target: Phi += A_0 log|z| + sum_k A_k (rho/z)^k,
+// z = t - z_d, by Horner's rule
+__global__ void k_w_points(EvalView E, int npt, const int *__restrict__ pt_owner, const double2 *__restrict__ M,
+                           double *__restrict__ pot) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npt) return;
     int b = pt_owner[t];
     int beg = E.loff[3][b], end = E.loff[3][b + 1];
     if (beg == end) return;
     int P = E.P, P1 = P + 1;
     double2 tz = E.sp_xy[t];
     double acc = 0.0;
-    for (int i = beg + lane; i < end; i += 32) {
+    for (int i = beg; i < end; ++i) {
         int d = E.lidx[3][i];
         int l = E.blev[d];
         double rho = box_rho(E.R, l);
         double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
         double2 z = make_double2(tz.x - zd.x, tz.y - zd.y);
         double n2 = z.x * z.x + z.y * z.y, inv = 1.0 / n2;
-        double2 v = make_double2(rho * z.x * inv, -rho * z.y * inv);   // rho / z
+        double2 v = make_double2(rho * z.x * inv, -rho * z.y * inv);
         const double2 *A = M + (size_t)d * P1;
         double2 h = A[P];
         for (int k = P - 1; k >= 1; --k) h = cadd(cmul(h, v), A[k]);
         h = cmul(h, v);
         acc += h.x + A[0].x * 0.5 * log(n2);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) pot[t] += acc;
+    pot[t] += acc;
 }
 
 // ------------------------------------------------------------------ Stage 8
@@ -657,6 +708,19 @@ static void make_tables(gq_geom *g, EvalTables &T) {
             }
             lt[off] = n2 > 0 ? 0.5 * log(n2) : 0.0;
         }
+    static std::mutex mu;
+    static unsigned long long inited = 0;   // devices whose constant table is loaded
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        int dev = g->ctx->device;
+        if (dev < 64 && !(inited >> dev & 1ull)) {
+            std::vector<double> pc((GQ_MAX_PQBX + 1) * 33, 0.0);
+            for (int m = 0; m <= GQ_MAX_PQBX; ++m)
+                for (int k = 1; k <= 32; ++k) pc[m * 33 + k] = bn[(m + k - 1) * kBinN + (k - 1)];
+            GQ_CUDA(cudaMemcpyToSymbol(c_pascal, pc.data(), sizeof(double) * pc.size()));
+            inited |= 1ull << dev;
+        }
+    }
     cudaStream_t st = g->ctx->stream;
     T.binom.alloc(bn.size());
     T.dtab.alloc(dt.size());
@@ -737,9 +801,13 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     GQ_CUDA(cudaMemsetAsync(g->L.p, 0, sizeof(double2) * g->nbox * P1, st));
     mark(1);
     // Stage 2
-    if (g->n_leaf_src)
-        GQ_LAUNCH(ctx, k_p2m, gq_blocks((long long)g->n_leaf_src * 32, 128), 128, 0, E, g->n_leaf_src,
-                  (const int *)g->leaf_src_boxes, g->M.p);
+    if (g->n_leaf_src) {
+        auto k8 = k_p2m<8>;
+        auto k16 = k_p2m<16>;
+        auto k32 = k_p2m<GQ_MAX_PFMM>;
+        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * 32, 128), 128, 0,
+                  E, g->n_leaf_src, (const int *)g->leaf_src_boxes, g->M.p);
+    }
     for (int l = g->nlev - 2; l >= 0; --l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
         GQ_LAUNCH(ctx, k_m2m, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->M.p);
@@ -780,12 +848,16 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     }
     mark(7);
     // Stage 5b
-    if (g->nc)
-        GQ_LAUNCH(ctx, k_w_centres, gq_blocks((long long)g->nc * 32, 128), 128, 0, E, g->nc, (const int *)g->ctr_owner,
-                  (const double2 *)g->M, g->Q.p);
+    if (g->nc) {
+        auto k8 = k_w_centres<8>;
+        auto k16 = k_w_centres<16>;
+        auto k32 = k_w_centres<GQ_MAX_PFMM>;
+        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks(g->nc, 128), 128, 0, E, g->nc,
+                  (const int *)g->ctr_owner, (const double2 *)g->M, g->Q.p);
+    }
     mark(8);
     if (g->npt)
-        GQ_LAUNCH(ctx, k_w_points2, gq_blocks((long long)g->npt * 32, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,
+        GQ_LAUNCH(ctx, k_w_points, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,
                   (const double2 *)g->M, g->pot.p);
     mark(9);
     // Stage 8
