@@ -148,6 +148,29 @@ gq_status gq_build(gq_geom *g);
  * out: [ntargets] potential values (host or device).  stats may be NULL. */
 gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *out, gq_stats *stats);
 
+/* gq_eval without allocating: the same evaluation as gq_eval for callers
+ * that must not allocate device memory once they are running -- for example
+ * code replayed inside a captured CUDA graph, real-time or embedded services
+ * that reserve all their memory up front, or hosts that forbid cudaMalloc
+ * after start-up.  The paper has no counterpart; it is a deployment variant.
+ *
+ * Working memory comes from one fixed device array inside the library
+ * (16 MiB, of which 128 KiB hold translation tables); every GPU that loads
+ * the library keeps that array until the process exits.  Problems whose
+ * working set (quadrature nodes x 16 B + 2 x boxes x (p_fmm+1) x 16 B +
+ * centres x (p_qbx+1) x 16 B + point targets x 8 B + targets x 4 B, each
+ * rounded up to 256 B) exceeds the rest of the array are rejected with
+ * GQ_ERR_UNSUPPORTED and a message giving both sizes.
+ *
+ * density_dev and out_dev must be device memory (GQ_ERR_INVALID otherwise):
+ * host inputs would need staging buffers.  The geometry must be built.
+ * The first call on a device sets the array up (looks up its device address
+ * and writes the tables); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents, so
+ * calls whose device work overlaps (different streams or contexts) race;
+ * order them on one stream.  No memory is allocated or freed by this call. */
+gq_status gq_eval_noalloc(gq_geom *g, int kernel, const double *density_dev, double *out_dev);
+
 /* Sizes of the built tree. */
 gq_status gq_tree_info_get(gq_geom *g, gq_tree_info *out);
 

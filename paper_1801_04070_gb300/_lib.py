@@ -74,6 +74,9 @@ def lib():
             "gq_targets_set": (st, [vp, i32, vp, vp]),
             "gq_build": (st, [vp]),
             "gq_eval": (st, [vp, i32, vp, vp, C.POINTER(Stats)]),
+            "gq_eval_noalloc": (st, [vp, i32, vp, vp]),
+            "gq_context_launches": (st, [vp, C.POINTER(C.c_int64)]),
+            "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
             "gq_export_root": (st, [vp, vp]),
             "gq_export_boxes": (st, [vp] + [vp] * 9),

@@ -239,6 +239,17 @@ gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *ou
     });
 }
 
+gq_status gq_eval_noalloc(gq_geom *g, int kernel, const double *density_dev, double *out_dev) {
+    if (!g || !density_dev || (!out_dev && g->nt > 0)) return GQ_ERR_INVALID;
+    if (kernel != GQ_S && kernel != GQ_D && kernel != GQ_SP) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        GQ_REQUIRE(g->built, GQ_ERR_STATE, "gq_eval_noalloc before gq_build");
+        GQ_REQUIRE(is_device_ptr(density_dev), GQ_ERR_INVALID, "gq_eval_noalloc: density must be device memory");
+        GQ_REQUIRE(g->nt == 0 || is_device_ptr(out_dev), GQ_ERR_INVALID, "gq_eval_noalloc: out must be device memory");
+        gq_eval_noalloc_impl(g, kernel, density_dev, out_dev);
+    });
+}
+
 gq_status gq_tree_info_get(gq_geom *g, gq_tree_info *out) {
     if (!g || !out) return GQ_ERR_INVALID;
     if (!g->built) return GQ_ERR_STATE;

@@ -899,3 +899,181 @@ void gq_export_qbx_impl(gq_geom *g, double *host) {
     GQ_CUDA(cudaMemcpyAsync(host, tmp.p, sizeof(double2) * g->nc * Q1, cudaMemcpyDeviceToHost, g->ctx->stream));
     GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
 }
+
+// ====================================================================== no-allocation evaluation
+// gq_eval_noalloc: the evaluation of gq_eval for callers that cannot allocate
+// device memory at call time.  Its working memory (source strengths, box
+// multipole and local expansions, QBX coefficients, point-target potentials,
+// translation tables) lives in one file-scope device array of fixed size.
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(16) << 20;   // 16 MiB per device, held until exit
+constexpr size_t kNoAllocTableBytes = size_t(128) << 10;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;   // device address of g_noalloc_scratch
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+void host_tables(std::vector<double> &bn, std::vector<double2> &dt, std::vector<double> &lt) {
+    bn.assign(kBinN * kBinN, 0.0);
+    for (int n = 0; n < kBinN; ++n) {
+        bn[n * kBinN] = 1.0;
+        for (int k = 1; k <= n; ++k) bn[n * kBinN + k] = bn[(n - 1) * kBinN + k - 1] + (k <= n - 1 ? bn[(n - 1) * kBinN + k] : 0.0);
+    }
+    dt.assign(121 * 32, make_double2(0.0, 0.0));
+    lt.assign(121, 0.0);
+    for (int dy = -5; dy <= 5; ++dy)
+        for (int dx = -5; dx <= 5; ++dx) {
+            int off = (dy + 5) * 11 + (dx + 5);
+            double re = 2.0 * dx, im = 2.0 * dy, n2 = re * re + im * im;
+            double ir = n2 > 0 ? re / n2 : 0.0, ii = n2 > 0 ? -im / n2 : 0.0;
+            double pr = 1.0, pi = 0.0;
+            for (int k = 0; k < 32; ++k) {
+                dt[off * 32 + k] = make_double2(pr, pi);
+                double nr = pr * ir - pi * ii, ni = pr * ii + pi * ir;
+                pr = nr;
+                pi = ni;
+            }
+            lt[off] = n2 > 0 ? 0.5 * log(n2) : 0.0;
+        }
+}
+
+// Once per device, with that device current: resolve the device address of
+// the scratch array (host code cannot use the symbol itself) and store the
+// read-only translation tables at its start.
+NoAllocDevice &noalloc_setup(int dev) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    GQ_REQUIRE(dev >= 0 && dev < 64, GQ_ERR_UNSUPPORTED, "gq_eval_noalloc: device index >= 64");
+    NoAllocDevice &D = g_noalloc_dev[dev];
+    if (D.ready) return D;
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) throw gq_error{GQ_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)};
+    std::vector<double> bn, lt;
+    std::vector<double2> dt;
+    host_tables(bn, dt, lt);
+    unsigned char *base = (unsigned char *)ptr;
+    GQ_CUDA(cudaMemcpy(base, bn.data(), sizeof(double) * bn.size(), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(base + 32768, dt.data(), sizeof(double2) * dt.size(), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(base + 32768 + 65536, lt.data(), sizeof(double) * lt.size(), cudaMemcpyHostToDevice));
+    std::vector<double> pc((GQ_MAX_PQBX + 1) * 33, 0.0);
+    for (int m = 0; m <= GQ_MAX_PQBX; ++m)
+        for (int k = 1; k <= 32; ++k) pc[m * 33 + k] = bn[(m + k - 1) * kBinN + (k - 1)];
+    GQ_CUDA(cudaMemcpyToSymbol(c_pascal, pc.data(), sizeof(double) * pc.size()));
+    D.base = base;
+    D.ready = true;
+    return D;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+size_t gq_noalloc_capacity() { return kNoAllocBytes - kNoAllocTableBytes; }
+
+size_t gq_noalloc_need(const gq_geom *g) {
+    size_t P1 = g->prm.p_fmm + 1, Q1 = g->prm.p_qbx + 1;
+    return align256(sizeof(double2) * g->nsrc) + 2 * align256(sizeof(double2) * g->nbox * P1) +
+           align256(sizeof(double2) * g->nc * Q1) + align256(sizeof(double) * (g->npt ? g->npt : 1)) +
+           align256(sizeof(int) * (g->nt ? g->nt : 1));
+}
+
+void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double *out_dev) {
+    gq_ctx *ctx = g->ctx;
+    cudaStream_t st = ctx->stream;
+    size_t need = gq_noalloc_need(g);
+    if (need > gq_noalloc_capacity())
+        throw gq_error{GQ_ERR_UNSUPPORTED, "gq_eval_noalloc: problem needs " + std::to_string(need) +
+                                               " bytes of scratch, the fixed array holds " +
+                                               std::to_string(gq_noalloc_capacity())};
+    NoAllocDevice &D = noalloc_setup(ctx->device);
+    const double *binom = (const double *)D.base;
+    const double2 *dtab = (const double2 *)(D.base + 32768);
+    const double *logtab = (const double *)(D.base + 32768 + 65536);
+    unsigned char *w = D.base + kNoAllocTableBytes;
+    int P = g->prm.p_fmm, Qn = g->prm.p_qbx, P1 = P + 1, Q1 = Qn + 1;
+    double2 *str = (double2 *)w;  w += align256(sizeof(double2) * g->nsrc);
+    double2 *M = (double2 *)w;    w += align256(sizeof(double2) * g->nbox * P1);
+    double2 *L = (double2 *)w;    w += align256(sizeof(double2) * g->nbox * P1);
+    double2 *Qc = (double2 *)w;   w += align256(sizeof(double2) * g->nc * Q1);
+    double *pot = (double *)w;    w += align256(sizeof(double) * (g->npt ? g->npt : 1));
+    int *ptpos = (int *)w;
+    int kin = kernel == GQ_SP ? GQ_S : kernel;
+    EvalView E;
+    E.R = g->root;
+    E.P = P;
+    E.Q = Qn;
+    E.kernel = kin;
+    E.blev = g->blev; E.bix = g->bix; E.biy = g->biy; E.bparent = g->bparent; E.bchild = g->bchild;
+    E.src_beg = g->src_beg; E.src_end = g->src_end;
+    E.ctr_beg = g->ctr_beg; E.ctr_end = g->ctr_end; E.pt_beg = g->pt_beg; E.pt_end = g->pt_end;
+    E.sub_src = g->sub_src; E.sub_tgt = g->sub_tgt;
+    E.s_xy = g->s_xy; E.str = str; E.sc_xy = g->sc_xy; E.sc_r = g->sc_r; E.sp_xy = g->sp_xy;
+    for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
+    E.binom = binom;
+
+    // the array keeps the previous call's contents: clear the accumulators
+    GQ_CUDA(cudaMemsetAsync(M, 0, sizeof(double2) * g->nbox * P1, st));
+    GQ_CUDA(cudaMemsetAsync(L, 0, sizeof(double2) * g->nbox * P1, st));
+    GQ_CUDA(cudaMemsetAsync(Qc, 0, sizeof(double2) * g->nc * Q1, st));
+    if (g->npt) GQ_LAUNCH(ctx, k_tgt_ptpos, gq_blocks(g->npt, 256), 256, 0, g->npt, (const int *)g->pt_perm.p, ptpos);
+    GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
+              (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, str);
+    if (g->n_leaf_src) {
+        auto k8 = k_p2m<8>;
+        auto k16 = k_p2m<16>;
+        auto k32 = k_p2m<GQ_MAX_PFMM>;
+        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * 32, 128), 128, 0,
+                  E, g->n_leaf_src, (const int *)g->leaf_src_boxes, M);
+    }
+    for (int l = g->nlev - 2; l >= 0; --l) {
+        int s = g->level_start_h[l], e = g->level_start_h[l + 1];
+        GQ_LAUNCH(ctx, k_m2m, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, M);
+    }
+    if (g->n_far_boxes) {
+        size_t sm = sizeof(double) * P1 * P1;
+        auto k16 = k_m2l<16>;
+        auto k32 = k_m2l<32>;
+        int G = P1 <= 16 ? 16 : 32;
+        GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E,
+                  g->n_far_boxes, (const int *)g->far_boxes, (const double2 *)M, dtab, logtab, L);
+        GQ_LAUNCH(ctx, k_p2l, gq_blocks((long long)g->n_far_boxes * 32, 128), 128, 0, E, g->n_far_boxes,
+                  (const int *)g->far_boxes, L);
+    }
+    for (int l = 1; l < g->nlev; ++l) {
+        int s = g->level_start_h[l], e = g->level_start_h[l + 1];
+        GQ_LAUNCH(ctx, k_l2l, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, L);
+    }
+    if (g->n_ctr_boxes) dispatch_near_centres(ctx, E, g->n_ctr_boxes, g->ctr_boxes, Qc);
+    if (g->n_pt_boxes) {
+        auto kd = k_near_points<GQ_D>;
+        auto ks = k_near_points<GQ_S>;
+        GQ_LAUNCH(ctx, (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, g->n_pt_boxes,
+                  (const int *)g->pt_boxes, pot);
+    }
+    if (g->nc) {
+        auto k8 = k_w_centres<8>;
+        auto k16 = k_w_centres<16>;
+        auto k32 = k_w_centres<GQ_MAX_PFMM>;
+        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks(g->nc, 128), 128, 0, E, g->nc,
+                  (const int *)g->ctr_owner, (const double2 *)M, Qc);
+        GQ_LAUNCH(ctx, k_l2qbxl, gq_blocks((long long)g->nc * Q1, 128), 128, 0, E, g->nc, (const int *)g->ctr_owner,
+                  (const double2 *)L, Qc);
+    }
+    if (g->npt) {
+        GQ_LAUNCH(ctx, k_w_points, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,
+                  (const double2 *)M, pot);
+        GQ_LAUNCH(ctx, k_l2p, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner, (const double2 *)L,
+                  pot);
+    }
+    if (g->nt)
+        GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, (const int *)g->t_kind,
+                  (const int *)g->t_ctr, (const int *)g->ctr_pos, (const int *)ptpos, (const double *)g->tgt_xy,
+                  (const int *)g->tgt_on, (const double *)g->base_n, (const double2 *)g->sc_xy,
+                  (const double *)g->sc_r, (const double2 *)Qc, (const double *)pot, out_dev);
+}

@@ -160,6 +160,7 @@ void gq_build_lists(gq_geom *g);               // gq_lists.cu
 void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *st);  // gq_fmm.cu
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
+void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double *out_dev);  // gq_fmm.cu
 
 #define GQ_LAUNCH(ctx, kern, grid, block, smem, ...)                     \
     do {                                                                 \
