@@ -114,6 +114,17 @@ __global__ void k_cell_of_centre(int nc, const double *__restrict__ c_xy, double
     val[c] = c;
 }
 
+// centres in cell order as float (x, y, threshold): the threshold bounds the
+// squared distance of any centre the exact test could accept
+__global__ void k_cell_floats(int n, const int *__restrict__ items, const double *__restrict__ c_xy,
+                              const double *__restrict__ c_r, double slack, double delta, float4 *__restrict__ cf) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int c = items[k];
+    double lim = slack * c_r[c] * 1.001 + delta;
+    cf[k] = make_float4((float)c_xy[2 * c], (float)c_xy[2 * c + 1], __double2float_ru(lim * lim * 1.001), 0.0f);
+}
+
 __global__ void k_cell_bounds(int n, const uint32_t *__restrict__ key, int *__restrict__ start, int *__restrict__ end) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -127,10 +138,10 @@ __global__ void k_cell_bounds(int n, const uint32_t *__restrict__ key, int *__re
 // ratio is <= slack^2, else it is a point target.
 __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on,
                             const double *__restrict__ c_xy, const double *__restrict__ c_r,
-                            const int *__restrict__ cell_items, const int *__restrict__ cstart,
-                            const int *__restrict__ cend, double x0, double y0, double cell, int ncx, int ncy,
-                            double slack2, int have_grid, int *__restrict__ kind, int *__restrict__ ctr,
-                            int *__restrict__ is_pt) {
+                            const int *__restrict__ cell_items, const float4 *__restrict__ cell_f,
+                            const int *__restrict__ cstart, const int *__restrict__ cend, double x0, double y0,
+                            double cell, int ncx, int ncy, double slack2, int have_grid, int *__restrict__ kind,
+                            int *__restrict__ ctr, int *__restrict__ is_pt) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     if (tgt_on[t] >= 0) {
@@ -138,6 +149,7 @@ __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int
         return;
     }
     double tx = tgt_xy[2 * t], ty = tgt_xy[2 * t + 1];
+    float txf = (float)tx, tyf = (float)ty;
     int best = -1;
     double bestk = INFINITY;
     double fgx = floor((tx - x0) / cell), fgy = floor((ty - y0) / cell);
@@ -149,6 +161,9 @@ __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int
                 if (xx < 0 || xx >= ncx) continue;
                 int cid = yy * ncx + xx;
                 for (int k = cstart[cid]; k < cend[cid]; ++k) {
+                    float4 f = cell_f[k];
+                    float fx = txf - f.x, fy = tyf - f.y;
+                    if (fx * fx + fy * fy > f.z) continue;     // cannot pass the exact test below
                     int c = cell_items[k];
                     double dx = tx - c_xy[2 * c], dy = ty - c_xy[2 * c + 1];
                     double d2 = dx * dx + dy * dy;
@@ -485,8 +500,10 @@ static void associate(gq_geom *g) {
     long long ncell = (long long)ncx * ncy;
     dbuf<uint32_t> ckey;
     dbuf<int> cval, cstart, cend;
+    dbuf<float4> cf;
     ckey.alloc(nc);
     cval.alloc(nc);
+    cf.alloc(nc);
     cstart.alloc(ncell);
     cend.alloc(ncell);
     GQ_CUDA(cudaMemsetAsync(cstart.p, 0, sizeof(int) * ncell, ctx->stream));
@@ -498,11 +515,18 @@ static void associate(gq_geom *g) {
         while ((1ll << bits) < ncell) ++bits;
         gq_radix_sort_pairs32(ctx, ckey.p, cval.p, nc, bits);
         GQ_LAUNCH(ctx, k_cell_bounds, gq_blocks(nc, kT), kT, 0, nc, (const uint32_t *)ckey.p, cstart.p, cend.p);
+        // float prefilter margin: rounding of coordinates of magnitude <= X to float moves a
+        // distance by at most 3 X 2^-24; searched targets lie within two cells of the centres
+        double X = fmax(fmax(fabs(ce.x0), fabs(ce.x1)), fmax(fabs(ce.y0), fabs(ce.y1))) + 2.0 * cell;
+        double delta = 16.0 * X * 0x1p-24;
+        GQ_LAUNCH(ctx, k_cell_floats, gq_blocks(nc, kT), kT, 0, nc, (const int *)cval.p, (const double *)g->c_xy,
+                  (const double *)g->c_r, slack, delta, cf.p);
     }
     if (nt > 0)
         GQ_LAUNCH(ctx, k_associate, gq_blocks(nt, kT), kT, 0, nt, (const double *)g->tgt_xy, (const int *)g->tgt_on,
-                  (const double *)g->c_xy, (const double *)g->c_r, (const int *)cval.p, (const int *)cstart.p,
-                  (const int *)cend.p, ce.x0, ce.y0, cell, ncx, ncy, slack * slack, have_grid, g->t_kind.p,
+                  (const double *)g->c_xy, (const double *)g->c_r, (const int *)cval.p, (const float4 *)cf.p,
+                  (const int *)cstart.p, (const int *)cend.p, ce.x0, ce.y0, cell, ncx, ncy, slack * slack, have_grid,
+                  g->t_kind.p,
                   g->t_ctr.p, is_pt.p);
     g->npt = compact_flags(g, is_pt.p, nt, g->pt_tgt);
 }
