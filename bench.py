@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--kernel", default="S", choices=["S", "D"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time FP64 and MIXED evaluations at eps = 1e-4 ... 1e-12 (orders from eps)")
     ap.add_argument("--grid", type=int, nargs=2, default=[16, 16],
                     help="curves per row / column (the benchmark workload is 16 16; smaller grids are "
                          "profiling cases with the same per-curve sizes)")
@@ -371,6 +373,39 @@ def run_gpu(args, rank, world, local):
                "sample": (f"serial C oracle, build + {args.kernel} evaluation of a {SAMPLE_GRID[0]}x{SAMPLE_GRID[1]} "
                           f"sub-grid of the workload ({nts} targets), {times[0]:.1f} s")}
 
+    # ---- accuracy sweep: orders from eps, FP64 vs MIXED evaluation throughput
+    sweep = None
+    if args.sweep:
+        sweep = []
+        for eps in (1e-4, 1e-6, 1e-8, 1e-10, 1e-12):
+            row = {"eps": eps}
+            ref = None
+            for prec, name in ((0, "fp64"), (1, "mixed")):
+                pr = params_default(p_qbx=0, p_fmm=0, n_max=int(g["n_max"]), eps=eps, precision=prec)
+                sg = C.c_void_p()
+                chk(L.gq_geometry_create(ctx, C.byref(desc), C.byref(pr), C.byref(sg)))
+                chk(L.gq_targets_set(sg, nt, d_txy.data_ptr(), d_ton.data_ptr()))
+                chk(L.gq_build(sg))
+                sst = Stats()
+                for _ in range(2):
+                    chk(L.gq_eval(sg, kern, d_mu.data_ptr(), d_out.data_ptr(), C.byref(sst)))
+                ms = []
+                for _ in range(3):
+                    flush.zero_()
+                    chk(L.gq_eval(sg, kern, d_mu.data_ptr(), d_out.data_ptr(), C.byref(sst)))
+                    ms.append(sst.ms_total)
+                rp = params_default()
+                chk(L.gq_geometry_params(sg, C.byref(rp)))
+                row["p_qbx"], row["p_fmm"] = rp.p_qbx, rp.p_fmm
+                row[name + "_eval_targets_per_s"] = nt / (statistics.mean(ms) * 1e-3)
+                out = d_out.clone()
+                if ref is None:
+                    ref = out
+                else:
+                    row["mixed_rel_err_vs_fp64_path"] = float((out - ref).abs().max() / ref.abs().max())
+                L.gq_geometry_destroy(sg)
+            sweep.append(row)
+
     L.gq_geometry_destroy(geom)
     L.gq_destroy(ctx)
     if rank != 0:
@@ -389,6 +424,7 @@ def run_gpu(args, rank, world, local):
                       "ms": statistics.mean(eval_ms)},
         "stages_ms": stage_report,
         "rel_err_vs_oracle": rel_err,
+        "precision_sweep": sweep,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

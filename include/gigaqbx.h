@@ -55,8 +55,12 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
 /* Algorithm parameters (Sec. 4.1 and 4.3).
  *  p_qbx, p_fmm : QBX and FMM orders, 1 <= p_qbx <= 16, 1 <= p_fmm <= 30.
  *                 0 means "choose from eps": p_fmm = ceil(log2(1/eps)) - 1
- *                 (FMM error ~ (1/2)^(p_fmm+1), Sec. 4.1, 5.1) and p_qbx by
- *                 the same rule capped at 16.
+ *                 (FMM error ~ (1/2)^(p_fmm+1), Sec. 4.1, 5.1), capped at 30;
+ *                 p_qbx = ceil((log10(2/eps) - 2.06) / 1.26), the smallest
+ *                 order whose QBX truncation error, measured as 10^(-2.06 -
+ *                 1.26 q) with Green's identity on starfish curves with
+ *                 centres half a panel length off the curve, is <= eps/2
+ *                 (the paper leaves the truncation constant open, Sec. 2.1).
  *  n_max        : subdivide a box owning more than n_max particles eligible
  *                 for its children (Sec. 4.3, Stage 1).
  *  tf_num/tf_den: target confinement factor t_f as an exact fraction
@@ -70,6 +74,18 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
  *                 |t-c|/r when that ratio is <= assoc_slack (Sec. 2.2.2
  *                 reports up to 20% slack as harmless); otherwise it is an
  *                 ordinary FMM point target.
+ *  eps          : requested accuracy (used for orders of 0 and by GQ_PREC_MIXED).
+ *  precision    : GQ_PREC_FP64 (default): every stage in FP64.
+ *                 GQ_PREC_MIXED: when eps >= 1e-6, the direct interactions
+ *                 (Lists 1, 3 close, 4 close to centres and to point targets)
+ *                 and the List 3 far multipole evaluation at point targets
+ *                 run in FP32 on coordinates taken relative to box centres,
+ *                 with FP64 sums across lanes; a source inside a centre's
+ *                 expansion disk (|r/w| > 1, where rounding would grow as
+ *                 |r/w|^m) is taken in FP64.  Their rounding error, about
+ *                 1e-7 relative, stays below eps/5.  All translations (M2M,
+ *                 M2L, L2L, M2QBXL, L2QBXL), P2M, P2L and the final QBX
+ *                 evaluation stay FP64.  For eps < 1e-6 MIXED runs as FP64.
  */
 typedef struct {
     int p_qbx, p_fmm, n_max;
@@ -79,7 +95,10 @@ typedef struct {
     double radius_factor;
     double assoc_slack;
     double eps;
+    int precision;
 } gq_params;
+
+enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1 };
 
 /* Discretised curve (Sec. 2.1, 2.2.1).  Panel k owns base nodes
  * [k*nb, (k+1)*nb) and quadrature (upsampled) nodes [k*nu, (k+1)*nu).
@@ -132,6 +151,8 @@ gq_status gq_set_stream(gq_ctx *ctx, void *cuda_stream);
 gq_status gq_geometry_create(gq_ctx *ctx, const gq_geometry_desc *desc, const gq_params *params,
                              gq_geom **out);
 gq_status gq_geometry_destroy(gq_geom *g);
+/* The parameters in use, with orders of 0 resolved from eps. */
+gq_status gq_geometry_params(const gq_geom *g, gq_params *out);
 
 /* Set the n targets (host or device).  on_surface_node[i] >= 0 marks an
  * on-surface target evaluated by the two centres of that base node and
@@ -147,6 +168,22 @@ gq_status gq_build(gq_geom *g);
  * density_base: [npanels*nb] density at base nodes (host or device).
  * out: [ntargets] potential values (host or device).  stats may be NULL. */
 gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *out, gq_stats *stats);
+
+/* Exterior Neumann problem (Sec. 1): with u = S mu outside the curve and the
+ * normal derivative g prescribed on it, solve the second-kind equation
+ *     -mu/2 + S' mu = g
+ * for mu at the base nodes by restarted GMRES(restart) from mu = 0.  S' is
+ * evaluated by gq_eval(GQ_SP) (two-sided QBX, principal value); the Arnoldi
+ * vectors and their orthogonalisation (classical Gram-Schmidt, twice) are
+ * FP64 device work.  The targets must be the base nodes, on-surface, in
+ * order (gq_targets_set with xy = base nodes, on_surface_node[i] = i), else
+ * GQ_ERR_STATE.  rhs: [npanels*nb] g (host or device).  mu: [npanels*nb]
+ * solution (host or device).  Stops when the residual estimate drops below
+ * tol * |rhs| or after maxit iterations; *iters receives the iteration count
+ * and *resid the true relative residual |rhs - A mu| / |rhs| (either may be
+ * NULL). */
+gq_status gq_gmres(gq_geom *g, const double *rhs, double tol, int maxit, int restart, double *mu, int *iters,
+                   double *resid);
 
 /* gq_eval without allocating: the same evaluation as gq_eval for callers
  * that must not allocate device memory once they are running -- for example

@@ -13,6 +13,7 @@ _lock = threading.Lock()
 _lib = None
 
 GQ_S, GQ_D, GQ_SP = 0, 1, 2
+GQ_PREC_FP64, GQ_PREC_MIXED = 0, 1
 KERNELS = {"S": GQ_S, "D": GQ_D, "SP": GQ_SP}
 LISTS = ("U", "V", "WC", "WF", "XC", "XF")
 
@@ -27,7 +28,7 @@ class Params(C.Structure):
     _fields_ = [("p_qbx", C.c_int), ("p_fmm", C.c_int), ("n_max", C.c_int),
                 ("tf_num", C.c_int), ("tf_den", C.c_int), ("w3_demote", C.c_int),
                 ("max_level", C.c_int), ("radius_factor", C.c_double),
-                ("assoc_slack", C.c_double), ("eps", C.c_double)]
+                ("assoc_slack", C.c_double), ("eps", C.c_double), ("precision", C.c_int)]
 
 
 class GeometryDesc(C.Structure):
@@ -71,10 +72,12 @@ def lib():
             "gq_set_stream": (st, [vp, vp]),
             "gq_geometry_create": (st, [vp, C.POINTER(GeometryDesc), C.POINTER(Params), C.POINTER(vp)]),
             "gq_geometry_destroy": (st, [vp]),
+            "gq_geometry_params": (st, [vp, C.POINTER(Params)]),
             "gq_targets_set": (st, [vp, i32, vp, vp]),
             "gq_build": (st, [vp]),
             "gq_eval": (st, [vp, i32, vp, vp, C.POINTER(Stats)]),
             "gq_eval_noalloc": (st, [vp, i32, vp, vp]),
+            "gq_gmres": (st, [vp, vp, C.c_double, i32, i32, vp, C.POINTER(i32), C.POINTER(C.c_double)]),
             "gq_context_launches": (st, [vp, C.POINTER(C.c_int64)]),
             "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
@@ -139,6 +142,9 @@ class Geometry:
                          _ptr(keep["panel_len"]))
         self._geom = C.c_void_p()
         self._check(self.L.gq_geometry_create(self._ctx, C.byref(d), C.byref(self.params), C.byref(self._geom)))
+        resolved = Params()
+        self._check(self.L.gq_geometry_params(self._geom, C.byref(resolved)))
+        self.params = resolved
         self.nbase = int(g["npanels"]) * int(g["nb"])
         self.nsrc = int(g["npanels"]) * int(g["nu"])
         self.nt = 0
@@ -198,6 +204,18 @@ class Geometry:
         st = Stats()
         self._check(self.L.gq_eval(self._geom, k, _ptr(density), _ptr(out), C.byref(st)))
         return (out, st) if stats else out
+
+    def gmres(self, rhs, tol=1e-10, maxit=500, restart=50, mu=None):
+        """Solve -mu/2 + S' mu = rhs at the base nodes (targets must be the base
+        nodes, on-surface, in order).  Returns (mu, iterations, relative residual)."""
+        if isinstance(rhs, np.ndarray):
+            rhs = np.ascontiguousarray(rhs, np.float64)
+        if mu is None:
+            mu = np.empty(self.nbase, np.float64)
+        it = C.c_int()
+        res = C.c_double()
+        self._check(self.L.gq_gmres(self._geom, _ptr(rhs), tol, maxit, restart, _ptr(mu), C.byref(it), C.byref(res)))
+        return mu, it.value, res.value
 
     # -------------------------------------------------------------- exports
     def root(self):

@@ -65,9 +65,13 @@ std::vector<double> lagrange_matrix(const double *rb, int nb, const double *ru, 
 void resolve_orders(gq_params &p) {
     if (p.p_fmm <= 0 || p.p_qbx <= 0) {
         GQ_REQUIRE(p.eps > 0 && p.eps < 1, GQ_ERR_INVALID, "orders of 0 need 0 < eps < 1");
+        // FMM order: the idealised FMM error (1/2)^(p+1) <= eps (Sec. 4.1, 5.1)
         int k = (int)ceil(log2(1.0 / p.eps)) - 1;
         if (p.p_fmm <= 0) p.p_fmm = k < 1 ? 1 : (k > GQ_MAX_PFMM ? GQ_MAX_PFMM : k);
-        if (p.p_qbx <= 0) p.p_qbx = k < 1 ? 1 : (k > GQ_MAX_PQBX ? GQ_MAX_PQBX : k);
+        // QBX order: truncation error ~ 10^(-2.06 - 1.26 q) measured with Green's identity on
+        // starfish curves with centres half a panel length off the curve; q with error <= eps/2
+        int q = (int)ceil((log10(2.0 / p.eps) - 2.06) / 1.26);
+        if (p.p_qbx <= 0) p.p_qbx = q < 1 ? 1 : (q > GQ_MAX_PQBX ? GQ_MAX_PQBX : q);
     }
     GQ_REQUIRE(p.p_qbx >= 1 && p.p_qbx <= GQ_MAX_PQBX, GQ_ERR_INVALID, "p_qbx must be in [1, 16]");
     GQ_REQUIRE(p.p_fmm >= 1 && p.p_fmm <= GQ_MAX_PFMM, GQ_ERR_INVALID, "p_fmm must be in [1, 30]");
@@ -77,6 +81,7 @@ void resolve_orders(gq_params &p) {
     GQ_REQUIRE(p.radius_factor > 0, GQ_ERR_INVALID, "radius_factor must be > 0");
     GQ_REQUIRE(p.assoc_slack >= 0, GQ_ERR_INVALID, "assoc_slack must be >= 0");
     GQ_REQUIRE(p.w3_demote >= 1, GQ_ERR_INVALID, "w3_demote must be >= 1");
+    GQ_REQUIRE(p.precision == GQ_PREC_FP64 || p.precision == GQ_PREC_MIXED, GQ_ERR_INVALID, "unknown precision");
 }
 
 }  // namespace
@@ -96,6 +101,7 @@ gq_status gq_params_default(gq_params *out) {
     out->radius_factor = 0.5;
     out->assoc_slack = 1.2;
     out->eps = 0.0;
+    out->precision = GQ_PREC_FP64;
     return GQ_OK;
 }
 
@@ -182,6 +188,12 @@ gq_status gq_geometry_destroy(gq_geom *g) {
     return GQ_OK;
 }
 
+gq_status gq_geometry_params(const gq_geom *g, gq_params *out) {
+    if (!g || !out) return GQ_ERR_INVALID;
+    *out = g->prm;
+    return GQ_OK;
+}
+
 gq_status gq_targets_set(gq_geom *g, int n, const double *xy, const int *on_surface_node) {
     if (!g || n < 0 || (n > 0 && (!xy || !on_surface_node))) return GQ_ERR_INVALID;
     return guarded(g->ctx, [&] {
@@ -190,6 +202,9 @@ gq_status gq_targets_set(gq_geom *g, int n, const double *xy, const int *on_surf
         for (int i = 0; i < n; ++i)
             GQ_REQUIRE(on[i] >= -1 && on[i] < g->nbase, GQ_ERR_INVALID, "on_surface_node out of range");
         g->nt = n;
+        bool base = n == g->nbase;
+        for (int i = 0; base && i < n; ++i) base = on[i] == i;
+        g->targets_are_base_nodes = base;
         upload(g->ctx, g->tgt_xy, xy, 2 * (size_t)n);
         upload(g->ctx, g->tgt_on, on.data(), (size_t)n);
         GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
@@ -205,6 +220,7 @@ gq_status gq_build(gq_geom *g) {
     return guarded(g->ctx, [&] {
         GQ_CUDA(cudaSetDevice(g->ctx->device));
         gq_tables_release(g);
+        g->mixed_ready = false;
         gq_form_centres(g);
         gq_build_all(g);
         GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
@@ -247,6 +263,36 @@ gq_status gq_eval_noalloc(gq_geom *g, int kernel, const double *density_dev, dou
         GQ_REQUIRE(is_device_ptr(density_dev), GQ_ERR_INVALID, "gq_eval_noalloc: density must be device memory");
         GQ_REQUIRE(g->nt == 0 || is_device_ptr(out_dev), GQ_ERR_INVALID, "gq_eval_noalloc: out must be device memory");
         gq_eval_noalloc_impl(g, kernel, density_dev, out_dev);
+    });
+}
+
+gq_status gq_gmres(gq_geom *g, const double *rhs, double tol, int maxit, int restart, double *mu, int *iters,
+                   double *resid) {
+    if (!g || !rhs || !mu || !(tol > 0) || maxit < 1 || restart < 1 || restart > 1000) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        GQ_REQUIRE(g->built, GQ_ERR_STATE, "gq_gmres before gq_build");
+        GQ_REQUIRE(g->targets_are_base_nodes, GQ_ERR_STATE,
+                   "gq_gmres needs the targets to be the base nodes, on-surface, in order");
+        cudaStream_t st = g->ctx->stream;
+        dbuf<double> b, x;
+        const double *bd = rhs;
+        if (!is_device_ptr(rhs)) {
+            b.alloc(g->nbase);
+            GQ_CUDA(cudaMemcpyAsync(b.p, rhs, sizeof(double) * g->nbase, cudaMemcpyDefault, st));
+            bd = b.p;
+        }
+        bool mu_dev = is_device_ptr(mu);
+        double *xd = mu;
+        if (!mu_dev) {
+            x.alloc(g->nbase);
+            xd = x.p;
+        }
+        double rr = 0;
+        int it = gq_gmres_impl(g, bd, tol, maxit, restart, xd, &rr);
+        if (!mu_dev) GQ_CUDA(cudaMemcpyAsync(mu, xd, sizeof(double) * g->nbase, cudaMemcpyDefault, st));
+        GQ_CUDA(cudaStreamSynchronize(st));
+        if (iters) *iters = it;
+        if (resid) *resid = rr;
     });
 }
 

@@ -652,6 +652,280 @@ __global__ void k_export_qbx(int nc, int Q, const int *__restrict__ ctr_perm, co
     out[(size_t)ctr_perm[c] * (Q + 1) + m] = cscale(Qc[(size_t)c * (Q + 1) + m], s);
 }
 
+// ------------------------------------------------------------------ mixed precision: FP32 direct sums
+// Coordinates are stored relative to box centres so that the FP32 differences
+// y - c do not cancel: a source is kept relative to its leaf centre, a centre
+// or point target relative to its own box centre, and the offset between the
+// two box centres is formed in FP64 once per source range.
+struct MixedView {
+    const float2 *s_rel, *str, *c_rel, *p_rel, *M;
+    const float *c_r;
+};
+
+__device__ __forceinline__ float2 fcmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void k_rel_coords(int n, const double2 *__restrict__ xy, const int *__restrict__ owner, EvalView E,
+                             float2 *__restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int b = owner[j];
+    double2 z = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
+    out[j] = make_float2((float)(xy[j].x - z.x), (float)(xy[j].y - z.y));
+}
+
+__global__ void k_to_float2(long long n, const double2 *__restrict__ in, float2 *__restrict__ out) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = make_float2((float)in[j].x, (float)in[j].y);
+}
+
+__global__ void k_to_float(int n, const double *__restrict__ in, float *__restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = (float)in[j];
+}
+
+struct NearRangesF {
+    int beg[kNearRanges];
+    int pre[kNearRanges + 1];
+    float2 off[kNearRanges];   // centre of the source leaf minus centre of the target box
+    int n;
+};
+
+__device__ void load_ranges_f(const EvalView &E, int b, double2 zb, int e0, int ne, NearRangesF &R, int *wsum) {
+    int n0 = E.loff[0][b + 1] - E.loff[0][b], n2 = E.loff[2][b + 1] - E.loff[2][b];
+    int cnt = min(kNearRanges, ne - e0);
+    int lens[2] = {0, 0};
+    for (int r = 0; r < 2; ++r) {
+        int i = threadIdx.x * 2 + r;
+        if (i < cnt) {
+            int e = e0 + i, d;
+            if (e < n0) d = E.lidx[0][E.loff[0][b] + e];
+            else if (e < n0 + n2) d = E.lidx[2][E.loff[2][b] + e - n0];
+            else d = E.lidx[4][E.loff[4][b] + e - n0 - n2];
+            R.beg[i] = E.src_beg[d];
+            lens[r] = E.src_end[d] - E.src_beg[d];
+            double2 zd = box_centre(E.R, E.blev[d], E.bix[d], E.biy[d]);
+            R.off[i] = make_float2((float)(zd.x - zb.x), (float)(zd.y - zb.y));
+        }
+    }
+    int pre = block_excl_scan_128(lens[0] + lens[1], wsum);
+    if (threadIdx.x * 2 < kNearRanges) R.pre[threadIdx.x * 2] = pre;
+    if (threadIdx.x * 2 + 1 < kNearRanges) R.pre[threadIdx.x * 2 + 1] = pre + lens[0];
+    if (threadIdx.x == kNearThreads - 1) R.pre[kNearRanges] = pre + lens[0] + lens[1];
+    if (threadIdx.x == 0) R.n = cnt;
+    __syncthreads();
+}
+
+template <int QQ, int KERNEL>
+__global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, MixedView X, int nwork,
+                                                                    const int *__restrict__ work,
+                                                                    double2 *__restrict__ Qout) {
+    __shared__ NearRangesF R;
+    __shared__ int wsum[kNearThreads / 32];
+    int b = work[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
+    int cb = E.ctr_beg[b], ce = E.ctr_end[b];
+    double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
+    bool single = ne <= kNearRanges;
+    if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
+    for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
+        int c = c0 + w;
+        bool valid = c < ce;
+        float2 cz = valid ? X.c_rel[c] : make_float2(0.f, 0.f);
+        float rc = valid ? X.c_r[c] : 1.f;
+        float rc2 = rc * rc;
+        double2 czd = valid ? E.sc_xy[c] : make_double2(0.0, 0.0);
+        double rcd = valid ? E.sc_r[c] : 1.0;
+        float2 acc[QQ + 1];
+        double2 acc64[QQ + 1];   // sources inside the expansion disk (|r/w| > 1): FP64
+#pragma unroll
+        for (int m = 0; m <= QQ; ++m) {
+            acc[m] = make_float2(0.f, 0.f);
+            acc64[m] = make_double2(0.0, 0.0);
+        }
+        for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
+            if (!single) {
+                __syncthreads();
+                load_ranges_f(E, b, zb, e0, ne, R, wsum);
+            }
+            int T = R.pre[R.n];
+            if (valid) {
+                int r = 0;
+                for (int v = lane; v < T; v += 32) {
+                    while (R.pre[r + 1] <= v) ++r;
+                    int s = R.beg[r] + (v - R.pre[r]);
+                    float2 y = X.s_rel[s], o = R.off[r], st = X.str[s];
+                    float wx = (y.x + o.x) - cz.x, wy = (y.y + o.y) - cz.y;
+                    float n2 = wx * wx + wy * wy;
+                    if (n2 < rc2) {
+                        // rounding would be amplified by |r/w|^m: take this pair in FP64
+                        double2 yd = E.s_xy[s], sd = E.str[s];
+                        double dx = yd.x - czd.x, dy = yd.y - czd.y;
+                        double d2 = dx * dx + dy * dy, dinv = 1.0 / d2;
+                        double2 wi = make_double2(dx * dinv, -dy * dinv);
+                        double2 uu = make_double2(rcd * wi.x, rcd * wi.y);
+                        if (KERNEL == GQ_D) {
+                            double2 t = cmul(sd, wi);
+                            acc64[0] = cadd(acc64[0], t);
+#pragma unroll
+                            for (int m = 1; m <= QQ; ++m) {
+                                t = cmul(t, uu);
+                                acc64[m] = cadd(acc64[m], t);
+                            }
+                        } else {
+                            acc64[0].x += sd.x * (0.5 * log(d2));
+                            double2 t = make_double2(sd.x * uu.x, sd.x * uu.y);
+                            acc64[1] = cadd(acc64[1], t);
+#pragma unroll
+                            for (int m = 2; m <= QQ; ++m) {
+                                t = cmul(t, uu);
+                                acc64[m] = cadd(acc64[m], t);
+                            }
+                        }
+                        continue;
+                    }
+                    float inv = __fdividef(1.0f, n2);
+                    float2 winv = make_float2(wx * inv, -wy * inv);
+                    float2 u = make_float2(rc * winv.x, rc * winv.y);
+                    if (KERNEL == GQ_D) {
+                        float2 t = fcmul(st, winv);
+                        acc[0].x += t.x;
+                        acc[0].y += t.y;
+#pragma unroll
+                        for (int m = 1; m <= QQ; ++m) {
+                            t = fcmul(t, u);
+                            acc[m].x += t.x;
+                            acc[m].y += t.y;
+                        }
+                    } else {
+                        acc[0].x += st.x * 0.5f * logf(n2);
+                        float2 t = make_float2(st.x * u.x, st.x * u.y);
+                        acc[1].x += t.x;
+                        acc[1].y += t.y;
+#pragma unroll
+                        for (int m = 2; m <= QQ; ++m) {
+                            t = fcmul(t, u);
+                            acc[m].x += t.x;
+                            acc[m].y += t.y;
+                        }
+                    }
+                }
+            }
+        }
+        double2 dacc[QQ + 1];
+#pragma unroll
+        for (int m = 0; m <= QQ; ++m) {
+            dacc[m] = make_double2((double)acc[m].x + acc64[m].x, (double)acc[m].y + acc64[m].y);
+            for (int o = 16; o > 0; o >>= 1) dacc[m] = cadd(dacc[m], shfl2_xor(dacc[m], o));
+        }
+        if (valid && lane <= QQ) {
+            double2 v = dacc[0];
+#pragma unroll
+            for (int m = 1; m <= QQ; ++m)
+                if (lane == m) v = dacc[m];
+            if (KERNEL != GQ_D && lane >= 1) v = cscale(v, -1.0 / lane);
+            Qout[(size_t)c * (QQ + 1) + lane] = v;
+        }
+    }
+}
+
+template <int KERNEL>
+__global__ void __launch_bounds__(kNearThreads) k_near_points_f32(EvalView E, MixedView X, int nwork,
+                                                                   const int *__restrict__ work,
+                                                                   double *__restrict__ pot) {
+    __shared__ NearRangesF R;
+    __shared__ int wsum[kNearThreads / 32];
+    int b = work[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
+    int tb = E.pt_beg[b], te = E.pt_end[b];
+    double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
+    bool single = ne <= kNearRanges;
+    if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
+    for (int t0 = tb; t0 < te; t0 += kNearThreads / 32) {
+        int t = t0 + w;
+        bool valid = t < te;
+        float2 tz = valid ? X.p_rel[t] : make_float2(0.f, 0.f);
+        float acc = 0.f;
+        for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
+            if (!single) {
+                __syncthreads();
+                load_ranges_f(E, b, zb, e0, ne, R, wsum);
+            }
+            int T = R.pre[R.n];
+            if (valid) {
+                int r = 0;
+                for (int v = lane; v < T; v += 32) {
+                    while (R.pre[r + 1] <= v) ++r;
+                    int s = R.beg[r] + (v - R.pre[r]);
+                    float2 y = X.s_rel[s], o = R.off[r], st = X.str[s];
+                    float wx = (y.x + o.x) - tz.x, wy = (y.y + o.y) - tz.y;
+                    float n2 = wx * wx + wy * wy;
+                    if (n2 == 0.f) continue;
+                    if (KERNEL == GQ_D) acc += (st.x * wx + st.y * wy) * __fdividef(1.0f, n2);
+                    else acc += st.x * 0.5f * logf(n2);
+                }
+            }
+        }
+        double dacc = (double)acc;
+        for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+        if (valid && lane == 0) pot[t] = dacc;
+    }
+}
+
+// M2P in FP32: thread per point target, Horner in v = rho / (t - z_d)
+__global__ void k_w_points_f32(EvalView E, MixedView X, int npt, const int *__restrict__ pt_owner,
+                               double *__restrict__ pot) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npt) return;
+    int b = pt_owner[t];
+    int beg = E.loff[3][b], end = E.loff[3][b + 1];
+    if (beg == end) return;
+    int P = E.P, P1 = P + 1;
+    double2 tz = E.sp_xy[t];
+    float acc = 0.f;
+    for (int i = beg; i < end; ++i) {
+        int d = E.lidx[3][i];
+        int l = E.blev[d];
+        double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
+        float zx = (float)(tz.x - zd.x), zy = (float)(tz.y - zd.y);
+        float rho = (float)box_rho(E.R, l);
+        float n2 = zx * zx + zy * zy, inv = __fdividef(1.0f, n2);
+        float2 v = make_float2(rho * zx * inv, -rho * zy * inv);
+        const float2 *A = X.M + (size_t)d * P1;
+        float2 h = A[P];
+        for (int k = P - 1; k >= 1; --k) {
+            h = fcmul(h, v);
+            h.x += A[k].x;
+            h.y += A[k].y;
+        }
+        h = fcmul(h, v);
+        acc += h.x + A[0].x * 0.5f * logf(n2);
+    }
+    pot[t] += (double)acc;
+}
+
+template <int QQ>
+void launch_near_centres_f32(gq_ctx *ctx, const EvalView &E, const MixedView &X, int nwork, const int *work,
+                             double2 *Q) {
+    auto kd = k_near_centres_f32<QQ, GQ_D>;
+    auto ks = k_near_centres_f32<QQ, GQ_S>;
+    GQ_LAUNCH(ctx, (E.kernel == GQ_D ? kd : ks), nwork, kNearThreads, 0, E, X, nwork, work, Q);
+}
+
+void dispatch_near_centres_f32(gq_ctx *ctx, const EvalView &E, const MixedView &X, int nwork, const int *work,
+                               double2 *Q) {
+    switch (E.Q) {
+#define GQ_CASE(v) case v: launch_near_centres_f32<v>(ctx, E, X, nwork, work, Q); break;
+        GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
+        GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
+#undef GQ_CASE
+        default: throw gq_error{GQ_ERR_INVALID, "p_qbx out of range"};
+    }
+}
+
 template <int QQ>
 void launch_near_centres(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, double2 *Q) {
     auto kd = k_near_centres<QQ, GQ_D>;
@@ -837,14 +1111,51 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     }
     // Stages 3, 5a, 6a (near field)
     GQ_CUDA(cudaMemsetAsync(g->Q.p, 0, sizeof(double2) * g->nc * Q1, st));
+    const bool f32 = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-6;
+    MixedView X{};
+    if (f32) {
+        if (!g->mixed_ready) {
+            g->s_rel.alloc(g->nsrc);
+            g->c_rel.alloc(g->nc);
+            g->c_rf.alloc(g->nc);
+            g->p_rel.alloc(g->npt);
+            if (g->nsrc) GQ_LAUNCH(ctx, k_rel_coords, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, (const double2 *)g->s_xy,
+                                   (const int *)g->src_owner, E, g->s_rel.p);
+            if (g->nc) {
+                GQ_LAUNCH(ctx, k_rel_coords, gq_blocks(g->nc, 256), 256, 0, g->nc, (const double2 *)g->sc_xy,
+                          (const int *)g->ctr_owner, E, g->c_rel.p);
+                GQ_LAUNCH(ctx, k_to_float, gq_blocks(g->nc, 256), 256, 0, g->nc, (const double *)g->sc_r, g->c_rf.p);
+            }
+            if (g->npt) GQ_LAUNCH(ctx, k_rel_coords, gq_blocks(g->npt, 256), 256, 0, g->npt, (const double2 *)g->sp_xy,
+                                  (const int *)g->pt_owner, E, g->p_rel.p);
+            g->mixed_ready = true;
+        }
+        g->str_f.alloc(g->nsrc);
+        g->M_f.alloc((size_t)g->nbox * P1);
+        if (g->nsrc) GQ_LAUNCH(ctx, k_to_float2, gq_blocks(g->nsrc, 256), 256, 0, (long long)g->nsrc,
+                               (const double2 *)g->strength, g->str_f.p);
+        GQ_LAUNCH(ctx, k_to_float2, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
+                  (const double2 *)g->M, g->M_f.p);
+        X.s_rel = g->s_rel; X.str = g->str_f; X.c_rel = g->c_rel; X.p_rel = g->p_rel; X.M = g->M_f; X.c_r = g->c_rf;
+    }
     mark(5);
-    if (g->n_ctr_boxes) dispatch_near_centres(ctx, E, g->n_ctr_boxes, g->ctr_boxes, g->Q.p);
+    if (g->n_ctr_boxes) {
+        if (f32) dispatch_near_centres_f32(ctx, E, X, g->n_ctr_boxes, g->ctr_boxes, g->Q.p);
+        else dispatch_near_centres(ctx, E, g->n_ctr_boxes, g->ctr_boxes, g->Q.p);
+    }
     mark(6);
     if (g->n_pt_boxes) {
-        auto kd = k_near_points<GQ_D>;
-        auto ks = k_near_points<GQ_S>;
-        GQ_LAUNCH(ctx, (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, g->n_pt_boxes, (const int *)g->pt_boxes,
-                  g->pot.p);
+        if (f32) {
+            auto kd = k_near_points_f32<GQ_D>;
+            auto ks = k_near_points_f32<GQ_S>;
+            GQ_LAUNCH(ctx, (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, X, g->n_pt_boxes,
+                      (const int *)g->pt_boxes, g->pot.p);
+        } else {
+            auto kd = k_near_points<GQ_D>;
+            auto ks = k_near_points<GQ_S>;
+            GQ_LAUNCH(ctx, (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, g->n_pt_boxes,
+                      (const int *)g->pt_boxes, g->pot.p);
+        }
     }
     mark(7);
     // Stage 5b
@@ -856,9 +1167,14 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
                   (const int *)g->ctr_owner, (const double2 *)g->M, g->Q.p);
     }
     mark(8);
-    if (g->npt)
-        GQ_LAUNCH(ctx, k_w_points, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,
-                  (const double2 *)g->M, g->pot.p);
+    if (g->npt) {
+        if (f32)
+            GQ_LAUNCH(ctx, k_w_points_f32, gq_blocks(g->npt, 128), 128, 0, E, X, g->npt, (const int *)g->pt_owner,
+                      g->pot.p);
+        else
+            GQ_LAUNCH(ctx, k_w_points, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,
+                      (const double2 *)g->M, g->pot.p);
+    }
     mark(9);
     // Stage 8
     if (g->nc)

@@ -87,6 +87,7 @@ struct gq_geom {
     dbuf<double> tgt_xy;
     dbuf<int> tgt_on;
     bool targets_set = false;
+    bool targets_are_base_nodes = false;   // target i is on-surface at base node i, nt == nbase
     // association
     dbuf<int> t_kind, t_ctr;
     int npt = 0;
@@ -137,6 +138,14 @@ struct gq_geom {
     dbuf<double> dens_dev;           // [nbase] staging for host inputs
     int last_kernel = -1;
     bool have_eval = false;
+    // mixed precision (FP32 direct sums): coordinates relative to box centres
+    bool mixed_ready = false;
+    dbuf<float2> s_rel;   // sorted sources minus their leaf centre
+    dbuf<float2> c_rel;   // sorted centres minus their owner-box centre
+    dbuf<float> c_rf;     // centre radii
+    dbuf<float2> p_rel;   // sorted point targets minus their leaf centre
+    dbuf<float2> str_f;   // strengths
+    dbuf<float2> M_f;     // multipoles (List 3 far evaluation at point targets)
 };
 
 // ------------------------------------------------------------------ launch helpers
@@ -161,6 +170,8 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
 void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double *out_dev);  // gq_fmm.cu
+int gq_gmres_impl(gq_geom *g, const double *rhs_dev, double tol, int maxit, int restart, double *mu_dev,
+                  double *resid);                                                           // gq_gmres.cu
 
 #define GQ_LAUNCH(ctx, kern, grid, block, smem, ...)                     \
     do {                                                                 \

@@ -1,0 +1,77 @@
+"""GMRES for the exterior Neumann equation -mu/2 + S' mu = g (Sec. 1) on the
+GPU: closed form on the unit circle, a known exterior harmonic function on
+the starfish, and parity with GMRES driven by the oracle's S'."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _geo(g, **kw):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_04070_gb300 import Geometry, params_default
+    p = oracle.default_params(g, **kw)
+    geo = Geometry(g, params_default(p_qbx=p["p_qbx"], p_fmm=p["p_fmm"], n_max=p["n_max"]))
+    geo.set_targets(g["base_xy"], np.arange(len(g["base_xy"]), dtype=np.int32))
+    geo.build()
+    return geo, p
+
+
+def _exterior_check(g, p, mu, z0, radius):
+    from paper_1801_04070_gb300 import Geometry, params_default
+    th = np.linspace(0, 2 * np.pi, 200, endpoint=False)
+    t = np.stack([radius * np.cos(th), radius * np.sin(th)], 1)
+    geo = Geometry(g, params_default(p_qbx=p["p_qbx"], p_fmm=p["p_fmm"], n_max=p["n_max"]))
+    geo.set_targets(t, -np.ones(len(t), np.int32))
+    geo.build()
+    u = geo.eval("S", mu)
+    z = t[:, 0] + 1j * t[:, 1]
+    return np.abs(u - (1.0 / (z - z0)).real).max()
+
+
+def test_unit_circle_closed_form():
+    g = workloads.unit_circle(24)
+    geo, p = _geo(g, p_qbx=12, p_fmm=20)
+    th = g["base_theta"]
+    mu, it, res = geo.gmres(-np.cos(th), tol=1e-12, maxit=100, restart=30)
+    assert res < 1e-11 and it < 20
+    assert np.abs(mu - 2 * np.cos(th)).max() < 1e-8
+    assert _exterior_check(g, p, mu, 0.0, 2.0) < 1e-8
+
+
+def test_starfish_known_solution_and_oracle_parity():
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    g = workloads.starfish_c1()
+    geo, p = _geo(g, p_qbx=10, p_fmm=20)
+    z0 = 0.1 + 0.2j
+    x = g["base_xy"][:, 0] + 1j * g["base_xy"][:, 1]
+    nrm = g["base_n"][:, 0] + 1j * g["base_n"][:, 1]
+    rhs = (nrm * (-1.0 / (x - z0) ** 2)).real          # d/dn Re(1/(z - z0))
+    mu, it, res = geo.gmres(rhs, tol=1e-12, maxit=300, restart=60)
+    assert res < 1e-11
+    assert _exterior_check(g, p, mu, z0, 2.5) < 2e-5     # QBX truncation of S' at 64 panels
+    # parity with GMRES on the oracle's operator
+    g2 = dict(g)
+    g2["tgt_xy"] = g["base_xy"]
+    g2["tgt_onsurf"] = np.arange(len(x), dtype=np.int32)
+    o = oracle.Oracle(g2, p)
+    n = len(x)
+    A = spla.LinearOperator((n, n), matvec=lambda v: -0.5 * v + o.eval("SP", np.asarray(v).ravel()))
+    mu_o, info = spla.gmres(A, rhs, rtol=1e-13, atol=0.0, restart=60, maxiter=300)
+    assert info == 0
+    assert np.abs(mu - mu_o).max() <= 1e-9 * np.abs(mu_o).max()
+
+
+def test_requires_base_node_targets():
+    from paper_1801_04070_gb300 import GigaQBXError
+    g = workloads.starfish_c1()
+    geo, p = _geo(g)
+    geo.set_targets(g["base_xy"][:10], np.arange(10, dtype=np.int32))
+    geo.build()
+    with pytest.raises(GigaQBXError):
+        geo.gmres(np.ones(len(g["base_xy"])))

@@ -1,0 +1,62 @@
+"""Precision modes (MIXED: FP32 direct sums when eps >= 1e-6) and the accuracy
+sweep with orders chosen from the requested accuracy, checked against the
+FP64 oracle: O2 at the same orders (rounding of the mixed path) and O1,
+unaccelerated QBX at the same p_qbx (FMM + rounding error, the quantity the
+Theorem of Sec. 4.5 bounds)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _geo(g, **kw):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_04070_gb300 import Geometry, params_default
+    geo = Geometry(g, params_default(**kw))
+    geo.build()
+    return geo
+
+
+@pytest.mark.parametrize("kern", ["S", "D"])
+def test_mixed_fp32_tier_matches_oracle(kern):
+    g = workloads.small_grid(3, 2, 24, 5000, seed=11, on_surface="up", p_qbx=8, p_fmm=15)
+    geo = _geo(g, p_qbx=8, p_fmm=15, n_max=32, eps=1e-6, precision=1)
+    v = geo.eval(kern, g["density"])
+    ref = oracle.Oracle(g, oracle.default_params(g)).eval(kern, g["density"])
+    err = np.abs(v - ref).max() / np.abs(ref).max()
+    print(f"MIXED (FP32 direct) {kern}: rel err vs FP64 oracle {err:.2e}")
+    assert err <= 2e-7          # <= eps/5 at the FP32 tier threshold eps = 1e-6
+
+
+def test_mixed_below_threshold_is_fp64():
+    g = workloads.small_grid(2, 2, 16, 3000, seed=7)
+    geo = _geo(g, p_qbx=5, p_fmm=10, n_max=32, eps=1e-8, precision=1)
+    v = geo.eval("S", g["density"])
+    ref = oracle.Oracle(g, oracle.default_params(g)).eval("S", g["density"])
+    assert np.abs(v - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-8, 1e-10, 1e-12])
+def test_accuracy_sweep(eps):
+    g = workloads.starfish_grid(4, 4, 64, n_off=1 << 16, on_surface="up", seed=1)
+    from paper_1801_04070_gb300 import params_default
+    geo = _geo(g, p_qbx=0, p_fmm=0, n_max=32, eps=eps, precision=1)
+    prm = geo.params
+    v = geo.eval("S", g["density"])
+    o = oracle.Oracle(g, oracle.default_params(g, p_qbx=prm.p_qbx, p_fmm=prm.p_fmm))
+    kind, _ = o.association()
+    rng = np.random.default_rng(1)
+    mask = np.zeros(len(kind), np.int32)
+    for k in (1, 2):
+        ids = np.nonzero(kind == k)[0]
+        mask[rng.choice(ids, min(150, len(ids)), replace=False)] = 1
+    sel = mask.astype(bool)
+    o1 = o.direct("S", g["density"], target_mask=mask)
+    err = np.abs(v[sel] - o1[sel]).max() / np.abs(o1[sel]).max()
+    print(f"eps {eps:.0e}: p_qbx {prm.p_qbx} p_fmm {prm.p_fmm}: rel err vs unaccelerated QBX {err:.2e}")
+    assert err <= max(eps, 1e-11)
