@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="also time FP64 and MIXED evaluations at eps = 1e-4 ... 1e-12 (orders from eps)")
+    ap.add_argument("--batched", action="store_true",
+                    help="also time 64 geometries of uneven size (2k-200k quadrature nodes, log-uniform) x 8 "
+                         "densities: one CUDA-graph launch against one gq_eval after another")
     ap.add_argument("--grid", type=int, nargs=2, default=[16, 16],
                     help="curves per row / column (the benchmark workload is 16 16; smaller grids are "
                          "profiling cases with the same per-curve sizes)")
@@ -217,6 +220,81 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- batched workload
+def batched_workloads(n_geom=64, n_dens=8, seed=4):
+    """n_geom starfish arrays with quadrature-node counts log-uniform in
+    [2k, 200k] (64 nodes per panel, 64 panels per curve; the smallest are one
+    curve with fewer panels), on-surface targets at the base nodes plus as many
+    off-surface targets, n_dens random-Fourier densities each."""
+    import workloads
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_geom):
+        ns = float(np.exp(rng.uniform(np.log(2000), np.log(200000))))
+        curves = max(1, int(round(ns / 4096)))
+        panels = 64 if curves > 1 else max(8, int(round(ns / 64)))
+        nx = int(np.ceil(np.sqrt(curves)))
+        ny = int(np.ceil(curves / nx))
+        g = workloads.starfish_grid(nx, ny, panels, n_off=nx * ny * panels * 16, on_surface="base", seed=100 + i)
+        dens = np.stack([workloads.starfish.fourier_density(g, rng) for _ in range(n_dens)])
+        out.append((g, dens))
+    return out
+
+
+def run_batched(args, dev, stream):
+    import torch
+
+    from paper_1801_04070_gb300 import Batch, Geometry, params_default
+    items = batched_workloads()
+    geos, dens, outs = [], [], []
+    for g, d in items:
+        geo = Geometry(g, params_default(p_qbx=8, p_fmm=15, n_max=32), device=dev.index)
+        geo.build()
+        geos.append(geo)
+        dens.append(torch.tensor(d, dtype=torch.float64, device=dev))
+        outs.append(torch.empty((d.shape[0], len(g["tgt_xy"])), dtype=torch.float64, device=dev))
+    ntot = sum(o.numel() for o in outs)
+    nsrc = [int(len(g["up_w"])) for g, _ in items]
+    kern = args.kernel
+
+    def sequential():
+        for geo, d, o in zip(geos, dens, outs):
+            for j in range(d.shape[0]):
+                geo.eval(kern, d[j], o[j])
+
+    b = Batch(geos)
+    b.eval(kern, dens, outs)            # eager pass, autotune, capture
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    sequential()
+    torch.cuda.synchronize()
+    same = all(torch.equal(a, c) for a, c in zip(ref, outs))
+    res = {}
+    for name, fn in (("graph", lambda: b.eval(kern, dens, outs)), ("sequential", sequential)):
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        res[name] = statistics.mean(t)
+    streams = b.streams()
+    b.close()
+    for geo in geos:
+        geo.close()
+    return {"workload": f"{len(items)} starfish arrays, {min(nsrc)}-{max(nsrc)} quadrature nodes "
+                        f"(log-uniform), {dens[0].shape[0]} densities each, p_qbx 8, p_fmm 15, {kern}",
+            "targets_x_densities": ntot, "graph_ms": res["graph"], "sequential_ms": res["sequential"],
+            "graph_targets_per_s": ntot / (res["graph"] * 1e-3),
+            "sequential_targets_per_s": ntot / (res["sequential"] * 1e-3),
+            "streams": streams, "results_identical": bool(same)}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -406,6 +484,8 @@ def run_gpu(args, rank, world, local):
                 L.gq_geometry_destroy(sg)
             sweep.append(row)
 
+    batched = run_batched(args, dev, stream) if args.batched else None
+
     L.gq_geometry_destroy(geom)
     L.gq_destroy(ctx)
     if rank != 0:
@@ -425,6 +505,7 @@ def run_gpu(args, rank, world, local):
         "stages_ms": stage_report,
         "rel_err_vs_oracle": rel_err,
         "precision_sweep": sweep,
+        "batched": batched,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -185,6 +185,27 @@ gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *ou
 gq_status gq_gmres(gq_geom *g, const double *rhs, double tol, int maxit, int restart, double *mu, int *iters,
                    double *resid);
 
+/* Batched evaluation of independent geometries (each built, on the context's
+ * device).  gq_batch_eval evaluates `kernel` for ndens densities of every
+ * geometry: dens[i] points to ndens consecutive density vectors of geometry i
+ * ([ndens][npanels_i*nb_i], device memory) and out[i] receives
+ * [ndens][ntargets_i] values (device memory).  All evaluations run as one CUDA
+ * graph launch on the context's stream: each geometry is a branch of the
+ * graph (its densities in order), branches are spread over several streams,
+ * largest first.  The first call for a given (kernel, ndens, pointer set)
+ * runs the evaluations once, then an autotuner captures the graph with 1, 2,
+ * 4, 8 and 16 streams, times replays and keeps the fastest (cached per batch
+ * shape; written to the file named by GQ_AUTOTUNE_CACHE if set); later calls
+ * with the same arguments only replay the graph.  The geometries must stay
+ * alive and must not be rebuilt while the batch exists.  Results are those of
+ * gq_eval (the same kernels). */
+typedef struct gq_batch gq_batch;
+gq_status gq_batch_create(gq_ctx *ctx, int ngeom, gq_geom *const *geoms, gq_batch **out);
+gq_status gq_batch_destroy(gq_batch *b);
+gq_status gq_batch_eval(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out);
+/* Streams the autotuner chose for the captured graph (0 before the first gq_batch_eval). */
+gq_status gq_batch_streams(const gq_batch *b, int *streams);
+
 /* gq_eval without allocating: the same evaluation as gq_eval for callers
  * that must not allocate device memory once they are running -- for example
  * code replayed inside a captured CUDA graph, real-time or embedded services

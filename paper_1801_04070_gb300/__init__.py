@@ -9,6 +9,7 @@ There is no CPU fallback: without the compiled library the import of the
 binding fails.
 """
 from ._lib import (  # noqa: F401
+    Batch,
     GQ_D,
     GQ_S,
     GQ_SP,
@@ -19,4 +20,4 @@ from ._lib import (  # noqa: F401
     params_default,
 )
 
-__all__ = ["Geometry", "GigaQBXError", "params_default", "lib", "library_path", "GQ_S", "GQ_D", "GQ_SP"]
+__all__ = ["Batch", "Geometry", "GigaQBXError", "params_default", "lib", "library_path", "GQ_S", "GQ_D", "GQ_SP"]

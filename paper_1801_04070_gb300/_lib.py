@@ -81,6 +81,10 @@ def lib():
             "gq_context_launches": (st, [vp, C.POINTER(C.c_int64)]),
             "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
+            "gq_batch_create": (st, [vp, i32, C.POINTER(vp), C.POINTER(vp)]),
+            "gq_batch_destroy": (st, [vp]),
+            "gq_batch_eval": (st, [vp, i32, i32, C.POINTER(vp), C.POINTER(vp)]),
+            "gq_batch_streams": (st, [vp, C.POINTER(i32)]),
             "gq_export_root": (st, [vp, vp]),
             "gq_export_boxes": (st, [vp] + [vp] * 9),
             "gq_export_list": (st, [vp, i32, vp, vp]),
@@ -262,3 +266,46 @@ class Geometry:
         q = np.zeros((self.nc, self.params.p_qbx + 1, 2))
         self._check(self.L.gq_export_qbx(self._geom, _ptr(q)))
         return q[..., 0] + 1j * q[..., 1]
+
+
+class Batch:
+    """Independent built geometries evaluated together by one CUDA-graph launch
+    (gq_batch_*).  Densities and outputs are torch CUDA tensors of shape
+    [ndens, n] per geometry."""
+
+    def __init__(self, geoms):
+        self.L = lib()
+        self.geoms = list(geoms)
+        self._ctx = self.geoms[0]._ctx
+        arr = (C.c_void_p * len(self.geoms))(*[g._geom.value for g in self.geoms])
+        self._b = C.c_void_p()
+        st = self.L.gq_batch_create(self._ctx, len(self.geoms), arr, C.byref(self._b))
+        if st != 0:
+            raise GigaQBXError(st, self.L.gq_last_error(self._ctx).decode())
+
+    def eval(self, kernel, dens, outs):
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        nd = int(dens[0].shape[0])
+        dp = (C.c_void_p * len(dens))(*[d.data_ptr() for d in dens])
+        op = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        st = self.L.gq_batch_eval(self._b, k, nd, dp, op)
+        if st != 0:
+            raise GigaQBXError(st, self.L.gq_last_error(self._ctx).decode())
+        return outs
+
+    def streams(self):
+        s = C.c_int()
+        self.L.gq_batch_streams(self._b, C.byref(s))
+        return s.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self.L.gq_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

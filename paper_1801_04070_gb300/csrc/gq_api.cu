@@ -296,6 +296,41 @@ gq_status gq_gmres(gq_geom *g, const double *rhs, double tol, int maxit, int res
     });
 }
 
+gq_status gq_batch_create(gq_ctx *ctx, int ngeom, gq_geom *const *geoms, gq_batch **out) {
+    if (!ctx || ngeom < 1 || !geoms || !out) return GQ_ERR_INVALID;
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        for (int i = 0; i < ngeom; ++i) {
+            GQ_REQUIRE(geoms[i] != nullptr, GQ_ERR_INVALID, "gq_batch_create: null geometry");
+            GQ_REQUIRE(geoms[i]->built, GQ_ERR_STATE, "gq_batch_create: geometry not built");
+            GQ_REQUIRE(geoms[i]->ctx->device == ctx->device, GQ_ERR_INVALID, "gq_batch_create: other device");
+        }
+        *out = gq_batch_new(ctx, ngeom, geoms);
+    });
+}
+
+gq_status gq_batch_destroy(gq_batch *b) {
+    if (!b) return GQ_ERR_INVALID;
+    gq_batch_free(b);
+    return GQ_OK;
+}
+
+gq_status gq_batch_eval(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out) {
+    if (!b || ndens < 1 || !dens || !out) return GQ_ERR_INVALID;
+    if (kernel != GQ_S && kernel != GQ_D && kernel != GQ_SP) return GQ_ERR_INVALID;
+    gq_ctx *ctx = gq_batch_ctx(b);
+    return guarded(ctx, [&] {
+        GQ_CUDA(cudaSetDevice(ctx->device));
+        gq_batch_eval_impl(b, kernel, ndens, dens, out);
+    });
+}
+
+gq_status gq_batch_streams(const gq_batch *b, int *streams) {
+    if (!b || !streams) return GQ_ERR_INVALID;
+    *streams = gq_batch_streams(b);
+    return GQ_OK;
+}
+
 gq_status gq_tree_info_get(gq_geom *g, gq_tree_info *out) {
     if (!g || !out) return GQ_ERR_INVALID;
     if (!g->built) return GQ_ERR_STATE;

@@ -1,0 +1,234 @@
+// gq_batch.cu -- batched evaluation of many independent geometries and many
+// densities per geometry by one CUDA-graph launch.
+//
+// Each geometry's evaluations (one per density, in order: they share the
+// geometry's expansion buffers) form one branch of the graph; branches are
+// spread over S streams, largest first onto the least loaded stream, so small
+// problems run concurrently and fill the GPU.  The graph is captured once per
+// (kernel, densities, pointer set) and replayed afterwards.  S is chosen by an
+// autotuner that captures the candidates S = 1, 2, 4, 8, 16 (at most the number
+// of geometries), times two replays of each with CUDA events and keeps the
+// fastest; the choice is cached per batch shape in memory and, when the
+// environment variable GQ_AUTOTUNE_CACHE names a file, in that file.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "gq_internal.cuh"
+
+struct gq_batch {
+    gq_ctx *ctx = nullptr;
+    std::vector<gq_geom *> geoms;
+    // captured graph
+    cudaGraphExec_t exec = nullptr;
+    int kernel = -1, ndens = 0, streams = 0;
+    std::vector<const double *> dens;
+    std::vector<double *> out;
+    double tuned_ms = 0.0;
+    int64_t kernels_per_replay = 0;
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;   // batch shape -> stream count
+
+std::string shape_key(const gq_batch *b, int kernel, int ndens) {
+    long long ns = 0, nt = 0;
+    for (auto *g : b->geoms) {
+        ns += g->nsrc;
+        nt += g->nt;
+    }
+    char buf[160];
+    snprintf(buf, sizeof(buf), "g%zu_s%lld_t%lld_k%d_d%d_p%d_q%d", b->geoms.size(), ns, nt, kernel, ndens,
+             b->geoms.empty() ? 0 : b->geoms[0]->prm.p_fmm, b->geoms.empty() ? 0 : b->geoms[0]->prm.p_qbx);
+    return buf;
+}
+
+void load_cache_file() {
+    const char *path = getenv("GQ_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[200];
+    int v;
+    while (fscanf(f, " \"%199[^\"]\" : %d ,", key, &v) == 2) g_tune[key] = v;
+    fclose(f);
+}
+
+void save_cache_file() {
+    const char *path = getenv("GQ_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (auto &kv : g_tune) fprintf(f, "  \"%s\" : %d%s\n", kv.first.c_str(), kv.second, ++i < g_tune.size() ? " ," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+}
+
+// work estimate used to balance branches: quadrature nodes + targets + boxes
+double cost_of(const gq_geom *g) { return (double)g->nsrc + 2.0 * g->nt + 16.0 * g->nbox; }
+
+// capture all evaluations on `S` streams into an executable graph
+cudaGraphExec_t capture(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out, int S,
+                        int64_t *kernels) {
+    cudaStream_t origin;
+    GQ_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+    std::vector<cudaStream_t> st(S);
+    std::vector<gq_ctx> sctx(S);
+    for (int s = 0; s < S; ++s) {
+        GQ_CUDA(cudaStreamCreateWithFlags(&st[s], cudaStreamNonBlocking));
+        sctx[s].device = b->ctx->device;
+        sctx[s].stream = st[s];
+    }
+    // largest first onto the least loaded stream
+    std::vector<int> order(b->geoms.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return cost_of(b->geoms[a]) > cost_of(b->geoms[c]); });
+    std::vector<double> load(S, 0.0);
+    std::vector<int> assign(b->geoms.size());
+    for (int i : order) {
+        int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        assign[i] = s;
+        load[s] += cost_of(b->geoms[i]) * ndens;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaEvent_t fork;
+    std::vector<cudaEvent_t> joins(S);
+    GQ_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int s = 0; s < S; ++s) GQ_CUDA(cudaEventCreateWithFlags(&joins[s], cudaEventDisableTiming));
+    std::vector<gq_ctx *> saved(b->geoms.size());
+    GQ_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+    try {
+        GQ_CUDA(cudaEventRecord(fork, origin));
+        for (int s = 0; s < S; ++s) GQ_CUDA(cudaStreamWaitEvent(st[s], fork, 0));
+        for (size_t i = 0; i < b->geoms.size(); ++i) {
+            gq_geom *g = b->geoms[i];
+            saved[i] = g->ctx;
+            g->ctx = &sctx[assign[i]];
+            for (int j = 0; j < ndens; ++j)
+                gq_eval_all(g, kernel, dens[i] + (size_t)j * g->nbase, out[i] + (size_t)j * g->nt, nullptr);
+            g->ctx = saved[i];
+        }
+        for (int s = 0; s < S; ++s) {
+            GQ_CUDA(cudaEventRecord(joins[s], st[s]));
+            GQ_CUDA(cudaStreamWaitEvent(origin, joins[s], 0));
+        }
+        GQ_CUDA(cudaStreamEndCapture(origin, &graph));
+    } catch (...) {
+        for (size_t i = 0; i < b->geoms.size(); ++i)
+            if (saved[i]) b->geoms[i]->ctx = saved[i];
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(origin, &dummy);
+        if (dummy) cudaGraphDestroy(dummy);
+        throw;
+    }
+    int64_t launched = 0;
+    for (auto &c : sctx) launched += c.launches;
+    *kernels = launched;   // kernel nodes recorded into the graph
+    cudaGraphExec_t exec = nullptr;
+    GQ_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    cudaGraphDestroy(graph);
+    cudaEventDestroy(fork);
+    for (auto e : joins) cudaEventDestroy(e);
+    for (auto s : st) cudaStreamDestroy(s);
+    cudaStreamDestroy(origin);
+    return exec;
+}
+
+double time_replays(gq_batch *b, cudaGraphExec_t exec) {
+    cudaStream_t st = b->ctx->stream;
+    cudaEvent_t e0, e1;
+    GQ_CUDA(cudaEventCreate(&e0));
+    GQ_CUDA(cudaEventCreate(&e1));
+    GQ_CUDA(cudaGraphLaunch(exec, st));
+    GQ_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < 2; ++r) GQ_CUDA(cudaGraphLaunch(exec, st));
+    GQ_CUDA(cudaEventRecord(e1, st));
+    GQ_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    GQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / 2.0;
+}
+
+}  // namespace
+
+gq_batch *gq_batch_new(gq_ctx *ctx, int n, gq_geom *const *geoms) {
+    gq_batch *b = new gq_batch;
+    b->ctx = ctx;
+    b->geoms.assign(geoms, geoms + n);
+    return b;
+}
+
+void gq_batch_free(gq_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
+}
+
+void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out) {
+    gq_ctx *ctx = b->ctx;
+    size_t n = b->geoms.size();
+    bool same = b->exec && b->kernel == kernel && b->ndens == ndens && b->dens.size() == n;
+    for (size_t i = 0; same && i < n; ++i) same = b->dens[i] == dens[i] && b->out[i] == out[i];
+    if (!same) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        // eager pass: sizes every buffer and table so that capture allocates nothing
+        for (size_t i = 0; i < n; ++i) {
+            gq_geom *g = b->geoms[i];
+            gq_ctx *saved = g->ctx;
+            g->ctx = ctx;
+            for (int j = 0; j < ndens; ++j)
+                gq_eval_all(g, kernel, dens[i] + (size_t)j * g->nbase, out[i] + (size_t)j * g->nt, nullptr);
+            g->ctx = saved;
+        }
+        GQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        std::string key = shape_key(b, kernel, ndens);
+        int S = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (g_tune.empty()) load_cache_file();
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) S = it->second;
+        }
+        if (S <= 0) {
+            double best = 1e300;
+            for (int cand : {1, 2, 4, 8, 16}) {
+                if (cand > (int)n && cand != 1) break;
+                int64_t kn = 0;
+                cudaGraphExec_t ex = capture(b, kernel, ndens, dens, out, cand, &kn);
+                double ms = time_replays(b, ex);
+                cudaGraphExecDestroy(ex);
+                if (ms < best) {
+                    best = ms;
+                    S = cand;
+                }
+            }
+            b->tuned_ms = best;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = S;
+            save_cache_file();
+        }
+        b->exec = capture(b, kernel, ndens, dens, out, S, &b->kernels_per_replay);
+        b->kernel = kernel;
+        b->ndens = ndens;
+        b->streams = S;
+        b->dens.assign(dens, dens + n);
+        b->out.assign(out, out + n);
+    }
+    GQ_CUDA(cudaGraphLaunch(b->exec, ctx->stream));
+    ctx->launches += b->kernels_per_replay;
+}
+
+int gq_batch_streams(const gq_batch *b) { return b->streams; }
+gq_ctx *gq_batch_ctx(const gq_batch *b) { return b->ctx; }

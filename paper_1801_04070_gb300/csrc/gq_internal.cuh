@@ -170,6 +170,12 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
 void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double *out_dev);  // gq_fmm.cu
+struct gq_batch;
+gq_batch *gq_batch_new(gq_ctx *ctx, int n, gq_geom *const *geoms);                       // gq_batch.cu
+void gq_batch_free(gq_batch *b);
+void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out);
+int gq_batch_streams(const gq_batch *b);
+gq_ctx *gq_batch_ctx(const gq_batch *b);
 int gq_gmres_impl(gq_geom *g, const double *rhs_dev, double tol, int maxit, int restart, double *mu_dev,
                   double *resid);                                                           // gq_gmres.cu
 
