@@ -206,6 +206,62 @@ gq_status gq_batch_eval(gq_batch *b, int kernel, int ndens, const double *const 
 /* Streams the autotuner chose for the captured graph (0 before the first gq_batch_eval). */
 gq_status gq_batch_streams(const gq_batch *b, int *streams);
 
+/* Learned order selection (an extension; the paper picks orders from its
+ * bounds, Sec. 4.1, which it reports to overestimate the error by about two
+ * orders of magnitude, Sec. 5.1).  A fixed MLP 32 -> 64 -> 32 -> 32 -> 2 with
+ * ReLU maps 32 per-centre features to [log10 relative QBX truncation error at
+ * p_qbx = q_ref, log10 relative FMM error at p_fmm = p_ref].
+ *
+ * gq_centre_features: [ncentres][32] FP32 in centre-id order (host or device):
+ *   0-7  distance from the centre to the 8 nearest other panels (their nearest
+ *        quadrature node among the centre's direct-interaction sources) over
+ *        r, ascending (64 when fewer panels are near),
+ *   8-15 those panels' lengths over the centre's own panel length,
+ *   16-31 curvature times r at the base nodes k-8 .. k+7 of the centre's
+ *        panel, k its own node (indices clamped to the panel), positive where
+ *        the curve bends towards the centre.
+ * Needs gq_build. */
+gq_status gq_centre_features(gq_geom *g, float *features);
+
+typedef struct gq_mlp gq_mlp;
+/* He-initialised weights from `seed`; lives on the context's device. */
+gq_status gq_mlp_create(gq_ctx *ctx, uint64_t seed, gq_mlp **out);
+gq_status gq_mlp_destroy(gq_mlp *m);
+/* Number of parameters (*count), and optionally copy them out (get) or in
+ * (set), host or device, layout W1[64][32] b1[64] W2[32][64] b2[32]
+ * W3[32][32] b3[32] W4[2][32] b4[2]. */
+gq_status gq_mlp_weights(gq_mlp *m, float *get, const float *set, int *count);
+/* Mean squared error of the network (no normalisation) on n samples X[n][32],
+ * Y[n][2] and its gradient with respect to every parameter (FP32 forward and
+ * backward kernels).  grad: host [count] (may be NULL). */
+gq_status gq_mlp_loss_grad(gq_mlp *m, const float *X, const float *Y, int n, float *loss, float *grad);
+/* Train with Adam (FP32) on X[n][32], Y[n][2] (host or device), inputs and
+ * labels standardised by their mean and deviation (kept for prediction),
+ * `epochs` passes of shuffled mini-batches of `batch`.  *final_loss: mean
+ * squared error of the last epoch in standardised units. */
+gq_status gq_mlp_train(gq_mlp *m, const float *X, const float *Y, int n, int epochs, int batch, float lr,
+                       uint64_t seed, float *final_loss);
+/* BF16 inference (weights and activations rounded to BF16, FP32 sums):
+ * Y[n][2] from X[n][32] (host or device). */
+gq_status gq_mlp_predict(gq_mlp *m, const float *X, int n, float *Y);
+/* Set orders from the network's predictions: the tree gets
+ *   p_fmm = p_ref + ceil((max_c yf_c + margin_fmm - log10(eps/2)) / 0.5),
+ * capped at the bound-driven order p_bound (its fallback); when q_ref > 0
+ * centre c also gets its own QBX order
+ *   q_c = q_ref + ceil((yq_c + margin_qbx - log10(eps/2)) / 1.26)
+ * capped at 16 (q_ref <= 0 keeps the geometry's p_qbx for every centre).
+ * 0.5 and 1.26 decades per order are the FMM and QBX error decay rates
+ * measured on starfish curves.  *p_fmm and *q_max receive the orders used.
+ * Later gq_eval calls evaluate each centre's expansion to its own order. */
+gq_status gq_learned_orders(gq_geom *g, gq_mlp *m, double eps, double margin_qbx, double margin_fmm, int q_ref,
+                            int p_ref, int p_bound, int *p_fmm, int *q_max);
+/* Per-centre QBX orders q[ncentres] in centre-id order (host or device,
+ * each in [1, 16]); p_qbx becomes their maximum.  The direct interactions
+ * and the final evaluation of centre c stop at q[c]. */
+gq_status gq_set_centre_orders(gq_geom *g, const int *q);
+/* Set global orders (and drop per-centre orders) for later gq_eval calls. */
+gq_status gq_set_orders(gq_geom *g, int p_qbx, int p_fmm);
+
 /* gq_eval without allocating: the same evaluation as gq_eval for callers
  * that must not allocate device memory once they are running -- for example
  * code replayed inside a captured CUDA graph, real-time or embedded services

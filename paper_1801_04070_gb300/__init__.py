@@ -15,9 +15,10 @@ from ._lib import (  # noqa: F401
     GQ_SP,
     GigaQBXError,
     Geometry,
+    MLP,
     lib,
     library_path,
     params_default,
 )
 
-__all__ = ["Batch", "Geometry", "GigaQBXError", "params_default", "lib", "library_path", "GQ_S", "GQ_D", "GQ_SP"]
+__all__ = ["Batch", "Geometry", "MLP", "GigaQBXError", "params_default", "lib", "library_path", "GQ_S", "GQ_D", "GQ_SP"]

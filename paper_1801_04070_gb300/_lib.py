@@ -81,6 +81,17 @@ def lib():
             "gq_context_launches": (st, [vp, C.POINTER(C.c_int64)]),
             "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
+            "gq_centre_features": (st, [vp, vp]),
+            "gq_mlp_create": (st, [vp, C.c_uint64, C.POINTER(vp)]),
+            "gq_mlp_destroy": (st, [vp]),
+            "gq_mlp_weights": (st, [vp, vp, vp, C.POINTER(i32)]),
+            "gq_mlp_loss_grad": (st, [vp, vp, vp, i32, C.POINTER(C.c_float), vp]),
+            "gq_mlp_train": (st, [vp, vp, vp, i32, i32, i32, C.c_float, C.c_uint64, C.POINTER(C.c_float)]),
+            "gq_mlp_predict": (st, [vp, vp, i32, vp]),
+            "gq_learned_orders": (st, [vp, vp, C.c_double, C.c_double, C.c_double, i32, i32, i32, C.POINTER(i32),
+                                      C.POINTER(i32)]),
+            "gq_set_orders": (st, [vp, i32, i32]),
+            "gq_set_centre_orders": (st, [vp, vp]),
             "gq_batch_create": (st, [vp, i32, C.POINTER(vp), C.POINTER(vp)]),
             "gq_batch_destroy": (st, [vp]),
             "gq_batch_eval": (st, [vp, i32, i32, C.POINTER(vp), C.POINTER(vp)]),
@@ -221,6 +232,26 @@ class Geometry:
         self._check(self.L.gq_gmres(self._geom, _ptr(rhs), tol, maxit, restart, _ptr(mu), C.byref(it), C.byref(res)))
         return mu, it.value, res.value
 
+    def features(self):
+        """[ncentres, 32] FP32 per-centre features (gq_centre_features)."""
+        f = np.zeros((self.nc, 32), np.float32)
+        self._check(self.L.gq_centre_features(self._geom, _ptr(f)))
+        return f
+
+    def learned_orders(self, mlp, eps, margin_qbx=1.0, margin_fmm=1.0, q_ref=4, p_ref=8, p_bound=30):
+        p = C.c_int()
+        q = C.c_int()
+        self._check(self.L.gq_learned_orders(self._geom, mlp._m, eps, margin_qbx, margin_fmm, q_ref, p_ref, p_bound,
+                                             C.byref(p), C.byref(q)))
+        return p.value, q.value
+
+    def set_orders(self, p_qbx, p_fmm):
+        self._check(self.L.gq_set_orders(self._geom, p_qbx, p_fmm))
+
+    def set_centre_orders(self, q):
+        q = np.ascontiguousarray(q, np.int32)
+        self._check(self.L.gq_set_centre_orders(self._geom, _ptr(q)))
+
     # -------------------------------------------------------------- exports
     def root(self):
         o = np.zeros(4)
@@ -302,6 +333,61 @@ class Batch:
         if getattr(self, "_b", None):
             self.L.gq_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The order-selection network (gq_mlp_*): FP32 training, BF16 inference."""
+
+    def __init__(self, geo_or_ctx, seed=0):
+        self.L = lib()
+        self._ctx = geo_or_ctx._ctx if hasattr(geo_or_ctx, "_ctx") else geo_or_ctx
+        self._m = C.c_void_p()
+        self._check(self.L.gq_mlp_create(self._ctx, seed, C.byref(self._m)))
+        n = C.c_int()
+        self._check(self.L.gq_mlp_weights(self._m, None, None, C.byref(n)))
+        self.nparams = n.value
+
+    def _check(self, st):
+        if st != 0:
+            raise GigaQBXError(st, self.L.gq_last_error(self._ctx).decode())
+
+    def weights(self, set=None):
+        w = np.zeros(self.nparams, np.float32)
+        s = None if set is None else np.ascontiguousarray(set, np.float32)
+        self._check(self.L.gq_mlp_weights(self._m, _ptr(w), _ptr(s), None))
+        return w
+
+    def loss_grad(self, X, Y):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        loss = C.c_float()
+        grad = np.zeros(self.nparams, np.float32)
+        self._check(self.L.gq_mlp_loss_grad(self._m, _ptr(X), _ptr(Y), len(X), C.byref(loss), _ptr(grad)))
+        return loss.value, grad
+
+    def train(self, X, Y, epochs=50, batch=512, lr=1e-3, seed=0):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        loss = C.c_float()
+        self._check(self.L.gq_mlp_train(self._m, _ptr(X), _ptr(Y), len(X), epochs, batch, lr, seed, C.byref(loss)))
+        return loss.value
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.zeros((len(X), 2), np.float32)
+        self._check(self.L.gq_mlp_predict(self._m, _ptr(X), len(X), _ptr(Y)))
+        return Y
+
+    def close(self):
+        if getattr(self, "_m", None):
+            self.L.gq_mlp_destroy(self._m)
+            self._m = None
 
     def __del__(self):
         try:

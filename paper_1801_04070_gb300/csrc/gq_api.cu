@@ -331,6 +331,104 @@ gq_status gq_batch_streams(const gq_batch *b, int *streams) {
     return GQ_OK;
 }
 
+gq_status gq_centre_features(gq_geom *g, float *features) {
+    if (!g || !features) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        GQ_REQUIRE(g->built, GQ_ERR_STATE, "gq_centre_features before gq_build");
+        GQ_REQUIRE(g->nb >= 2, GQ_ERR_UNSUPPORTED, "features need at least two base nodes per panel");
+        if (is_device_ptr(features)) {
+            gq_centre_features_impl(g, features);
+        } else {
+            dbuf<float> f;
+            f.alloc((size_t)g->nc * 32);
+            gq_centre_features_impl(g, f.p);
+            GQ_CUDA(cudaMemcpy(features, f.p, sizeof(float) * g->nc * 32, cudaMemcpyDeviceToHost));
+        }
+    });
+}
+
+gq_status gq_mlp_create(gq_ctx *ctx, uint64_t seed, gq_mlp **out) {
+    if (!ctx || !out) return GQ_ERR_INVALID;
+    *out = nullptr;
+    return guarded(ctx, [&] { *out = gq_mlp_new(ctx, seed); });
+}
+
+gq_status gq_mlp_destroy(gq_mlp *m) {
+    if (!m) return GQ_ERR_INVALID;
+    gq_mlp_free(m);
+    return GQ_OK;
+}
+
+gq_status gq_mlp_weights(gq_mlp *m, float *get, const float *set, int *count) {
+    if (!m) return GQ_ERR_INVALID;
+    gq_ctx *ctx = gq_mlp_ctx(m);
+    if (count) *count = gq_mlp_param_count();
+    return guarded(ctx, [&] { gq_mlp_weights_impl(m, get, set); });
+}
+
+gq_status gq_mlp_loss_grad(gq_mlp *m, const float *X, const float *Y, int n, float *loss, float *grad) {
+    if (!m || !X || !Y || n < 1) return GQ_ERR_INVALID;
+    gq_ctx *ctx = gq_mlp_ctx(m);
+    return guarded(ctx, [&] {
+        bool dev = is_device_ptr(X) && is_device_ptr(Y);
+        gq_mlp_loss_grad_impl(m, X, Y, n, dev, loss, grad);
+    });
+}
+
+gq_status gq_mlp_train(gq_mlp *m, const float *X, const float *Y, int n, int epochs, int batch, float lr,
+                       uint64_t seed, float *final_loss) {
+    if (!m || !X || !Y || n < 1 || epochs < 1 || batch < 1 || !(lr > 0)) return GQ_ERR_INVALID;
+    gq_ctx *ctx = gq_mlp_ctx(m);
+    return guarded(ctx, [&] {
+        bool dev = is_device_ptr(X) && is_device_ptr(Y);
+        double l = gq_mlp_train_impl(m, X, Y, n, dev, epochs, batch, lr, seed);
+        if (final_loss) *final_loss = (float)l;
+    });
+}
+
+gq_status gq_mlp_predict(gq_mlp *m, const float *X, int n, float *Y) {
+    if (!m || !X || !Y || n < 0) return GQ_ERR_INVALID;
+    gq_ctx *ctx = gq_mlp_ctx(m);
+    return guarded(ctx, [&] { gq_mlp_predict_impl(m, X, n, is_device_ptr(X), Y, is_device_ptr(Y)); });
+}
+
+gq_status gq_learned_orders(gq_geom *g, gq_mlp *m, double eps, double margin_qbx, double margin_fmm, int q_ref,
+                            int p_ref, int p_bound, int *p_fmm, int *q_max) {
+    if (!g || !m || !(eps > 0 && eps < 1) || q_ref > GQ_MAX_PQBX || p_ref < 1 || p_bound < 1 ||
+        p_bound > GQ_MAX_PFMM)
+        return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        GQ_REQUIRE(g->built, GQ_ERR_STATE, "gq_learned_orders before gq_build");
+        int p = 0, q = 0;
+        gq_learned_orders_impl(g, m, eps, margin_qbx, margin_fmm, q_ref, p_ref, GQ_MAX_PQBX, p_bound, &p, &q);
+        if (p_fmm) *p_fmm = p;
+        if (q_max) *q_max = q;
+    });
+}
+
+gq_status gq_set_centre_orders(gq_geom *g, const int *q) {
+    if (!g || !q) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        GQ_REQUIRE(g->built, GQ_ERR_STATE, "gq_set_centre_orders before gq_build");
+        std::vector<int> h(g->nc);
+        GQ_CUDA(cudaMemcpy(h.data(), q, sizeof(int) * g->nc, cudaMemcpyDefault));
+        for (int v : h) GQ_REQUIRE(v >= 1 && v <= GQ_MAX_PQBX, GQ_ERR_INVALID, "centre order outside [1, 16]");
+        dbuf<int> d;
+        d.alloc(g->nc);
+        GQ_CUDA(cudaMemcpy(d.p, h.data(), sizeof(int) * g->nc, cudaMemcpyHostToDevice));
+        gq_set_centre_orders_impl(g, d.p);
+    });
+}
+
+gq_status gq_set_orders(gq_geom *g, int p_qbx, int p_fmm) {
+    if (!g || p_qbx < 1 || p_qbx > GQ_MAX_PQBX || p_fmm < 1 || p_fmm > GQ_MAX_PFMM) return GQ_ERR_INVALID;
+    g->prm.p_qbx = p_qbx;
+    g->prm.p_fmm = p_fmm;
+    g->has_qc = false;
+    g->have_eval = false;
+    return GQ_OK;
+}
+
 gq_status gq_tree_info_get(gq_geom *g, gq_tree_info *out) {
     if (!g || !out) return GQ_ERR_INVALID;
     if (!g->built) return GQ_ERR_STATE;

@@ -53,6 +53,7 @@ struct EvalView {
     const int *loff[6];
     const int *lidx[6];
     const double *binom;   // [kBinN][kBinN]
+    const int *qc;         // per-centre QBX order (sorted centres) or nullptr: all use Q
 };
 
 __device__ __forceinline__ double box_rho(const RootInfo &R, int l) { return ldexp(R.H, -l); }
@@ -367,6 +368,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
         bool valid = c < ce;
         double2 cz = valid ? E.sc_xy[c] : make_double2(0.0, 0.0);
         double rc = valid ? E.sc_r[c] : 1.0;
+        const int qc = (valid && E.qc) ? E.qc[c] : QQ;
         double2 acc[QQ + 1];
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) acc[m] = make_double2(0.0, 0.0);
@@ -392,6 +394,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                         acc[0] = cadd(acc[0], t);
 #pragma unroll
                         for (int m = 1; m <= QQ; ++m) {
+                            if (m > qc) break;
                             t = cmul(t, u);
                             acc[m] = cadd(acc[m], t);
                         }
@@ -401,6 +404,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                         acc[1] = cadd(acc[1], t);
 #pragma unroll
                         for (int m = 2; m <= QQ; ++m) {
+                            if (m > qc) break;
                             t = cmul(t, u);
                             acc[m] = cadd(acc[m], t);
                         }
@@ -604,7 +608,8 @@ __global__ void k_l2p(EvalView E, int npt, const int *__restrict__ pt_owner, con
 }
 
 // final values at the targets (eq. qbx; two-sided targets average both centres)
-__global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ kind, const int *__restrict__ ctr,
+__global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, const int *__restrict__ kind,
+                        const int *__restrict__ ctr,
                         const int *__restrict__ ctr_pos, const int *__restrict__ tgt_ptpos,
                         const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on,
                         const double *__restrict__ base_n, const double2 *__restrict__ sc_xy,
@@ -626,16 +631,17 @@ __global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ kind,
         double r = sc_r[cp];
         double2 zeta = make_double2((tz.x - cz.x) / r, (tz.y - cz.y) / r);
         const double2 *B = Qc + (size_t)cp * (Q + 1);
+        const int q = qcs ? qcs[cp] : Q;
         if (kernel == GQ_SP) {
             int node = tgt_on[t];
             if (node < 0) { sum = nan(""); break; }
-            double2 h = cscale(B[Q], (double)Q);
-            for (int m = Q - 1; m >= 1; --m) h = cadd(cmul(h, zeta), cscale(B[m], (double)m));
+            double2 h = cscale(B[q], (double)q);
+            for (int m = q - 1; m >= 1; --m) h = cadd(cmul(h, zeta), cscale(B[m], (double)m));
             double2 n = make_double2(base_n[2 * node], base_n[2 * node + 1]);
             sum += -kInv2Pi * cmul(n, h).x / r;
         } else {
-            double2 h = B[Q];
-            for (int m = Q - 1; m >= 0; --m) h = cadd(cmul(h, zeta), B[m]);
+            double2 h = B[q];
+            for (int m = q - 1; m >= 0; --m) h = cadd(cmul(h, zeta), B[m]);
             sum += -kInv2Pi * h.x;
         }
     }
@@ -736,6 +742,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
         float2 cz = valid ? X.c_rel[c] : make_float2(0.f, 0.f);
         float rc = valid ? X.c_r[c] : 1.f;
         float rc2 = rc * rc;
+        const int qc = (valid && E.qc) ? E.qc[c] : QQ;
         double2 czd = valid ? E.sc_xy[c] : make_double2(0.0, 0.0);
         double rcd = valid ? E.sc_r[c] : 1.0;
         float2 acc[QQ + 1];
@@ -795,6 +802,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
                         acc[0].y += t.y;
 #pragma unroll
                         for (int m = 1; m <= QQ; ++m) {
+                            if (m > qc) break;
                             t = fcmul(t, u);
                             acc[m].x += t.x;
                             acc[m].y += t.y;
@@ -806,6 +814,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
                         acc[1].y += t.y;
 #pragma unroll
                         for (int m = 2; m <= QQ; ++m) {
+                            if (m > qc) break;
                             t = fcmul(t, u);
                             acc[m].x += t.x;
                             acc[m].y += t.y;
@@ -1048,6 +1057,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     E.s_xy = g->s_xy; E.str = g->strength; E.sc_xy = g->sc_xy; E.sc_r = g->sc_r; E.sp_xy = g->sp_xy;
     for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
     E.binom = T.binom;
+    E.qc = g->has_qc ? (const int *)g->q_ctr.p : nullptr;
 
     g->strength.alloc(g->nsrc);
     E.str = g->strength;
@@ -1185,7 +1195,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
                   g->pot.p);
     mark(10);
     if (g->nt)
-        GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, (const int *)g->t_kind,
+        GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, E.qc, (const int *)g->t_kind,
                   (const int *)g->t_ctr, (const int *)g->ctr_pos, (const int *)T.tgt_ptpos, (const double *)g->tgt_xy,
                   (const int *)g->tgt_on, (const double *)g->base_n, (const double2 *)g->sc_xy,
                   (const double *)g->sc_r, (const double2 *)g->Q, (const double *)g->pot, out_dev);
@@ -1332,6 +1342,7 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
     E.s_xy = g->s_xy; E.str = str; E.sc_xy = g->sc_xy; E.sc_r = g->sc_r; E.sp_xy = g->sp_xy;
     for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
     E.binom = binom;
+    E.qc = g->has_qc ? (const int *)g->q_ctr.p : nullptr;
 
     // the array keeps the previous call's contents: clear the accumulators
     GQ_CUDA(cudaMemsetAsync(M, 0, sizeof(double2) * g->nbox * P1, st));
@@ -1388,7 +1399,7 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
                   pot);
     }
     if (g->nt)
-        GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, (const int *)g->t_kind,
+        GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, E.qc, (const int *)g->t_kind,
                   (const int *)g->t_ctr, (const int *)g->ctr_pos, (const int *)ptpos, (const double *)g->tgt_xy,
                   (const int *)g->tgt_on, (const double *)g->base_n, (const double2 *)g->sc_xy,
                   (const double *)g->sc_r, (const double2 *)Qc, (const double *)pot, out_dev);

@@ -138,6 +138,9 @@ struct gq_geom {
     dbuf<double> dens_dev;           // [nbase] staging for host inputs
     int last_kernel = -1;
     bool have_eval = false;
+    // learned orders: per-centre QBX order (sorted centre order), used when has_qc
+    bool has_qc = false;
+    dbuf<int> q_ctr;
     // mixed precision (FP32 direct sums): coordinates relative to box centres
     bool mixed_ready = false;
     dbuf<float2> s_rel;   // sorted sources minus their leaf centre
@@ -170,6 +173,20 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
 void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double *out_dev);  // gq_fmm.cu
+struct gq_mlp;
+int gq_mlp_param_count();                                                                   // gq_learned.cu
+gq_mlp *gq_mlp_new(gq_ctx *ctx, uint64_t seed);
+void gq_mlp_free(gq_mlp *M);
+gq_ctx *gq_mlp_ctx(const gq_mlp *M);
+void gq_mlp_weights_impl(gq_mlp *M, float *get, const float *set);
+void gq_mlp_loss_grad_impl(gq_mlp *M, const float *X, const float *Y, int n, bool dev, float *loss, float *grad);
+double gq_mlp_train_impl(gq_mlp *M, const float *X, const float *Y, int n, bool dev, int epochs, int B, float lr,
+                         uint64_t seed);
+void gq_mlp_predict_impl(gq_mlp *M, const float *X, int n, bool xdev, float *Y, bool ydev);
+void gq_centre_features_impl(gq_geom *g, float *feat_dev);
+void gq_set_centre_orders_impl(gq_geom *g, const int *q_dev);
+void gq_learned_orders_impl(gq_geom *g, gq_mlp *M, double eps, double margin, double margin_fmm, int q_ref,
+                            int p_ref, int q_bound, int p_bound, int *p_out, int *q_out);
 struct gq_batch;
 gq_batch *gq_batch_new(gq_ctx *ctx, int n, gq_geom *const *geoms);                       // gq_batch.cu
 void gq_batch_free(gq_batch *b);

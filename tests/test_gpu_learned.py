@@ -1,0 +1,179 @@
+"""Learned order selection on the GPU: gradients of the training kernels
+against the FP64 reference network, BF16 inference against FP32, and the
+full loop -- features on the GPU, labels from the oracle on random star-
+shaped curves, training by the CUDA kernels, deployment on starfish curves at
+a requested accuracy of 1e-8 -- compared with the bound-driven orders: both
+must meet the accuracy against converged unaccelerated QBX (the oracle), and
+the learned orders must evaluate faster."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import mlp as ref_mlp
+
+pytestmark = pytest.mark.gpu
+
+Q_REF, P_REF, Q_HI = 4, 8, 12
+
+
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_04070_gb300 as pkg
+    return torch, pkg
+
+
+def _mlp(pkg, seed=0):
+    g = workloads.starfish_c1()
+    geo = pkg.Geometry(g)
+    return geo, pkg.MLP(geo, seed=seed)
+
+
+def test_gradients_match_fp64_reference():
+    torch, pkg = _gpu()
+    geo, m = _mlp(pkg)
+    rng = np.random.default_rng(0)
+    w = rng.normal(0, 0.2, m.nparams).astype(np.float32)
+    m.weights(set=w)
+    X = rng.normal(size=(300, 32)).astype(np.float32)
+    Y = rng.normal(size=(300, 2)).astype(np.float32)
+    loss, g = m.loss_grad(X, Y)
+    rloss, rg = ref_mlp.loss_grad(w.astype(np.float64), X.astype(np.float64), Y.astype(np.float64))
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss)
+    assert np.abs(g - rg).max() <= 1e-5 * np.abs(rg).max()
+
+
+def test_bf16_inference_close_to_fp32():
+    torch, pkg = _gpu()
+    geo, m = _mlp(pkg, seed=3)
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(1000, 32)).astype(np.float32)
+    w = m.weights()
+    y = m.predict(X)
+    yr = ref_mlp.forward(w.astype(np.float64), X.astype(np.float64))[0]
+    assert np.abs(y - yr).max() <= 3e-2 * np.abs(yr).max()
+
+
+def _labels(g, o_hi, o_ref):
+    """Per centre: log10 relative QBX truncation error at Q_REF and log10
+    relative FMM error at P_REF, at the centre's own base node."""
+    _, b_hi = o_hi.direct("S", g["density"], want_qbx=True)
+    _, b_ref = o_ref.eval("S", g["density"], want_qbx=True)
+    xy, _, _ = o_hi.centres()
+    node = np.arange(len(xy)) // 2
+    t = g["base_xy"][node, 0] + 1j * g["base_xy"][node, 1]
+    z = t - (xy[:, 0] + 1j * xy[:, 1])
+    pw = z[:, None] ** np.arange(Q_HI + 1)[None, :]
+    full = (b_hi * pw).sum(1).real
+    scale = np.abs(full).max()
+    tail = (b_hi[:, Q_REF + 1:] * pw[:, Q_REF + 1:]).sum(1).real
+    fmm = ((b_ref - b_hi[:, :Q_REF + 1]) * pw[:, :Q_REF + 1]).sum(1).real
+    return np.stack([np.log10(np.abs(tail) / scale + 1e-16), np.log10(np.abs(fmm) / scale + 1e-16)], 1)
+
+
+def _training_set(pkg, curves, seed, per_curve=False):
+    rng = np.random.default_rng(seed)
+    X, Y = [], []
+    for cv in curves:
+        g = workloads.discretize([cv], 32)
+        g["density"] = workloads.starfish.fourier_density(g, rng)
+        g["tgt_xy"] = g["base_xy"]
+        g["tgt_onsurf"] = np.arange(len(g["base_xy"]), dtype=np.int32)
+        geo = pkg.Geometry(g, pkg.params_default(p_qbx=Q_REF, p_fmm=P_REF, n_max=32))
+        geo.build()
+        X.append(geo.features())
+        geo.close()
+        o_hi = oracle.Oracle(g, oracle.default_params(p_qbx=Q_HI, p_fmm=P_REF))
+        o_ref = oracle.Oracle(g, oracle.default_params(p_qbx=Q_REF, p_fmm=P_REF))
+        Y.append(_labels(g, o_hi, o_ref))
+    if per_curve:
+        return [x.astype(np.float32) for x in X], [y.astype(np.float32) for y in Y]
+    return np.concatenate(X).astype(np.float32), np.concatenate(Y).astype(np.float32)
+
+
+def test_train_and_deploy_beats_bound_driven_orders():
+    torch, pkg = _gpu()
+    curves = workloads.random_fourier_curves(60, seed=5)
+    X, Y = _training_set(pkg, curves[:50], seed=1)
+    Xs, Ys = _training_set(pkg, curves[50:], seed=2, per_curve=True)
+    Xv, Yv = np.concatenate(Xs), np.concatenate(Ys)
+    geo0, m = _mlp(pkg, seed=7)
+    loss = m.train(X, Y, epochs=150, batch=256, lr=1e-3, seed=0)
+    pv = m.predict(Xv)
+    r2 = [1 - ((pv[:, k] - Yv[:, k]) ** 2).mean() / Yv[:, k].var() for k in (0, 1)]
+    # deployment margins from held-out curves: per centre for the QBX order (upper tail
+    # of the residuals); per geometry for the one FMM order of the tree (largest excess
+    # of a curve's worst measured error over its worst prediction)
+    margin_q = float(np.quantile(Yv[:, 0] - pv[:, 0], 0.995)) + 0.25
+    margin_f = max(float(y[:, 1].max() - m.predict(x)[:, 1].max()) for x, y in zip(Xs, Ys)) + 0.5
+    print(f"training loss {loss:.3f}; held-out R^2 QBX {r2[0]:.3f} FMM {r2[1]:.3f}; "
+          f"margins {margin_q:.2f} {margin_f:.2f}")
+    assert r2[0] > 0.2          # better than the mean; the density, unseen by the features, drives the rest
+
+    eps = 1e-8
+    g = workloads.starfish_grid(4, 4, 64, n_off=1 << 16, on_surface="up", seed=1)
+    q_fixed = 5
+    results = {}
+    for mode in ("bound", "learned"):
+        geo = pkg.Geometry(g, pkg.params_default(p_qbx=q_fixed, p_fmm=0, n_max=32, eps=eps))
+        geo.build()
+        pb = geo.params.p_fmm
+        if mode == "learned":
+            p, q = geo.learned_orders(m, eps, margin_qbx=margin_q, margin_fmm=margin_f, q_ref=0, p_ref=P_REF,
+                                      p_bound=pb)
+        else:
+            p, q = pb, q_fixed
+        v = geo.eval("S", g["density"])
+        ms = []
+        for _ in range(3):
+            _, st = geo.eval("S", g["density"], stats=True)
+            ms.append(st.ms_total)
+        results[mode] = (v, min(ms), p, q)
+        geo.close()
+    # the acceleration error (what the FMM order controls, the Theorem of Sec. 4.5)
+    # against unaccelerated QBX of the same order, at sampled targets of every kind
+    o = oracle.Oracle(g, oracle.default_params(g, p_qbx=q_fixed, p_fmm=P_REF))
+    kind, _ = o.association()
+    rng = np.random.default_rng(9)
+    mask = np.zeros(len(kind), np.int32)
+    for k in (0, 1, 2):
+        ids = np.nonzero(kind == k)[0]
+        mask[rng.choice(ids, min(200, len(ids)), replace=False)] = 1
+    sel = mask.astype(bool)
+    ref = o.direct("S", g["density"], target_mask=mask)
+    scale = np.abs(ref[sel]).max()
+    for mode, (v, ms, p, q) in results.items():
+        err = np.abs(v[sel] - ref[sel]).max() / scale
+        print(f"{mode}: p_fmm {p} p_qbx {q} eval {ms:.2f} ms, error vs unaccelerated QBX {err:.2e}")
+        assert err <= eps, mode
+    assert results["learned"][2] < results["bound"][2]
+    assert results["learned"][1] < results["bound"][1]
+
+
+def test_centre_orders_truncate_each_expansion():
+    """Per-centre orders: all centres at q equal the global order q; mixed
+    orders give, at each target, the value of its centre's own order."""
+    torch, pkg = _gpu()
+    g = workloads.small_grid(2, 2, 16, 2000, seed=7, p_qbx=8, p_fmm=15)
+    vals = {}
+    for q in (3, 8):
+        geo = pkg.Geometry(g, pkg.params_default(p_qbx=q, p_fmm=15, n_max=32))
+        geo.build()
+        vals[q] = geo.eval("S", g["density"])
+        nc = geo.nc
+        geo.close()
+    geo = pkg.Geometry(g, pkg.params_default(p_qbx=8, p_fmm=15, n_max=32))
+    geo.build()
+    geo.set_centre_orders(np.full(nc, 3, np.int32))
+    v3 = geo.eval("S", g["density"])
+    assert np.abs(v3 - vals[3]).max() <= 1e-12 * np.abs(vals[3]).max()
+    kind, ctr = geo.association()
+    qs = np.where(np.arange(nc) % 4 == 0, 3, 8).astype(np.int32)
+    geo.set_centre_orders(qs)
+    vm = geo.eval("S", g["density"])
+    one = kind == 1
+    want = np.where(qs[ctr[one]] == 3, vals[3][one], vals[8][one])
+    assert np.abs(vm[one] - want).max() <= 1e-12 * np.abs(want).max()
+    geo.close()
