@@ -313,6 +313,12 @@ gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out);
  * the paper has no counterpart.  Runs about 0.1 s of device work. */
 gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops);
 
+/* Check helper for the FP64 logarithm and reciprocal the direct kernels use
+ * (no counterpart in the paper): y[i] = f(x[i]) on the device, x and y device
+ * arrays of n doubles; fn = 0: the table-driven logarithm, 1: CUDA's log,
+ * 2: the Newton reciprocal, 3: IEEE division 1/x. */
+gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,7 @@ def lib():
             "gq_gmres": (st, [vp, vp, C.c_double, i32, i32, vp, C.POINTER(i32), C.POINTER(C.c_double)]),
             "gq_context_launches": (st, [vp, C.POINTER(C.c_int64)]),
             "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
+            "gq_probe_math": (st, [vp, i32, i32, vp, vp]),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
             "gq_centre_features": (st, [vp, vp]),
             "gq_mlp_create": (st, [vp, C.c_uint64, C.POINTER(vp)]),

@@ -183,6 +183,12 @@ gq_status gq_geometry_create(gq_ctx *ctx, const gq_geometry_desc *d, const gq_pa
 gq_status gq_geometry_destroy(gq_geom *g) {
     if (!g) return GQ_ERR_INVALID;
     cudaStreamSynchronize(g->ctx->stream);
+    if (g->s2) {
+        cudaStreamSynchronize(g->s2);
+        cudaStreamDestroy(g->s2);
+        cudaEventDestroy(g->ev_str);
+        cudaEventDestroy(g->ev_near);
+    }
     gq_tables_release(g);
     delete g;
     return GQ_OK;
@@ -553,6 +559,14 @@ gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out) {
 gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops) {
     if (!ctx || !tflops || (what != 0 && what != 1)) return GQ_ERR_INVALID;
     return guarded(ctx, [&] { *tflops = gq_probe_fma(ctx, what); });
+}
+
+gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y) {
+    if (!ctx || fn < 0 || fn > 3 || n < 0 || (n > 0 && (!x || !y))) return GQ_ERR_INVALID;
+    return guarded(ctx, [&] {
+        GQ_REQUIRE(n == 0 || (is_device_ptr(x) && is_device_ptr(y)), GQ_ERR_INVALID, "gq_probe_math: device arrays");
+        gq_probe_math_impl(ctx, fn, n, x, y);
+    });
 }
 
 gq_status gq_export_qbx(gq_geom *g, double *coeffs) {

@@ -21,11 +21,13 @@
 // M2L is evaluated in that factored form: scale a_k by y^-k, apply the real
 // matrix C(m+k-1,k-1) shared by every pair, scale by (-1)^m y^-m.
 #include <math.h>
+#include <stdlib.h>
 
 #include <map>
 #include <mutex>
 
 #include "gq_internal.cuh"
+#include "gq_math.cuh"
 
 namespace {
 
@@ -54,6 +56,7 @@ struct EvalView {
     const int *lidx[6];
     const double *binom;   // [kBinN][kBinN]
     const int *qc;         // per-centre QBX order (sorted centres) or nullptr: all use Q
+    const double *logt;    // GqLogTable: t[128] then logc[128]
 };
 
 __device__ __forceinline__ double box_rho(const RootInfo &R, int l) { return ldexp(R.H, -l); }
@@ -261,13 +264,13 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
         for (int s = E.src_beg[d]; s < E.src_end[d]; ++s) {
             double2 y = E.s_xy[s], st = E.str[s];
             double2 w = make_double2(y.x - zc.x, y.y - zc.y);
-            double n2 = w.x * w.x + w.y * w.y, inv = 1.0 / n2;
+            double n2 = w.x * w.x + w.y * w.y, inv = gq_rcp(n2);
             double2 winv = make_double2(w.x * inv, -w.y * inv);      // 1/w
             double2 um = lane_powers(cscale(winv, rho), m, 32);      // (rho/w)^m
             if (E.kernel == GQ_D) {
                 acc = cadd(acc, cmul(cmul(st, winv), um));
             } else if (m == 0) {
-                acc.x += st.x * 0.5 * log(n2);
+                acc.x += st.x * 0.5 * gq_log(n2, E.logt, E.logt + 128);
             } else {
                 acc = csub(acc, cscale(um, st.x / m));
             }
@@ -357,6 +360,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                                                                 double2 *__restrict__ Qout) {
     __shared__ NearRanges R;
     __shared__ int wsum[kNearThreads / 32];
+    __shared__ double lt[256];
+    for (int i = threadIdx.x; i < 256; i += kNearThreads) lt[i] = E.logt[i];
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
@@ -386,7 +391,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                     double2 y = E.s_xy[s], st = E.str[s];
                     double wx = y.x - cz.x, wy = y.y - cz.y;
                     double n2 = wx * wx + wy * wy;
-                    double inv = 1.0 / n2;
+                    double inv = gq_rcp(n2);
                     double2 winv = make_double2(wx * inv, -wy * inv);    // 1/w
                     double2 u = make_double2(rc * winv.x, rc * winv.y);   // r/w
                     if (KERNEL == GQ_D) {
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                             acc[m] = cadd(acc[m], t);
                         }
                     } else {
-                        acc[0].x += st.x * (0.5 * log(n2));
+                        acc[0].x += st.x * (0.5 * gq_log(n2, lt, lt + 128));
                         double2 t = make_double2(st.x * u.x, st.x * u.y);
                         acc[1] = cadd(acc[1], t);
 #pragma unroll
@@ -432,6 +437,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
                                                                double *__restrict__ pot) {
     __shared__ NearRanges R;
     __shared__ int wsum[kNearThreads / 32];
+    __shared__ double lt[256];
+    for (int i = threadIdx.x; i < 256; i += kNearThreads) lt[i] = E.logt[i];
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
@@ -458,8 +465,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
                     double wx = y.x - tz.x, wy = y.y - tz.y;
                     double n2 = wx * wx + wy * wy;
                     if (n2 == 0.0) continue;
-                    if (KERNEL == GQ_D) acc += (st.x * wx + st.y * wy) / n2;
-                    else acc += st.x * (0.5 * log(n2));
+                    if (KERNEL == GQ_D) acc += (st.x * wx + st.y * wy) * gq_rcp(n2);
+                    else acc += st.x * (0.5 * gq_log(n2, lt, lt + 128));
                 }
             }
         }
@@ -494,7 +501,7 @@ __global__ void k_w_centres(EvalView E, int nc, const int *__restrict__ ctr_box_
         double rho = box_rho(E.R, l);
         double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
         double2 y = make_double2(cz.x - zd.x, cz.y - zd.y);
-        double n2 = y.x * y.x + y.y * y.y, inv = 1.0 / n2;
+        double n2 = y.x * y.x + y.y * y.y, inv = gq_rcp(n2);
         double2 yinv = make_double2(y.x * inv, -y.y * inv);
         double2 v = cscale(yinv, rho), sv = cscale(yinv, rc);
         const double2 *A = M + (size_t)d * P1;
@@ -510,7 +517,7 @@ __global__ void k_w_centres(EvalView E, int nc, const int *__restrict__ ctr_box_
                 vk = cmul(vk, v);
             }
         }
-        acc[0].x += A0 * 0.5 * log(n2) + sum.x;
+        acc[0].x += A0 * 0.5 * gq_log(n2, E.logt, E.logt + 128) + sum.x;
         acc[0].y += sum.y;
         double2 sm = make_double2(1.0, 0.0);
 #pragma unroll
@@ -556,13 +563,13 @@ __global__ void k_w_points(EvalView E, int npt, const int *__restrict__ pt_owner
         double rho = box_rho(E.R, l);
         double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
         double2 z = make_double2(tz.x - zd.x, tz.y - zd.y);
-        double n2 = z.x * z.x + z.y * z.y, inv = 1.0 / n2;
+        double n2 = z.x * z.x + z.y * z.y, inv = gq_rcp(n2);
         double2 v = make_double2(rho * z.x * inv, -rho * z.y * inv);
         const double2 *A = M + (size_t)d * P1;
         double2 h = A[P];
         for (int k = P - 1; k >= 1; --k) h = cadd(cmul(h, v), A[k]);
         h = cmul(h, v);
-        acc += h.x + A[0].x * 0.5 * log(n2);
+        acc += h.x + A[0].x * 0.5 * gq_log(n2, E.logt, E.logt + 128);
     }
     pot[t] += acc;
 }
@@ -613,13 +620,15 @@ __global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, 
                         const int *__restrict__ ctr_pos, const int *__restrict__ tgt_ptpos,
                         const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on,
                         const double *__restrict__ base_n, const double2 *__restrict__ sc_xy,
-                        const double *__restrict__ sc_r, const double2 *__restrict__ Qc, const double *__restrict__ pot,
+                        const double *__restrict__ sc_r, const double2 *__restrict__ Qc,
+                        const double2 *__restrict__ Qc2, const double *__restrict__ pot, const double *__restrict__ pot2,
                         double *__restrict__ out) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     int k = kind[t];
     if (k == 0) {
-        out[t] = kernel == GQ_SP ? nan("") : -kInv2Pi * pot[tgt_ptpos[t]];
+        int j = tgt_ptpos[t];
+        out[t] = kernel == GQ_SP ? nan("") : -kInv2Pi * (pot[j] + (pot2 ? pot2[j] : 0.0));
         return;
     }
     double2 tz = make_double2(tgt_xy[2 * t], tgt_xy[2 * t + 1]);
@@ -631,17 +640,19 @@ __global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, 
         double r = sc_r[cp];
         double2 zeta = make_double2((tz.x - cz.x) / r, (tz.y - cz.y) / r);
         const double2 *B = Qc + (size_t)cp * (Q + 1);
+        const double2 *B2 = Qc2 ? Qc2 + (size_t)cp * (Q + 1) : nullptr;
         const int q = qcs ? qcs[cp] : Q;
+        auto coef = [&](int m) { return B2 ? cadd(B[m], B2[m]) : B[m]; };
         if (kernel == GQ_SP) {
             int node = tgt_on[t];
             if (node < 0) { sum = nan(""); break; }
-            double2 h = cscale(B[q], (double)q);
-            for (int m = q - 1; m >= 1; --m) h = cadd(cmul(h, zeta), cscale(B[m], (double)m));
+            double2 h = cscale(coef(q), (double)q);
+            for (int m = q - 1; m >= 1; --m) h = cadd(cmul(h, zeta), cscale(coef(m), (double)m));
             double2 n = make_double2(base_n[2 * node], base_n[2 * node + 1]);
             sum += -kInv2Pi * cmul(n, h).x / r;
         } else {
-            double2 h = B[q];
-            for (int m = q - 1; m >= 0; --m) h = cadd(cmul(h, zeta), B[m]);
+            double2 h = coef(q);
+            for (int m = q - 1; m >= 0; --m) h = cadd(cmul(h, zeta), coef(m));
             sum += -kInv2Pi * h.x;
         }
     }
@@ -649,13 +660,15 @@ __global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, 
 }
 
 __global__ void k_export_qbx(int nc, int Q, const int *__restrict__ ctr_perm, const double *__restrict__ sc_r,
-                             const double2 *__restrict__ Qc, double2 *__restrict__ out) {
+                             const double2 *__restrict__ Qc, const double2 *__restrict__ Qc2, double2 *__restrict__ out) {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int c = (int)(t / (Q + 1)), m = (int)(t % (Q + 1));
     if (c >= nc) return;
     double r = sc_r[c], s = 1.0;
     for (int i = 0; i < m; ++i) s /= r;
-    out[(size_t)ctr_perm[c] * (Q + 1) + m] = cscale(Qc[(size_t)c * (Q + 1) + m], s);
+    double2 v = Qc[(size_t)c * (Q + 1) + m];
+    if (Qc2) v = cadd(v, Qc2[(size_t)c * (Q + 1) + m]);
+    out[(size_t)ctr_perm[c] * (Q + 1) + m] = cscale(v, s);
 }
 
 // ------------------------------------------------------------------ mixed precision: FP32 direct sums
@@ -964,6 +977,7 @@ __global__ void k_tgt_ptpos(int npt, const int *__restrict__ pt_perm, int *__res
 
 // ------------------------------------------------------------------ tables (per geometry)
 struct EvalTables {
+    dbuf<double> logt;       // GqLogTable
     dbuf<double> binom;      // [64][64]
     dbuf<double2> dtab;      // [121][32] delta^-k
     dbuf<double> logtab;     // [121] log|delta|
@@ -1005,6 +1019,10 @@ static void make_tables(gq_geom *g, EvalTables &T) {
         }
     }
     cudaStream_t st = g->ctx->stream;
+    GqLogTable LT;
+    gq_log_table_host(&LT);
+    T.logt.alloc(256);
+    GQ_CUDA(cudaMemcpyAsync(T.logt.p, &LT, sizeof(LT), cudaMemcpyHostToDevice, st));
     T.binom.alloc(bn.size());
     T.dtab.alloc(dt.size());
     T.logtab.alloc(lt.size());
@@ -1058,69 +1076,46 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
     E.binom = T.binom;
     E.qc = g->has_qc ? (const int *)g->q_ctr.p : nullptr;
+    E.logt = T.logt;
 
     g->strength.alloc(g->nsrc);
     E.str = g->strength;
     g->M.alloc((size_t)g->nbox * P1);
     g->L.alloc((size_t)g->nbox * P1);
-    g->Q.alloc((size_t)g->nc * Q1);
+    g->Q.alloc((size_t)g->nc * Q1);    // List 3 far + box-local part of the QBX coefficients
+    g->Qn.alloc((size_t)g->nc * Q1);   // direct part
     g->pot.alloc(g->npt);
+    g->potn.alloc(g->npt);
+    if (!g->s2) {
+        GQ_CUDA(cudaStreamCreateWithFlags(&g->s2, cudaStreamNonBlocking));
+        GQ_CUDA(cudaEventCreateWithFlags(&g->ev_str, cudaEventDisableTiming));
+        GQ_CUDA(cudaEventCreateWithFlags(&g->ev_near, cudaEventDisableTiming));
+    }
+    // The direct part may run on a second stream, concurrently with the FMM passes
+    // (GQ_OVERLAP=1); by default both run in order on the context's stream: the
+    // direct kernels alone keep the FP64 pipe busy, so concurrency gains nothing.
+    static const bool overlap = getenv("GQ_OVERLAP") && getenv("GQ_OVERLAP")[0] == '1';
+    cudaStream_t s2 = overlap ? g->s2 : st;
+    gq_ctx ctx2 = *ctx;   // launches of the direct part
+    ctx2.stream = s2;
+    ctx2.launches = 0;
 
-    // stage events (recorded only when statistics are requested)
-    const int kStages = 11;
-    cudaEvent_t ev[kStages + 1];
+    // stage events (only when statistics are requested); the direct stages run on
+    // the second stream, concurrently with the FMM passes
+    enum { S0, S_STR, S_FMM, S_M2M, S_M2L, S_P2L, S_L2L, S_WC, S_WP, S_L2Q, S_END, N_BEG, N_CTR, N_PT, NEV };
+    cudaEvent_t ev[NEV];
     bool timed = stt != nullptr;
     if (timed)
-        for (int i = 0; i <= kStages; ++i) GQ_CUDA(cudaEventCreate(&ev[i]));
-    auto mark = [&](int i) {
-        if (timed) GQ_CUDA(cudaEventRecord(ev[i], st));
+        for (int i = 0; i < NEV; ++i) GQ_CUDA(cudaEventCreate(&ev[i]));
+    auto mark = [&](int i, cudaStream_t on) {
+        if (timed) GQ_CUDA(cudaEventRecord(ev[i], on));
     };
-    mark(0);
+    mark(S0, st);
     int64_t l0 = ctx->launches;
 
     // A1
     GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
               (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, g->strength.p);
-    GQ_CUDA(cudaMemsetAsync(g->M.p, 0, sizeof(double2) * g->nbox * P1, st));
-    GQ_CUDA(cudaMemsetAsync(g->L.p, 0, sizeof(double2) * g->nbox * P1, st));
-    mark(1);
-    // Stage 2
-    if (g->n_leaf_src) {
-        auto k8 = k_p2m<8>;
-        auto k16 = k_p2m<16>;
-        auto k32 = k_p2m<GQ_MAX_PFMM>;
-        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * 32, 128), 128, 0,
-                  E, g->n_leaf_src, (const int *)g->leaf_src_boxes, g->M.p);
-    }
-    for (int l = g->nlev - 2; l >= 0; --l) {
-        int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_m2m, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->M.p);
-    }
-    mark(2);
-    // Stage 4
-    if (g->n_far_boxes) {
-        size_t sm = sizeof(double) * P1 * P1;
-        auto k16 = k_m2l<16>;
-        auto k32 = k_m2l<32>;
-        int G = P1 <= 16 ? 16 : 32;
-        GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E,
-                  g->n_far_boxes, (const int *)g->far_boxes, (const double2 *)g->M, (const double2 *)T.dtab,
-                  (const double *)T.logtab, g->L.p);
-    }
-    mark(3);
-    if (g->n_far_boxes) {
-        // Stage 6b
-        GQ_LAUNCH(ctx, k_p2l, gq_blocks((long long)g->n_far_boxes * 32, 128), 128, 0, E, g->n_far_boxes,
-                  (const int *)g->far_boxes, g->L.p);
-    }
-    mark(4);
-    // Stage 7
-    for (int l = 1; l < g->nlev; ++l) {
-        int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_l2l, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->L.p);
-    }
-    // Stages 3, 5a, 6a (near field)
-    GQ_CUDA(cudaMemsetAsync(g->Q.p, 0, sizeof(double2) * g->nc * Q1, st));
     const bool f32 = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-6;
     MixedView X{};
     if (f32) {
@@ -1144,30 +1139,80 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         g->M_f.alloc((size_t)g->nbox * P1);
         if (g->nsrc) GQ_LAUNCH(ctx, k_to_float2, gq_blocks(g->nsrc, 256), 256, 0, (long long)g->nsrc,
                                (const double2 *)g->strength, g->str_f.p);
-        GQ_LAUNCH(ctx, k_to_float2, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
-                  (const double2 *)g->M, g->M_f.p);
         X.s_rel = g->s_rel; X.str = g->str_f; X.c_rel = g->c_rel; X.p_rel = g->p_rel; X.M = g->M_f; X.c_r = g->c_rf;
     }
-    mark(5);
+    mark(S_STR, st);
+    GQ_CUDA(cudaEventRecord(g->ev_str, st));
+
+    // ---- Stages 3, 5a, 6a (direct interactions) on the second stream
+    GQ_CUDA(cudaStreamWaitEvent(s2, g->ev_str, 0));
+    mark(N_BEG, s2);
     if (g->n_ctr_boxes) {
-        if (f32) dispatch_near_centres_f32(ctx, E, X, g->n_ctr_boxes, g->ctr_boxes, g->Q.p);
-        else dispatch_near_centres(ctx, E, g->n_ctr_boxes, g->ctr_boxes, g->Q.p);
+        if (f32) dispatch_near_centres_f32(&ctx2, E, X, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
+        else dispatch_near_centres(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
     }
-    mark(6);
+    mark(N_CTR, s2);
     if (g->n_pt_boxes) {
         if (f32) {
             auto kd = k_near_points_f32<GQ_D>;
             auto ks = k_near_points_f32<GQ_S>;
-            GQ_LAUNCH(ctx, (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, X, g->n_pt_boxes,
-                      (const int *)g->pt_boxes, g->pot.p);
+            GQ_LAUNCH((&ctx2), (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, X, g->n_pt_boxes,
+                      (const int *)g->pt_boxes, g->potn.p);
         } else {
             auto kd = k_near_points<GQ_D>;
             auto ks = k_near_points<GQ_S>;
-            GQ_LAUNCH(ctx, (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, g->n_pt_boxes,
-                      (const int *)g->pt_boxes, g->pot.p);
+            GQ_LAUNCH((&ctx2), (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, g->n_pt_boxes,
+                      (const int *)g->pt_boxes, g->potn.p);
         }
     }
-    mark(7);
+    mark(N_PT, s2);
+    GQ_CUDA(cudaEventRecord(g->ev_near, s2));
+
+    // ---- FMM passes on the context's stream
+    mark(S_FMM, st);
+    GQ_CUDA(cudaMemsetAsync(g->M.p, 0, sizeof(double2) * g->nbox * P1, st));
+    GQ_CUDA(cudaMemsetAsync(g->L.p, 0, sizeof(double2) * g->nbox * P1, st));
+    GQ_CUDA(cudaMemsetAsync(g->Q.p, 0, sizeof(double2) * g->nc * Q1, st));
+    if (g->npt) GQ_CUDA(cudaMemsetAsync(g->pot.p, 0, sizeof(double) * g->npt, st));
+    // Stage 2
+    if (g->n_leaf_src) {
+        auto k8 = k_p2m<8>;
+        auto k16 = k_p2m<16>;
+        auto k32 = k_p2m<GQ_MAX_PFMM>;
+        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * 32, 128), 128, 0,
+                  E, g->n_leaf_src, (const int *)g->leaf_src_boxes, g->M.p);
+    }
+    for (int l = g->nlev - 2; l >= 0; --l) {
+        int s = g->level_start_h[l], e = g->level_start_h[l + 1];
+        GQ_LAUNCH(ctx, k_m2m, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->M.p);
+    }
+    mark(S_M2M, st);
+    // Stage 4
+    if (g->n_far_boxes) {
+        size_t sm = sizeof(double) * P1 * P1;
+        auto k16 = k_m2l<16>;
+        auto k32 = k_m2l<32>;
+        int G = P1 <= 16 ? 16 : 32;
+        GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E,
+                  g->n_far_boxes, (const int *)g->far_boxes, (const double2 *)g->M, (const double2 *)T.dtab,
+                  (const double *)T.logtab, g->L.p);
+    }
+    mark(S_M2L, st);
+    if (g->n_far_boxes) {
+        // Stage 6b
+        GQ_LAUNCH(ctx, k_p2l, gq_blocks((long long)g->n_far_boxes * 32, 128), 128, 0, E, g->n_far_boxes,
+                  (const int *)g->far_boxes, g->L.p);
+    }
+    mark(S_P2L, st);
+    // Stage 7
+    for (int l = 1; l < g->nlev; ++l) {
+        int s = g->level_start_h[l], e = g->level_start_h[l + 1];
+        GQ_LAUNCH(ctx, k_l2l, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->L.p);
+    }
+    if (f32)
+        GQ_LAUNCH(ctx, k_to_float2, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
+                  (const double2 *)g->M, g->M_f.p);
+    mark(S_L2L, st);
     // Stage 5b
     if (g->nc) {
         auto k8 = k_w_centres<8>;
@@ -1176,7 +1221,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks(g->nc, 128), 128, 0, E, g->nc,
                   (const int *)g->ctr_owner, (const double2 *)g->M, g->Q.p);
     }
-    mark(8);
+    mark(S_WC, st);
     if (g->npt) {
         if (f32)
             GQ_LAUNCH(ctx, k_w_points_f32, gq_blocks(g->npt, 128), 128, 0, E, X, g->npt, (const int *)g->pt_owner,
@@ -1185,7 +1230,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
             GQ_LAUNCH(ctx, k_w_points, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,
                       (const double2 *)g->M, g->pot.p);
     }
-    mark(9);
+    mark(S_WP, st);
     // Stage 8
     if (g->nc)
         GQ_LAUNCH(ctx, k_l2qbxl, gq_blocks((long long)g->nc * Q1, 128), 128, 0, E, g->nc, (const int *)g->ctr_owner,
@@ -1193,24 +1238,38 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     if (g->npt)
         GQ_LAUNCH(ctx, k_l2p, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner, (const double2 *)g->L,
                   g->pot.p);
-    mark(10);
+    mark(S_L2Q, st);
+    // join the direct part, then evaluate at the targets
+    GQ_CUDA(cudaStreamWaitEvent(st, g->ev_near, 0));
     if (g->nt)
         GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, E.qc, (const int *)g->t_kind,
                   (const int *)g->t_ctr, (const int *)g->ctr_pos, (const int *)T.tgt_ptpos, (const double *)g->tgt_xy,
                   (const int *)g->tgt_on, (const double *)g->base_n, (const double2 *)g->sc_xy,
-                  (const double *)g->sc_r, (const double2 *)g->Q, (const double *)g->pot, out_dev);
-    mark(kStages);
+                  (const double *)g->sc_r, (const double2 *)g->Q, (const double2 *)g->Qn, (const double *)g->pot,
+                  (const double *)g->potn, out_dev);
+    mark(S_END, st);
+    ctx->launches += ctx2.launches;
     if (timed) {
-        GQ_CUDA(cudaEventSynchronize(ev[kStages]));
-        float ms = 0;
-        GQ_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[kStages]));
-        stt->ms_total = ms;
-        for (int i = 0; i < kStages; ++i) {
-            GQ_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-            stt->ms_stage[i] = ms;
-        }
+        GQ_CUDA(cudaEventSynchronize(ev[S_END]));
+        auto el = [&](int a, int b2) {
+            float ms = 0;
+            GQ_CUDA(cudaEventElapsedTime(&ms, ev[a], ev[b2]));
+            return (double)ms;
+        };
+        stt->ms_total = el(S0, S_END);
+        stt->ms_stage[0] = el(S0, S_STR);
+        stt->ms_stage[1] = el(S_FMM, S_M2M);
+        stt->ms_stage[2] = el(S_M2M, S_M2L);
+        stt->ms_stage[3] = el(S_M2L, S_P2L);
+        stt->ms_stage[4] = el(S_P2L, S_L2L);
+        stt->ms_stage[5] = el(N_BEG, N_CTR);
+        stt->ms_stage[6] = el(N_CTR, N_PT);
+        stt->ms_stage[7] = el(S_L2L, S_WC);
+        stt->ms_stage[8] = el(S_WC, S_WP);
+        stt->ms_stage[9] = el(S_WP, S_L2Q);
+        stt->ms_stage[10] = el(S_L2Q, S_END);
         stt->kernel_launches = ctx->launches - l0;
-        for (int i = 0; i <= kStages; ++i) cudaEventDestroy(ev[i]);
+        for (int i = 0; i < NEV; ++i) cudaEventDestroy(ev[i]);
     }
     g->have_eval = true;
     g->last_kernel = kernel;
@@ -1221,7 +1280,7 @@ void gq_export_qbx_impl(gq_geom *g, double *host) {
     dbuf<double2> tmp;
     tmp.alloc((size_t)g->nc * Q1);
     GQ_LAUNCH(g->ctx, k_export_qbx, gq_blocks((long long)g->nc * Q1, 256), 256, 0, g->nc, g->prm.p_qbx,
-              (const int *)g->ctr_perm, (const double *)g->sc_r, (const double2 *)g->Q, tmp.p);
+              (const int *)g->ctr_perm, (const double *)g->sc_r, (const double2 *)g->Q, (const double2 *)g->Qn, tmp.p);
     GQ_CUDA(cudaMemcpyAsync(host, tmp.p, sizeof(double2) * g->nc * Q1, cudaMemcpyDeviceToHost, g->ctx->stream));
     GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
 }
@@ -1287,6 +1346,9 @@ NoAllocDevice &noalloc_setup(int dev) {
     GQ_CUDA(cudaMemcpy(base, bn.data(), sizeof(double) * bn.size(), cudaMemcpyHostToDevice));
     GQ_CUDA(cudaMemcpy(base + 32768, dt.data(), sizeof(double2) * dt.size(), cudaMemcpyHostToDevice));
     GQ_CUDA(cudaMemcpy(base + 32768 + 65536, lt.data(), sizeof(double) * lt.size(), cudaMemcpyHostToDevice));
+    GqLogTable LT;
+    gq_log_table_host(&LT);
+    GQ_CUDA(cudaMemcpy(base + 32768 + 65536 + 1024, &LT, sizeof(LT), cudaMemcpyHostToDevice));
     std::vector<double> pc((GQ_MAX_PQBX + 1) * 33, 0.0);
     for (int m = 0; m <= GQ_MAX_PQBX; ++m)
         for (int k = 1; k <= 32; ++k) pc[m * 33 + k] = bn[(m + k - 1) * kBinN + (k - 1)];
@@ -1343,6 +1405,7 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
     for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
     E.binom = binom;
     E.qc = g->has_qc ? (const int *)g->q_ctr.p : nullptr;
+    E.logt = (const double *)(D.base + 32768 + 65536 + 1024);
 
     // the array keeps the previous call's contents: clear the accumulators
     GQ_CUDA(cudaMemsetAsync(M, 0, sizeof(double2) * g->nbox * P1, st));
@@ -1402,5 +1465,6 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
         GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, E.qc, (const int *)g->t_kind,
                   (const int *)g->t_ctr, (const int *)g->ctr_pos, (const int *)ptpos, (const double *)g->tgt_xy,
                   (const int *)g->tgt_on, (const double *)g->base_n, (const double2 *)g->sc_xy,
-                  (const double *)g->sc_r, (const double2 *)Qc, (const double *)pot, out_dev);
+                  (const double *)g->sc_r, (const double2 *)Qc, (const double2 *)nullptr, (const double *)pot,
+                  (const double *)nullptr, out_dev);
 }

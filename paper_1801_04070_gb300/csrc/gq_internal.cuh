@@ -132,8 +132,12 @@ struct gq_geom {
     // evaluation buffers
     dbuf<double2> strength;          // sorted sources: S -> (q, 0), D -> d
     dbuf<double2> M, L;              // [nbox][p_fmm+1] box-scaled expansions
-    dbuf<double2> Q;                 // [nc][p_qbx+1] r-scaled QBX coefficients (sorted centres)
-    dbuf<double> pot;                // sorted point targets: Re Phi
+    dbuf<double2> Q;                 // [nc][p_qbx+1] r-scaled QBX coefficients (sorted centres): far part
+    dbuf<double2> Qn;                // the same, direct part
+    dbuf<double> pot;                // sorted point targets: Re Phi, far part
+    dbuf<double> potn;               // the same, direct part
+    cudaStream_t s2 = nullptr;       // second stream for the direct part of an evaluation
+    cudaEvent_t ev_str = nullptr, ev_near = nullptr;
     dbuf<double> out_dev;            // [nt] staging for host outputs
     dbuf<double> dens_dev;           // [nbase] staging for host inputs
     int last_kernel = -1;
@@ -172,6 +176,7 @@ void gq_build_lists(gq_geom *g);               // gq_lists.cu
 void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *st);  // gq_fmm.cu
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
+void gq_probe_math_impl(gq_ctx *ctx, int fn, int n, const double *x_dev, double *y_dev);
 void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double *out_dev);  // gq_fmm.cu
 struct gq_mlp;
 int gq_mlp_param_count();                                                                   // gq_learned.cu

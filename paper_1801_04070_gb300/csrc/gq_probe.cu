@@ -1,6 +1,7 @@
 // gq_probe.cu -- FMA-throughput probe used as the measured FP64 / FP32 peak
 // of the ALU roofline (the measured peaks cover HBM and BF16 only).
 #include "gq_internal.cuh"
+#include "gq_math.cuh"
 
 namespace {
 
@@ -54,3 +55,24 @@ double run(gq_ctx *ctx) {
 }  // namespace
 
 double gq_probe_fma(gq_ctx *ctx, int what) { return what == 0 ? run<double>(ctx) : run<float>(ctx); }
+
+namespace {
+__global__ void k_probe_math(int fn, int n, const double *__restrict__ x, const double *__restrict__ tab,
+                             double *__restrict__ y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = x[i];
+    y[i] = fn == 0 ? gq_log(v, tab, tab + 128) : fn == 1 ? log(v) : fn == 2 ? gq_rcp(v) : 1.0 / v;
+}
+}  // namespace
+
+void gq_probe_math_impl(gq_ctx *ctx, int fn, int n, const double *x_dev, double *y_dev) {
+    GqLogTable T;
+    gq_log_table_host(&T);
+    dbuf<double> tab;
+    tab.alloc(256);
+    GQ_CUDA(cudaMemcpyAsync(tab.p, &T, sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    if (n > 0) GQ_LAUNCH(ctx, k_probe_math, gq_blocks(n, 256), 256, 0, fn, n, x_dev, (const double *)tab.p, y_dev);
+    GQ_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+

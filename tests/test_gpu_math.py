@@ -1,0 +1,45 @@
+"""The FP64 logarithm (Tang's table-driven method) and reciprocal (FP32 seed +
+two Newton steps) used by the direct-interaction kernels, checked against
+CUDA's log and IEEE division over the ranges the kernels meet and beyond."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(fn, x):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_04070_gb300 as pkg
+    import workloads
+    geo = pkg.Geometry(workloads.starfish_c1())
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(xd)
+    assert pkg.lib().gq_probe_math(geo._ctx, fn, len(x), xd.data_ptr(), yd.data_ptr()) == 0
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+def _inputs():
+    rng = np.random.default_rng(0)
+    return np.concatenate([10.0 ** rng.uniform(-12, 12, 200000), 1.0 + rng.uniform(-1e-3, 1e-3, 20000),
+                           np.array([1.0, 2.0, 0.5, 1e-300, 1e300, 0.0, np.inf, 7.0 / 3.0])])
+
+
+def test_log_matches_cuda_log():
+    x = _inputs()
+    mine, ref = _run(0, x), _run(1, x)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(mine), fin)
+    err = np.abs(mine[fin] - ref[fin])
+    # absolute error within a few ulp of max(|log x|, 1), i.e. of the terms it multiplies
+    assert (err <= 4 * np.spacing(np.maximum(np.abs(ref[fin]), 1.0))).all(), err.max()
+
+
+def test_reciprocal_matches_division():
+    x = _inputs()
+    x = x[(x > 0) & np.isfinite(x)]
+    x = np.concatenate([x, -x])
+    mine, ref = _run(2, x), _run(3, x)
+    assert (np.abs(mine - ref) <= 2 * np.spacing(np.abs(ref))).all()
