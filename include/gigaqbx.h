@@ -313,6 +313,12 @@ gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out);
  * the paper has no counterpart.  Runs about 0.1 s of device work. */
 gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops);
 
+/* Device memory the library keeps cached for reuse (bytes), and a call that
+ * returns all of it to the driver (call when no library work is in flight).
+ * Buffers of live geometries are not affected. */
+gq_status gq_memory_cached(int64_t *bytes);
+gq_status gq_memory_release(void);
+
 /* Check helper for the FP64 logarithm and reciprocal the direct kernels use
  * (no counterpart in the paper): y[i] = f(x[i]) on the device, x and y device
  * arrays of n doubles; fn = 0: the table-driven logarithm, 1: CUDA's log,

@@ -81,6 +81,8 @@ def lib():
             "gq_context_launches": (st, [vp, C.POINTER(C.c_int64)]),
             "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
             "gq_probe_math": (st, [vp, i32, i32, vp, vp]),
+            "gq_memory_cached": (st, [C.POINTER(C.c_int64)]),
+            "gq_memory_release": (st, []),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
             "gq_centre_features": (st, [vp, vp]),
             "gq_mlp_create": (st, [vp, C.c_uint64, C.POINTER(vp)]),

@@ -561,6 +561,17 @@ gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops) {
     return guarded(ctx, [&] { *tflops = gq_probe_fma(ctx, what); });
 }
 
+gq_status gq_memory_cached(int64_t *bytes) {
+    if (!bytes) return GQ_ERR_INVALID;
+    *bytes = (int64_t)gq_dev_cached_bytes();
+    return GQ_OK;
+}
+
+gq_status gq_memory_release(void) {
+    gq_dev_release_cache();
+    return GQ_OK;
+}
+
 gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y) {
     if (!ctx || fn < 0 || fn > 3 || n < 0 || (n > 0 && (!x || !y))) return GQ_ERR_INVALID;
     return guarded(ctx, [&] {

@@ -31,34 +31,48 @@ struct gq_error {
         if (!(cond)) throw gq_error{code, text}; \
     } while (0)
 
-// ------------------------------------------------------------------ device buffers
+// ------------------------------------------------------------------ device memory
+// Caching allocator (gq_alloc.cu): blocks come in power-of-two size classes per
+// device; a released block goes back to its class's free list instead of to
+// cudaFree, so steady-state builds and evaluations allocate nothing from the
+// driver and never hit cudaFree's implicit device synchronisation.  On an
+// allocation failure the device's cached blocks are freed and the call retried.
+// A block released while kernels still read it may be handed out again: every
+// user in this library releases only after the last use on the same stream or
+// after synchronising with it.
+void *gq_dev_alloc(size_t bytes, size_t *cap, int *device);
+void gq_dev_free(void *p, size_t cap, int device);
+size_t gq_dev_cached_bytes();
+void gq_dev_release_cache();
+
 template <class T>
 struct dbuf {
     T *p = nullptr;
     size_t n = 0;
+    size_t cap = 0;
+    int dev = 0;
     dbuf() = default;
     dbuf(const dbuf &) = delete;
     dbuf &operator=(const dbuf &) = delete;
     ~dbuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) gq_dev_free(p, cap, dev);
         p = nullptr;
         n = 0;
+        cap = 0;
     }
     void alloc(size_t count) {
         if (count <= n && p) return;
         release();
         size_t bytes = (count ? count : 1) * sizeof(T);
-        cudaError_t e = cudaMalloc((void **)&p, bytes);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            throw gq_error{GQ_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
-        }
+        p = (T *)gq_dev_alloc(bytes, &cap, &dev);
         n = count;
     }
     void swap(dbuf &o) {
         T *tp = p; p = o.p; o.p = tp;
         size_t tn = n; n = o.n; o.n = tn;
+        size_t tc = cap; cap = o.cap; o.cap = tc;
+        int td = dev; dev = o.dev; o.dev = td;
     }
     operator T *() const { return p; }
 };
