@@ -929,6 +929,147 @@ __global__ void k_w_points_f32(EvalView E, MixedView X, int npt, const int *__re
     pot[t] += (double)acc;
 }
 
+// ------------------------------------------------------------------ split precision: double-FP32 pairs
+// A value is an unevaluated sum hi + lo of two FP32 numbers (about 48
+// significant bits).  Sums use Knuth's two-sum, products Dekker's two-product
+// with a fused multiply-add (T. J. Dekker, "A floating-point technique for
+// extending the available precision", Numer. Math. 18, 1971); the low parts are
+// renormalised after every operation.
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl dfl_from(double x) {
+    float h = __double2float_rn(x);
+    return dfl{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ dfl dfl_fast(float a, float b) {   // |a| >= |b|
+    float s = a + b;
+    return dfl{s, b - (s - a)};
+}
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+    float s = a.hi + b.hi;
+    float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    return dfl_fast(s, e);
+}
+__device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, dfl{-b.hi, -b.lo}); }
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return dfl_fast(p, e);
+}
+struct dflc {
+    dfl re, im;
+};
+__device__ __forceinline__ dflc dflc_mul(dflc a, dflc b) {
+    return dflc{dfl_sub(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)), dfl_add(dfl_mul(a.re, b.im), dfl_mul(a.im, b.re))};
+}
+__device__ __forceinline__ dflc dflc_add(dflc a, dflc b) { return dflc{dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
+
+// Direct interactions to centres with the per-pair geometry (difference,
+// reciprocal, logarithm, r/w) in FP64 and the power recurrence and per-lane
+// sums of the coefficients in double-FP32 pairs; lanes are summed in FP64.
+template <int QQ, int KERNEL>
+__global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E, int nwork, const int *__restrict__ work,
+                                                                      double2 *__restrict__ Qout) {
+    __shared__ NearRanges R;
+    __shared__ int wsum[kNearThreads / 32];
+    __shared__ double lt[256];
+    for (int i = threadIdx.x; i < 256; i += kNearThreads) lt[i] = E.logt[i];
+    int b = work[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
+    int cb = E.ctr_beg[b], ce = E.ctr_end[b];
+    bool single = ne <= kNearRanges;
+    if (single) load_ranges(E, b, 0, ne, R, wsum);
+    for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
+        int c = c0 + w;
+        bool valid = c < ce;
+        double2 cz = valid ? E.sc_xy[c] : make_double2(0.0, 0.0);
+        double rc = valid ? E.sc_r[c] : 1.0;
+        const int qc = (valid && E.qc) ? E.qc[c] : QQ;
+        double acc0 = 0.0;              // S constant term (FP64)
+        dflc acc[QQ + 1];
+#pragma unroll
+        for (int m = 0; m <= QQ; ++m) acc[m] = dflc{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+        for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
+            if (!single) {
+                __syncthreads();
+                load_ranges(E, b, e0, ne, R, wsum);
+            }
+            int T = R.pre[R.n];
+            if (valid) {
+                int r = 0;
+                for (int v = lane; v < T; v += 32) {
+                    while (R.pre[r + 1] <= v) ++r;
+                    int s = R.beg[r] + (v - R.pre[r]);
+                    double2 y = E.s_xy[s], st = E.str[s];
+                    double wx = y.x - cz.x, wy = y.y - cz.y;
+                    double n2 = wx * wx + wy * wy;
+                    double inv = gq_rcp(n2);
+                    double2 winv = make_double2(wx * inv, -wy * inv);
+                    dflc u{dfl_from(rc * winv.x), dfl_from(rc * winv.y)};
+                    dflc t;
+                    int m0;
+                    if (KERNEL == GQ_D) {
+                        double2 t0 = cmul(st, winv);
+                        t = dflc{dfl_from(t0.x), dfl_from(t0.y)};
+                        acc[0] = dflc_add(acc[0], t);
+                        m0 = 1;
+                    } else {
+                        acc0 += st.x * (0.5 * gq_log(n2, lt, lt + 128));
+                        t = dflc{dfl_from(st.x * (rc * winv.x)), dfl_from(st.x * (rc * winv.y))};
+                        acc[1] = dflc_add(acc[1], t);
+                        m0 = 2;
+                    }
+#pragma unroll
+                    for (int m = 1; m <= QQ; ++m) {
+                        if (m < m0) continue;
+                        if (m > qc) break;
+                        t = dflc_mul(t, u);
+                        acc[m] = dflc_add(acc[m], t);
+                    }
+                }
+            }
+        }
+        double2 dacc[QQ + 1];
+#pragma unroll
+        for (int m = 0; m <= QQ; ++m) {
+            dacc[m] = make_double2((double)acc[m].re.hi + (double)acc[m].re.lo, (double)acc[m].im.hi + (double)acc[m].im.lo);
+            if (m == 0 && KERNEL != GQ_D) dacc[0] = make_double2(acc0, 0.0);
+            for (int o = 16; o > 0; o >>= 1) dacc[m] = cadd(dacc[m], shfl2_xor(dacc[m], o));
+        }
+        if (valid && lane <= QQ) {
+            double2 vv = dacc[0];
+#pragma unroll
+            for (int m = 1; m <= QQ; ++m)
+                if (lane == m) vv = dacc[m];
+            if (KERNEL != GQ_D && lane >= 1) vv = cscale(vv, -1.0 / lane);
+            Qout[(size_t)c * (QQ + 1) + lane] = vv;
+        }
+    }
+}
+
+template <int QQ>
+void launch_near_centres_split(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, double2 *Q) {
+    auto kd = k_near_centres_split<QQ, GQ_D>;
+    auto ks = k_near_centres_split<QQ, GQ_S>;
+    GQ_LAUNCH(ctx, (E.kernel == GQ_D ? kd : ks), nwork, kNearThreads, 0, E, nwork, work, Q);
+}
+
+void dispatch_near_centres_split(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, double2 *Q) {
+    switch (E.Q) {
+#define GQ_CASE(v) case v: launch_near_centres_split<v>(ctx, E, nwork, work, Q); break;
+        GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
+        GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
+#undef GQ_CASE
+        default: throw gq_error{GQ_ERR_INVALID, "p_qbx out of range"};
+    }
+}
+
 template <int QQ>
 void launch_near_centres_f32(gq_ctx *ctx, const EvalView &E, const MixedView &X, int nwork, const int *work,
                              double2 *Q) {
@@ -1117,6 +1258,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
               (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, g->strength.p);
     const bool f32 = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-6;
+    const bool split = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-10 && g->prm.eps < 1e-6;
     MixedView X{};
     if (f32) {
         if (!g->mixed_ready) {
@@ -1149,6 +1291,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     mark(N_BEG, s2);
     if (g->n_ctr_boxes) {
         if (f32) dispatch_near_centres_f32(&ctx2, E, X, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
+        else if (split) dispatch_near_centres_split(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
         else dispatch_near_centres(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
     }
     mark(N_CTR, s2);
