@@ -467,15 +467,17 @@ def run_gpu(args, rank, world, local):
                 sst = Stats()
                 for _ in range(2):
                     chk(L.gq_eval(sg, kern, d_mu.data_ptr(), d_out.data_ptr(), C.byref(sst)))
-                ms = []
+                ms, sms = [], np.zeros(11)
                 for _ in range(3):
                     flush.zero_()
                     chk(L.gq_eval(sg, kern, d_mu.data_ptr(), d_out.data_ptr(), C.byref(sst)))
                     ms.append(sst.ms_total)
+                    sms += np.array(sst.ms_stage[:11]) / 3
                 rp = params_default()
                 chk(L.gq_geometry_params(sg, C.byref(rp)))
                 row["p_qbx"], row["p_fmm"] = rp.p_qbx, rp.p_fmm
                 row[name + "_eval_targets_per_s"] = nt / (statistics.mean(ms) * 1e-3)
+                row[name + "_stage_ms"] = {STAGE_NAMES[i]: round(float(sms[i]), 3) for i in range(11)}
                 out = d_out.clone()
                 if ref is None:
                     ref = out

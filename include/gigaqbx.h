@@ -322,7 +322,9 @@ gq_status gq_memory_release(void);
 /* Check helper for the FP64 logarithm and reciprocal the direct kernels use
  * (no counterpart in the paper): y[i] = f(x[i]) on the device, x and y device
  * arrays of n doubles; fn = 0: the table-driven logarithm, 1: CUDA's log,
- * 2: the Newton reciprocal, 3: IEEE division 1/x. */
+ * 2: the Newton reciprocal, 3: IEEE division 1/x, 4: the double-FP32
+ * logarithm of the split-precision kernels (x rounded to an FP32 pair,
+ * x in [2^-126, 2^126]), 5: the double-FP32 reciprocal (same range). */
 gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y);
 
 #ifdef __cplusplus

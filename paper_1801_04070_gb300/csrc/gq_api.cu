@@ -227,6 +227,7 @@ gq_status gq_build(gq_geom *g) {
         GQ_CUDA(cudaSetDevice(g->ctx->device));
         gq_tables_release(g);
         g->mixed_ready = false;
+        g->split_ready = false;
         gq_form_centres(g);
         gq_build_all(g);
         GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
@@ -573,7 +574,7 @@ gq_status gq_memory_release(void) {
 }
 
 gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y) {
-    if (!ctx || fn < 0 || fn > 3 || n < 0 || (n > 0 && (!x || !y))) return GQ_ERR_INVALID;
+    if (!ctx || fn < 0 || fn > 5 || n < 0 || (n > 0 && (!x || !y))) return GQ_ERR_INVALID;
     return guarded(ctx, [&] {
         GQ_REQUIRE(n == 0 || (is_device_ptr(x) && is_device_ptr(y)), GQ_ERR_INVALID, "gq_probe_math: device arrays");
         gq_probe_math_impl(ctx, fn, n, x, y);

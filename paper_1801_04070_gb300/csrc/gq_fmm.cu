@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "gq_internal.cuh"
+#include "gq_dfl.cuh"
 #include "gq_math.cuh"
 
 namespace {
@@ -930,107 +931,186 @@ __global__ void k_w_points_f32(EvalView E, MixedView X, int npt, const int *__re
 }
 
 // ------------------------------------------------------------------ split precision: double-FP32 pairs
-// A value is an unevaluated sum hi + lo of two FP32 numbers (about 48
-// significant bits).  Sums use Knuth's two-sum, products Dekker's two-product
-// with a fused multiply-add (T. J. Dekker, "A floating-point technique for
-// extending the available precision", Numer. Math. 18, 1971); the low parts are
-// renormalised after every operation.
-struct dfl {
-    float hi, lo;
+// Coordinates, radii and strengths as FP32 pairs (gq_dfl.cuh), relative to box
+// centres as in the FP32 tier: a source relative to its leaf centre, a centre
+// relative to its own box centre; the offset between two box centres is a
+// short dyadic number, exact in FP32.  Per centre, (r.hi, r.lo, 1/r^2 hi, lo).
+struct SplitView {
+    const float4 *s_rel, *str, *c_rel, *c_r, *p_rel;
+    const float4 *M;     // multipoles, (re.hi, re.lo, im.hi, im.lo) per coefficient
+    const float4 *lvl;   // per level l: [2l] = (rho, 1/rho), [2l+1] = (log rho, 1/rho^2)
+    const float *logt;   // GqDflLogTable
+    float H;             // root half-width (a power of two)
 };
-__device__ __forceinline__ dfl dfl_from(double x) {
-    float h = __double2float_rn(x);
-    return dfl{h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ dfl dfl_fast(float a, float b) {   // |a| >= |b|
-    float s = a + b;
-    return dfl{s, b - (s - a)};
-}
-__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
-    float s = a.hi + b.hi;
-    float bb = s - a.hi;
-    float e = (a.hi - (s - bb)) + (b.hi - bb);
-    e += a.lo + b.lo;
-    return dfl_fast(s, e);
-}
-__device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, dfl{-b.hi, -b.lo}); }
-__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
-    float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return dfl_fast(p, e);
-}
-struct dflc {
-    dfl re, im;
-};
-__device__ __forceinline__ dflc dflc_mul(dflc a, dflc b) {
-    return dflc{dfl_sub(dfl_mul(a.re, b.re), dfl_mul(a.im, b.im)), dfl_add(dfl_mul(a.re, b.im), dfl_mul(a.im, b.re))};
-}
-__device__ __forceinline__ dflc dflc_add(dflc a, dflc b) { return dflc{dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
 
-// Direct interactions to centres with the per-pair geometry (difference,
-// reciprocal, logarithm, r/w) in FP64 and the power recurrence and per-lane
-// sums of the coefficients in double-FP32 pairs; lanes are summed in FP64.
+__device__ __forceinline__ dflc dflc_add(dflc a, dflc b) { return dflc{dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
+__device__ __forceinline__ dflc dflc_sub(dflc a, dflc b) {
+    return dflc{dfl_add(a.re, dfl_neg(b.re)), dfl_add(a.im, dfl_neg(b.im))};
+}
+__device__ __forceinline__ dflc dflc_scale(dflc a, dfl s) { return dflc{dfl_mul(a.re, s), dfl_mul(a.im, s)}; }
+__device__ __forceinline__ dflc dflc_ld(float4 v) { return dflc{dfl{v.x, v.y}, dfl{v.z, v.w}}; }
+
+// Centre of box b minus centre of box d, exact in FP32: both centres are odd
+// multiples of their half-widths H 2^-l, which FP32 holds exactly for l <= 23,
+// and the difference of two neighbouring boxes has few significant bits.
+__device__ __forceinline__ float2 box_offset_f(float H, int lb, int ixb, int iyb, int ld, int ixd, int iyd) {
+    float hb = ldexpf(H, -lb), hd = ldexpf(H, -ld);
+    return make_float2(__fsub_rn(__fmul_rn((float)(2 * ixb + 1), hb), __fmul_rn((float)(2 * ixd + 1), hd)),
+                       __fsub_rn(__fmul_rn((float)(2 * iyb + 1), hb), __fmul_rn((float)(2 * iyd + 1), hd)));
+}
+
+__global__ void k_level_split(int nlev, double H, float4 *__restrict__ out) {
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nlev) return;
+    double rho = ldexp(H, -l);
+    dfl a = dfl_from_double(rho), b = dfl_from_double(1.0 / rho), c = dfl_from_double(log(rho)),
+        d = dfl_from_double(1.0 / (rho * rho));
+    out[2 * l] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    out[2 * l + 1] = make_float4(c.hi, c.lo, d.hi, d.lo);
+}
+
+__global__ void k_rel_coords_split(int n, const double2 *__restrict__ xy, const int *__restrict__ owner, EvalView E,
+                                   float4 *__restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int b = owner[j];
+    double2 z = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
+    dfl x = dfl_from_double(xy[j].x - z.x), y = dfl_from_double(xy[j].y - z.y);
+    out[j] = make_float4(x.hi, x.lo, y.hi, y.lo);
+}
+
+__global__ void k_radius_split(int n, const double *__restrict__ r, float4 *__restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    dfl a = dfl_from_double(r[j]), b = dfl_from_double(1.0 / (r[j] * r[j]));
+    out[j] = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+__global__ void k_to_dfl4(long long n, const double2 *__restrict__ in, float4 *__restrict__ out) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    dfl a = dfl_from_double(in[j].x), b = dfl_from_double(in[j].y);
+    out[j] = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+// Direct interactions to centres with every per-pair step in FP32 pairs: the
+// difference w = y - c, 1/|w|^2, 1/w, r/w, the power recurrence and the lane
+// sums of the coefficients.  For S the logarithm is split as
+// log|w| = log r + (1/2) log(|w|^2 / r^2), so that the pair logarithm sees
+// arguments >= 1 of modest size and log r enters once per centre in FP64.
+// Sources inside the expansion disk (|r/w| > 1) would amplify the rounding by
+// |r/w|^m and are taken in FP64, as in the FP32 tier.
 template <int QQ, int KERNEL>
-__global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E, int nwork, const int *__restrict__ work,
+__global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E, SplitView X, int nwork,
+                                                                      const int *__restrict__ work,
                                                                       double2 *__restrict__ Qout) {
-    __shared__ NearRanges R;
+    __shared__ NearRangesF R;
     __shared__ int wsum[kNearThreads / 32];
-    __shared__ double lt[256];
-    for (int i = threadIdx.x; i < 256; i += kNearThreads) lt[i] = E.logt[i];
+    __shared__ float lt[KERNEL == GQ_D ? 1 : 384];
+    __shared__ double lt64[KERNEL == GQ_D ? 1 : 256];
+    if (KERNEL != GQ_D) {
+        for (int i = threadIdx.x; i < 384; i += kNearThreads) lt[i] = X.logt[i];
+        for (int i = threadIdx.x; i < 256; i += kNearThreads) lt64[i] = E.logt[i];
+    }
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
     int cb = E.ctr_beg[b], ce = E.ctr_end[b];
+    double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
     bool single = ne <= kNearRanges;
-    if (single) load_ranges(E, b, 0, ne, R, wsum);
+    if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
     for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
         int c = c0 + w;
         bool valid = c < ce;
-        double2 cz = valid ? E.sc_xy[c] : make_double2(0.0, 0.0);
-        double rc = valid ? E.sc_r[c] : 1.0;
+        float4 c4 = valid ? X.c_rel[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 r4 = valid ? X.c_r[c] : make_float4(1.f, 0.f, 1.f, 0.f);
+        dfl rc{r4.x, r4.y}, irc2{r4.z, r4.w};
+        float rc2 = r4.x * r4.x;
         const int qc = (valid && E.qc) ? E.qc[c] : QQ;
-        double acc0 = 0.0;              // S constant term (FP64)
+        double2 czd = valid ? E.sc_xy[c] : make_double2(0.0, 0.0);
+        double rcd = valid ? E.sc_r[c] : 1.0;
         dflc acc[QQ + 1];
+        double2 acc64[QQ + 1];   // sources inside the expansion disk: FP64
 #pragma unroll
-        for (int m = 0; m <= QQ; ++m) acc[m] = dflc{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+        for (int m = 0; m <= QQ; ++m) {
+            acc[m] = dflc{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+            acc64[m] = make_double2(0.0, 0.0);
+        }
+        dfl acc_log{0.f, 0.f}, acc_str{0.f, 0.f};   // S: sum of st log(|w|^2/r^2), sum of st
         for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
             if (!single) {
                 __syncthreads();
-                load_ranges(E, b, e0, ne, R, wsum);
+                load_ranges_f(E, b, zb, e0, ne, R, wsum);
             }
             int T = R.pre[R.n];
             if (valid) {
-                int r = 0;
+                int r = 0, rcur = -1;
+                dfl ex{0.f, 0.f}, ey{0.f, 0.f};   // source-box offset minus the centre
                 for (int v = lane; v < T; v += 32) {
                     while (R.pre[r + 1] <= v) ++r;
-                    int s = R.beg[r] + (v - R.pre[r]);
-                    double2 y = E.s_xy[s], st = E.str[s];
-                    double wx = y.x - cz.x, wy = y.y - cz.y;
-                    double n2 = wx * wx + wy * wy;
-                    double inv = gq_rcp(n2);
-                    double2 winv = make_double2(wx * inv, -wy * inv);
-                    dflc u{dfl_from(rc * winv.x), dfl_from(rc * winv.y)};
-                    dflc t;
-                    int m0;
-                    if (KERNEL == GQ_D) {
-                        double2 t0 = cmul(st, winv);
-                        t = dflc{dfl_from(t0.x), dfl_from(t0.y)};
-                        acc[0] = dflc_add(acc[0], t);
-                        m0 = 1;
-                    } else {
-                        acc0 += st.x * (0.5 * gq_log(n2, lt, lt + 128));
-                        t = dflc{dfl_from(st.x * (rc * winv.x)), dfl_from(st.x * (rc * winv.y))};
-                        acc[1] = dflc_add(acc[1], t);
-                        m0 = 2;
+                    if (r != rcur) {
+                        float2 o = R.off[r];
+                        ex = dfl_add_f(dfl{-c4.x, -c4.y}, o.x);
+                        ey = dfl_add_f(dfl{-c4.z, -c4.w}, o.y);
+                        rcur = r;
                     }
+                    int s = R.beg[r] + (v - R.pre[r]);
+                    float4 y4 = X.s_rel[s];
+                    dfl wx = dfl_add(dfl{y4.x, y4.y}, ex), wy = dfl_add(dfl{y4.z, y4.w}, ey);
+                    dfl n2 = dfl_add(dfl_sqr(wx), dfl_sqr(wy));
+                    if (n2.hi < rc2) {
+                        double2 yd = E.s_xy[s], sd = E.str[s];
+                        double dx = yd.x - czd.x, dy = yd.y - czd.y;
+                        double d2 = dx * dx + dy * dy, dinv = 1.0 / d2;
+                        double2 wi = make_double2(dx * dinv, -dy * dinv);
+                        double2 uu = make_double2(rcd * wi.x, rcd * wi.y);
+                        if (KERNEL == GQ_D) {
+                            double2 t = cmul(sd, wi);
+                            acc64[0] = cadd(acc64[0], t);
 #pragma unroll
-                    for (int m = 1; m <= QQ; ++m) {
-                        if (m < m0) continue;
-                        if (m > qc) break;
-                        t = dflc_mul(t, u);
-                        acc[m] = dflc_add(acc[m], t);
+                            for (int m = 1; m <= QQ; ++m) {
+                                t = cmul(t, uu);
+                                acc64[m] = cadd(acc64[m], t);
+                            }
+                        } else {
+                            acc64[0].x += sd.x * (0.5 * gq_log(d2, lt64, lt64 + 128));
+                            double2 t = make_double2(sd.x * uu.x, sd.x * uu.y);
+                            acc64[1] = cadd(acc64[1], t);
+#pragma unroll
+                            for (int m = 2; m <= QQ; ++m) {
+                                t = cmul(t, uu);
+                                acc64[m] = cadd(acc64[m], t);
+                            }
+                        }
+                        continue;
+                    }
+                    float4 s4 = X.str[s];
+                    dfl inv = dfl_rcp(n2);
+                    dflc winv{dfl_mul(wx, inv), dfl_neg(dfl_mul(wy, inv))};
+                    dflc u{dfl_mul(rc, winv.re), dfl_mul(rc, winv.im)};
+                    dflc t;
+                    if (KERNEL == GQ_D) {
+                        t = dflc_mul(dflc{dfl{s4.x, s4.y}, dfl{s4.z, s4.w}}, winv);
+                        dflc_acc(acc[0], t);
+#pragma unroll
+                        for (int m = 1; m <= QQ; ++m) {
+                            if (m > qc) break;
+                            t = dflc_mul(t, u);
+                            dflc_acc(acc[m], t);
+                        }
+                    } else {
+                        dfl st{s4.x, s4.y};
+                        dfl lg = dfl_log(dfl_mul(n2, irc2), lt, lt + 128, lt + 256);
+                        dfl_acc(acc_log, dfl_mul(st, lg));
+                        dfl_acc(acc_str, st);
+                        t = dflc{dfl_mul(st, u.re), dfl_mul(st, u.im)};
+                        dflc_acc(acc[1], t);
+#pragma unroll
+                        for (int m = 2; m <= QQ; ++m) {
+                            if (m > qc) break;
+                            t = dflc_mul(t, u);
+                            dflc_acc(acc[m], t);
+                        }
                     }
                 }
             }
@@ -1038,9 +1118,15 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
         double2 dacc[QQ + 1];
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) {
-            dacc[m] = make_double2((double)acc[m].re.hi + (double)acc[m].re.lo, (double)acc[m].im.hi + (double)acc[m].im.lo);
-            if (m == 0 && KERNEL != GQ_D) dacc[0] = make_double2(acc0, 0.0);
+            dacc[m] = make_double2(dfl_to_double(acc[m].re) + acc64[m].x, dfl_to_double(acc[m].im) + acc64[m].y);
+            if (KERNEL != GQ_D && m == 0)
+                dacc[0].x = 0.5 * dfl_to_double(acc_log) + acc64[0].x;
             for (int o = 16; o > 0; o >>= 1) dacc[m] = cadd(dacc[m], shfl2_xor(dacc[m], o));
+        }
+        if (KERNEL != GQ_D) {
+            double sst = dfl_to_double(acc_str);
+            for (int o = 16; o > 0; o >>= 1) sst += __shfl_xor_sync(0xffffffffu, sst, o);
+            dacc[0].x += sst * gq_log(rcd, lt64, lt64 + 128);
         }
         if (valid && lane <= QQ) {
             double2 vv = dacc[0];
@@ -1053,16 +1139,217 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
     }
 }
 
-template <int QQ>
-void launch_near_centres_split(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, double2 *Q) {
-    auto kd = k_near_centres_split<QQ, GQ_D>;
-    auto ks = k_near_centres_split<QQ, GQ_S>;
-    GQ_LAUNCH(ctx, (E.kernel == GQ_D ? kd : ks), nwork, kNearThreads, 0, E, nwork, work, Q);
+// Potential at point targets from List 1 sources, every pair step in FP32
+// pairs; pairs closer than 2^-50 fall back to FP64.
+template <int KERNEL>
+__global__ void __launch_bounds__(kNearThreads) k_near_points_split(EvalView E, SplitView X, int nwork,
+                                                                     const int *__restrict__ work,
+                                                                     double *__restrict__ pot) {
+    __shared__ NearRangesF R;
+    __shared__ int wsum[kNearThreads / 32];
+    __shared__ float lt[KERNEL == GQ_D ? 1 : 384];
+    if (KERNEL != GQ_D)
+        for (int i = threadIdx.x; i < 384; i += kNearThreads) lt[i] = X.logt[i];
+    int b = work[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
+    int tb = E.pt_beg[b], te = E.pt_end[b];
+    double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
+    bool single = ne <= kNearRanges;
+    if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
+    for (int t0 = tb; t0 < te; t0 += kNearThreads / 32) {
+        int t = t0 + w;
+        bool valid = t < te;
+        float4 t4 = valid ? X.p_rel[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        dfl acc{0.f, 0.f};
+        double acc64 = 0.0;
+        for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
+            if (!single) {
+                __syncthreads();
+                load_ranges_f(E, b, zb, e0, ne, R, wsum);
+            }
+            int T = R.pre[R.n];
+            if (valid) {
+                int r = 0, rcur = -1;
+                dfl ex{0.f, 0.f}, ey{0.f, 0.f};
+                for (int v = lane; v < T; v += 32) {
+                    while (R.pre[r + 1] <= v) ++r;
+                    if (r != rcur) {
+                        float2 o = R.off[r];
+                        ex = dfl_add_f(dfl{-t4.x, -t4.y}, o.x);
+                        ey = dfl_add_f(dfl{-t4.z, -t4.w}, o.y);
+                        rcur = r;
+                    }
+                    int s = R.beg[r] + (v - R.pre[r]);
+                    float4 y4 = X.s_rel[s];
+                    dfl wx = dfl_add(dfl{y4.x, y4.y}, ex), wy = dfl_add(dfl{y4.z, y4.w}, ey);
+                    dfl n2 = dfl_add(dfl_sqr(wx), dfl_sqr(wy));
+                    if (n2.hi < 0x1p-100f) {
+                        double2 yd = E.s_xy[s], td = E.sp_xy[t], sd = E.str[s];
+                        double dx = yd.x - td.x, dy = yd.y - td.y, d2 = dx * dx + dy * dy;
+                        if (d2 == 0.0) continue;
+                        if (KERNEL == GQ_D) acc64 += (sd.x * dx + sd.y * dy) / d2;
+                        else acc64 += sd.x * (0.5 * log(d2));
+                        continue;
+                    }
+                    float4 s4 = X.str[s];
+                    if (KERNEL == GQ_D) {
+                        dfl dot = dfl_dot2(s4.x, s4.y, wx.hi, wx.lo, s4.z, s4.w, wy.hi, wy.lo);
+                        dfl_acc(acc, dfl_mul(dot, dfl_rcp(n2)));
+                    } else {
+                        dfl lg = dfl_log(n2, lt, lt + 128, lt + 256);
+                        dfl_acc(acc, dfl_mul(dfl{s4.x, s4.y}, lg));
+                    }
+                }
+            }
+        }
+        double dacc = (KERNEL == GQ_D ? 1.0 : 0.5) * dfl_to_double(acc) + acc64;
+        for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+        if (valid && lane == 0) pot[t] = dacc;
+    }
 }
 
-void dispatch_near_centres_split(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, double2 *Q) {
+// M2P in FP32 pairs, one thread per point target, Horner in v = rho / (t - z_d);
+// A_0 log|t - z_d| = A_0 (log rho + (1/2) log(|t - z_d|^2 / rho^2)).
+__global__ void k_w_points_split(EvalView E, SplitView X, int npt, const int *__restrict__ pt_owner,
+                                 double *__restrict__ pot) {
+    __shared__ float lt[384];
+    for (int i = threadIdx.x; i < 384; i += blockDim.x) lt[i] = X.logt[i];
+    __syncthreads();
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npt) return;
+    int b = pt_owner[t];
+    int beg = E.loff[3][b], end = E.loff[3][b + 1];
+    if (beg == end) return;
+    int P = E.P, P1 = P + 1;
+    int lb = E.blev[b], ixb = E.bix[b], iyb = E.biy[b];
+    float4 t4 = X.p_rel[t];
+    dfl acc{0.f, 0.f};
+    for (int i = beg; i < end; ++i) {
+        int d = E.lidx[3][i];
+        int l = E.blev[d];
+        float2 off = box_offset_f(X.H, lb, ixb, iyb, l, E.bix[d], E.biy[d]);
+        dfl zx = dfl_add_f(dfl{t4.x, t4.y}, off.x), zy = dfl_add_f(dfl{t4.z, t4.w}, off.y);
+        dfl n2 = dfl_add(dfl_sqr(zx), dfl_sqr(zy));
+        dfl inv = dfl_rcp(n2);
+        float4 la = X.lvl[2 * l], lb4 = X.lvl[2 * l + 1];
+        dfl rho{la.x, la.y};
+        dflc v{dfl_mul(rho, dfl_mul(zx, inv)), dfl_neg(dfl_mul(rho, dfl_mul(zy, inv)))};
+        const float4 *A = X.M + (size_t)d * P1;
+        dflc h = dflc_ld(A[P]);
+        for (int k = P - 1; k >= 1; --k) h = dflc_add(dflc_mul(h, v), dflc_ld(A[k]));
+        h = dflc_mul(h, v);
+        dfl lg = dfl_log(dfl_mul(n2, dfl{lb4.z, lb4.w}), lt, lt + 128, lt + 256);
+        dfl lz = dfl_add(dfl{0.5f * lg.hi, 0.5f * lg.lo}, dfl{lb4.x, lb4.y});
+        float4 a0 = A[0];
+        dfl_acc(acc, h.re);
+        dfl_acc(acc, dfl_mul(dfl{a0.x, a0.y}, lz));
+    }
+    pot[t] += dfl_to_double(acc);
+}
+
+// M2QBXL in FP32 pairs, one thread per centre.  With y = c - z_d, v = rho/y,
+// omega = (z - c)/y and At_k = A_k v^k, the local expansion of
+// sum_k At_k (1 + omega)^-k is built by Horner's rule in (1 + omega)^-1 on
+// a series truncated after omega^q: from k = K down to 1, add At_k to the
+// constant term, then divide the series by (1 + omega), which is the
+// recurrence S_m <- S_m - S_{m-1}.  The coefficient of omega^m equals
+// (-1)^m sum_k C(m+k-1, k-1) At_k, the same sum as the FP64 kernel forms with
+// the binomial table, and Q_m += (r/y)^m (S_m - (-1)^m A_0/m).  The powers
+// v^k run downwards from v^K, K = P unless |v|^P < 2^-80, where K is cut so
+// that v^K keeps its low part above FP32's normal range (the terms beyond are
+// below 2^-80 A_k).
+template <int QQ>
+__global__ void __launch_bounds__(128) k_w_centres_split(EvalView E, SplitView X, int nc,
+                                                         const int *__restrict__ ctr_box_of, double2 *__restrict__ Qout) {
+    __shared__ float lt[384];
+    for (int i = threadIdx.x; i < 384; i += blockDim.x) lt[i] = X.logt[i];
+    __syncthreads();
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int b = ctr_box_of[c];
+    int beg = E.loff[3][b], end = E.loff[3][b + 1];
+    if (beg == end) return;
+    const int P = E.P, P1 = P + 1;
+    int lb = E.blev[b], ixb = E.bix[b], iyb = E.biy[b];
+    float4 c4 = X.c_rel[c], r4 = X.c_r[c];
+    dfl rc{r4.x, r4.y};
+    dflc acc[QQ + 1];
+#pragma unroll
+    for (int m = 0; m <= QQ; ++m) acc[m] = dflc{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+    for (int i = beg; i < end; ++i) {
+        int d = E.lidx[3][i];
+        int l = E.blev[d];
+        float2 off = box_offset_f(X.H, lb, ixb, iyb, l, E.bix[d], E.biy[d]);
+        dfl yx = dfl_add_f(dfl{c4.x, c4.y}, off.x), yy = dfl_add_f(dfl{c4.z, c4.w}, off.y);
+        dfl n2 = dfl_add(dfl_sqr(yx), dfl_sqr(yy));
+        dfl inv = dfl_rcp(n2);
+        dflc yinv{dfl_mul(yx, inv), dfl_neg(dfl_mul(yy, inv))};
+        float4 la = X.lvl[2 * l], lb4 = X.lvl[2 * l + 1];
+        dfl rho{la.x, la.y}, irho{la.z, la.w};
+        dflc v = dflc_scale(yinv, rho), sv = dflc_scale(yinv, rc);
+        dflc vinv{dfl_mul(yx, irho), dfl_mul(yy, irho)};
+        int K = P;
+        float av2 = v.re.hi * v.re.hi + v.im.hi * v.im.hi;
+        if ((float)P * __log2f(av2) < -160.f) K = max(1, min(P, (int)(-160.f / __log2f(av2))));
+        dflc vk{dfl{1.f, 0.f}, dfl{0.f, 0.f}}, base = v;
+        for (int e = K; e; e >>= 1) {
+            if (e & 1) vk = dflc_mul(vk, base);
+            if (e > 1) base = dflc_mul(base, base);
+        }
+        const float4 *A = X.M + (size_t)d * P1;
+        dflc S[QQ + 1];
+#pragma unroll
+        for (int m = 0; m <= QQ; ++m) S[m] = dflc{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+        for (int k = K; k >= 1; --k) {
+            S[0] = dflc_add(S[0], dflc_mul(dflc_ld(A[k]), vk));
+#pragma unroll
+            for (int m = 1; m <= QQ; ++m) S[m] = dflc_sub(S[m], S[m - 1]);
+            vk = dflc_mul(vk, vinv);
+        }
+        dfl A0{A[0].x, A[0].y};
+        dfl lg = dfl_log(dfl_mul(n2, dfl{lb4.z, lb4.w}), lt, lt + 128, lt + 256);
+        dfl ly = dfl_add(dfl{0.5f * lg.hi, 0.5f * lg.lo}, dfl{lb4.x, lb4.y});
+        dflc_acc(acc[0], dflc{dfl_add(S[0].re, dfl_mul(A0, ly)), S[0].im});
+        dflc sm = sv;
+#pragma unroll
+        for (int m = 1; m <= QQ; ++m) {
+            float ih = __frcp_rn((float)m);
+            dfl a = dfl_mul(A0, dfl{ih, fmaf(-(float)m, ih, 1.0f) * ih});   // A_0 / m
+            dflc g{(m & 1) ? dfl_add(S[m].re, a) : dfl_add(S[m].re, dfl_neg(a)), S[m].im};
+            dflc_acc(acc[m], dflc_mul(sm, g));
+            sm = dflc_mul(sm, sv);
+        }
+    }
+    double2 *dst = Qout + (size_t)c * (QQ + 1);
+#pragma unroll
+    for (int m = 0; m <= QQ; ++m)
+        dst[m] = make_double2(dst[m].x + dfl_to_double(acc[m].re), dst[m].y + dfl_to_double(acc[m].im));
+}
+
+void dispatch_w_centres_split(gq_ctx *ctx, const EvalView &E, const SplitView &X, int nc, const int *owner,
+                              double2 *Q) {
     switch (E.Q) {
-#define GQ_CASE(v) case v: launch_near_centres_split<v>(ctx, E, nwork, work, Q); break;
+#define GQ_CASE(v) case v: GQ_LAUNCH(ctx, k_w_centres_split<v>, gq_blocks(nc, 128), 128, 0, E, X, nc, owner, Q); break;
+        GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
+        GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
+#undef GQ_CASE
+        default: throw gq_error{GQ_ERR_INVALID, "p_qbx out of range"};
+    }
+}
+
+template <int QQ>
+void launch_near_centres_split(gq_ctx *ctx, const EvalView &E, const SplitView &X, int nwork, const int *work,
+                               double2 *Q) {
+    auto kd = k_near_centres_split<QQ, GQ_D>;
+    auto ks = k_near_centres_split<QQ, GQ_S>;
+    GQ_LAUNCH(ctx, (E.kernel == GQ_D ? kd : ks), nwork, kNearThreads, 0, E, X, nwork, work, Q);
+}
+
+void dispatch_near_centres_split(gq_ctx *ctx, const EvalView &E, const SplitView &X, int nwork, const int *work,
+                                 double2 *Q) {
+    switch (E.Q) {
+#define GQ_CASE(v) case v: launch_near_centres_split<v>(ctx, E, X, nwork, work, Q); break;
         GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
         GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
 #undef GQ_CASE
@@ -1119,6 +1406,7 @@ __global__ void k_tgt_ptpos(int npt, const int *__restrict__ pt_perm, int *__res
 // ------------------------------------------------------------------ tables (per geometry)
 struct EvalTables {
     dbuf<double> logt;       // GqLogTable
+    dbuf<float> dlogt;       // GqDflLogTable
     dbuf<double> binom;      // [64][64]
     dbuf<double2> dtab;      // [121][32] delta^-k
     dbuf<double> logtab;     // [121] log|delta|
@@ -1164,6 +1452,10 @@ static void make_tables(gq_geom *g, EvalTables &T) {
     gq_log_table_host(&LT);
     T.logt.alloc(256);
     GQ_CUDA(cudaMemcpyAsync(T.logt.p, &LT, sizeof(LT), cudaMemcpyHostToDevice, st));
+    GqDflLogTable DT;
+    gq_dfl_log_table_host(&DT);
+    T.dlogt.alloc(384);
+    GQ_CUDA(cudaMemcpyAsync(T.dlogt.p, &DT, sizeof(DT), cudaMemcpyHostToDevice, st));
     T.binom.alloc(bn.size());
     T.dtab.alloc(dt.size());
     T.logtab.alloc(lt.size());
@@ -1283,6 +1575,34 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
                                (const double2 *)g->strength, g->str_f.p);
         X.s_rel = g->s_rel; X.str = g->str_f; X.c_rel = g->c_rel; X.p_rel = g->p_rel; X.M = g->M_f; X.c_r = g->c_rf;
     }
+    SplitView SX{};
+    const bool split_w = split && g->nlev <= 24;   // exact FP32 box offsets
+    if (split) {
+        if (!g->split_ready) {
+            g->s_rel2.alloc(g->nsrc);
+            g->c_rel2.alloc(g->nc);
+            g->c_r2.alloc(g->nc);
+            if (g->nsrc) GQ_LAUNCH(ctx, k_rel_coords_split, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc,
+                                   (const double2 *)g->s_xy, (const int *)g->src_owner, E, g->s_rel2.p);
+            if (g->nc) {
+                GQ_LAUNCH(ctx, k_rel_coords_split, gq_blocks(g->nc, 256), 256, 0, g->nc, (const double2 *)g->sc_xy,
+                          (const int *)g->ctr_owner, E, g->c_rel2.p);
+                GQ_LAUNCH(ctx, k_radius_split, gq_blocks(g->nc, 256), 256, 0, g->nc, (const double *)g->sc_r, g->c_r2.p);
+            }
+            g->p_rel2.alloc(g->npt);
+            if (g->npt) GQ_LAUNCH(ctx, k_rel_coords_split, gq_blocks(g->npt, 256), 256, 0, g->npt,
+                                  (const double2 *)g->sp_xy, (const int *)g->pt_owner, E, g->p_rel2.p);
+            g->lvl2.alloc(2 * (size_t)g->nlev);
+            GQ_LAUNCH(ctx, k_level_split, 1, 64, 0, g->nlev, g->root.H, g->lvl2.p);
+            g->split_ready = true;
+        }
+        g->M2.alloc((size_t)g->nbox * P1);
+        g->str2.alloc(g->nsrc);
+        if (g->nsrc) GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks(g->nsrc, 256), 256, 0, (long long)g->nsrc,
+                               (const double2 *)g->strength, g->str2.p);
+        SX.s_rel = g->s_rel2; SX.str = g->str2; SX.c_rel = g->c_rel2; SX.c_r = g->c_r2; SX.p_rel = g->p_rel2;
+        SX.M = g->M2; SX.lvl = g->lvl2; SX.logt = T.dlogt; SX.H = (float)g->root.H;
+    }
     mark(S_STR, st);
     GQ_CUDA(cudaEventRecord(g->ev_str, st));
 
@@ -1291,7 +1611,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     mark(N_BEG, s2);
     if (g->n_ctr_boxes) {
         if (f32) dispatch_near_centres_f32(&ctx2, E, X, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
-        else if (split) dispatch_near_centres_split(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
+        else if (split) dispatch_near_centres_split(&ctx2, E, SX, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
         else dispatch_near_centres(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
     }
     mark(N_CTR, s2);
@@ -1300,6 +1620,11 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
             auto kd = k_near_points_f32<GQ_D>;
             auto ks = k_near_points_f32<GQ_S>;
             GQ_LAUNCH((&ctx2), (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, X, g->n_pt_boxes,
+                      (const int *)g->pt_boxes, g->potn.p);
+        } else if (split) {
+            auto kd = k_near_points_split<GQ_D>;
+            auto ks = k_near_points_split<GQ_S>;
+            GQ_LAUNCH((&ctx2), (kin == GQ_D ? kd : ks), g->n_pt_boxes, kNearThreads, 0, E, SX, g->n_pt_boxes,
                       (const int *)g->pt_boxes, g->potn.p);
         } else {
             auto kd = k_near_points<GQ_D>;
@@ -1355,9 +1680,14 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     if (f32)
         GQ_LAUNCH(ctx, k_to_float2, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
                   (const double2 *)g->M, g->M_f.p);
+    if (split_w)
+        GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
+                  (const double2 *)g->M, g->M2.p);
     mark(S_L2L, st);
     // Stage 5b
-    if (g->nc) {
+    if (g->nc && split_w) {
+        dispatch_w_centres_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, g->Q.p);
+    } else if (g->nc) {
         auto k8 = k_w_centres<8>;
         auto k16 = k_w_centres<16>;
         auto k32 = k_w_centres<GQ_MAX_PFMM>;
@@ -1368,6 +1698,9 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     if (g->npt) {
         if (f32)
             GQ_LAUNCH(ctx, k_w_points_f32, gq_blocks(g->npt, 128), 128, 0, E, X, g->npt, (const int *)g->pt_owner,
+                      g->pot.p);
+        else if (split_w)
+            GQ_LAUNCH(ctx, k_w_points_split, gq_blocks(g->npt, 128), 128, 0, E, SX, g->npt, (const int *)g->pt_owner,
                       g->pot.p);
         else
             GQ_LAUNCH(ctx, k_w_points, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,

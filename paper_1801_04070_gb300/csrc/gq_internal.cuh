@@ -167,6 +167,15 @@ struct gq_geom {
     dbuf<float2> p_rel;   // sorted point targets minus their leaf centre
     dbuf<float2> str_f;   // strengths
     dbuf<float2> M_f;     // multipoles (List 3 far evaluation at point targets)
+    // split precision (double-FP32 direct sums): the same relative coordinates as pairs
+    bool split_ready = false;
+    dbuf<float4> s_rel2;  // (x.hi, x.lo, y.hi, y.lo)
+    dbuf<float4> c_rel2;
+    dbuf<float4> c_r2;    // (r.hi, r.lo, (1/r^2).hi, (1/r^2).lo)
+    dbuf<float4> str2;    // (re.hi, re.lo, im.hi, im.lo)
+    dbuf<float4> p_rel2;  // sorted point targets minus their leaf centre
+    dbuf<float4> M2;      // multipoles
+    dbuf<float4> lvl2;    // per level: (rho, 1/rho), (log rho, 1/rho^2)
 };
 
 // ------------------------------------------------------------------ launch helpers

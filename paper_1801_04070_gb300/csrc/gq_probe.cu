@@ -1,6 +1,7 @@
 // gq_probe.cu -- FMA-throughput probe used as the measured FP64 / FP32 peak
 // of the ALU roofline (the measured peaks cover HBM and BF16 only).
 #include "gq_internal.cuh"
+#include "gq_dfl.cuh"
 #include "gq_math.cuh"
 
 namespace {
@@ -58,11 +59,13 @@ double gq_probe_fma(gq_ctx *ctx, int what) { return what == 0 ? run<double>(ctx)
 
 namespace {
 __global__ void k_probe_math(int fn, int n, const double *__restrict__ x, const double *__restrict__ tab,
-                             double *__restrict__ y) {
+                             const float *__restrict__ ftab, double *__restrict__ y) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double v = x[i];
-    y[i] = fn == 0 ? gq_log(v, tab, tab + 128) : fn == 1 ? log(v) : fn == 2 ? gq_rcp(v) : 1.0 / v;
+    if (fn == 4) y[i] = dfl_to_double(dfl_log(dfl_from_double(v), ftab, ftab + 128, ftab + 256));
+    else if (fn == 5) y[i] = dfl_to_double(dfl_rcp(dfl_from_double(v)));
+    else y[i] = fn == 0 ? gq_log(v, tab, tab + 128) : fn == 1 ? log(v) : fn == 2 ? gq_rcp(v) : 1.0 / v;
 }
 }  // namespace
 
@@ -72,7 +75,13 @@ void gq_probe_math_impl(gq_ctx *ctx, int fn, int n, const double *x_dev, double 
     dbuf<double> tab;
     tab.alloc(256);
     GQ_CUDA(cudaMemcpyAsync(tab.p, &T, sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
-    if (n > 0) GQ_LAUNCH(ctx, k_probe_math, gq_blocks(n, 256), 256, 0, fn, n, x_dev, (const double *)tab.p, y_dev);
+    GqDflLogTable F;
+    gq_dfl_log_table_host(&F);
+    dbuf<float> ftab;
+    ftab.alloc(384);
+    GQ_CUDA(cudaMemcpyAsync(ftab.p, &F, sizeof(F), cudaMemcpyHostToDevice, ctx->stream));
+    if (n > 0) GQ_LAUNCH(ctx, k_probe_math, gq_blocks(n, 256), 256, 0, fn, n, x_dev, (const double *)tab.p,
+                         (const float *)ftab.p, y_dev);
     GQ_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 

@@ -1,5 +1,6 @@
 """The FP64 logarithm (Tang's table-driven method) and reciprocal (FP32 seed +
-two Newton steps) used by the direct-interaction kernels, checked against
+two Newton steps) used by the direct-interaction kernels, and their
+double-FP32 counterparts in the split-precision kernels, checked against
 CUDA's log and IEEE division over the ranges the kernels meet and beyond."""
 import numpy as np
 import pytest
@@ -43,3 +44,27 @@ def test_reciprocal_matches_division():
     x = np.concatenate([x, -x])
     mine, ref = _run(2, x), _run(3, x)
     assert (np.abs(mine - ref) <= 2 * np.spacing(np.abs(ref))).all()
+
+
+def _split_inputs():
+    rng = np.random.default_rng(2)
+    return np.concatenate([10.0 ** rng.uniform(-30, 30, 200000), 1.0 + rng.uniform(-1e-3, 1e-3, 20000),
+                           1.0 + rng.uniform(0, 64, 20000), np.array([1.0, 2.0, 0.5, 7.0 / 3.0, 2.0 ** 126])])
+
+
+def test_split_log_matches_cuda_log():
+    """Pair logarithm: absolute error about 2^-47 max(|log x|, 1) (48-bit pairs)."""
+    x = _split_inputs()
+    mine, ref = _run(4, x), _run(1, x)
+    err = np.abs(mine - ref) / np.maximum(np.abs(ref), 1.0)
+    print(f"double-FP32 log: max error {err.max():.2e} (2^{np.log2(err.max()):.1f})")
+    assert err.max() <= 2.0 ** -45
+
+
+def test_split_reciprocal_matches_division():
+    x = _split_inputs()
+    x = np.concatenate([x, -x])
+    mine, ref = _run(5, x), _run(3, x)
+    err = np.abs(mine - ref) / np.abs(ref)
+    print(f"double-FP32 reciprocal: max relative error {err.max():.2e} (2^{np.log2(err.max()):.1f})")
+    assert err.max() <= 2.0 ** -44

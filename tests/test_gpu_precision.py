@@ -48,6 +48,30 @@ def test_mixed_split_tier_matches_oracle(kern):
     assert err <= 2e-11
 
 
+@pytest.mark.parametrize("kern", ["S", "D"])
+def test_mixed_split_tier_sampled_at_eps_orders(kern):
+    """The double-FP32 tier on a 4x4 starfish grid at the orders eps = 1e-10
+    selects (p_qbx 7, p_fmm 30), where the List 3 far translations (M2QBXL,
+    M2P) and the point-target direct sums also run in pairs: sampled targets
+    of every kind against the FP64 oracle at the same orders."""
+    g = workloads.starfish_grid(4, 4, 64, n_off=1 << 16, on_surface="up", seed=1)
+    geo = _geo(g, p_qbx=0, p_fmm=0, n_max=32, eps=1e-10, precision=1)
+    prm = geo.params
+    v = geo.eval(kern, g["density"])
+    o = oracle.Oracle(g, oracle.default_params(g, p_qbx=prm.p_qbx, p_fmm=prm.p_fmm))
+    kind, _ = o.association()
+    rng = np.random.default_rng(3)
+    mask = np.zeros(len(kind), np.int32)
+    for k in (0, 1, 2):
+        ids = np.nonzero(kind == k)[0]
+        mask[rng.choice(ids, min(300, len(ids)), replace=False)] = 1
+    sel = mask.astype(bool)
+    ref = o.eval(kern, g["density"], target_mask=mask)
+    err = np.abs(v[sel] - ref[sel]).max() / np.abs(ref[sel]).max()
+    print(f"MIXED double-FP32 {kern} at p_qbx {prm.p_qbx} p_fmm {prm.p_fmm}: rel err vs FP64 oracle {err:.2e}")
+    assert err <= 2e-11
+
+
 def test_mixed_below_threshold_is_fp64():
     g = workloads.small_grid(2, 2, 16, 3000, seed=7)
     geo = _geo(g, p_qbx=5, p_fmm=10, n_max=32, eps=1e-12, precision=1)
