@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--kernel", default="S", choices=["S", "D"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--sweep", action="store_true",
-                    help="also time FP64 and MIXED evaluations at eps = 1e-4 ... 1e-12 (orders from eps)")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="skip the FP64 vs MIXED evaluation sweep at eps = 1e-4 ... 1e-12 (orders from eps)")
     ap.add_argument("--batched", action="store_true",
                     help="also time 64 geometries of uneven size (2k-200k quadrature nodes, log-uniform) x 8 "
                          "densities: one CUDA-graph launch against one gq_eval after another")
@@ -453,7 +453,7 @@ def run_gpu(args, rank, world, local):
 
     # ---- accuracy sweep: orders from eps, FP64 vs MIXED evaluation throughput
     sweep = None
-    if args.sweep:
+    if args.sweep and rank == 0:
         sweep = []
         for eps in (1e-4, 1e-6, 1e-8, 1e-10, 1e-12):
             row = {"eps": eps}

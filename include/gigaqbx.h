@@ -76,16 +76,21 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
  *                 ordinary FMM point target.
  *  eps          : requested accuracy (used for orders of 0 and by GQ_PREC_MIXED).
  *  precision    : GQ_PREC_FP64 (default): every stage in FP64.
- *                 GQ_PREC_MIXED: when eps >= 1e-6, the direct interactions
- *                 (Lists 1, 3 close, 4 close to centres and to point targets)
- *                 and the List 3 far multipole evaluation at point targets
- *                 run in FP32 on coordinates taken relative to box centres,
- *                 with FP64 sums across lanes; a source inside a centre's
- *                 expansion disk (|r/w| > 1, where rounding would grow as
- *                 |r/w|^m) is taken in FP64.  Their rounding error, about
- *                 1e-7 relative, stays below eps/5.  All translations (M2M,
- *                 M2L, L2L, M2QBXL, L2QBXL), P2M, P2L and the final QBX
- *                 evaluation stay FP64.  For eps < 1e-6 MIXED runs as FP64.
+ *                 GQ_PREC_MIXED: a tier chosen from eps.
+ *                 eps >= 1e-6: the direct interactions (Lists 1, 3 close,
+ *                 4 close to centres and to point targets) and the List 3
+ *                 far multipole evaluation at point targets run in FP32 on
+ *                 coordinates taken relative to box centres, with FP64 sums
+ *                 across lanes (rounding about 1e-7 relative, below eps/5).
+ *                 1e-10 <= eps < 1e-6: the same steps run in double-FP32
+ *                 pairs (about 48 significant bits; measured 1e-15 .. 5e-13
+ *                 relative to the FP64 path).  In both tiers a source inside
+ *                 a centre's expansion disk (|r/w| > 1, where rounding would
+ *                 grow as |r/w|^m) is taken in FP64, and the List 3 far
+ *                 translation to centres (M2QBXL) runs in pairs when the tree
+ *                 has at most 24 levels.  M2M, M2L, L2L, L2QBXL, P2M, P2L
+ *                 and the final QBX evaluation stay FP64.  For eps < 1e-10
+ *                 MIXED runs as FP64.
  */
 typedef struct {
     int p_qbx, p_fmm, n_max;

@@ -1576,8 +1576,9 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         X.s_rel = g->s_rel; X.str = g->str_f; X.c_rel = g->c_rel; X.p_rel = g->p_rel; X.M = g->M_f; X.c_r = g->c_rf;
     }
     SplitView SX{};
-    const bool split_w = split && g->nlev <= 24;   // exact FP32 box offsets
-    if (split) {
+    // List 3 far at centres runs in pairs in both mixed tiers (exact FP32 box offsets need l <= 23)
+    const bool split_w = (split || f32) && g->nlev <= 24;
+    if (split || f32) {
         if (!g->split_ready) {
             g->s_rel2.alloc(g->nsrc);
             g->c_rel2.alloc(g->nc);
@@ -1597,9 +1598,11 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
             g->split_ready = true;
         }
         g->M2.alloc((size_t)g->nbox * P1);
-        g->str2.alloc(g->nsrc);
-        if (g->nsrc) GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks(g->nsrc, 256), 256, 0, (long long)g->nsrc,
-                               (const double2 *)g->strength, g->str2.p);
+        if (split) {
+            g->str2.alloc(g->nsrc);
+            if (g->nsrc) GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks(g->nsrc, 256), 256, 0, (long long)g->nsrc,
+                                   (const double2 *)g->strength, g->str2.p);
+        }
         SX.s_rel = g->s_rel2; SX.str = g->str2; SX.c_rel = g->c_rel2; SX.c_r = g->c_r2; SX.p_rel = g->p_rel2;
         SX.M = g->M2; SX.lvl = g->lvl2; SX.logt = T.dlogt; SX.H = (float)g->root.H;
     }
