@@ -289,12 +289,56 @@ def run_batched(args, dev, stream):
     b.close()
     for geo in geos:
         geo.close()
+
+    # exterior Neumann solves -mu/2 + S' mu = g on the same geometries (base nodes
+    # as targets), g the normal derivative of Re 1/(z - z0), z0 inside the first curve
+    ggeos, rhs, mus, refs = [], [], [], []
+    for g, _ in items:
+        geo = Geometry(g, params_default(p_qbx=8, p_fmm=15, n_max=32), device=dev.index)
+        geo.set_targets(g["base_xy"], np.arange(len(g["base_xy"]), dtype=np.int32))
+        geo.build()
+        ggeos.append(geo)
+        x = g["base_xy"][:, 0] + 1j * g["base_xy"][:, 1]
+        z0 = x[g["base_curve"] == 0].mean()
+        nrm = g["base_n"][:, 0] + 1j * g["base_n"][:, 1]
+        rhs.append(torch.tensor((nrm * (-1.0 / (x - z0) ** 2)).real, dtype=torch.float64, device=dev))
+        mus.append(torch.zeros_like(rhs[-1]))
+        refs.append(torch.zeros_like(rhs[-1]))
+    gb = Batch(ggeos)
+    tol, maxit, restart = 1e-10, 100, 30
+    gb.gmres(rhs, mus, tol=tol, maxit=maxit, restart=restart)   # capture and autotune the S' graph
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    ms_b, (its, res_b) = timed(lambda: gb.gmres(rhs, mus, tol=tol, maxit=maxit, restart=restart))
+
+    def seq():
+        return [geo.gmres(r, tol=tol, maxit=maxit, restart=restart, mu=m)[1:] for geo, r, m in zip(ggeos, rhs, refs)]
+    ms_s, seq_out = timed(seq)
+    diff = max(float((m - r).abs().max() / r.abs().max()) for m, r in zip(mus, refs))
+    gmres = {"tol": tol, "restart": restart, "maxit": maxit, "unknowns": int(sum(r.numel() for r in rhs)),
+             "batched_ms": ms_b, "sequential_ms": ms_s, "iterations_max": int(max(its)),
+             "iterations_total": int(sum(its)), "max_rel_residual": float(max(res_b)),
+             "converged": int(sum(r <= 2 * tol for r in res_b)), "geometries": len(ggeos),
+             "max_rel_diff_vs_sequential": diff,
+             "same_iterations_as_sequential": bool(all(a == c[0] for a, c in zip(its, seq_out)))}
+    gb.close()
+    for geo in ggeos:
+        geo.close()
     return {"workload": f"{len(items)} starfish arrays, {min(nsrc)}-{max(nsrc)} quadrature nodes "
                         f"(log-uniform), {dens[0].shape[0]} densities each, p_qbx 8, p_fmm 15, {kern}",
             "targets_x_densities": ntot, "graph_ms": res["graph"], "sequential_ms": res["sequential"],
             "graph_targets_per_s": ntot / (res["graph"] * 1e-3),
             "sequential_targets_per_s": ntot / (res["sequential"] * 1e-3),
-            "streams": streams, "results_identical": bool(same)}
+            "streams": streams, "results_identical": bool(same), "gmres": gmres}
 
 
 # ---------------------------------------------------------------- GPU arm

@@ -211,6 +211,22 @@ gq_status gq_batch_eval(gq_batch *b, int kernel, int ndens, const double *const 
 /* Streams the autotuner chose for the captured graph (0 before the first gq_batch_eval). */
 gq_status gq_batch_streams(const gq_batch *b, int *streams);
 
+/* Exterior Neumann solves (Sec. 1, as gq_gmres) for every geometry of the
+ * batch at once: restarted GMRES(restart) from mu = 0 on each geometry in
+ * lockstep, where each Arnoldi step applies S' to all geometries by one replay
+ * of the batch's CUDA graph (captured with kernel GQ_SP and one density per
+ * geometry on the first call, autotuned as in gq_batch_eval; a later
+ * gq_batch_eval with other arguments recaptures).  Every geometry must have
+ * the base nodes as targets (as gq_gmres requires), else GQ_ERR_STATE.
+ * rhs[i], mu[i]: device arrays of npanels_i*nb_i doubles (g and the solution).
+ * iters[i], resid[i] (host arrays of ngeom, either may be NULL): iterations and
+ * true relative residual per geometry.  Per geometry the arithmetic is that of
+ * gq_gmres, so the solutions are those of one gq_gmres after another; a
+ * geometry that has converged stays in the graph replays (its vectors are
+ * frozen) until the last one converges or reaches maxit. */
+gq_status gq_batch_gmres(gq_batch *b, const double *const *rhs, double tol, int maxit, int restart,
+                         double *const *mu, int *iters, double *resid);
+
 /* Learned order selection (an extension; the paper picks orders from its
  * bounds, Sec. 4.1, which it reports to overestimate the error by about two
  * orders of magnitude, Sec. 5.1).  A fixed MLP 32 -> 64 -> 32 -> 32 -> 2 with

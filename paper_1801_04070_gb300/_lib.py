@@ -99,6 +99,8 @@ def lib():
             "gq_batch_destroy": (st, [vp]),
             "gq_batch_eval": (st, [vp, i32, i32, C.POINTER(vp), C.POINTER(vp)]),
             "gq_batch_streams": (st, [vp, C.POINTER(i32)]),
+            "gq_batch_gmres": (st, [vp, C.POINTER(vp), C.c_double, i32, i32, C.POINTER(vp), C.POINTER(i32),
+                                    C.POINTER(C.c_double)]),
             "gq_export_root": (st, [vp, vp]),
             "gq_export_boxes": (st, [vp] + [vp] * 9),
             "gq_export_list": (st, [vp, i32, vp, vp]),
@@ -331,6 +333,20 @@ class Batch:
         s = C.c_int()
         self.L.gq_batch_streams(self._b, C.byref(s))
         return s.value
+
+    def gmres(self, rhs, mus, tol=1e-10, maxit=500, restart=50):
+        """Exterior Neumann solves for all geometries at once (gq_batch_gmres):
+        rhs and mus are lists of torch CUDA tensors [npanels*nb].  Returns
+        (iterations, relative residuals) per geometry."""
+        n = len(self.geoms)
+        rp = (C.c_void_p * n)(*[r.data_ptr() for r in rhs])
+        mp = (C.c_void_p * n)(*[m.data_ptr() for m in mus])
+        it = (C.c_int * n)()
+        res = (C.c_double * n)()
+        st = self.L.gq_batch_gmres(self._b, rp, tol, maxit, restart, mp, it, res)
+        if st != 0:
+            raise GigaQBXError(st, self.L.gq_last_error(self._ctx).decode())
+        return list(it), list(res)
 
     def close(self):
         if getattr(self, "_b", None):

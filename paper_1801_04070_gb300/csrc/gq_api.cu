@@ -332,6 +332,23 @@ gq_status gq_batch_eval(gq_batch *b, int kernel, int ndens, const double *const 
     });
 }
 
+gq_status gq_batch_gmres(gq_batch *b, const double *const *rhs, double tol, int maxit, int restart,
+                         double *const *mu, int *iters, double *resid) {
+    if (!b || !rhs || !mu || !(tol > 0) || maxit < 1 || restart < 1 || restart > 1000) return GQ_ERR_INVALID;
+    gq_ctx *ctx = gq_batch_ctx(b);
+    return guarded(ctx, [&] {
+        GQ_CUDA(cudaSetDevice(ctx->device));
+        for (int i = 0; i < gq_batch_size(b); ++i) {
+            gq_geom *g = gq_batch_geom(b, i);
+            GQ_REQUIRE(g->built && g->targets_are_base_nodes, GQ_ERR_STATE,
+                       "gq_batch_gmres needs every geometry built with the base nodes as targets");
+            GQ_REQUIRE(rhs[i] && mu[i] && is_device_ptr(rhs[i]) && is_device_ptr(mu[i]), GQ_ERR_INVALID,
+                       "gq_batch_gmres: rhs and mu must be device arrays");
+        }
+        gq_batch_gmres_impl(b, rhs, tol, maxit, restart, mu, iters, resid);
+    });
+}
+
 gq_status gq_batch_streams(const gq_batch *b, int *streams) {
     if (!b || !streams) return GQ_ERR_INVALID;
     *streams = gq_batch_streams(b);

@@ -231,4 +231,6 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
 }
 
 int gq_batch_streams(const gq_batch *b) { return b->streams; }
+int gq_batch_size(const gq_batch *b) { return (int)b->geoms.size(); }
+gq_geom *gq_batch_geom(const gq_batch *b, int i) { return b->geoms[i]; }
 gq_ctx *gq_batch_ctx(const gq_batch *b) { return b->ctx; }

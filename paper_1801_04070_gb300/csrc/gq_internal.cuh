@@ -221,8 +221,12 @@ void gq_batch_free(gq_batch *b);
 void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out);
 int gq_batch_streams(const gq_batch *b);
 gq_ctx *gq_batch_ctx(const gq_batch *b);
+int gq_batch_size(const gq_batch *b);
+gq_geom *gq_batch_geom(const gq_batch *b, int i);
 int gq_gmres_impl(gq_geom *g, const double *rhs_dev, double tol, int maxit, int restart, double *mu_dev,
                   double *resid);                                                           // gq_gmres.cu
+void gq_batch_gmres_impl(gq_batch *b, const double *const *rhs_dev, double tol, int maxit, int restart,
+                         double *const *mu_dev, int *iters, double *resid);
 
 #define GQ_LAUNCH(ctx, kern, grid, block, smem, ...)                     \
     do {                                                                 \

@@ -75,3 +75,37 @@ def test_requires_base_node_targets():
     geo.build()
     with pytest.raises(GigaQBXError):
         geo.gmres(np.ones(len(g["base_xy"])))
+
+
+def test_batched_gmres_equals_individual_solves():
+    """gq_batch_gmres: four single-curve geometries of different sizes solved
+    in lockstep (each Arnoldi step one graph replay of S' over all of them)
+    give the solutions and iteration counts of one gq_gmres after another."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_04070_gb300 import Batch, Geometry, params_default
+    curves = workloads.random_fourier_curves(2, seed=11)
+    gs = [workloads.starfish_c1(), workloads.unit_circle(24), workloads.discretize([curves[0]], 32),
+          workloads.discretize([curves[1]], 48)]
+    z0 = 0.1 + 0.1j
+    geos, rhs = [], []
+    for g in gs:
+        geo = Geometry(g, params_default(p_qbx=8, p_fmm=20, n_max=32))
+        geo.set_targets(g["base_xy"], np.arange(len(g["base_xy"]), dtype=np.int32))
+        geo.build()
+        geos.append(geo)
+        x = g["base_xy"][:, 0] + 1j * g["base_xy"][:, 1]
+        nrm = g["base_n"][:, 0] + 1j * g["base_n"][:, 1]
+        rhs.append(torch.tensor((nrm * (-1.0 / (x - z0) ** 2)).real, dtype=torch.float64, device="cuda"))
+    mus = [torch.zeros_like(r) for r in rhs]
+    b = Batch(geos)
+    its, res = b.gmres(rhs, mus, tol=1e-10, maxit=200, restart=20)
+    torch.cuda.synchronize()
+    for geo, r, mu, it, rr in zip(geos, rhs, mus, its, res):
+        ref = torch.empty_like(r)
+        _, it1, rr1 = geo.gmres(r, tol=1e-10, maxit=200, restart=20, mu=ref)
+        torch.cuda.synchronize()
+        assert rr <= 2e-10 and it == it1
+        assert torch.abs(mu - ref).max().item() <= 1e-13 * torch.abs(ref).max().item()
+    b.close()
