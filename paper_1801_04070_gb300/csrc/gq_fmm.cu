@@ -57,7 +57,7 @@ struct EvalView {
     const int *lidx[6];
     const double *binom;   // [kBinN][kBinN]
     const int *qc;         // per-centre QBX order (sorted centres) or nullptr: all use Q
-    const double *logt;    // GqLogTable: t[128] then logc[128]
+    const double *logt;    // GqLogTable: t[256] then hl[256]
 };
 
 __device__ __forceinline__ double box_rho(const RootInfo &R, int l) { return ldexp(R.H, -l); }
@@ -271,7 +271,7 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
             if (E.kernel == GQ_D) {
                 acc = cadd(acc, cmul(cmul(st, winv), um));
             } else if (m == 0) {
-                acc.x += st.x * 0.5 * gq_log(n2, E.logt, E.logt + 128);
+                acc.x += st.x * gq_log_half(n2, E.logt, E.logt + 256);
             } else {
                 acc = csub(acc, cscale(um, st.x / m));
             }
@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                                                                 double2 *__restrict__ Qout) {
     __shared__ NearRanges R;
     __shared__ int wsum[kNearThreads / 32];
-    __shared__ double lt[256];
-    for (int i = threadIdx.x; i < 256; i += kNearThreads) lt[i] = E.logt[i];
+    __shared__ double lt[512];
+    for (int i = threadIdx.x; i < 512; i += kNearThreads) lt[i] = E.logt[i];
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
@@ -393,8 +393,14 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                     double wx = y.x - cz.x, wy = y.y - cz.y;
                     double n2 = wx * wx + wy * wy;
                     double inv = gq_rcp(n2);
-                    double2 winv = make_double2(wx * inv, -wy * inv);    // 1/w
-                    double2 u = make_double2(rc * winv.x, rc * winv.y);   // r/w
+                    double2 winv = make_double2(wx * inv, -wy * inv);    // 1/w (D only)
+                    double2 u;                                            // r/w
+                    if (KERNEL == GQ_D) {
+                        u = make_double2(rc * winv.x, rc * winv.y);
+                    } else {
+                        double ir = rc * inv;
+                        u = make_double2(wx * ir, -wy * ir);
+                    }
                     if (KERNEL == GQ_D) {
                         double2 t = cmul(st, winv);
                         acc[0] = cadd(acc[0], t);
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                             acc[m] = cadd(acc[m], t);
                         }
                     } else {
-                        acc[0].x += st.x * (0.5 * gq_log(n2, lt, lt + 128));
+                        acc[0].x += st.x * gq_log_half(n2, lt, lt + 256);
                         double2 t = make_double2(st.x * u.x, st.x * u.y);
                         acc[1] = cadd(acc[1], t);
 #pragma unroll
@@ -438,8 +444,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
                                                                double *__restrict__ pot) {
     __shared__ NearRanges R;
     __shared__ int wsum[kNearThreads / 32];
-    __shared__ double lt[256];
-    for (int i = threadIdx.x; i < 256; i += kNearThreads) lt[i] = E.logt[i];
+    __shared__ double lt[512];
+    for (int i = threadIdx.x; i < 512; i += kNearThreads) lt[i] = E.logt[i];
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
@@ -467,7 +473,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
                     double n2 = wx * wx + wy * wy;
                     if (n2 == 0.0) continue;
                     if (KERNEL == GQ_D) acc += (st.x * wx + st.y * wy) * gq_rcp(n2);
-                    else acc += st.x * (0.5 * gq_log(n2, lt, lt + 128));
+                    else acc += st.x * gq_log_half(n2, lt, lt + 256);
                 }
             }
         }
@@ -518,7 +524,7 @@ __global__ void k_w_centres(EvalView E, int nc, const int *__restrict__ ctr_box_
                 vk = cmul(vk, v);
             }
         }
-        acc[0].x += A0 * 0.5 * gq_log(n2, E.logt, E.logt + 128) + sum.x;
+        acc[0].x += A0 * gq_log_half(n2, E.logt, E.logt + 256) + sum.x;
         acc[0].y += sum.y;
         double2 sm = make_double2(1.0, 0.0);
 #pragma unroll
@@ -570,7 +576,7 @@ __global__ void k_w_points(EvalView E, int npt, const int *__restrict__ pt_owner
         double2 h = A[P];
         for (int k = P - 1; k >= 1; --k) h = cadd(cmul(h, v), A[k]);
         h = cmul(h, v);
-        acc += h.x + A[0].x * 0.5 * gq_log(n2, E.logt, E.logt + 128);
+        acc += h.x + A[0].x * gq_log_half(n2, E.logt, E.logt + 256);
     }
     pot[t] += acc;
 }
@@ -1007,10 +1013,10 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
     __shared__ NearRangesF R;
     __shared__ int wsum[kNearThreads / 32];
     __shared__ float lt[KERNEL == GQ_D ? 1 : 384];
-    __shared__ double lt64[KERNEL == GQ_D ? 1 : 256];
+    __shared__ double lt64[KERNEL == GQ_D ? 1 : 512];
     if (KERNEL != GQ_D) {
         for (int i = threadIdx.x; i < 384; i += kNearThreads) lt[i] = X.logt[i];
-        for (int i = threadIdx.x; i < 256; i += kNearThreads) lt64[i] = E.logt[i];
+        for (int i = threadIdx.x; i < 512; i += kNearThreads) lt64[i] = E.logt[i];
     }
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1073,7 +1079,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
                                 acc64[m] = cadd(acc64[m], t);
                             }
                         } else {
-                            acc64[0].x += sd.x * (0.5 * gq_log(d2, lt64, lt64 + 128));
+                            acc64[0].x += sd.x * gq_log_half(d2, lt64, lt64 + 256);
                             double2 t = make_double2(sd.x * uu.x, sd.x * uu.y);
                             acc64[1] = cadd(acc64[1], t);
 #pragma unroll
@@ -1126,7 +1132,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
         if (KERNEL != GQ_D) {
             double sst = dfl_to_double(acc_str);
             for (int o = 16; o > 0; o >>= 1) sst += __shfl_xor_sync(0xffffffffu, sst, o);
-            dacc[0].x += sst * gq_log(rcd, lt64, lt64 + 128);
+            dacc[0].x += sst * gq_log(rcd, lt64, lt64 + 256);
         }
         if (valid && lane <= QQ) {
             double2 vv = dacc[0];
@@ -1450,7 +1456,7 @@ static void make_tables(gq_geom *g, EvalTables &T) {
     cudaStream_t st = g->ctx->stream;
     GqLogTable LT;
     gq_log_table_host(&LT);
-    T.logt.alloc(256);
+    T.logt.alloc(512);
     GQ_CUDA(cudaMemcpyAsync(T.logt.p, &LT, sizeof(LT), cudaMemcpyHostToDevice, st));
     GqDflLogTable DT;
     gq_dfl_log_table_host(&DT);

@@ -10,54 +10,60 @@
 // ---------------------------------------------------------------- logarithm
 // Table-driven method of P. T. P. Tang, "Table-driven implementation of the
 // logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990:
-// write x = 2^k m with m in [1, 2); let j be the leading 7 fraction bits of m
-// and t_j the FP64 value nearest 1 / (1 + (j + 1/2)/128).  Then
+// write x = 2^k m with m in [1, 2); let j be the leading 8 fraction bits of m
+// and t_j the FP64 value nearest 1 / (1 + (j + 1/2)/256).  Then
 //     log x = k log 2 + log(1/t_j) + log1p(r),   r = m t_j - 1,
-// with r formed by one fused multiply-add (m t_j is exact in the FMA), |r| < 2^-8,
-// and log1p(r) = r - r^2/2 + ... + r^7/7 (the truncation is below 2^-64/8).
-// log(1/t_j) is tabulated to full FP64 precision.
+// with r formed by one fused multiply-add (m t_j is exact in the FMA), |r| < 2^-9,
+// and log1p(r) = r - r^2/2 + ... + r^5/5 (the truncation is below 2^-57).
+// The kernels need log|w| from |w|^2, so the primitive is (1/2) log x, with
+// the halving folded into the table and the coefficients.  The range test
+// looks at the exponent bits only (integer pipe).
 struct GqLogTable {
-    double t[128];       // t_j
-    double logc[128];    // log(1 / t_j)
+    double t[256];       // t_j
+    double hl[256];      // (1/2) log(1 / t_j)
 };
 
 #ifndef __CUDACC_RTC__
 inline void gq_log_table_host(GqLogTable *T) {
-    for (int j = 0; j < 128; ++j) {
-        long double c = 1.0L + (j + 0.5L) / 128.0L;
+    for (int j = 0; j < 256; ++j) {
+        long double c = 1.0L + (j + 0.5L) / 256.0L;
         double t = (double)(1.0L / c);
         T->t[j] = t;
-        T->logc[j] = (double)(-logl((long double)t));
+        T->hl[j] = (double)(-0.5L * logl((long double)t));
     }
 }
 #endif
 
-__device__ __forceinline__ double gq_log(double x, const double *__restrict__ tt, const double *__restrict__ tl) {
-    if (!(x >= 0x1p-1000 && x <= 0x1p1000)) return log(x);   // zero, subnormal, huge, inf, nan
+// (1/2) log x
+__device__ __forceinline__ double gq_log_half(double x, const double *__restrict__ tt, const double *__restrict__ th) {
     long long bits = __double_as_longlong(x);
-    int k = (int)(bits >> 52) - 1023;
-    int j = (int)((bits >> 45) & 0x7f);
+    unsigned long long e = (unsigned long long)bits >> 52;    // biased exponent, sign bit above it
+    if (e - 23ull > 2000ull) return 0.5 * log(x);             // outside [2^-1000, 2^1001): zero, subnormal, huge, inf, nan, x < 0
+    int k = (int)e - 1023;
+    int j = (int)((bits >> 44) & 0xff);
     double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
     double r = fma(m, tt[j], -1.0);
-    double a = fma(r, 1.0 / 7.0, -1.0 / 6.0);
-    a = fma(r, a, 1.0 / 5.0);
+    double a = fma(r, 0.1, -0.125);
+    a = fma(r, a, 1.0 / 6.0);
     a = fma(r, a, -0.25);
-    a = fma(r, a, 1.0 / 3.0);
-    a = fma(r, a, -0.5);
-    a = fma(r, a, 1.0);
+    a = fma(r, a, 0.5);
     double p = r * a;
-    const double ln2 = 0.693147180559945309417232121458176568;
-    return fma((double)k, ln2, tl[j] + p);
+    const double hln2 = 0.346573590279972654708616060729088284;   // (log 2) / 2
+    return fma((double)k, hln2, th[j] + p);
+}
+
+__device__ __forceinline__ double gq_log(double x, const double *__restrict__ tt, const double *__restrict__ th) {
+    return 2.0 * gq_log_half(x, tt, th);
 }
 
 // ---------------------------------------------------------------- reciprocal
 // 1/x from the FP32 reciprocal of x (relative error < 2^-23) refined by two
 // Newton steps y <- y + y (1 - x y), each squaring the relative error, so the
-// result is within about one unit in the last place.  Outside [2^-120, 2^120]
-// the library division is used.
+// result is within about one unit in the last place.  Outside [2^-120, 2^121)
+// (tested on the exponent bits) the library division is used.
 __device__ __forceinline__ double gq_rcp(double x) {
-    double ax = fabs(x);
-    if (!(ax >= 0x1p-120 && ax <= 0x1p120)) return 1.0 / x;
+    unsigned long long ex = ((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff;
+    if (ex - 903ull > 240ull) return 1.0 / x;                 // |x| outside [2^-120, 2^121)
     double y = (double)__frcp_rn(__double2float_rn(x));
     double e = fma(-x, y, 1.0);
     y = fma(y, e, y);
