@@ -2,6 +2,9 @@
 // target-confinement quadtree, as CSR arrays over boxes, built by a count
 // pass, a prefix scan and a fill pass that share one enumeration routine.
 //
+// Same-level neighbours come from a 5x5 window of box indices per box, built
+// level by level from the parent's window (no searches).
+//
 // All relations are integer tests on box coordinates measured in units of
 // half a level-30 box: a level-l box has half-width h = 2^(30-l) and centre
 // (2 ix + 1) h.  With d the l-inf distance of two box centres:
@@ -29,12 +32,15 @@ struct TreeView {
     int nlev;
     const int *level_start;
     const uint64_t *bkey;
-    const int *blev, *bix, *biy;
+    const int *blev, *bix, *biy, *bparent;
     const int4 *bchild;
     const int *sub_src, *sub_tgt, *own_tgt;
+    const int *win;   // [nbox][25]: box at (ix + dx, iy + dy) of the same level, dx, dy in [-2, 2], or -1
     int64_t tn, td;
     int demote;
 };
+
+__device__ __forceinline__ int child_q(int4 c, int q) { return q == 0 ? c.x : q == 1 ? c.y : q == 2 ? c.z : c.w; }
 
 struct IBox {
     int l;
@@ -61,18 +67,36 @@ __device__ __forceinline__ bool is_leaf(const TreeView &T, int b) {
     return c.x < 0 && c.y < 0 && c.z < 0 && c.w < 0;
 }
 
-// box index of (l, x, y) or -1
-__device__ int lookup(const TreeView &T, int l, int64_t x, int64_t y) {
-    if (l < 0 || l >= T.nlev) return -1;
-    int64_t side = (int64_t)1 << l;
-    if (x < 0 || y < 0 || x >= side || y >= side) return -1;
-    uint64_t k = gq_morton((uint64_t)x, (uint64_t)y);
-    int lo = T.level_start[l], hi = T.level_start[l + 1];
-    while (lo < hi) {
-        int m = (lo + hi) >> 1;
-        if (T.bkey[m] < k) lo = m + 1; else hi = m;
+// 5x5 windows of same-level boxes, one level at a time from the parent's
+// window: the box at (X, Y) is child (X & 1) + 2 (Y & 1) of the parent-level
+// box at (X >> 1, Y >> 1), which lies in the parent's window.
+__global__ void k_windows(int lstart, int lend, const int *__restrict__ bparent, const int *__restrict__ bix,
+                          const int *__restrict__ biy, const int4 *__restrict__ bchild, int *__restrict__ win) {
+    int b = lstart + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= lend) return;
+    int p = bparent[b];
+    int x = bix[b], y = biy[b];
+    int *w = win + (size_t)b * 25;
+    if (p < 0) {
+        for (int i = 0; i < 25; ++i) w[i] = -1;
+        w[12] = b;
+        return;
     }
-    return (lo < T.level_start[l + 1] && T.bkey[lo] == k) ? lo : -1;
+    const int *pw = win + (size_t)p * 25;
+    int px = x >> 1, py = y >> 1;
+    for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+            int X = x + dx, Y = y + dy, d = -1;
+            if (X >= 0 && Y >= 0) {
+                int q = pw[((Y >> 1) - py + 2) * 5 + ((X >> 1) - px + 2)];
+                if (q >= 0) d = child_q(bchild[q], (X & 1) | ((Y & 1) << 1));
+            }
+            w[(dy + 2) * 5 + dx + 2] = d;
+        }
+}
+
+__device__ __forceinline__ int wlook(const TreeView &T, int b, int dx, int dy) {
+    return T.win[(size_t)b * 25 + (dy + 2) * 5 + dx + 2];
 }
 
 enum { LU = 0, LV = 1, LWC = 2, LWF = 3, LXC = 4, LXF = 5 };
@@ -154,13 +178,20 @@ __device__ void enumerate(const TreeView &T, int b, Emitter &E, int *err) {
     int stk[kStack];
     int sp = 0;
 
+    // ancestors of b by level: anc[m] is the level-m box containing b
+    int anc[GQ_KEYBITS + 1];
+    anc[l] = b;
+    for (int m = l; m > 0; --m) anc[m - 1] = T.bparent[anc[m]];
+
     // ---- List 2: children of the 2-colleagues of parent(b), 2-well-separated from b
     if (l >= 1) {
         int64_t px = B.x >> 1, py = B.y >> 1;
         for (int64_t jy = 2 * (py - 2); jy <= 2 * (py + 2) + 1; ++jy)
             for (int64_t jx = 2 * (px - 2); jx <= 2 * (px + 2) + 1; ++jx) {
                 if (i64abs(jx - B.x) <= 2 && i64abs(jy - B.y) <= 2) continue;
-                int d = lookup(T, l, jx, jy);
+                if (jx < 0 || jy < 0) continue;
+                int q = wlook(T, anc[l - 1], (int)((jx >> 1) - px), (int)((jy >> 1) - py));
+                int d = q >= 0 ? child_q(T.bchild[q], (int)((jx & 1) | ((jy & 1) << 1))) : -1;
                 if (d >= 0 && T.sub_src[d] > 0) E.emit(LV, d);
             }
     }
@@ -172,11 +203,10 @@ __device__ void enumerate(const TreeView &T, int b, Emitter &E, int *err) {
         if (*err) return;
         // ---- List 1 (b): coarser or same-level leaves adjacent to b
         for (int m = 0; m <= l; ++m) {
-            int64_t ax = B.x >> (l - m), ay = B.y >> (l - m);
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
                     if (!dx && !dy) continue;
-                    int d = lookup(T, m, ax + dx, ay + dy);
+                    int d = wlook(T, anc[m], dx, dy);
                     if (d < 0 || !is_leaf(T, d) || T.sub_src[d] == 0) continue;
                     if (adjacent(ibox(T, d), B)) E.emit(LU, d);
                 }
@@ -186,7 +216,7 @@ __device__ void enumerate(const TreeView &T, int b, Emitter &E, int *err) {
     for (int dy = -2; dy <= 2; ++dy)
         for (int dx = -2; dx <= 2; ++dx) {
             if (!dx && !dy) continue;
-            int t = lookup(T, l, B.x + dx, B.y + dy);
+            int t = wlook(T, b, dx, dy);
             if (!tb || t < 0 || is_leaf(T, t) || T.sub_src[t] == 0) continue;
             push_children(T, t, M_COLL, stk, sp, err);
             drain(T, B, stk, sp, E, err);
@@ -195,11 +225,10 @@ __device__ void enumerate(const TreeView &T, int b, Emitter &E, int *err) {
 
     // ---- List 4 close / far: source leaves that are 2-colleagues of b or of an ancestor
     for (int m = 0; m <= l; ++m) {
-        IBox A{m, B.x >> (l - m), B.y >> (l - m)};
         for (int dy = -2; dy <= 2; ++dy)
             for (int dx = -2; dx <= 2; ++dx) {
                 if (!dx && !dy) continue;
-                int d = lookup(T, m, A.x + dx, A.y + dy);
+                int d = wlook(T, anc[m], dx, dy);
                 if (d < 0 || !is_leaf(T, d) || T.sub_src[d] == 0) continue;
                 IBox D = ibox(T, d);
                 bool in_upto_l = false, in_upto_lm1 = false, in_b = false;
@@ -265,6 +294,7 @@ void gq_build_lists(gq_geom *g) {
     T.bix = g->bix.p;
     T.biy = g->biy.p;
     T.bchild = g->bchild.p;
+    T.bparent = g->bparent.p;
     T.sub_src = g->sub_src.p;
     T.sub_tgt = g->sub_tgt.p;
     T.own_tgt = g->own_tgt.p;
@@ -272,6 +302,14 @@ void gq_build_lists(gq_geom *g) {
     T.td = g->prm.tf_den;
     T.demote = g->prm.w3_demote;
     int nbox = g->nbox;
+    dbuf<int> win;
+    win.alloc((size_t)nbox * 25);
+    for (int l = 0; l < g->nlev; ++l) {
+        int s0 = g->level_start_h[l], s1 = g->level_start_h[l + 1];
+        GQ_LAUNCH(ctx, k_windows, gq_blocks(s1 - s0, kT), kT, 0, s0, s1, (const int *)g->bparent.p,
+                  (const int *)g->bix.p, (const int *)g->biy.p, (const int4 *)g->bchild.p, win.p);
+    }
+    T.win = win.p;
     dbuf<int> cnt[6], err, tmp;
     for (int i = 0; i < 6; ++i) {
         cnt[i].alloc(nbox);
@@ -284,13 +322,15 @@ void gq_build_lists(gq_geom *g) {
               (const int *)nullptr, (const int *)nullptr, (const int *)nullptr, (const int *)nullptr, (int *)nullptr,
               (int *)nullptr, (int *)nullptr, (int *)nullptr, (int *)nullptr, (int *)nullptr, cnt[0].p, cnt[1].p,
               cnt[2].p, cnt[3].p, cnt[4].p, cnt[5].p, err.p);
+    int tot[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < 6; ++i) {
         gq_exclusive_scan(ctx, cnt[i].p, g->list_off[i].p, nbox, tmp.p);
-        int tot = 0;
-        GQ_CUDA(cudaMemcpyAsync(&tot, g->list_off[i].p + nbox, sizeof(int), cudaMemcpyDeviceToHost, st));
-        GQ_CUDA(cudaStreamSynchronize(st));
-        g->list_size[i] = tot;
-        g->list_idx[i].alloc(tot);
+        GQ_CUDA(cudaMemcpyAsync(&tot[i], g->list_off[i].p + nbox, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    GQ_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < 6; ++i) {
+        g->list_size[i] = tot[i];
+        g->list_idx[i].alloc(tot[i]);
     }
     GQ_LAUNCH(ctx, k_lists, gq_blocks(nbox, kT), kT, 0, T, nbox, 1, (const int *)g->list_off[0].p,
               (const int *)g->list_off[1].p, (const int *)g->list_off[2].p, (const int *)g->list_off[3].p,

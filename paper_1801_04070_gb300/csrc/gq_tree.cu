@@ -122,7 +122,8 @@ __global__ void k_cell_floats(int n, const int *__restrict__ items, const double
     if (k >= n) return;
     int c = items[k];
     double lim = slack * c_r[c] * 1.001 + delta;
-    cf[k] = make_float4((float)c_xy[2 * c], (float)c_xy[2 * c + 1], __double2float_ru(lim * lim * 1.001), 0.0f);
+    cf[k] = make_float4((float)c_xy[2 * c], (float)c_xy[2 * c + 1], __double2float_ru(lim * lim * 1.001),
+                        (float)c_r[c]);
 }
 
 __global__ void k_cell_bounds(int n, const uint32_t *__restrict__ key, int *__restrict__ start, int *__restrict__ end) {
@@ -140,8 +141,8 @@ __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int
                             const double *__restrict__ c_xy, const double *__restrict__ c_r,
                             const int *__restrict__ cell_items, const float4 *__restrict__ cell_f,
                             const int *__restrict__ cstart, const int *__restrict__ cend, double x0, double y0,
-                            double cell, int ncx, int ncy, double slack2, int have_grid, int *__restrict__ kind,
-                            int *__restrict__ ctr, int *__restrict__ is_pt) {
+                            double cell, int ncx, int ncy, double slack2, float delta, int have_grid,
+                            int *__restrict__ kind, int *__restrict__ ctr, int *__restrict__ is_pt) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     if (tgt_on[t] >= 0) {
@@ -152,6 +153,7 @@ __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int
     float txf = (float)tx, tyf = (float)ty;
     int best = -1;
     double bestk = INFINITY;
+    float sbest = INFINITY;   // about sqrt(bestk), for the float bound below
     double fgx = floor((tx - x0) / cell), fgy = floor((ty - y0) / cell);
     if (have_grid && fgx >= -1 && fgx <= ncx && fgy >= -1 && fgy <= ncy) {
         int gx = (int)fgx, gy = (int)fgy;
@@ -163,12 +165,21 @@ __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int
                 for (int k = cstart[cid]; k < cend[cid]; ++k) {
                     float4 f = cell_f[k];
                     float fx = txf - f.x, fy = tyf - f.y;
-                    if (fx * fx + fy * fy > f.z) continue;     // cannot pass the exact test below
+                    float d2f = fx * fx + fy * fy;
+                    if (d2f > f.z) continue;     // cannot pass the slack test
+                    // nor reach the best key so far: |t - c| <= sqrt(bestk) r must hold, and
+                    // the float distance exceeds the exact one by at most delta
+                    float lim = fmaf(sbest, f.w * 1.00002f, delta);
+                    if (d2f > lim * lim * 1.00002f) continue;
                     int c = cell_items[k];
                     double dx = tx - c_xy[2 * c], dy = ty - c_xy[2 * c + 1];
                     double d2 = dx * dx + dy * dy;
                     double key = d2 / (c_r[c] * c_r[c]);
-                    if (key < bestk || (key == bestk && c < best)) { bestk = key; best = c; }
+                    if (key < bestk || (key == bestk && c < best)) {
+                        bestk = key;
+                        best = c;
+                        sbest = sqrtf(__double2float_ru(key)) * 1.00001f;
+                    }
                 }
             }
         }
@@ -498,6 +509,7 @@ static void associate(gq_geom *g) {
         ncy = (int)fy;
     }
     long long ncell = (long long)ncx * ncy;
+    double delta_assoc = 0.0;
     dbuf<uint32_t> ckey;
     dbuf<int> cval, cstart, cend;
     dbuf<float4> cf;
@@ -519,14 +531,15 @@ static void associate(gq_geom *g) {
         // distance by at most 3 X 2^-24; searched targets lie within two cells of the centres
         double X = fmax(fmax(fabs(ce.x0), fabs(ce.x1)), fmax(fabs(ce.y0), fabs(ce.y1))) + 2.0 * cell;
         double delta = 16.0 * X * 0x1p-24;
+        delta_assoc = delta;
         GQ_LAUNCH(ctx, k_cell_floats, gq_blocks(nc, kT), kT, 0, nc, (const int *)cval.p, (const double *)g->c_xy,
                   (const double *)g->c_r, slack, delta, cf.p);
     }
     if (nt > 0)
         GQ_LAUNCH(ctx, k_associate, gq_blocks(nt, kT), kT, 0, nt, (const double *)g->tgt_xy, (const int *)g->tgt_on,
                   (const double *)g->c_xy, (const double *)g->c_r, (const int *)cval.p, (const float4 *)cf.p,
-                  (const int *)cstart.p, (const int *)cend.p, ce.x0, ce.y0, cell, ncx, ncy, slack * slack, have_grid,
-                  g->t_kind.p,
+                  (const int *)cstart.p, (const int *)cend.p, ce.x0, ce.y0, cell, ncx, ncy, slack * slack,
+                  (float)(delta_assoc * 1.001), have_grid, g->t_kind.p,
                   g->t_ctr.p, is_pt.p);
     g->npt = compact_flags(g, is_pt.p, nt, g->pt_tgt);
 }
