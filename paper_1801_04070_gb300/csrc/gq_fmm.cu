@@ -103,13 +103,16 @@ __global__ void k_strengths(int nsrc, int nu, int nb, const int *__restrict__ sr
 }
 
 // ------------------------------------------------------------------ Stage 2: P2M
-// One warp per source leaf; lanes stride over its sources and keep all p+1
-// coefficients in registers (PM >= p, guarded unrolled loops); a warp
-// reduction sums the lanes.  S: A_0 = sum q, A_k = -(1/k) sum q u^k;
-// D: A_k = -(1/rho) sum d u^(k-1), u = (y - z_b)/rho.
+// A group of kP2MG lanes per source leaf; the lanes stride over its sources
+// and keep all p+1 coefficients in registers (PM >= p, guarded unrolled
+// loops); a butterfly inside the group sums them.  S: A_0 = sum q,
+// A_k = -(1/k) sum q u^k; D: A_k = -(1/rho) sum d u^(k-1), u = (y - z_b)/rho.
+constexpr int kP2MG = 4;
+
 template <int PM>
 __global__ void k_p2m(EvalView E, int nwork, const int *__restrict__ work, double2 *__restrict__ M) {
-    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) / kP2MG, lane = threadIdx.x % kP2MG;
+    // whole groups leave together; the shuffles below stay inside a group
     if (wid >= nwork) return;
     int b = work[wid];
     int l = E.blev[b], P = E.P;
@@ -118,7 +121,7 @@ __global__ void k_p2m(EvalView E, int nwork, const int *__restrict__ work, doubl
     double2 acc[PM + 1];
 #pragma unroll
     for (int k = 0; k <= PM; ++k) acc[k] = make_double2(0.0, 0.0);
-    for (int s = E.src_beg[b] + lane; s < E.src_end[b]; s += 32) {
+    for (int s = E.src_beg[b] + lane; s < E.src_end[b]; s += kP2MG) {
         double2 y = E.s_xy[s], st = E.str[s];
         double2 u = make_double2((y.x - zc.x) * irho, (y.y - zc.y) * irho);
         if (E.kernel == GQ_D) {
@@ -142,18 +145,19 @@ __global__ void k_p2m(EvalView E, int nwork, const int *__restrict__ work, doubl
                 }
         }
     }
+    const unsigned gmask = ((1u << kP2MG) - 1u) << (threadIdx.x & 31 & ~(kP2MG - 1));
 #pragma unroll
     for (int k = 0; k <= PM; ++k)
         if (k <= P)
-            for (int o = 16; o > 0; o >>= 1) acc[k] = cadd(acc[k], shfl2_xor(acc[k], o));
-    double2 v = acc[0];
+            for (int o = kP2MG / 2; o > 0; o >>= 1)
+                acc[k] = cadd(acc[k], make_double2(__shfl_xor_sync(gmask, acc[k].x, o), __shfl_xor_sync(gmask, acc[k].y, o)));
 #pragma unroll
-    for (int k = 1; k <= PM; ++k)
-        if (lane == k) v = acc[k];
-    if (lane <= P) {
-        if (lane >= 1) v = E.kernel == GQ_D ? make_double2(-v.x, -v.y) : cscale(v, -1.0 / lane);
-        M[(size_t)b * (P + 1) + lane] = v;
-    }
+    for (int k = 0; k <= PM; ++k)
+        if (k <= P && k % kP2MG == lane) {
+            double2 v = acc[k];
+            if (k >= 1) v = E.kernel == GQ_D ? make_double2(-v.x, -v.y) : cscale(v, -1.0 / k);
+            M[(size_t)b * (P + 1) + k] = v;
+        }
 }
 
 // ------------------------------------------------------------------ Stage 2: M2M, one thread per (parent, m)
@@ -191,6 +195,60 @@ __global__ void k_m2m(EvalView E, int lstart, int lend, double2 *__restrict__ M)
         acc = cadd(acc, s);
     }
     M[(size_t)b * P1 + m] = acc;
+}
+
+// M2M and L2L with the translation matrices tabulated: with box-scaled
+// coefficients the child offsets (z_c - z_p)/rho_p are the four numbers
+// eta_q = (+-1 +- i)/2 at every level, so each translation is a fixed lower
+// (M2M) or upper (L2L) triangular complex matrix per quadrant q:
+//   M2M  T_q[m][0] = -eta_q^m / m,  T_q[m][k] = C(m-1, k-1) 2^-k eta_q^(m-k)  (1 <= k <= m)
+//   L2L  U_q[m][k] = 2^-m C(k, m) eta_q^(k-m)                                 (k >= m)
+// applied as complex multiply-adds (four FMAs each).
+constexpr int kTN = GQ_MAX_PFMM + 1;
+
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+__global__ void k_m2m_t(EvalView E, int lstart, int lend, const double2 *__restrict__ T, double2 *__restrict__ M) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int P1 = E.P + 1;
+    int b = lstart + (int)(t / P1), m = (int)(t % P1);
+    if (b >= lend) return;
+    int4 c4 = E.bchild[b];
+    int ch[4] = {c4.x, c4.y, c4.z, c4.w};
+    if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;  // leaf
+    if (E.sub_src[b] == 0) return;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int q = 0; q < 4; ++q) {
+        int c = ch[q];
+        if (c < 0 || E.sub_src[c] == 0) continue;
+        const double2 *A = M + (size_t)c * P1;
+        if (m == 0) {
+            acc = cadd(acc, A[0]);
+            continue;
+        }
+        const double2 *Tq = T + ((size_t)q * kTN + m) * kTN;
+        double2 sacc = cscale(__ldg(&Tq[0]), A[0].x);
+        for (int k = 1; k <= m; ++k) sacc = cfma(__ldg(&Tq[k]), A[k], sacc);
+        acc = cadd(acc, sacc);
+    }
+    M[(size_t)b * P1 + m] = acc;
+}
+
+__global__ void k_l2l_t(EvalView E, int lstart, int lend, const double2 *__restrict__ U, double2 *__restrict__ L) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int P1 = E.P + 1;
+    int c = lstart + (int)(t / P1), m = (int)(t % P1);
+    if (c >= lend || E.sub_tgt[c] == 0) return;
+    int p = E.bparent[c];
+    int q = (E.bix[c] & 1) | ((E.biy[c] & 1) << 1);
+    const double2 *B = L + (size_t)p * P1;
+    const double2 *Uq = U + ((size_t)q * kTN + m) * kTN;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = m; k <= E.P; ++k) acc = cfma(__ldg(&Uq[k]), B[k], acc);
+    double2 *dst = L + (size_t)c * P1 + m;
+    *dst = cadd(*dst, acc);
 }
 
 // ------------------------------------------------------------------ Stage 4: M2L over List 2
@@ -354,8 +412,50 @@ __device__ void load_ranges(const EvalView &E, int b, int e0, int ne, NearRanges
     __syncthreads();
 }
 
+// Lanes per centre in the mixed-precision centre kernels (a warp holds
+// 32/kNearG centres of one box; a short butterfly sums a group).
+constexpr int kNearG = 4;
+
+// Warp reduce-scatter of NV values per lane: at each of the five butterfly
+// steps a lane keeps one half of its values, sends the other half to its
+// partner and adds what it receives, so a warp spends about NV adds instead of
+// 5 NV.  Afterwards lane L holds the warp sums of the original entries
+// base .. base + cnt - 1 in v[0 .. cnt) (cnt may be 0; for NV <= 32 it is 0 or 1).
+template <int N, int O, class V, class Add, class Shfl>
+__device__ __forceinline__ void rs_step(V *v, int lane, V zero, Add add, Shfl shfl, int &base, int &cnt) {
+    constexpr int H = (N + 1) / 2;
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        V x = v[i], y = (i + H < N) ? v[i + H < N ? i + H : 0] : zero;
+        V send = up ? x : y, keep = up ? y : x;
+        v[i] = add(keep, shfl(send, O));
+    }
+    if (up) {
+        base += H;
+        cnt -= H;
+    } else if (cnt > H) {
+        cnt = H;
+    }
+}
+
+template <int NV, class V, class Add, class Shfl>
+__device__ __forceinline__ void warp_reduce_scatter(V (&v)[NV], V zero, int lane, Add add, Shfl shfl, int &base,
+                                                    int &cnt) {
+    constexpr int H1 = (NV + 1) / 2, H2 = (H1 + 1) / 2, H3 = (H2 + 1) / 2, H4 = (H3 + 1) / 2;
+    base = 0;
+    cnt = NV;
+    rs_step<NV, 16>(v, lane, zero, add, shfl, base, cnt);
+    rs_step<H1, 8>(v, lane, zero, add, shfl, base, cnt);
+    rs_step<H2, 4>(v, lane, zero, add, shfl, base, cnt);
+    rs_step<H3, 2>(v, lane, zero, add, shfl, base, cnt);
+    rs_step<H4, 1>(v, lane, zero, add, shfl, base, cnt);
+    if (cnt < 0) cnt = 0;
+}
+
 // QBX coefficients at centres: S: Q_0 = sum q log|w|, Q_m = -(1/m) sum q (r/w)^m;
-// D: Q_m = sum (d/w) (r/w)^m, with w = y - c.
+// D: Q_m = sum (d/w) (r/w)^m, with w = y - c.  One warp per centre, lanes
+// stride over the sources; the coefficients are summed by a reduce-scatter.
 template <int QQ, int KERNEL>
 __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int nwork, const int *__restrict__ work,
                                                                 double2 *__restrict__ Qout) {
@@ -424,16 +524,25 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                 }
             }
         }
+        double vals[2 * (QQ + 1)];
 #pragma unroll
-        for (int m = 0; m <= QQ; ++m)
-            for (int o = 16; o > 0; o >>= 1) acc[m] = cadd(acc[m], shfl2_xor(acc[m], o));
-        if (valid && lane <= QQ) {
-            double2 v = acc[0];
+        for (int m = 0; m <= QQ; ++m) {
+            vals[2 * m] = acc[m].x;
+            vals[2 * m + 1] = acc[m].y;
+        }
+        int base, cnt;
+        warp_reduce_scatter(vals, 0.0, lane, [](double a, double x) { return a + x; },
+                            [](double x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }, base, cnt);
+        if (valid) {
+            double *dst = reinterpret_cast<double *>(Qout + (size_t)c * (QQ + 1));
 #pragma unroll
-            for (int m = 1; m <= QQ; ++m)
-                if (lane == m) v = acc[m];
-            if (KERNEL != GQ_D && lane >= 1) v = cscale(v, -1.0 / lane);
-            Qout[(size_t)c * (QQ + 1) + lane] = v;
+            for (int j = 0; j < (2 * (QQ + 1) + 31) / 32; ++j)
+                if (j < cnt) {
+                    int i = base + j, m = i >> 1;
+                    double x = vals[j];
+                    if (KERNEL != GQ_D && m >= 1) x *= -1.0 / m;
+                    dst[i] = x;
+                }
         }
     }
 }
@@ -750,14 +859,14 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
     __shared__ NearRangesF R;
     __shared__ int wsum[kNearThreads / 32];
     int b = work[blockIdx.x];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int sub = threadIdx.x % kNearG, grp = threadIdx.x / kNearG;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
     int cb = E.ctr_beg[b], ce = E.ctr_end[b];
     double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
     bool single = ne <= kNearRanges;
     if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
-    for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
-        int c = c0 + w;
+    for (int c0 = cb; c0 < ce; c0 += kNearThreads / kNearG) {
+        int c = c0 + grp;
         bool valid = c < ce;
         float2 cz = valid ? X.c_rel[c] : make_float2(0.f, 0.f);
         float rc = valid ? X.c_r[c] : 1.f;
@@ -780,7 +889,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
             int T = R.pre[R.n];
             if (valid) {
                 int r = 0;
-                for (int v = lane; v < T; v += 32) {
+                for (int v = sub; v < T; v += kNearG) {
                     while (R.pre[r + 1] <= v) ++r;
                     int s = R.beg[r] + (v - R.pre[r]);
                     float2 y = X.s_rel[s], o = R.off[r], st = X.str[s];
@@ -843,19 +952,20 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
                 }
             }
         }
-        double2 dacc[QQ + 1];
+        // group sums in FP64 (two butterfly steps)
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) {
-            dacc[m] = make_double2((double)acc[m].x + acc64[m].x, (double)acc[m].y + acc64[m].y);
-            for (int o = 16; o > 0; o >>= 1) dacc[m] = cadd(dacc[m], shfl2_xor(dacc[m], o));
+            acc64[m] = make_double2((double)acc[m].x + acc64[m].x, (double)acc[m].y + acc64[m].y);
+            for (int o = kNearG / 2; o > 0; o >>= 1) acc64[m] = cadd(acc64[m], shfl2_xor(acc64[m], o));
         }
-        if (valid && lane <= QQ) {
-            double2 v = dacc[0];
+        if (valid) {
 #pragma unroll
-            for (int m = 1; m <= QQ; ++m)
-                if (lane == m) v = dacc[m];
-            if (KERNEL != GQ_D && lane >= 1) v = cscale(v, -1.0 / lane);
-            Qout[(size_t)c * (QQ + 1) + lane] = v;
+            for (int m = 0; m <= QQ; ++m)
+                if (m % kNearG == sub) {
+                    double2 v = acc64[m];
+                    if (KERNEL != GQ_D && m >= 1) v = cscale(v, -1.0 / m);
+                    Qout[(size_t)c * (QQ + 1) + m] = v;
+                }
         }
     }
 }
@@ -1019,14 +1129,14 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
         for (int i = threadIdx.x; i < 512; i += kNearThreads) lt64[i] = E.logt[i];
     }
     int b = work[blockIdx.x];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int sub = threadIdx.x % kNearG, grp = threadIdx.x / kNearG;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
     int cb = E.ctr_beg[b], ce = E.ctr_end[b];
     double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
     bool single = ne <= kNearRanges;
     if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
-    for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
-        int c = c0 + w;
+    for (int c0 = cb; c0 < ce; c0 += kNearThreads / kNearG) {
+        int c = c0 + grp;
         bool valid = c < ce;
         float4 c4 = valid ? X.c_rel[c] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 r4 = valid ? X.c_r[c] : make_float4(1.f, 0.f, 1.f, 0.f);
@@ -1043,6 +1153,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
             acc64[m] = make_double2(0.0, 0.0);
         }
         dfl acc_log{0.f, 0.f}, acc_str{0.f, 0.f};   // S: sum of st log(|w|^2/r^2), sum of st
+        bool used64 = false;
         for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
             if (!single) {
                 __syncthreads();
@@ -1052,7 +1163,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
             if (valid) {
                 int r = 0, rcur = -1;
                 dfl ex{0.f, 0.f}, ey{0.f, 0.f};   // source-box offset minus the centre
-                for (int v = lane; v < T; v += 32) {
+                for (int v = sub; v < T; v += kNearG) {
                     while (R.pre[r + 1] <= v) ++r;
                     if (r != rcur) {
                         float2 o = R.off[r];
@@ -1065,6 +1176,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
                     dfl wx = dfl_add(dfl{y4.x, y4.y}, ex), wy = dfl_add(dfl{y4.z, y4.w}, ey);
                     dfl n2 = dfl_add(dfl_sqr(wx), dfl_sqr(wy));
                     if (n2.hi < rc2) {
+                        used64 = true;
                         double2 yd = E.s_xy[s], sd = E.str[s];
                         double dx = yd.x - czd.x, dy = yd.y - czd.y;
                         double d2 = dx * dx + dy * dy, dinv = 1.0 / d2;
@@ -1121,26 +1233,44 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
                 }
             }
         }
-        double2 dacc[QQ + 1];
+        // group sums: pairs in the FP32 pipe, the FP64 part only where a lane of the warp used it
+        const bool any64 = __any_sync(0xffffffffu, used64);
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) {
-            dacc[m] = make_double2(dfl_to_double(acc[m].re) + acc64[m].x, dfl_to_double(acc[m].im) + acc64[m].y);
-            if (KERNEL != GQ_D && m == 0)
-                dacc[0].x = 0.5 * dfl_to_double(acc_log) + acc64[0].x;
-            for (int o = 16; o > 0; o >>= 1) dacc[m] = cadd(dacc[m], shfl2_xor(dacc[m], o));
+            acc[m] = dflc{dfl_two_sum(acc[m].re.hi, acc[m].re.lo), dfl_two_sum(acc[m].im.hi, acc[m].im.lo)};
+            for (int o = kNearG / 2; o > 0; o >>= 1) {
+                dflc t{dfl{__shfl_xor_sync(0xffffffffu, acc[m].re.hi, o), __shfl_xor_sync(0xffffffffu, acc[m].re.lo, o)},
+                       dfl{__shfl_xor_sync(0xffffffffu, acc[m].im.hi, o), __shfl_xor_sync(0xffffffffu, acc[m].im.lo, o)}};
+                acc[m] = dflc_add(acc[m], t);
+            }
+            if (any64)
+                for (int o = kNearG / 2; o > 0; o >>= 1) acc64[m] = cadd(acc64[m], shfl2_xor(acc64[m], o));
         }
         if (KERNEL != GQ_D) {
-            double sst = dfl_to_double(acc_str);
-            for (int o = 16; o > 0; o >>= 1) sst += __shfl_xor_sync(0xffffffffu, sst, o);
-            dacc[0].x += sst * gq_log(rcd, lt64, lt64 + 256);
+            acc_log = dfl_two_sum(acc_log.hi, acc_log.lo);
+            acc_str = dfl_two_sum(acc_str.hi, acc_str.lo);
+            for (int o = kNearG / 2; o > 0; o >>= 1) {
+                acc_log = dfl_add(acc_log, dfl{__shfl_xor_sync(0xffffffffu, acc_log.hi, o),
+                                               __shfl_xor_sync(0xffffffffu, acc_log.lo, o)});
+                acc_str = dfl_add(acc_str, dfl{__shfl_xor_sync(0xffffffffu, acc_str.hi, o),
+                                               __shfl_xor_sync(0xffffffffu, acc_str.lo, o)});
+            }
         }
-        if (valid && lane <= QQ) {
-            double2 vv = dacc[0];
+        if (valid) {
 #pragma unroll
-            for (int m = 1; m <= QQ; ++m)
-                if (lane == m) vv = dacc[m];
-            if (KERNEL != GQ_D && lane >= 1) vv = cscale(vv, -1.0 / lane);
-            Qout[(size_t)c * (QQ + 1) + lane] = vv;
+            for (int m = 0; m <= QQ; ++m)
+                if (m % kNearG == sub) {
+                    double2 vv = make_double2(dfl_to_double(acc[m].re) + acc64[m].x,
+                                              dfl_to_double(acc[m].im) + acc64[m].y);
+                    if (KERNEL != GQ_D) {
+                        if (m == 0)
+                            vv.x = 0.5 * dfl_to_double(acc_log) + dfl_to_double(acc_str) * gq_log(rcd, lt64, lt64 + 256) +
+                                   acc64[0].x;
+                        else
+                            vv = cscale(vv, -1.0 / m);
+                    }
+                    Qout[(size_t)c * (QQ + 1) + m] = vv;
+                }
         }
     }
 }
@@ -1416,6 +1546,8 @@ struct EvalTables {
     dbuf<double> binom;      // [64][64]
     dbuf<double2> dtab;      // [121][32] delta^-k
     dbuf<double> logtab;     // [121] log|delta|
+    dbuf<double2> tm2m;      // [4][kTN][kTN] M2M matrices
+    dbuf<double2> tl2l;      // [4][kTN][kTN] L2L matrices
     dbuf<int> tgt_ptpos;     // [nt] target -> sorted point index
 };
 
@@ -1468,6 +1600,43 @@ static void make_tables(gq_geom *g, EvalTables &T) {
     GQ_CUDA(cudaMemcpyAsync(T.binom.p, bn.data(), sizeof(double) * bn.size(), cudaMemcpyHostToDevice, st));
     GQ_CUDA(cudaMemcpyAsync(T.dtab.p, dt.data(), sizeof(double2) * dt.size(), cudaMemcpyHostToDevice, st));
     GQ_CUDA(cudaMemcpyAsync(T.logtab.p, lt.data(), sizeof(double) * lt.size(), cudaMemcpyHostToDevice, st));
+    {
+        // translation matrices for the four child quadrants, in long double
+        std::vector<double2> tm((size_t)4 * kTN * kTN, make_double2(0.0, 0.0)), tl(tm.size(), make_double2(0.0, 0.0));
+        std::vector<long double> C((size_t)(2 * kTN) * (2 * kTN), 0.0L);
+        auto Cb = [&](int n, int k) -> long double & { return C[(size_t)n * (2 * kTN) + k]; };
+        for (int n = 0; n < 2 * kTN; ++n) {
+            Cb(n, 0) = 1.0L;
+            for (int k = 1; k <= n; ++k) Cb(n, k) = Cb(n - 1, k - 1) + (k <= n - 1 ? Cb(n - 1, k) : 0.0L);
+        }
+        for (int q = 0; q < 4; ++q) {
+            long double ex = (q & 1) ? 0.5L : -0.5L, ey = (q & 2) ? 0.5L : -0.5L;
+            std::vector<long double> pr(kTN + 1), pi(kTN + 1);   // eta^j
+            pr[0] = 1.0L;
+            pi[0] = 0.0L;
+            for (int j = 1; j <= kTN; ++j) {
+                pr[j] = pr[j - 1] * ex - pi[j - 1] * ey;
+                pi[j] = pr[j - 1] * ey + pi[j - 1] * ex;
+            }
+            for (int m = 0; m < kTN; ++m)
+                for (int k = 0; k < kTN; ++k) {
+                    size_t i = ((size_t)q * kTN + m) * kTN + k;
+                    if (m >= 1 && k == 0) tm[i] = make_double2((double)(-pr[m] / m), (double)(-pi[m] / m));
+                    if (m >= 1 && k >= 1 && k <= m) {
+                        long double f = Cb(m - 1, k - 1) * ldexpl(1.0L, -k);
+                        tm[i] = make_double2((double)(f * pr[m - k]), (double)(f * pi[m - k]));
+                    }
+                    if (k >= m) {
+                        long double f = Cb(k, m) * ldexpl(1.0L, -m);
+                        tl[i] = make_double2((double)(f * pr[k - m]), (double)(f * pi[k - m]));
+                    }
+                }
+        }
+        T.tm2m.alloc(tm.size());
+        T.tl2l.alloc(tl.size());
+        GQ_CUDA(cudaMemcpyAsync(T.tm2m.p, tm.data(), sizeof(double2) * tm.size(), cudaMemcpyHostToDevice, st));
+        GQ_CUDA(cudaMemcpyAsync(T.tl2l.p, tl.data(), sizeof(double2) * tl.size(), cudaMemcpyHostToDevice, st));
+    }
     T.tgt_ptpos.alloc(g->nt);
     if (g->npt) GQ_LAUNCH(g->ctx, k_tgt_ptpos, gq_blocks(g->npt, 256), 256, 0, g->npt, (const int *)g->pt_perm.p, T.tgt_ptpos.p);
     GQ_CUDA(cudaStreamSynchronize(st));
@@ -1656,12 +1825,13 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         auto k8 = k_p2m<8>;
         auto k16 = k_p2m<16>;
         auto k32 = k_p2m<GQ_MAX_PFMM>;
-        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * 32, 128), 128, 0,
+        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * kP2MG, 128), 128, 0,
                   E, g->n_leaf_src, (const int *)g->leaf_src_boxes, g->M.p);
     }
     for (int l = g->nlev - 2; l >= 0; --l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_m2m, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->M.p);
+        GQ_LAUNCH(ctx, k_m2m_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, (const double2 *)T.tm2m,
+                  g->M.p);
     }
     mark(S_M2M, st);
     // Stage 4
@@ -1684,7 +1854,8 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     // Stage 7
     for (int l = 1; l < g->nlev; ++l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_l2l, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, g->L.p);
+        GQ_LAUNCH(ctx, k_l2l_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, (const double2 *)T.tl2l,
+                  g->L.p);
     }
     if (f32)
         GQ_LAUNCH(ctx, k_to_float2, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
@@ -1903,7 +2074,7 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
         auto k8 = k_p2m<8>;
         auto k16 = k_p2m<16>;
         auto k32 = k_p2m<GQ_MAX_PFMM>;
-        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * 32, 128), 128, 0,
+        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * kP2MG, 128), 128, 0,
                   E, g->n_leaf_src, (const int *)g->leaf_src_boxes, M);
     }
     for (int l = g->nlev - 2; l >= 0; --l) {

@@ -14,6 +14,12 @@
 #include <algorithm>
 #include <memory>
 
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <utility>
+#include <vector>
+
 #include "gq_internal.cuh"
 
 namespace {
@@ -567,11 +573,41 @@ struct LevelBufs {
     int n = 0;
 };
 
+// Optional phase timing of the build (environment variable GQ_BUILD_TIMING set):
+// CUDA events between phases, printed to stderr when the build ends.
+struct PhaseTimer {
+    cudaStream_t st;
+    bool on;
+    std::vector<std::pair<const char *, cudaEvent_t>> ev;
+    explicit PhaseTimer(cudaStream_t s) : st(s), on(getenv("GQ_BUILD_TIMING") != nullptr) { mark("start"); }
+    void mark(const char *name) {
+        if (!on) return;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        cudaEventRecord(e, st);
+        ev.emplace_back(name, e);
+    }
+    ~PhaseTimer() {
+        if (!on || ev.empty()) return;
+        cudaEventSynchronize(ev.back().second);
+        fprintf(stderr, "gq_build phases (ms):");
+        for (size_t i = 1; i < ev.size(); ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[i - 1].second, ev[i].second);
+            fprintf(stderr, " %s %.3f", ev[i].first, ms);
+        }
+        fprintf(stderr, "\n");
+        for (auto &e : ev) cudaEventDestroy(e.second);
+    }
+};
+
 void gq_build_all(gq_geom *g) {
     gq_ctx *ctx = g->ctx;
     cudaStream_t st = ctx->stream;
     GQ_REQUIRE(g->targets_set, GQ_ERR_STATE, "gq_build: targets not set");
+    PhaseTimer pt(st);
     associate(g);
+    pt.mark("associate");
 
     // ---- root and keys
     Ext re = device_extent(g, 1);
@@ -592,6 +628,7 @@ void gq_build_all(gq_geom *g) {
     gq_radix_sort_pairs(ctx, K.p, V.p, N, 2 * GQ_KEYBITS);
     GQ_LAUNCH(ctx, k_gather_int, gq_blocks(N, kT), kT, 0, N, (const int *)V.p, (const int *)elig0.p, elig.p);
 
+    pt.mark("keys_sort");
     // ---- level-by-level subdivision
     std::vector<std::unique_ptr<LevelBufs>> lv;
     lv.emplace_back(new LevelBufs);
@@ -661,6 +698,7 @@ void gq_build_all(gq_geom *g) {
     GQ_CUDA(cudaMemcpyAsync(g->level_start.p, g->level_start_h.data(), sizeof(int) * (g->nlev + 1),
                             cudaMemcpyHostToDevice, st));
 
+    pt.mark("levels");
     // ---- final box arrays
     int nbox = g->nbox;
     g->bkey.alloc(nbox);
@@ -676,6 +714,7 @@ void gq_build_all(gq_geom *g) {
                   g->bparent.p, g->bchild.p);
     }
 
+    pt.mark("box_arrays");
     // ---- per-type arrays
     dbuf<int> pos;
     pos.alloc(N + 1);
@@ -723,6 +762,7 @@ void gq_build_all(gq_geom *g) {
               (const int *)V.p, (const int *)owner.p, (const uint64_t *)K.p, g->nsrc + g->nc, pid_m.p,
               g->pt_owner.p, (uint64_t *)nullptr);
 
+    pt.mark("type_arrays");
     // ---- box ranges and counts
     for (dbuf<int> *a : {&g->src_beg, &g->src_end, &g->ctr_beg, &g->ctr_end, &g->pt_beg, &g->pt_end, &g->ssub_beg,
                          &g->ssub_end, &g->sub_src, &g->sub_tgt, &g->own_tgt}) {
@@ -742,6 +782,7 @@ void gq_build_all(gq_geom *g) {
         GQ_LAUNCH(ctx, k_sub_tgt_level, gq_blocks(e - s, kT), kT, 0, s, e, (const int4 *)g->bchild.p, g->sub_tgt.p);
     }
 
+    pt.mark("ranges");
     // ---- gathered particle data
     g->s_xy.alloc(g->nsrc);
     g->s_w.alloc(g->nsrc);
@@ -758,6 +799,7 @@ void gq_build_all(gq_geom *g) {
     if (g->npt) GQ_LAUNCH(ctx, k_gather_points, gq_blocks(g->npt, kT), kT, 0, g->npt, (const int *)pid_m.p,
               (const int *)g->pt_tgt, (const double *)g->tgt_xy, g->pt_perm.p, g->sp_xy.p);
 
+    pt.mark("gather");
     // ---- work lists
     dbuf<int> bflag;
     bflag.alloc(nbox);
@@ -768,8 +810,10 @@ void gq_build_all(gq_geom *g) {
     GQ_LAUNCH(ctx, k_flag_nonempty, gq_blocks(nbox, kT), kT, 0, nbox, (const int *)g->pt_beg.p, (const int *)g->pt_end.p, bflag.p);
     g->n_pt_boxes = compact_flags(g, bflag.p, nbox, g->pt_boxes);
     GQ_CUDA(cudaStreamSynchronize(st));
+    pt.mark("work_lists");
 
     gq_build_lists(g);
+    pt.mark("lists");
 }
 
 // flags boxes with a nonempty V or X-far list (computed after the lists)
