@@ -412,10 +412,6 @@ __device__ void load_ranges(const EvalView &E, int b, int e0, int ne, NearRanges
     __syncthreads();
 }
 
-// Lanes per centre in the mixed-precision centre kernels (a warp holds
-// 32/kNearG centres of one box; a short butterfly sums a group).
-constexpr int kNearG = 4;
-
 // Warp reduce-scatter of NV values per lane: at each of the five butterfly
 // steps a lane keeps one half of its values, sends the other half to its
 // partner and adds what it receives, so a warp spends about NV adds instead of
@@ -859,14 +855,14 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
     __shared__ NearRangesF R;
     __shared__ int wsum[kNearThreads / 32];
     int b = work[blockIdx.x];
-    int sub = threadIdx.x % kNearG, grp = threadIdx.x / kNearG;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
     int cb = E.ctr_beg[b], ce = E.ctr_end[b];
     double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
     bool single = ne <= kNearRanges;
     if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
-    for (int c0 = cb; c0 < ce; c0 += kNearThreads / kNearG) {
-        int c = c0 + grp;
+    for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
+        int c = c0 + w;
         bool valid = c < ce;
         float2 cz = valid ? X.c_rel[c] : make_float2(0.f, 0.f);
         float rc = valid ? X.c_r[c] : 1.f;
@@ -876,6 +872,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
         double rcd = valid ? E.sc_r[c] : 1.0;
         float2 acc[QQ + 1];
         double2 acc64[QQ + 1];   // sources inside the expansion disk (|r/w| > 1): FP64
+        bool used64 = false;
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) {
             acc[m] = make_float2(0.f, 0.f);
@@ -889,13 +886,14 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
             int T = R.pre[R.n];
             if (valid) {
                 int r = 0;
-                for (int v = sub; v < T; v += kNearG) {
+                for (int v = lane; v < T; v += 32) {
                     while (R.pre[r + 1] <= v) ++r;
                     int s = R.beg[r] + (v - R.pre[r]);
                     float2 y = X.s_rel[s], o = R.off[r], st = X.str[s];
                     float wx = (y.x + o.x) - cz.x, wy = (y.y + o.y) - cz.y;
                     float n2 = wx * wx + wy * wy;
                     if (n2 < rc2) {
+                        used64 = true;
                         // rounding would be amplified by |r/w|^m: take this pair in FP64
                         double2 yd = E.s_xy[s], sd = E.str[s];
                         double dx = yd.x - czd.x, dy = yd.y - czd.y;
@@ -952,19 +950,47 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_f32(EvalView E, M
                 }
             }
         }
-        // group sums in FP64 (two butterfly steps)
+        // warp sums by reduce-scatter in FP32 pairs (exact from the FP32 lane sums);
+        // the FP64 part only where a lane of the warp used it
+        const bool any64 = __any_sync(0xffffffffu, used64);
+        dfl vals[2 * (QQ + 1)];
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) {
-            acc64[m] = make_double2((double)acc[m].x + acc64[m].x, (double)acc[m].y + acc64[m].y);
-            for (int o = kNearG / 2; o > 0; o >>= 1) acc64[m] = cadd(acc64[m], shfl2_xor(acc64[m], o));
+            vals[2 * m] = dfl{acc[m].x, 0.f};
+            vals[2 * m + 1] = dfl{acc[m].y, 0.f};
+        }
+        int base, cnt;
+        warp_reduce_scatter(vals, dfl{0.f, 0.f}, lane, [](dfl a, dfl x) { return dfl_add(a, x); },
+                            [](dfl x, int o) {
+                                return dfl{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+                            },
+                            base, cnt);
+        constexpr int NJ = (2 * (QQ + 1) + 31) / 32;
+        double v64[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) v64[j] = 0.0;
+        if (any64) {
+            double d64[2 * (QQ + 1)];
+#pragma unroll
+            for (int m = 0; m <= QQ; ++m) {
+                d64[2 * m] = acc64[m].x;
+                d64[2 * m + 1] = acc64[m].y;
+            }
+            int b2, c2;
+            warp_reduce_scatter(d64, 0.0, lane, [](double a, double x) { return a + x; },
+                                [](double x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }, b2, c2);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) v64[j] = d64[j];
         }
         if (valid) {
+            double *dst = reinterpret_cast<double *>(Qout + (size_t)c * (QQ + 1));
 #pragma unroll
-            for (int m = 0; m <= QQ; ++m)
-                if (m % kNearG == sub) {
-                    double2 v = acc64[m];
-                    if (KERNEL != GQ_D && m >= 1) v = cscale(v, -1.0 / m);
-                    Qout[(size_t)c * (QQ + 1) + m] = v;
+            for (int j = 0; j < NJ; ++j)
+                if (j < cnt) {
+                    int i = base + j, m = i >> 1;
+                    double x = dfl_to_double(vals[j]) + v64[j];
+                    if (KERNEL != GQ_D && m >= 1) x *= -1.0 / m;
+                    dst[i] = x;
                 }
         }
     }
@@ -1129,14 +1155,14 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
         for (int i = threadIdx.x; i < 512; i += kNearThreads) lt64[i] = E.logt[i];
     }
     int b = work[blockIdx.x];
-    int sub = threadIdx.x % kNearG, grp = threadIdx.x / kNearG;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
     int cb = E.ctr_beg[b], ce = E.ctr_end[b];
     double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
     bool single = ne <= kNearRanges;
     if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
-    for (int c0 = cb; c0 < ce; c0 += kNearThreads / kNearG) {
-        int c = c0 + grp;
+    for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
+        int c = c0 + w;
         bool valid = c < ce;
         float4 c4 = valid ? X.c_rel[c] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 r4 = valid ? X.c_r[c] : make_float4(1.f, 0.f, 1.f, 0.f);
@@ -1163,7 +1189,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
             if (valid) {
                 int r = 0, rcur = -1;
                 dfl ex{0.f, 0.f}, ey{0.f, 0.f};   // source-box offset minus the centre
-                for (int v = sub; v < T; v += kNearG) {
+                for (int v = lane; v < T; v += 32) {
                     while (R.pre[r + 1] <= v) ++r;
                     if (r != rcur) {
                         float2 o = R.off[r];
@@ -1233,43 +1259,53 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
                 }
             }
         }
-        // group sums: pairs in the FP32 pipe, the FP64 part only where a lane of the warp used it
+        // warp sums by reduce-scatter: pairs in the FP32 pipe, the FP64 part only
+        // where a lane of the warp used it.  For S the constant term is folded
+        // first: Q_0 = (1/2) sum st log(|w|^2/r^2) + log r sum st.
         const bool any64 = __any_sync(0xffffffffu, used64);
+        if (KERNEL != GQ_D) {
+            dfl lrc = dfl_log(dfl_sqr(rc), lt, lt + 128, lt + 256);   // log r^2
+            acc[0].re = dfl_add(dfl_mul_f(dfl_two_sum(acc_log.hi, acc_log.lo), 0.5f),
+                                dfl_mul(dfl_two_sum(acc_str.hi, acc_str.lo), dfl{0.5f * lrc.hi, 0.5f * lrc.lo}));
+        }
+        dfl vals[2 * (QQ + 1)];
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) {
-            acc[m] = dflc{dfl_two_sum(acc[m].re.hi, acc[m].re.lo), dfl_two_sum(acc[m].im.hi, acc[m].im.lo)};
-            for (int o = kNearG / 2; o > 0; o >>= 1) {
-                dflc t{dfl{__shfl_xor_sync(0xffffffffu, acc[m].re.hi, o), __shfl_xor_sync(0xffffffffu, acc[m].re.lo, o)},
-                       dfl{__shfl_xor_sync(0xffffffffu, acc[m].im.hi, o), __shfl_xor_sync(0xffffffffu, acc[m].im.lo, o)}};
-                acc[m] = dflc_add(acc[m], t);
-            }
-            if (any64)
-                for (int o = kNearG / 2; o > 0; o >>= 1) acc64[m] = cadd(acc64[m], shfl2_xor(acc64[m], o));
+            vals[2 * m] = dfl_two_sum(acc[m].re.hi, acc[m].re.lo);
+            vals[2 * m + 1] = dfl_two_sum(acc[m].im.hi, acc[m].im.lo);
         }
-        if (KERNEL != GQ_D) {
-            acc_log = dfl_two_sum(acc_log.hi, acc_log.lo);
-            acc_str = dfl_two_sum(acc_str.hi, acc_str.lo);
-            for (int o = kNearG / 2; o > 0; o >>= 1) {
-                acc_log = dfl_add(acc_log, dfl{__shfl_xor_sync(0xffffffffu, acc_log.hi, o),
-                                               __shfl_xor_sync(0xffffffffu, acc_log.lo, o)});
-                acc_str = dfl_add(acc_str, dfl{__shfl_xor_sync(0xffffffffu, acc_str.hi, o),
-                                               __shfl_xor_sync(0xffffffffu, acc_str.lo, o)});
+        int base, cnt;
+        warp_reduce_scatter(vals, dfl{0.f, 0.f}, lane, [](dfl a, dfl x) { return dfl_add(a, x); },
+                            [](dfl x, int o) {
+                                return dfl{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+                            },
+                            base, cnt);
+        constexpr int NJ = (2 * (QQ + 1) + 31) / 32;
+        double v64[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) v64[j] = 0.0;
+        if (any64) {
+            double d64[2 * (QQ + 1)];
+#pragma unroll
+            for (int m = 0; m <= QQ; ++m) {
+                d64[2 * m] = acc64[m].x;
+                d64[2 * m + 1] = acc64[m].y;
             }
+            int b2, c2;
+            warp_reduce_scatter(d64, 0.0, lane, [](double a, double x) { return a + x; },
+                                [](double x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }, b2, c2);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) v64[j] = d64[j];
         }
         if (valid) {
+            double *dst = reinterpret_cast<double *>(Qout + (size_t)c * (QQ + 1));
 #pragma unroll
-            for (int m = 0; m <= QQ; ++m)
-                if (m % kNearG == sub) {
-                    double2 vv = make_double2(dfl_to_double(acc[m].re) + acc64[m].x,
-                                              dfl_to_double(acc[m].im) + acc64[m].y);
-                    if (KERNEL != GQ_D) {
-                        if (m == 0)
-                            vv.x = 0.5 * dfl_to_double(acc_log) + dfl_to_double(acc_str) * gq_log(rcd, lt64, lt64 + 256) +
-                                   acc64[0].x;
-                        else
-                            vv = cscale(vv, -1.0 / m);
-                    }
-                    Qout[(size_t)c * (QQ + 1) + m] = vv;
+            for (int j = 0; j < NJ; ++j)
+                if (j < cnt) {
+                    int i = base + j, m = i >> 1;
+                    double x = dfl_to_double(vals[j]) + v64[j];
+                    if (KERNEL != GQ_D && m >= 1) x *= -1.0 / m;
+                    dst[i] = x;
                 }
         }
     }
