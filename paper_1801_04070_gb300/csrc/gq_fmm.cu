@@ -274,6 +274,7 @@ __global__ void k_m2l(EvalView E, int nwork, const int *__restrict__ work, const
     for (int o = G; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
     int l = E.blev[b], bx = E.bix[b], by = E.biy[b];
     double logrho = log(box_rho(E.R, l));
+    const double ig = g >= 1 ? 1.0 / g : 0.0;   // 1/g, once per lane
     double2 acc = make_double2(0.0, 0.0);
     const double *prow = pasc + (g <= P ? g : 0) * P1;
     for (int i = 0; i < nmax; ++i) {
@@ -296,7 +297,7 @@ __global__ void k_m2l(EvalView E, int nwork, const int *__restrict__ work, const
             acc.x += A0 * (logrho + logtab[off]) + Gm.x;
             acc.y += Gm.y;
         } else if (g <= P) {
-            double2 t = make_double2(Gm.x - A0 / g, Gm.y);
+            double2 t = make_double2(Gm.x - A0 * ig, Gm.y);
             double2 s = (g & 1) ? make_double2(-tk.x, -tk.y) : tk;
             acc = cadd(acc, cmul(s, t));
         }
@@ -317,6 +318,7 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
     int l = E.blev[b];
     double rho = box_rho(E.R, l);
     double2 zc = box_centre(E.R, l, E.bix[b], E.biy[b]);
+    const double im = m >= 1 ? 1.0 / m : 0.0;   // 1/m, once per lane
     double2 acc = make_double2(0.0, 0.0);
     for (int i = beg; i < end; ++i) {
         int d = E.lidx[5][i];
@@ -331,7 +333,7 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
             } else if (m == 0) {
                 acc.x += st.x * gq_log_half(n2, E.logt, E.logt + 256);
             } else {
-                acc = csub(acc, cscale(um, st.x / m));
+                acc = csub(acc, cscale(um, st.x * im));
             }
         }
     }
@@ -644,7 +646,7 @@ __global__ void k_w_centres(EvalView E, int nc, const int *__restrict__ ctr_box_
                         G.x += cc * At[k].x;
                         G.y += cc * At[k].y;
                     }
-                G.x -= A0 / m;
+                G.x -= A0 * (1.0 / m);   // m is a constant here: the reciprocal folds
                 double2 t = cmul(sm, G);
                 if (m & 1) acc[m] = csub(acc[m], t);
                 else acc[m] = cadd(acc[m], t);
