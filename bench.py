@@ -98,6 +98,14 @@ def max_over_ranks(x, world, device=None):
     return float(t.item())
 
 
+def replica_throughput(step_ms, units, world, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    `units` per step; the job time is the slowest rank's total.  Returns
+    (ms per step, units/s over all ranks)."""
+    tot_ms = max_over_ranks(sum(step_ms), world, device)
+    return tot_ms / len(step_ms), world * units * len(step_ms) / (tot_ms * 1e-3)
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -411,9 +419,7 @@ def run_gpu(args, rank, world, local):
     n1 = C.c_int64()
     chk(L.gq_context_launches(ctx, C.byref(n1)))
     launches = int(n1.value - n0.value)
-    tot_ms = max_over_ranks(sum(step_ms), world, dev)
-    ms_step = tot_ms / args.steps
-    value = world * nt * args.steps / (tot_ms * 1e-3)
+    ms_step, value = replica_throughput(step_ms, nt, world, dev)
     stage_ms /= args.steps
 
     # ---- roofline of the dominant kernel (longest stage), FP64 ALU bound
