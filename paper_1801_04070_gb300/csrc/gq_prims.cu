@@ -111,8 +111,9 @@ constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsChunks = 8;                       // 32-element chunks per warp
 constexpr int kRsTile = kRsThreads * kRsChunks;    // 2048 elements per block
-constexpr int kRsBits = 4;
+constexpr int kRsBits = 8;
 constexpr int kRsDigits = 1 << kRsBits;
+static_assert(kRsDigits <= kRsThreads, "one thread per digit in the histogram and prefix steps");
 
 template <class K>
 __global__ void k_rs_hist(const K *__restrict__ keys, long long n, int shift, int nblk, int *__restrict__ hist) {
@@ -137,7 +138,7 @@ __global__ void k_rs_scatter(const K *__restrict__ keys, const int *__restrict__
     __shared__ int wrun[kRsWarps][kRsDigits];
     __shared__ int wpre[kRsWarps][kRsDigits];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane < kRsDigits) wrun[w][lane] = 0;
+    for (int i = lane; i < kRsDigits; i += 32) wrun[w][i] = 0;
     __syncwarp();
     long long base = (long long)blockIdx.x * kRsTile + (long long)w * (32 * kRsChunks);
     int rank[kRsChunks], dig[kRsChunks];
