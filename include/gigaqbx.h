@@ -161,7 +161,10 @@ gq_status gq_geometry_params(const gq_geom *g, gq_params *out);
 
 /* Set the n targets (host or device).  on_surface_node[i] >= 0 marks an
  * on-surface target evaluated by the two centres of that base node and
- * averaged (principal value); -1 marks an off-surface target. */
+ * averaged (principal value); -1 marks an off-surface target.  An entry
+ * outside [-1, npanels*nb) gives GQ_ERR_INVALID and leaves the geometry
+ * without targets (gq_build then fails with GQ_ERR_STATE until a valid
+ * gq_targets_set). */
 gq_status gq_targets_set(gq_geom *g, int n, const double *xy, const int *on_surface_node);
 
 /* Stage 1 and the lists: target association, root box, Morton keys, the

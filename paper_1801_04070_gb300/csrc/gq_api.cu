@@ -41,6 +41,19 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// flags[0]: some on[i] outside [-1, nbase); flags[1]: some on[i] != i
+__global__ void k_check_targets(int n, const int *__restrict__ on, int nbase, int *__restrict__ flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false, notbase = false;
+    if (i < n) {
+        int v = on[i];
+        bad = v < -1 || v >= nbase;
+        notbase = v != i;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&flags[0], 1);
+    if (__any_sync(0xffffffffu, notbase) && (threadIdx.x & 31) == 0) atomicOr(&flags[1], 1);
+}
+
 template <class T>
 void upload(gq_ctx *ctx, dbuf<T> &dst, const T *src, size_t n) {
     GQ_REQUIRE(src != nullptr || n == 0, GQ_ERR_INVALID, "null input array");
@@ -203,17 +216,26 @@ gq_status gq_geometry_params(const gq_geom *g, gq_params *out) {
 gq_status gq_targets_set(gq_geom *g, int n, const double *xy, const int *on_surface_node) {
     if (!g || n < 0 || (n > 0 && (!xy || !on_surface_node))) return GQ_ERR_INVALID;
     return guarded(g->ctx, [&] {
-        std::vector<int> on(n);
-        if (n) GQ_CUDA(cudaMemcpy(on.data(), on_surface_node, sizeof(int) * n, cudaMemcpyDefault));
-        for (int i = 0; i < n; ++i)
-            GQ_REQUIRE(on[i] >= -1 && on[i] < g->nbase, GQ_ERR_INVALID, "on_surface_node out of range");
-        g->nt = n;
-        bool base = n == g->nbase;
-        for (int i = 0; base && i < n; ++i) base = on[i] == i;
-        g->targets_are_base_nodes = base;
         upload(g->ctx, g->tgt_xy, xy, 2 * (size_t)n);
-        upload(g->ctx, g->tgt_on, on.data(), (size_t)n);
+        upload(g->ctx, g->tgt_on, on_surface_node, (size_t)n);
+        // range check and "the base nodes in order" test on the device
+        dbuf<int> flags;
+        flags.alloc(2);
+        GQ_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), g->ctx->stream));
+        if (n) GQ_LAUNCH(g->ctx, k_check_targets, gq_blocks(n, 256), 256, 0, n, (const int *)g->tgt_on.p, g->nbase,
+                         flags.p);
+        int hf[2] = {0, 0};
+        GQ_CUDA(cudaMemcpyAsync(hf, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, g->ctx->stream));
         GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
+        if (hf[0] != 0) {   // the target arrays were replaced: the geometry has no valid targets now
+            g->targets_set = false;
+            g->built = false;
+            g->have_eval = false;
+            gq_tables_release(g);
+            throw gq_error{GQ_ERR_INVALID, "on_surface_node out of range"};
+        }
+        g->nt = n;
+        g->targets_are_base_nodes = n == g->nbase && hf[1] == 0;
         g->targets_set = true;
         g->built = false;
         g->have_eval = false;

@@ -159,10 +159,10 @@ __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int
     float txf = (float)tx, tyf = (float)ty;
     int best = -1;
     double bestk = INFINITY;
-    float sbest = INFINITY;   // about sqrt(bestk), for the float bound below
     double fgx = floor((tx - x0) / cell), fgy = floor((ty - y0) / cell);
     if (have_grid && fgx >= -1 && fgx <= ncx && fgy >= -1 && fgy <= ncy) {
         int gx = (int)fgx, gy = (int)fgy;
+        float sbest = INFINITY;   // bounds sqrt(bestk) from above: candidates beyond cannot reach it
         for (int yy = gy - 1; yy <= gy + 1; ++yy) {
             if (yy < 0 || yy >= ncy) continue;
             for (int xx = gx - 1; xx <= gx + 1; ++xx) {
@@ -173,8 +173,8 @@ __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int
                     float fx = txf - f.x, fy = tyf - f.y;
                     float d2f = fx * fx + fy * fy;
                     if (d2f > f.z) continue;     // cannot pass the slack test
-                    // nor reach the best key so far: |t - c| <= sqrt(bestk) r must hold, and
-                    // the float distance exceeds the exact one by at most delta
+                    // nor reach the best key so far: |t - c| <= sqrt(bestk) r must hold, and the
+                    // float distance exceeds the exact one by at most delta
                     float lim = fmaf(sbest, f.w * 1.00002f, delta);
                     if (d2f > lim * lim * 1.00002f) continue;
                     int c = cell_items[k];
@@ -184,7 +184,7 @@ __global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int
                     if (key < bestk || (key == bestk && c < best)) {
                         bestk = key;
                         best = c;
-                        sbest = sqrtf(__double2float_ru(key)) * 1.00001f;
+                        sbest = fminf(sbest, sqrtf(__double2float_ru(key)) * 1.00001f);
                     }
                 }
             }

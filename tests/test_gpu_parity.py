@@ -173,3 +173,26 @@ def test_repeat_and_alternate(c1_pair, seed):
     b = geo.eval("S", mu)
     assert np.array_equal(a, b)
     assert rel(a, orc.eval("S", mu)) <= TOL
+
+
+def test_invalid_on_surface_index_leaves_no_targets():
+    """An on-surface index outside [-1, nbase) is refused, the geometry then has
+    no targets (build refused) until a valid set is given."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_04070_gb300 import Geometry, GigaQBXError, params_default
+    g = workloads.starfish_c1()
+    geo = Geometry(g, params_default(p_qbx=5, p_fmm=10, n_max=32))
+    on = np.arange(len(g["base_xy"]), dtype=np.int32)
+    bad = on.copy()
+    bad[7] = len(on)
+    with pytest.raises(GigaQBXError):
+        geo.set_targets(g["base_xy"], bad)
+    with pytest.raises(GigaQBXError):
+        geo.build()
+    geo.set_targets(g["base_xy"], on)
+    geo.build()
+    v = geo.eval("S", g["density"])
+    assert np.isfinite(v).all() and len(v) == len(on)
+    geo.close()
