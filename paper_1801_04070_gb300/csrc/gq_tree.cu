@@ -120,6 +120,30 @@ __global__ void k_cell_of_centre(int nc, const double *__restrict__ c_xy, double
     val[c] = c;
 }
 
+// targets in grid-cell order, so that a warp of k_associate walks the same
+// cells and candidate lists: off-surface targets by cell (targets outside the
+// searched grid after them), on-surface targets last
+__global__ void k_cell_of_target(int nt, const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on, double x0,
+                                 double y0, double cell, int ncx, int ncy, uint32_t *__restrict__ key,
+                                 int *__restrict__ val) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    uint32_t ncell = (uint32_t)ncx * (uint32_t)ncy, k;
+    if (tgt_on[t] >= 0) {
+        k = ncell + 1;
+    } else {
+        double fgx = floor((tgt_xy[2 * t] - x0) / cell), fgy = floor((tgt_xy[2 * t + 1] - y0) / cell);
+        if (fgx >= -1 && fgx <= ncx && fgy >= -1 && fgy <= ncy) {
+            int gx = min(max((int)fgx, 0), ncx - 1), gy = min(max((int)fgy, 0), ncy - 1);
+            k = (uint32_t)gy * (uint32_t)ncx + (uint32_t)gx;
+        } else {
+            k = ncell;
+        }
+    }
+    key[t] = k;
+    val[t] = t;
+}
+
 // centres in cell order as float (x, y, threshold): the threshold bounds the
 // squared distance of any centre the exact test could accept
 __global__ void k_cell_floats(int n, const int *__restrict__ items, const double *__restrict__ c_xy,
@@ -143,14 +167,16 @@ __global__ void k_cell_bounds(int n, const uint32_t *__restrict__ key, int *__re
 // On-surface targets use the centre pair of their base node; an off-surface
 // target takes the centre minimising |t-c|^2/r^2 (lowest id on ties) if that
 // ratio is <= slack^2, else it is a point target.
-__global__ void k_associate(int nt, const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on,
+__global__ void k_associate(int nt, const int *__restrict__ order, const double *__restrict__ tgt_xy,
+                            const int *__restrict__ tgt_on,
                             const double *__restrict__ c_xy, const double *__restrict__ c_r,
                             const int *__restrict__ cell_items, const float4 *__restrict__ cell_f,
                             const int *__restrict__ cstart, const int *__restrict__ cend, double x0, double y0,
                             double cell, int ncx, int ncy, double slack2, float delta, int have_grid,
                             int *__restrict__ kind, int *__restrict__ ctr, int *__restrict__ is_pt) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    int t = order ? order[i] : i;
     if (tgt_on[t] >= 0) {
         kind[t] = 2; ctr[t] = 2 * tgt_on[t]; is_pt[t] = 0;
         return;
@@ -541,8 +567,20 @@ static void associate(gq_geom *g) {
         GQ_LAUNCH(ctx, k_cell_floats, gq_blocks(nc, kT), kT, 0, nc, (const int *)cval.p, (const double *)g->c_xy,
                   (const double *)g->c_r, slack, delta, cf.p);
     }
+    dbuf<uint32_t> tkey;
+    dbuf<int> torder;
+    if (have_grid && nt > 0) {
+        tkey.alloc(nt);
+        torder.alloc(nt);
+        GQ_LAUNCH(ctx, k_cell_of_target, gq_blocks(nt, kT), kT, 0, nt, (const double *)g->tgt_xy,
+                  (const int *)g->tgt_on, ce.x0, ce.y0, cell, ncx, ncy, tkey.p, torder.p);
+        int bits = 1;
+        while ((1ll << bits) < ncell + 2) ++bits;
+        gq_radix_sort_pairs32(ctx, tkey.p, torder.p, nt, bits);
+    }
     if (nt > 0)
-        GQ_LAUNCH(ctx, k_associate, gq_blocks(nt, kT), kT, 0, nt, (const double *)g->tgt_xy, (const int *)g->tgt_on,
+        GQ_LAUNCH(ctx, k_associate, gq_blocks(nt, kT), kT, 0, nt, (const int *)torder.p, (const double *)g->tgt_xy,
+                  (const int *)g->tgt_on,
                   (const double *)g->c_xy, (const double *)g->c_r, (const int *)cval.p, (const float4 *)cf.p,
                   (const int *)cstart.p, (const int *)cend.p, ce.x0, ce.y0, cell, ncx, ncy, slack * slack,
                   (float)(delta_assoc * 1.001), have_grid, g->t_kind.p,
