@@ -712,6 +712,60 @@ __global__ void k_l2qbxl(EvalView E, int nc, const int *__restrict__ ctr_box_of,
 }
 
 // L2P: thread per point target
+// L2QBXL by a Taylor shift, one thread per centre: with the box-scaled local
+// expansion sum_k L_k z^k, z = (x - z_b)/rho, and eta = (c - z_b)/rho, the
+// coefficients of the shifted polynomial in zeta = z - eta come from q+1
+// passes of repeated synthetic division (pass i: b_k += eta b_{k+1} for
+// k = p-1 .. i, after which b_i is final), i.e. sum_k C(k, m) L_k eta^(k-m)
+// without binomials; Q_m += b_m (r/rho)^m.  rho is a power of two, so the
+// scalings by 1/rho are exact.
+template <int PM, int QQ>
+__global__ void __launch_bounds__(128) k_l2qbxl_t(EvalView E, int nc, const int *__restrict__ ctr_box_of,
+                                                  const double2 *__restrict__ L, double2 *__restrict__ Qout) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const int P = E.P;
+    int b = ctr_box_of[c];
+    int l = E.blev[b];
+    double irho = ldexp(1.0 / E.R.H, l);
+    double2 zb = box_centre(E.R, l, E.bix[b], E.biy[b]);
+    double2 cz = E.sc_xy[c];
+    double2 eta = make_double2((cz.x - zb.x) * irho, (cz.y - zb.y) * irho);
+    const double2 *B = L + (size_t)b * (P + 1);
+    double2 bk[PM + 1];
+#pragma unroll
+    for (int k = 0; k <= PM; ++k) bk[k] = k <= P ? B[k] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i <= QQ; ++i)
+#pragma unroll
+        for (int k = PM - 1; k >= i; --k)
+            if (k < P) bk[k] = cfma(eta, bk[k + 1], bk[k]);
+    double s = E.sc_r[c] * irho, sm = 1.0;
+    double2 *dst = Qout + (size_t)c * (QQ + 1);
+#pragma unroll
+    for (int m = 0; m <= QQ; ++m) {
+        if (m <= P) dst[m] = cadd(dst[m], cscale(bk[m], sm));
+        sm *= s;
+    }
+}
+
+template <int PM>
+void launch_l2qbxl_t(gq_ctx *ctx, const EvalView &E, int nc, const int *owner, const double2 *L, double2 *Q) {
+    switch (E.Q) {
+#define GQ_CASE(v) case v: GQ_LAUNCH(ctx, (k_l2qbxl_t<PM, v>), gq_blocks(nc, 128), 128, 0, E, nc, owner, L, Q); break;
+        GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
+        GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
+#undef GQ_CASE
+        default: throw gq_error{GQ_ERR_INVALID, "p_qbx out of range"};
+    }
+}
+
+void dispatch_l2qbxl_t(gq_ctx *ctx, const EvalView &E, int nc, const int *owner, const double2 *L, double2 *Q) {
+    if (E.P <= 8) launch_l2qbxl_t<8>(ctx, E, nc, owner, L, Q);
+    else if (E.P <= 16) launch_l2qbxl_t<16>(ctx, E, nc, owner, L, Q);
+    else launch_l2qbxl_t<GQ_MAX_PFMM>(ctx, E, nc, owner, L, Q);
+}
+
 __global__ void k_l2p(EvalView E, int npt, const int *__restrict__ pt_owner, const double2 *__restrict__ L,
                       double *__restrict__ pot) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1927,8 +1981,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     mark(S_WP, st);
     // Stage 8
     if (g->nc)
-        GQ_LAUNCH(ctx, k_l2qbxl, gq_blocks((long long)g->nc * Q1, 128), 128, 0, E, g->nc, (const int *)g->ctr_owner,
-                  (const double2 *)g->L, g->Q.p);
+        dispatch_l2qbxl_t(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->L, g->Q.p);
     if (g->npt)
         GQ_LAUNCH(ctx, k_l2p, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner, (const double2 *)g->L,
                   g->pot.p);
