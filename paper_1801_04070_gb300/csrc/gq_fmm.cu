@@ -503,21 +503,24 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                         double2 t = cmul(st, winv);
                         acc[0] = cadd(acc[0], t);
 #pragma unroll
-                        for (int m = 1; m <= QQ; ++m) {
+                        for (int m = 1; m < QQ; ++m) {
                             if (m > qc) break;
                             t = cmul(t, u);
                             acc[m] = cadd(acc[m], t);
                         }
+                        // last term: a multiply-add into the sum (t is not needed again)
+                        if (qc >= QQ) acc[QQ] = cfma(t, u, acc[QQ]);
                     } else {
                         acc[0].x += st.x * gq_log_half(n2, lt, lt + 256);
                         double2 t = make_double2(st.x * u.x, st.x * u.y);
                         acc[1] = cadd(acc[1], t);
 #pragma unroll
-                        for (int m = 2; m <= QQ; ++m) {
+                        for (int m = 2; m < QQ; ++m) {
                             if (m > qc) break;
                             t = cmul(t, u);
                             acc[m] = cadd(acc[m], t);
                         }
+                        if (QQ >= 2 && qc >= QQ) acc[QQ] = cfma(t, u, acc[QQ]);
                     }
                 }
             }
