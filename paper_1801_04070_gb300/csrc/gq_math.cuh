@@ -57,14 +57,16 @@ __device__ __forceinline__ double gq_log(double x, const double *__restrict__ tt
 }
 
 // ---------------------------------------------------------------- reciprocal
-// 1/x from the FP32 reciprocal of x (relative error < 2^-23) refined by two
-// Newton steps y <- y + y (1 - x y), each squaring the relative error, so the
-// result is within about one unit in the last place.  Outside [2^-120, 2^121)
-// (tested on the exponent bits) the library division is used.
+// 1/x from the hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64,
+// which works on the upper mantissa bits; no conversions through FP32) refined
+// by two Newton steps y <- y + y (1 - x y), each squaring the relative error,
+// so the result is within about one unit in the last place.  Outside
+// [2^-120, 2^121) (tested on the exponent bits) the library division is used.
 __device__ __forceinline__ double gq_rcp(double x) {
     unsigned long long ex = ((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff;
     if (ex - 903ull > 240ull) return 1.0 / x;                 // |x| outside [2^-120, 2^121)
-    double y = (double)__frcp_rn(__double2float_rn(x));
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     double e = fma(-x, y, 1.0);
     y = fma(y, e, y);
     e = fma(-x, y, 1.0);
