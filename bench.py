@@ -444,10 +444,18 @@ def run_gpu(args, rank, world, local):
         tf = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tf):
             traffic = json.load(open(tf)).get(m["name"])
+        # the other measured rates on this GPU: FP32 FMA, and the FP64 tensor cores (an FP64
+        # contraction would belong there only if they beat the FP64 FMA rate)
+        others = {}
+        for what, name in ((1, "fp32_fma"), (2, "fp64_tensor_mma")):
+            v = C.c_double()
+            if L.gq_probe_fma_peak(ctx, what, C.byref(v)) == 0:
+                others[name] = v.value
         roof = {"bound": "alu", "kernel": m["name"], "achieved": achieved, "peak": peak.value,
                 "unit": "TFLOP/s", "frac": achieved / peak.value, "traffic": traffic,
                 "peak_source": peak_src, "units_per_launch": m["units"], "unit_of_work": m["unit"],
-                "flops_per_unit": m["flops_per_unit"], "ms_per_launch": stage_ms[dom]}
+                "flops_per_unit": m["flops_per_unit"], "ms_per_launch": stage_ms[dom],
+                "other_measured_tflops": others}
     stage_report = {STAGE_NAMES[i]: round(float(stage_ms[i]), 4) for i in range(11)}
     for i, m in model.items():
         stage_report[STAGE_NAMES[i] + "_tflops"] = m["units"] * m["flops_per_unit"] / (stage_ms[i] * 1e-3) / 1e12

@@ -333,8 +333,10 @@ gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out);
 
 /* Measurement helper: throughput of a dependent-chain-free FMA loop on the
  * context's device, in TFLOP/s (2 flops per FMA).  what = 0: FP64 FMA,
- * what = 1: FP32 FMA.  Used as the measured peak of the FP64/FP32 roofline;
- * the paper has no counterpart.  Runs about 0.1 s of device work. */
+ * what = 1: FP32 FMA, what = 2: FP64 tensor-core MMA (warp-wide
+ * mma.sync m8n8k4 FP64, 512 flops each).  Used as the measured peak of the
+ * FP64/FP32 roofline and to decide whether a contraction should use the FP64
+ * tensor cores; the paper has no counterpart.  Runs about 0.1 s of device work. */
 gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops);
 
 /* Device memory the library keeps cached for reuse (bytes), and a call that

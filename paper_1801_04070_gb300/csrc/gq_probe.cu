@@ -53,9 +53,62 @@ double run(gq_ctx *ctx) {
     return best;
 }
 
+// FP64 tensor-core rate: warp-wide mma.sync m8n8k4 (D = A B + C, 8x8x4, FP64),
+// kMma independent accumulators per warp so that the latency is hidden.
+constexpr int kMma = 4;
+constexpr int kMmaIters = 2048;
+
+__global__ void k_dmma_loop(double *out, double a0, double b0) {
+    double a = a0 * (double)(threadIdx.x + 1), b = b0;
+    double c[kMma][2];
+#pragma unroll
+    for (int j = 0; j < kMma; ++j) c[j][0] = c[j][1] = 0.0;
+    for (int i = 0; i < kMmaIters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kMma; ++j)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                         : "+d"(c[j][0]), "+d"(c[j][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kMma; ++j) s += c[j][0] + c[j][1];
+    if (s == -1.2345) out[0] = s;   // keeps the loop alive; never true for these inputs
+}
+
+double run_dmma(gq_ctx *ctx) {
+    int dev = ctx->device, sms = 0;
+    GQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    dbuf<double> out;
+    out.alloc(1);
+    const int threads = 256;
+    const int blocks = sms * 8;
+    cudaEvent_t e0, e1;
+    GQ_CUDA(cudaEventCreate(&e0));
+    GQ_CUDA(cudaEventCreate(&e1));
+    GQ_LAUNCH(ctx, k_dmma_loop, blocks, threads, 0, out.p, 1e-3, 1e-7);  // warm-up
+    double best = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+        GQ_CUDA(cudaEventRecord(e0, ctx->stream));
+        GQ_LAUNCH(ctx, k_dmma_loop, blocks, threads, 0, out.p, 1e-3, 1e-7);
+        GQ_CUDA(cudaEventRecord(e1, ctx->stream));
+        GQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        GQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        double flops = 2.0 * 8 * 8 * 4 * (double)kMma * kMmaIters * (threads / 32) * blocks;
+        double tf = flops / (ms * 1e-3) / 1e12;
+        if (tf > best) best = tf;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
 }  // namespace
 
-double gq_probe_fma(gq_ctx *ctx, int what) { return what == 0 ? run<double>(ctx) : run<float>(ctx); }
+double gq_probe_fma(gq_ctx *ctx, int what) {
+    return what == 0 ? run<double>(ctx) : what == 1 ? run<float>(ctx) : run_dmma(ctx);
+}
 
 namespace {
 __global__ void k_probe_math(int fn, int n, const double *__restrict__ x, const double *__restrict__ tab,
