@@ -662,6 +662,85 @@ __global__ void k_w_centres(EvalView E, int nc, const int *__restrict__ ctr_box_
         if (m <= Qn) dst[m] = cadd(dst[m], acc[m]);
 }
 
+// The same M2QBXL with the QBX order a template parameter and the loops
+// exchanged: k outer, m inner, so that At_k = A_k v^k is used as soon as it is
+// formed (no array of p+1 terms) and G_m = sum_k C(m+k-1, k-1) At_k
+// accumulates in q+1 registers; (-r/y)^m carries the sign (-1)^m.
+template <int PM, int QQ>
+__global__ void __launch_bounds__(128) k_w_centres_q(EvalView E, int nc, const int *__restrict__ ctr_box_of,
+                                                     const double2 *__restrict__ M, double2 *__restrict__ Qout) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int b = ctr_box_of[c];
+    int beg = E.loff[3][b], end = E.loff[3][b + 1];
+    if (beg == end) return;
+    const int P = E.P, P1 = P + 1;
+    double2 cz = E.sc_xy[c];
+    double rc = E.sc_r[c];
+    double2 acc[QQ + 1];
+#pragma unroll
+    for (int m = 0; m <= QQ; ++m) acc[m] = make_double2(0.0, 0.0);
+    for (int i = beg; i < end; ++i) {
+        int d = E.lidx[3][i];
+        int l = E.blev[d];
+        double rho = box_rho(E.R, l);
+        double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
+        double2 y = make_double2(cz.x - zd.x, cz.y - zd.y);
+        double n2 = y.x * y.x + y.y * y.y, inv = gq_rcp(n2);
+        double2 yinv = make_double2(y.x * inv, -y.y * inv);
+        double2 v = cscale(yinv, rho), msv = cscale(yinv, -rc);
+        const double2 *A = M + (size_t)d * P1;
+        double A0 = A[0].x;
+        double2 G[QQ + 1];
+#pragma unroll
+        for (int m = 0; m <= QQ; ++m) G[m] = make_double2(0.0, 0.0);
+        double2 vk = v;
+#pragma unroll
+        for (int k = 1; k <= PM; ++k) {
+            if (k <= P) {
+                double2 at = cmul(A[k], vk);
+                G[0] = cadd(G[0], at);
+#pragma unroll
+                for (int m = 1; m <= QQ; ++m) {
+                    double cc = c_pascal[m][k];
+                    G[m].x = fma(cc, at.x, G[m].x);
+                    G[m].y = fma(cc, at.y, G[m].y);
+                }
+                vk = cmul(vk, v);
+            }
+        }
+        acc[0].x += A0 * gq_log_half(n2, E.logt, E.logt + 256) + G[0].x;
+        acc[0].y += G[0].y;
+        double2 sm = make_double2(1.0, 0.0);
+#pragma unroll
+        for (int m = 1; m <= QQ; ++m) {
+            sm = cmul(sm, msv);   // (-r/y)^m
+            G[m].x -= A0 * (1.0 / m);
+            acc[m] = cfma(sm, G[m], acc[m]);
+        }
+    }
+    double2 *dst = Qout + (size_t)c * (QQ + 1);
+#pragma unroll
+    for (int m = 0; m <= QQ; ++m) dst[m] = cadd(dst[m], acc[m]);
+}
+
+template <int PM>
+void launch_w_centres_q(gq_ctx *ctx, const EvalView &E, int nc, const int *owner, const double2 *M, double2 *Q) {
+    switch (E.Q) {
+#define GQ_CASE(v) case v: GQ_LAUNCH(ctx, (k_w_centres_q<PM, v>), gq_blocks(nc, 128), 128, 0, E, nc, owner, M, Q); break;
+        GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
+        GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
+#undef GQ_CASE
+        default: throw gq_error{GQ_ERR_INVALID, "p_qbx out of range"};
+    }
+}
+
+void dispatch_w_centres_q(gq_ctx *ctx, const EvalView &E, int nc, const int *owner, const double2 *M, double2 *Q) {
+    if (E.P <= 8) launch_w_centres_q<8>(ctx, E, nc, owner, M, Q);
+    else if (E.P <= 16) launch_w_centres_q<16>(ctx, E, nc, owner, M, Q);
+    else launch_w_centres_q<GQ_MAX_PFMM>(ctx, E, nc, owner, M, Q);
+}
+
 // M2P, one thread per point target: Phi += A_0 log|z| + sum_k A_k (rho/z)^k,
 // z = t - z_d, by Horner's rule
 __global__ void k_w_points(EvalView E, int npt, const int *__restrict__ pt_owner, const double2 *__restrict__ M,
@@ -1963,11 +2042,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     if (g->nc && split_w) {
         dispatch_w_centres_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, g->Q.p);
     } else if (g->nc) {
-        auto k8 = k_w_centres<8>;
-        auto k16 = k_w_centres<16>;
-        auto k32 = k_w_centres<GQ_MAX_PFMM>;
-        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks(g->nc, 128), 128, 0, E, g->nc,
-                  (const int *)g->ctr_owner, (const double2 *)g->M, g->Q.p);
+        dispatch_w_centres_q(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->M, g->Q.p);
     }
     mark(S_WC, st);
     if (g->npt) {
