@@ -759,11 +759,11 @@ __global__ void k_w_points(EvalView E, int npt, const int *__restrict__ pt_owner
         double rho = box_rho(E.R, l);
         double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
         double2 z = make_double2(tz.x - zd.x, tz.y - zd.y);
-        double n2 = z.x * z.x + z.y * z.y, inv = gq_rcp(n2);
-        double2 v = make_double2(rho * z.x * inv, -rho * z.y * inv);
+        double n2 = z.x * z.x + z.y * z.y, ri = rho * gq_rcp(n2);
+        double2 v = make_double2(z.x * ri, -z.y * ri);
         const double2 *A = M + (size_t)d * P1;
         double2 h = A[P];
-        for (int k = P - 1; k >= 1; --k) h = cadd(cmul(h, v), A[k]);
+        for (int k = P - 1; k >= 1; --k) h = cfma(h, v, A[k]);
         h = cmul(h, v);
         acc += h.x + A[0].x * gq_log_half(n2, E.logt, E.logt + 256);
     }
@@ -860,7 +860,7 @@ __global__ void k_l2p(EvalView E, int npt, const int *__restrict__ pt_owner, con
     double2 zeta = make_double2((tz.x - zb.x) / rho, (tz.y - zb.y) / rho);
     const double2 *B = L + (size_t)b * (E.P + 1);
     double2 h = B[E.P];
-    for (int k = E.P - 1; k >= 0; --k) h = cadd(cmul(h, zeta), B[k]);
+    for (int k = E.P - 1; k >= 0; --k) h = cfma(h, zeta, B[k]);
     pot[t] += h.x;
 }
 
@@ -897,12 +897,12 @@ __global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, 
             int node = tgt_on[t];
             if (node < 0) { sum = nan(""); break; }
             double2 h = cscale(coef(q), (double)q);
-            for (int m = q - 1; m >= 1; --m) h = cadd(cmul(h, zeta), cscale(coef(m), (double)m));
+            for (int m = q - 1; m >= 1; --m) h = cfma(h, zeta, cscale(coef(m), (double)m));
             double2 n = make_double2(base_n[2 * node], base_n[2 * node + 1]);
             sum += -kInv2Pi * cmul(n, h).x / r;
         } else {
             double2 h = coef(q);
-            for (int m = q - 1; m >= 0; --m) h = cadd(cmul(h, zeta), coef(m));
+            for (int m = q - 1; m >= 0; --m) h = cfma(h, zeta, coef(m));
             sum += -kInv2Pi * h.x;
         }
     }
