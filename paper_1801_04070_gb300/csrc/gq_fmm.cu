@@ -299,7 +299,7 @@ __global__ void k_m2l(EvalView E, int nwork, const int *__restrict__ work, const
         } else if (g <= P) {
             double2 t = make_double2(Gm.x - A0 * ig, Gm.y);
             double2 s = (g & 1) ? make_double2(-tk.x, -tk.y) : tk;
-            acc = cadd(acc, cmul(s, t));
+            acc = cfma(s, t, acc);
         }
     }
     if (act && g <= P) {
@@ -329,7 +329,7 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
             double2 winv = make_double2(w.x * inv, -w.y * inv);      // 1/w
             double2 um = lane_powers(cscale(winv, rho), m, 32);      // (rho/w)^m
             if (E.kernel == GQ_D) {
-                acc = cadd(acc, cmul(cmul(st, winv), um));
+                acc = cfma(cmul(st, winv), um, acc);
             } else if (m == 0) {
                 acc.x += st.x * gq_log_half(n2, E.logt, E.logt + 256);
             } else {
