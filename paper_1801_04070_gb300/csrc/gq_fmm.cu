@@ -57,7 +57,7 @@ struct EvalView {
     const int *lidx[6];
     const double *binom;   // [kBinN][kBinN]
     const int *qc;         // per-centre QBX order (sorted centres) or nullptr: all use Q
-    const double *logt;    // GqLogTable: t[256] then hl[256]
+    const double *logt;    // GqLogTable
 };
 
 __device__ __forceinline__ double box_rho(const RootInfo &R, int l) { return ldexp(R.H, -l); }
@@ -331,7 +331,7 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
             if (E.kernel == GQ_D) {
                 acc = cfma(cmul(st, winv), um, acc);
             } else if (m == 0) {
-                acc.x += st.x * gq_log_half(n2, E.logt, E.logt + 256);
+                acc.x += st.x * gq_log_half(n2, E.logt);
             } else {
                 acc = csub(acc, cscale(um, st.x * im));
             }
@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                                                                 double2 *__restrict__ Qout) {
     __shared__ NearRanges R;
     __shared__ int wsum[kNearThreads / 32];
-    __shared__ double lt[512];
-    for (int i = threadIdx.x; i < 512; i += kNearThreads) lt[i] = E.logt[i];
+    __shared__ double lt[kGqLogN];
+    for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                         // last term: a multiply-add into the sum (t is not needed again)
                         if (qc >= QQ) acc[QQ] = cfma(t, u, acc[QQ]);
                     } else {
-                        acc[0].x += st.x * gq_log_half(n2, lt, lt + 256);
+                        acc[0].x += st.x * gq_log_half(n2, lt);
                         double2 t = make_double2(st.x * u.x, st.x * u.y);
                         acc[1] = cadd(acc[1], t);
 #pragma unroll
@@ -554,8 +554,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
                                                                double *__restrict__ pot) {
     __shared__ NearRanges R;
     __shared__ int wsum[kNearThreads / 32];
-    __shared__ double lt[512];
-    for (int i = threadIdx.x; i < 512; i += kNearThreads) lt[i] = E.logt[i];
+    __shared__ double lt[kGqLogN];
+    for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
                     double n2 = wx * wx + wy * wy;
                     if (n2 == 0.0) continue;
                     if (KERNEL == GQ_D) acc += (st.x * wx + st.y * wy) * gq_rcp(n2);
-                    else acc += st.x * gq_log_half(n2, lt, lt + 256);
+                    else acc += st.x * gq_log_half(n2, lt);
                 }
             }
         }
@@ -634,7 +634,7 @@ __global__ void k_w_centres(EvalView E, int nc, const int *__restrict__ ctr_box_
                 vk = cmul(vk, v);
             }
         }
-        acc[0].x += A0 * gq_log_half(n2, E.logt, E.logt + 256) + sum.x;
+        acc[0].x += A0 * gq_log_half(n2, E.logt) + sum.x;
         acc[0].y += sum.y;
         double2 sm = make_double2(1.0, 0.0);
 #pragma unroll
@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(128) k_w_centres_q(EvalView E, int nc, const i
                 vk = cmul(vk, v);
             }
         }
-        acc[0].x += A0 * gq_log_half(n2, E.logt, E.logt + 256) + G[0].x;
+        acc[0].x += A0 * gq_log_half(n2, E.logt) + G[0].x;
         acc[0].y += G[0].y;
         double2 sm = make_double2(1.0, 0.0);
 #pragma unroll
@@ -765,7 +765,7 @@ __global__ void k_w_points(EvalView E, int npt, const int *__restrict__ pt_owner
         double2 h = A[P];
         for (int k = P - 1; k >= 1; --k) h = cfma(h, v, A[k]);
         h = cmul(h, v);
-        acc += h.x + A[0].x * gq_log_half(n2, E.logt, E.logt + 256);
+        acc += h.x + A[0].x * gq_log_half(n2, E.logt);
     }
     pot[t] += acc;
 }
@@ -1287,10 +1287,10 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
     __shared__ NearRangesF R;
     __shared__ int wsum[kNearThreads / 32];
     __shared__ float lt[KERNEL == GQ_D ? 1 : 384];
-    __shared__ double lt64[KERNEL == GQ_D ? 1 : 512];
+    __shared__ double lt64[KERNEL == GQ_D ? 1 : kGqLogN];
     if (KERNEL != GQ_D) {
         for (int i = threadIdx.x; i < 384; i += kNearThreads) lt[i] = X.logt[i];
-        for (int i = threadIdx.x; i < 512; i += kNearThreads) lt64[i] = E.logt[i];
+        for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt64[i] = E.logt[i];
     }
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1355,7 +1355,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
                                 acc64[m] = cadd(acc64[m], t);
                             }
                         } else {
-                            acc64[0].x += sd.x * gq_log_half(d2, lt64, lt64 + 256);
+                            acc64[0].x += sd.x * gq_log_half(d2, lt64);
                             double2 t = make_double2(sd.x * uu.x, sd.x * uu.y);
                             acc64[1] = cadd(acc64[1], t);
 #pragma unroll
@@ -1762,7 +1762,7 @@ static void make_tables(gq_geom *g, EvalTables &T) {
     cudaStream_t st = g->ctx->stream;
     GqLogTable LT;
     gq_log_table_host(&LT);
-    T.logt.alloc(512);
+    T.logt.alloc(kGqLogN);
     GQ_CUDA(cudaMemcpyAsync(T.logt.p, &LT, sizeof(LT), cudaMemcpyHostToDevice, st));
     GqDflLogTable DT;
     gq_dfl_log_table_host(&DT);

@@ -10,51 +10,51 @@
 // ---------------------------------------------------------------- logarithm
 // Table-driven method of P. T. P. Tang, "Table-driven implementation of the
 // logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990:
-// write x = 2^k m with m in [1, 2); let j be the leading 8 fraction bits of m
-// and t_j the FP64 value nearest 1 / (1 + (j + 1/2)/256).  Then
+// write x = 2^k m with m in [1, 2); let j be the leading 9 fraction bits of m
+// and t_j the FP64 value nearest 1 / (1 + (j + 1/2)/512).  Then
 //     log x = k log 2 + log(1/t_j) + log1p(r),   r = m t_j - 1,
-// with r formed by one fused multiply-add (m t_j is exact in the FMA), |r| < 2^-9,
-// and log1p(r) = r - r^2/2 + ... + r^5/5 (the truncation is below 2^-57).
+// with r formed by one fused multiply-add (m t_j is exact in the FMA), |r| < 2^-10,
+// and log1p(r) = r - r^2/2 + r^3/3 - r^4/4 (the truncation is below 2^-53).
 // The kernels need log|w| from |w|^2, so the primitive is (1/2) log x, with
-// the halving folded into the table and the coefficients.  The range test
-// looks at the exponent bits only (integer pipe).
+// the halving folded into the tables and the coefficients; (k/2) log 2 is a
+// third table indexed by the biased exponent (no integer-to-FP64 conversion).
+// The range test looks at the exponent bits only (integer pipe).
+constexpr int kGqLogJ = 512;
+constexpr int kGqLogN = 2 * kGqLogJ + 2048;   // doubles in GqLogTable
 struct GqLogTable {
-    double t[256];       // t_j
-    double hl[256];      // (1/2) log(1 / t_j)
+    double t[kGqLogJ];    // t_j
+    double hl[kGqLogJ];   // (1/2) log(1 / t_j)
+    double hk[2048];      // (e - 1023) (log 2)/2 for the biased exponent e
 };
 
 #ifndef __CUDACC_RTC__
 inline void gq_log_table_host(GqLogTable *T) {
-    for (int j = 0; j < 256; ++j) {
-        long double c = 1.0L + (j + 0.5L) / 256.0L;
+    for (int j = 0; j < kGqLogJ; ++j) {
+        long double c = 1.0L + (j + 0.5L) / (long double)kGqLogJ;
         double t = (double)(1.0L / c);
         T->t[j] = t;
         T->hl[j] = (double)(-0.5L * logl((long double)t));
     }
+    for (int e = 0; e < 2048; ++e) T->hk[e] = (double)((long double)(e - 1023) * 0.5L * logl(2.0L));
 }
 #endif
 
-// (1/2) log x
-__device__ __forceinline__ double gq_log_half(double x, const double *__restrict__ tt, const double *__restrict__ th) {
+// (1/2) log x; T points to a GqLogTable
+__device__ __forceinline__ double gq_log_half(double x, const double *__restrict__ T) {
     long long bits = __double_as_longlong(x);
     unsigned long long e = (unsigned long long)bits >> 52;    // biased exponent, sign bit above it
     if (e - 23ull > 2000ull) return 0.5 * log(x);             // outside [2^-1000, 2^1001): zero, subnormal, huge, inf, nan, x < 0
-    int k = (int)e - 1023;
-    int j = (int)((bits >> 44) & 0xff);
+    int j = (int)((bits >> 43) & (kGqLogJ - 1));
     double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
-    double r = fma(m, tt[j], -1.0);
-    double a = fma(r, 0.1, -0.125);
-    a = fma(r, a, 1.0 / 6.0);
+    double r = fma(m, T[j], -1.0);
+    double a = fma(r, -0.125, 1.0 / 6.0);
     a = fma(r, a, -0.25);
     a = fma(r, a, 0.5);
     double p = r * a;
-    const double hln2 = 0.346573590279972654708616060729088284;   // (log 2) / 2
-    return fma((double)k, hln2, th[j] + p);
+    return T[2 * kGqLogJ + (int)e] + (T[kGqLogJ + j] + p);
 }
 
-__device__ __forceinline__ double gq_log(double x, const double *__restrict__ tt, const double *__restrict__ th) {
-    return 2.0 * gq_log_half(x, tt, th);
-}
+__device__ __forceinline__ double gq_log(double x, const double *__restrict__ T) { return 2.0 * gq_log_half(x, T); }
 
 // ---------------------------------------------------------------- reciprocal
 // 1/x from the hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64,

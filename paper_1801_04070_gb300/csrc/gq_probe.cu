@@ -118,7 +118,7 @@ __global__ void k_probe_math(int fn, int n, const double *__restrict__ x, const 
     double v = x[i];
     if (fn == 4) y[i] = dfl_to_double(dfl_log(dfl_from_double(v), ftab, ftab + 128, ftab + 256));
     else if (fn == 5) y[i] = dfl_to_double(dfl_rcp(dfl_from_double(v)));
-    else y[i] = fn == 0 ? gq_log(v, tab, tab + 256) : fn == 1 ? log(v) : fn == 2 ? gq_rcp(v) : 1.0 / v;
+    else y[i] = fn == 0 ? gq_log(v, tab) : fn == 1 ? log(v) : fn == 2 ? gq_rcp(v) : 1.0 / v;
 }
 }  // namespace
 
@@ -126,7 +126,7 @@ void gq_probe_math_impl(gq_ctx *ctx, int fn, int n, const double *x_dev, double 
     GqLogTable T;
     gq_log_table_host(&T);
     dbuf<double> tab;
-    tab.alloc(512);
+    tab.alloc(kGqLogN);
     GQ_CUDA(cudaMemcpyAsync(tab.p, &T, sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
     GqDflLogTable F;
     gq_dfl_log_table_host(&F);
