@@ -226,8 +226,9 @@ __global__ void k_compact_index(int n, const int *__restrict__ flag, const int *
 }
 
 // ------------------------------------------------------------------ A4: keys and centre levels
-__device__ __forceinline__ uint64_t key1(double v, double lo, double u) {
-    double f = floor((v - lo) / u);
+// u is a power of two, so (v - lo) * (1/u) equals (v - lo) / u exactly
+__device__ __forceinline__ uint64_t key1(double v, double lo, double inv_u) {
+    double f = floor((v - lo) * inv_u);
     const double kmax = (double)((1ll << GQ_KEYBITS) - 1);
     if (f < 0) return 0;
     if (f > kmax) return (uint64_t)kmax;
@@ -253,7 +254,8 @@ __global__ void k_keys(int nsrc, int nc, int npt, const double *__restrict__ up_
         int t = pt_tgt[i - nsrc - nc];
         x = tgt_xy[2 * t]; y = tgt_xy[2 * t + 1];
     }
-    uint64_t kx = key1(x, R.lo_x, R.u), ky = key1(y, R.lo_y, R.u);
+    const double inv_u = 1.0 / R.u;
+    uint64_t kx = key1(x, R.lo_x, inv_u), ky = key1(y, R.lo_y, inv_u);
     if (i >= nsrc && i < nsrc + nc) {
         // deepest level whose TCR (half-width |b|(1 + t_f)) holds the whole disk,
         // for every box on the key path
