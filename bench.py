@@ -278,7 +278,7 @@ def run_batched(args, dev, stream):
     ref = [o.clone() for o in outs]
     sequential()
     torch.cuda.synchronize()
-    same = all(torch.equal(a, c) for a, c in zip(ref, outs))
+    diff = max(float((a - c).abs().max() / c.abs().max()) for a, c in zip(ref, outs))
     res = {}
     for name, fn in (("graph", lambda: b.eval(kern, dens, outs)), ("sequential", sequential)):
         fn()
@@ -346,7 +346,7 @@ def run_batched(args, dev, stream):
             "targets_x_densities": ntot, "graph_ms": res["graph"], "sequential_ms": res["sequential"],
             "graph_targets_per_s": ntot / (res["graph"] * 1e-3),
             "sequential_targets_per_s": ntot / (res["sequential"] * 1e-3),
-            "streams": streams, "results_identical": bool(same), "gmres": gmres}
+            "streams": streams, "max_rel_diff_vs_sequential": diff, "gmres": gmres}
 
 
 # ---------------------------------------------------------------- GPU arm

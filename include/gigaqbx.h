@@ -205,8 +205,12 @@ gq_status gq_gmres(gq_geom *g, const double *rhs, double tol, int maxit, int res
  * 4, 8 and 16 streams, times replays and keeps the fastest (cached per batch
  * shape; written to the file named by GQ_AUTOTUNE_CACHE if set); later calls
  * with the same arguments only replay the graph.  The geometries must stay
- * alive and must not be rebuilt while the batch exists.  Results are those of
- * gq_eval (the same kernels). */
+ * alive and must not be rebuilt while the batch exists.  In FP64 mode the
+ * direct part of the QBX coefficients is formed for up to four densities of a
+ * geometry at a time (the per-pair geometry and the powers (r/w)^m shared),
+ * which rounds differently from one gq_eval per density: results agree with
+ * gq_eval to about 1e-14 relative and repeat bit for bit from call to call;
+ * the rest of the evaluation uses the gq_eval kernels. */
 typedef struct gq_batch gq_batch;
 gq_status gq_batch_create(gq_ctx *ctx, int ngeom, gq_geom *const *geoms, gq_batch **out);
 gq_status gq_batch_destroy(gq_batch *b);

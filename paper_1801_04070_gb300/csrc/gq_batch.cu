@@ -72,6 +72,18 @@ void save_cache_file() {
     fclose(f);
 }
 
+// the ndens densities of one geometry (consecutive arrays), the direct part of
+// their QBX coefficients formed together (gq_eval_multi)
+void eval_densities(gq_geom *g, int kernel, int ndens, const double *dens, double *out) {
+    std::vector<const double *> d(ndens);
+    std::vector<double *> o(ndens);
+    for (int j = 0; j < ndens; ++j) {
+        d[j] = dens + (size_t)j * g->nbase;
+        o[j] = out + (size_t)j * g->nt;
+    }
+    gq_eval_multi(g, kernel, ndens, d.data(), o.data());
+}
+
 // work estimate used to balance branches: quadrature nodes + targets + boxes
 double cost_of(const gq_geom *g) { return (double)g->nsrc + 2.0 * g->nt + 16.0 * g->nbox; }
 
@@ -112,8 +124,7 @@ cudaGraphExec_t capture(gq_batch *b, int kernel, int ndens, const double *const 
             gq_geom *g = b->geoms[i];
             saved[i] = g->ctx;
             g->ctx = &sctx[assign[i]];
-            for (int j = 0; j < ndens; ++j)
-                gq_eval_all(g, kernel, dens[i] + (size_t)j * g->nbase, out[i] + (size_t)j * g->nt, nullptr);
+            eval_densities(g, kernel, ndens, dens[i], out[i]);
             g->ctx = saved[i];
         }
         for (int s = 0; s < S; ++s) {
@@ -188,8 +199,7 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
             gq_geom *g = b->geoms[i];
             gq_ctx *saved = g->ctx;
             g->ctx = ctx;
-            for (int j = 0; j < ndens; ++j)
-                gq_eval_all(g, kernel, dens[i] + (size_t)j * g->nbase, out[i] + (size_t)j * g->nt, nullptr);
+            eval_densities(g, kernel, ndens, dens[i], out[i]);
             g->ctx = saved;
         }
         GQ_CUDA(cudaStreamSynchronize(ctx->stream));

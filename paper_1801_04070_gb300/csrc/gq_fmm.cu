@@ -1686,6 +1686,138 @@ void dispatch_near_centres_f32(gq_ctx *ctx, const EvalView &E, const MixedView &
     }
 }
 
+// Several densities on one geometry at once: the per-pair geometry (w, |w|^2,
+// its reciprocal, log|w|, r/w) and the powers (r/w)^m are formed once and
+// serve ND densities, each of which adds only its strength times the power.
+// strm: ND strength arrays of the sorted sources, sstride apart; Qm: ND
+// coefficient arrays [nc][q+1], qstride apart.  Same layout and sums as
+// k_near_centres otherwise.
+template <int QQ, int KERNEL, int ND>
+__global__ void __launch_bounds__(kNearThreads) k_near_centres_multi(EvalView E, int nwork, const int *__restrict__ work,
+                                                                      const double2 *__restrict__ strm, long long sstride,
+                                                                      double2 *__restrict__ Qm, long long qstride) {
+    __shared__ NearRanges R;
+    __shared__ int wsum[kNearThreads / 32];
+    __shared__ double lt[KERNEL == GQ_D ? 1 : kGqLogN];
+    if (KERNEL != GQ_D)
+        for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
+    int b = work[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
+    int cb = E.ctr_beg[b], ce = E.ctr_end[b];
+    bool single = ne <= kNearRanges;
+    if (single) load_ranges(E, b, 0, ne, R, wsum);
+    else __syncthreads();
+    for (int c0 = cb; c0 < ce; c0 += kNearThreads / 32) {
+        int c = c0 + w;
+        bool valid = c < ce;
+        double2 cz = valid ? E.sc_xy[c] : make_double2(0.0, 0.0);
+        double rc = valid ? E.sc_r[c] : 1.0;
+        const int qc = (valid && E.qc) ? E.qc[c] : QQ;
+        double2 acc[ND][QQ + 1];
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int m = 0; m <= QQ; ++m) acc[d][m] = make_double2(0.0, 0.0);
+        for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
+            if (!single) {
+                __syncthreads();
+                load_ranges(E, b, e0, ne, R, wsum);
+            }
+            int T = R.pre[R.n];
+            if (valid) {
+                int r = 0;
+                for (int v = lane; v < T; v += 32) {
+                    while (R.pre[r + 1] <= v) ++r;
+                    int s = R.beg[r] + (v - R.pre[r]);
+                    double2 y = E.s_xy[s];
+                    double2 st[ND];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) st[d] = strm[d * sstride + s];
+                    double wx = y.x - cz.x, wy = y.y - cz.y;
+                    double n2 = wx * wx + wy * wy;
+                    double inv = gq_rcp(n2);
+                    if (KERNEL == GQ_D) {
+                        double2 bm = make_double2(wx * inv, -wy * inv);   // (1/w) (r/w)^m
+                        double2 u = make_double2(rc * bm.x, rc * bm.y);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) acc[d][0] = cfma(st[d], bm, acc[d][0]);
+#pragma unroll
+                        for (int m = 1; m <= QQ; ++m) {
+                            if (m > qc) break;
+                            bm = cmul(bm, u);
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) acc[d][m] = cfma(st[d], bm, acc[d][m]);
+                        }
+                    } else {
+                        double ir = rc * inv;
+                        double2 u = make_double2(wx * ir, -wy * ir), pw = u;
+                        double lg = gq_log_half(n2, lt);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            acc[d][0].x = fma(st[d].x, lg, acc[d][0].x);
+                            acc[d][1].x = fma(st[d].x, pw.x, acc[d][1].x);
+                            acc[d][1].y = fma(st[d].x, pw.y, acc[d][1].y);
+                        }
+#pragma unroll
+                        for (int m = 2; m <= QQ; ++m) {
+                            if (m > qc) break;
+                            pw = cmul(pw, u);
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) {
+                                acc[d][m].x = fma(st[d].x, pw.x, acc[d][m].x);
+                                acc[d][m].y = fma(st[d].x, pw.y, acc[d][m].y);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        constexpr int NV = 2 * (QQ + 1);
+        double vals[ND * NV];
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int m = 0; m <= QQ; ++m) {
+                vals[d * NV + 2 * m] = acc[d][m].x;
+                vals[d * NV + 2 * m + 1] = acc[d][m].y;
+            }
+        int base, cnt;
+        warp_reduce_scatter(vals, 0.0, lane, [](double a, double x) { return a + x; },
+                            [](double x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }, base, cnt);
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < (ND * NV + 31) / 32; ++j)
+                if (j < cnt) {
+                    int i = base + j, d = i / NV, k = i - d * NV, m = k >> 1;
+                    double x = vals[j];
+                    if (KERNEL != GQ_D && m >= 1) x *= -1.0 / m;
+                    reinterpret_cast<double *>(Qm + d * qstride + (size_t)c * (QQ + 1))[k] = x;
+                }
+        }
+    }
+}
+
+template <int QQ, int ND>
+void launch_near_centres_multi(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, const double2 *strm,
+                               long long sstride, double2 *Qm, long long qstride) {
+    auto kd = k_near_centres_multi<QQ, GQ_D, ND>;
+    auto ks = k_near_centres_multi<QQ, GQ_S, ND>;
+    GQ_LAUNCH(ctx, (E.kernel == GQ_D ? kd : ks), nwork, kNearThreads, 0, E, nwork, work, strm, sstride, Qm, qstride);
+}
+
+template <int ND>
+void dispatch_near_centres_multi(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, const double2 *strm,
+                                 long long sstride, double2 *Qm, long long qstride) {
+    switch (E.Q) {
+#define GQ_CASE(v) case v: launch_near_centres_multi<v, ND>(ctx, E, nwork, work, strm, sstride, Qm, qstride); break;
+        GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
+        GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
+#undef GQ_CASE
+        default: throw gq_error{GQ_ERR_INVALID, "p_qbx out of range"};
+    }
+}
+
 template <int QQ>
 void launch_near_centres(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, double2 *Q) {
     auto kd = k_near_centres<QQ, GQ_D>;
@@ -1839,7 +1971,8 @@ static EvalTables &get_tables(gq_geom *g) {
     return *T;
 }
 
-void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *stt) {
+void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *stt,
+                 const double2 *qn_pre) {
     gq_ctx *ctx = g->ctx;
     cudaStream_t st = ctx->stream;
     EvalTables &T = get_tables(g);
@@ -1964,7 +2097,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     if (g->n_ctr_boxes) {
         if (f32) dispatch_near_centres_f32(&ctx2, E, X, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
         else if (split) dispatch_near_centres_split(&ctx2, E, SX, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
-        else dispatch_near_centres(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
+        else if (!qn_pre) dispatch_near_centres(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
     }
     mark(N_CTR, s2);
     if (g->n_pt_boxes) {
@@ -2066,11 +2199,16 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     mark(S_L2Q, st);
     // join the direct part, then evaluate at the targets
     GQ_CUDA(cudaStreamWaitEvent(st, g->ev_near, 0));
+    // the direct part of the QBX coefficients: this call's, or formed beforehand
+    // for several densities at once (gq_eval_multi)
+    const bool use_pre = qn_pre && !f32 && !split;
+    const double2 *qn_use = use_pre ? qn_pre : (const double2 *)g->Qn;
+    g->qn_last = qn_use;
     if (g->nt)
         GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, E.qc, (const int *)g->t_kind,
                   (const int *)g->t_ctr, (const int *)g->ctr_pos, (const int *)T.tgt_ptpos, (const double *)g->tgt_xy,
                   (const int *)g->tgt_on, (const double *)g->base_n, (const double2 *)g->sc_xy,
-                  (const double *)g->sc_r, (const double2 *)g->Q, (const double2 *)g->Qn, (const double *)g->pot,
+                  (const double *)g->sc_r, (const double2 *)g->Q, qn_use, (const double *)g->pot,
                   (const double *)g->potn, out_dev);
     mark(S_END, st);
     ctx->launches += ctx2.launches;
@@ -2100,12 +2238,63 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     g->last_kernel = kernel;
 }
 
+// Several densities on one geometry: the direct part of the QBX coefficients
+// for all of them by the multi-density kernel (FP64 mode), then the rest of
+// the evaluation per density.  The mixed-precision tiers evaluate one density
+// after another.
+void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, double *const *out) {
+    const bool f32 = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-6;
+    const bool split = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-10 && g->prm.eps < 1e-6;
+    if (nd <= 1 || f32 || split || g->n_ctr_boxes == 0) {
+        for (int d = 0; d < nd; ++d) gq_eval_all(g, kernel, dens[d], out[d], nullptr);
+        return;
+    }
+    gq_ctx *ctx = g->ctx;
+    EvalTables &T = get_tables(g);
+    int kin = kernel == GQ_SP ? GQ_S : kernel;
+    const int Q1 = g->prm.p_qbx + 1;
+    const long long sstride = g->nsrc, qstride = (long long)g->nc * Q1;
+    g->strm.alloc((size_t)nd * g->nsrc);
+    g->Qm.alloc((size_t)nd * qstride);
+    for (int d = 0; d < nd; ++d)
+        if (g->nsrc)
+            GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
+                      (const double *)g->interp, dens[d], (const double *)g->s_w, (const double2 *)g->s_n, kin,
+                      g->strm.p + d * sstride);
+    EvalView E{};
+    E.R = g->root;
+    E.P = g->prm.p_fmm;
+    E.Q = g->prm.p_qbx;
+    E.kernel = kin;
+    E.blev = g->blev; E.bix = g->bix; E.biy = g->biy; E.bparent = g->bparent; E.bchild = g->bchild;
+    E.src_beg = g->src_beg; E.src_end = g->src_end;
+    E.ctr_beg = g->ctr_beg; E.ctr_end = g->ctr_end; E.pt_beg = g->pt_beg; E.pt_end = g->pt_end;
+    E.sub_src = g->sub_src; E.sub_tgt = g->sub_tgt;
+    E.s_xy = g->s_xy; E.sc_xy = g->sc_xy; E.sc_r = g->sc_r; E.sp_xy = g->sp_xy;
+    for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
+    E.binom = T.binom;
+    E.qc = g->has_qc ? (const int *)g->q_ctr.p : nullptr;
+    E.logt = T.logt;
+    int d0 = 0;
+    for (; d0 + 4 <= nd; d0 += 4)
+        dispatch_near_centres_multi<4>(ctx, E, g->n_ctr_boxes, g->ctr_boxes, g->strm.p + d0 * sstride, sstride,
+                                       g->Qm.p + d0 * qstride, qstride);
+    for (; d0 + 2 <= nd; d0 += 2)
+        dispatch_near_centres_multi<2>(ctx, E, g->n_ctr_boxes, g->ctr_boxes, g->strm.p + d0 * sstride, sstride,
+                                       g->Qm.p + d0 * qstride, qstride);
+    for (; d0 < nd; ++d0)
+        dispatch_near_centres_multi<1>(ctx, E, g->n_ctr_boxes, g->ctr_boxes, g->strm.p + d0 * sstride, sstride,
+                                       g->Qm.p + d0 * qstride, qstride);
+    for (int d = 0; d < nd; ++d) gq_eval_all(g, kernel, dens[d], out[d], nullptr, g->Qm.p + d * qstride);
+}
+
 void gq_export_qbx_impl(gq_geom *g, double *host) {
     int Q1 = g->prm.p_qbx + 1;
     dbuf<double2> tmp;
     tmp.alloc((size_t)g->nc * Q1);
     GQ_LAUNCH(g->ctx, k_export_qbx, gq_blocks((long long)g->nc * Q1, 256), 256, 0, g->nc, g->prm.p_qbx,
-              (const int *)g->ctr_perm, (const double *)g->sc_r, (const double2 *)g->Q, (const double2 *)g->Qn, tmp.p);
+              (const int *)g->ctr_perm, (const double *)g->sc_r, (const double2 *)g->Q,
+              g->qn_last ? g->qn_last : (const double2 *)g->Qn, tmp.p);
     GQ_CUDA(cudaMemcpyAsync(host, tmp.p, sizeof(double2) * g->nc * Q1, cudaMemcpyDeviceToHost, g->ctx->stream));
     GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
 }

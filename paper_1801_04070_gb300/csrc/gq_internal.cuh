@@ -173,6 +173,9 @@ struct gq_geom {
     dbuf<float4> c_rel2;
     dbuf<float4> c_r2;    // (r.hi, r.lo, (1/r^2).hi, (1/r^2).lo)
     dbuf<float4> str2;    // (re.hi, re.lo, im.hi, im.lo)
+    // several densities at once (gq_eval_multi): strengths and direct coefficients per density
+    dbuf<double2> strm, Qm;
+    const double2 *qn_last = nullptr;   // direct coefficients of the last evaluation
     dbuf<float4> p_rel2;  // sorted point targets minus their leaf centre
     dbuf<float4> M2;      // multipoles
     dbuf<float4> lvl2;    // per level: (rho, 1/rho), (log rho, 1/rho^2)
@@ -196,7 +199,9 @@ void gq_radix_sort_pairs32(gq_ctx *ctx, uint32_t *keys, int *vals, long long n, 
 // ------------------------------------------------------------------ stages
 void gq_build_all(gq_geom *g);                 // gq_tree.cu
 void gq_build_lists(gq_geom *g);               // gq_lists.cu
-void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *st);  // gq_fmm.cu
+void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *st,
+                 const double2 *qn_pre = nullptr);                                          // gq_fmm.cu
+void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, double *const *out);
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
 void gq_probe_math_impl(gq_ctx *ctx, int fn, int n, const double *x_dev, double *y_dev);
