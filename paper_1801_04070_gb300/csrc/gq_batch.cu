@@ -1,8 +1,10 @@
 // gq_batch.cu -- batched evaluation of many independent geometries and many
 // densities per geometry by one CUDA-graph launch.
 //
-// Each geometry's evaluations (one per density, in order: they share the
-// geometry's expansion buffers) form one branch of the graph; branches are
+// Each geometry's evaluations form one branch of the graph: the near-field QBX
+// coefficients of all its densities together (gq_eval_multi), then the rest of
+// the evaluation one density after another (they share the geometry's
+// expansion buffers); branches are
 // spread over S streams, largest first onto the least loaded stream, so small
 // problems run concurrently and fill the GPU.  The graph is captured once per
 // (kernel, densities, pointer set) and replayed afterwards.  S is chosen by an
