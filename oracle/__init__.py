@@ -19,6 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gq_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libgq_oracle.so")
+# a deliberately broken build of the oracle, for the mutation test only
+_LIB_OVERRIDE = os.environ.get("GQ_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -60,7 +62,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            L = C.CDLL(_LIB_OVERRIDE or build())
             L.orc_create.restype = C.c_void_p
             L.orc_create.argtypes = [C.POINTER(_Geom), C.POINTER(_Params)]
             L.orc_destroy.argtypes = [C.c_void_p]

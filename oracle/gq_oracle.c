@@ -7,6 +7,10 @@
  * Compile with -ffp-contract=off: the decisions that feed integer results
  * (keys, centre levels, association) must round every operation separately.
  *
+ * GQ_ORC_MUT (default 0) plants one deliberate mistake when compiled with
+ * -DGQ_ORC_MUT=k; tests/test_oracle_mutations.py builds such variants to show
+ * that the pins catch each of them.  Normal builds never set it.
+ *
  * Conventions (Sec. 2.1, eqs. slp/dlp/qbx, and Sec. 3.1):
  *   complex potential Phi with   S mu(x) = -(1/2pi) Re Phi_S(x),
  *                                D mu(x) = -(1/2pi) Re Phi_D(x),
@@ -21,6 +25,9 @@
  *   expanding log z about y: (-1)^(m+1) a_0 / (m y^m); the printed (-1)^m is
  *   a typo), L2L (eq. l2l).
  */
+#ifndef GQ_ORC_MUT
+#define GQ_ORC_MUT 0
+#endif
 #include "gq_oracle.h"
 
 #include <complex.h>
@@ -203,7 +210,7 @@ static void associate(orc_state *s) {
                 }
             }
         }
-        if (best >= 0 && bestk <= slack2) { s->t_kind[t] = 1; s->t_ctr[t] = best; }
+        if (best >= 0 && bestk <= (GQ_ORC_MUT == 8 ? s->p.assoc_slack : slack2)) { s->t_kind[t] = 1; s->t_ctr[t] = best; }
         else { s->t_kind[t] = 0; s->t_ctr[t] = -1; s->tgt_pt[t] = s->npt; s->pt_tgt[s->npt++] = t; }
     }
     free(cstart); free(citems);
@@ -361,7 +368,9 @@ static inline int64_t dcen(const obox *a, const obox *b) {
 /* 'adjacent': the closed squares intersect.  A box is adjacent to itself
  * (List 1 counts the self-interaction among the adjacent ones), to its
  * ancestors and to its descendants. */
-static inline int adjacent(const obox *a, const obox *b) { return dcen(a, b) <= bh(a) + bh(b); }
+static inline int adjacent(const obox *a, const obox *b) {
+    return GQ_ORC_MUT == 6 ? dcen(a, b) < bh(a) + bh(b) : dcen(a, b) <= bh(a) + bh(b);
+}
 /* k-colleagues with k = 2: same level, inside B_inf(5|b|, c_b). */
 static inline int colleague2(const obox *a, const obox *b) { return a->level == b->level && dcen(a, b) <= 4 * bh(b); }
 /* a < TCR(b): dist >= 3|a| + |b|(1 + t_f) */
@@ -674,7 +683,7 @@ static inline cplx pt(const double *xy, int i) { return xy[2 * i] + I * xy[2 * i
 static void p2local(int kernel, int q, cplx c, cplx y, cplx str, cplx *beta) {
     cplx w = y - c;
     if (kernel == ORC_D) {
-        for (int m = 0; m <= q; ++m) beta[m] += str / cpow_int(w, m + 1);
+        for (int m = 0; m <= q; ++m) beta[m] += str / cpow_int(w, GQ_ORC_MUT == 5 ? m : m + 1);
     } else {
         beta[0] += str * clog(c - y);
         for (int m = 1; m <= q; ++m) beta[m] += -str / (m * cpow_int(w, m));
@@ -692,7 +701,7 @@ static void p2mpole(int kernel, int p, cplx c, cplx y, cplx str, cplx *a) {
         for (int k = 1; k <= p; ++k) a[k] += -str * cpow_int(w, k - 1);
     } else {
         a[0] += str;
-        for (int k = 1; k <= p; ++k) a[k] += -str * cpow_int(w, k) / k;
+        for (int k = 1; k <= p; ++k) a[k] += -str * cpow_int(w, k) / (GQ_ORC_MUT == 3 ? 1 : k);
     }
 }
 /* eq. (m2m): shift multipole from c_old to c_new, y = c_new - c_old */
@@ -700,7 +709,8 @@ static void m2m(const double binom[128][128], int p, cplx y, const cplx *a, cplx
     out[0] += a[0];
     for (int m = 1; m <= p; ++m) {
         cplx acc = -a[0] * cpow_int(-y, m) / m;
-        for (int k = 1; k <= m; ++k) acc += binom[m - 1][k - 1] * a[k] * cpow_int(-y, m - k);
+        for (int k = 1; k <= m; ++k)
+            acc += (GQ_ORC_MUT == 2 ? binom[m][k - 1] : binom[m - 1][k - 1]) * a[k] * cpow_int(-y, m - k);
         out[m] += acc;
     }
 }
@@ -711,7 +721,7 @@ static void m2l(const double binom[128][128], int p_in, int p_out, cplx y, const
     out[0] += acc;
     for (int m = 1; m <= p_out; ++m) {
         double sg = (m % 2) ? -1.0 : 1.0;                    /* (-1)^m */
-        acc = -sg * a[0] / (m * cpow_int(y, m));
+        acc = (GQ_ORC_MUT == 1 ? sg : -sg) * a[0] / (m * cpow_int(y, m));
         for (int k = 1; k <= p_in; ++k) acc += sg * binom[m + k - 1][k - 1] * a[k] / cpow_int(y, m + k);
         out[m] += acc;
     }
@@ -720,7 +730,7 @@ static void m2l(const double binom[128][128], int p_in, int p_out, cplx y, const
 static void l2l(const double binom[128][128], int p_in, int p_out, cplx y, const cplx *b, cplx *out) {
     for (int m = 0; m <= p_out; ++m) {
         cplx acc = 0;
-        for (int k = m; k <= p_in; ++k) acc += binom[k][m] * b[k] * cpow_int(y, k - m);
+        for (int k = m; k <= p_in; ++k) acc += binom[k][m] * b[k] * cpow_int(GQ_ORC_MUT == 4 ? -y : y, k - m);
         out[m] += acc;
     }
 }
@@ -764,7 +774,7 @@ static void final_values(orc_state *s, int kernel, const int *target_mask, const
                 acc += -creal(eval_local(q, cc, Q + (size_t)c * (q + 1), tt)) / TWO_PI;
             }
         }
-        value[t] = acc / nside;
+        value[t] = GQ_ORC_MUT == 7 ? acc : acc / nside;
     }
 }
 

@@ -39,6 +39,36 @@ def test_o2_lists_equal_bruteforce_onsurface_up():
             assert sorted(_rows(A[name], b)) == sorted(_rows(B[name], b)), (name, b)
 
 
+@pytest.mark.parametrize("fix", ["c1_oracle", "small_oracle"])
+def test_touching_same_level_leaves_in_list1(fix, request):
+    """Def. 1 from box indices alone: a same-level leaf with sources whose
+    square shares an edge or a corner with a target-owning box b (index
+    offsets within one) belongs to List 1 of b.  This pins the adjacency
+    reading (closed squares that touch are adjacent) independently of the
+    distance test the list code uses."""
+    o = request.getfixturevalue(fix)
+    bx = o.boxes()
+    lists = o.lists()
+    n = o.nbox
+    has_child = np.zeros(n, bool)
+    has_child[bx["parent"][bx["parent"] >= 0]] = True
+    key = {(int(bx["level"][d]), int(bx["ix"][d]), int(bx["iy"][d])): d for d in range(n)}
+    checked = 0
+    for b in range(n):
+        if bx["nctr"][b] + bx["ntgt"][b] == 0:
+            continue
+        u = set(_rows(lists["U"], b).tolist())
+        l, x, y = int(bx["level"][b]), int(bx["ix"][b]), int(bx["iy"][b])
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                d = key.get((l, x + dx, y + dy))
+                if d is None or d == b or has_child[d] or bx["sub_src"][d] == 0:
+                    continue
+                assert d in u, (b, d)
+                checked += 1
+    assert checked > 0
+
+
 def _ancestor_table(o):
     bx = o.boxes()
     so, co, to = o.owners()
