@@ -191,13 +191,14 @@ STAGE_NAMES = ["upsample", "p2m_m2m", "m2l", "p2l", "l2l", "near_centres", "near
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(kernel, reps=1):
-    """The CPU oracle (serial C, FP64) on an 8 x 6 sub-grid of the workload:
-    same per-curve discretisation, density recipe and target density (3/16 of
-    the curves and of the off-surface targets).  Build + evaluation timed."""
+def oracle_sample(kernel, reps=1, grid=SAMPLE_GRID):
+    """The CPU oracle (serial C, FP64) on a sub-grid of the workload (8 x 6 by
+    default): same per-curve discretisation, density recipe and target density
+    (the sub-grid's share of the curves and of the off-surface targets).  Build
+    + evaluation timed."""
     import oracle
-    n_off = (1 << 20) * SAMPLE_GRID[0] * SAMPLE_GRID[1] // 256
-    g = workload(n_off=n_off, grid=SAMPLE_GRID)
+    n_off = (1 << 20) * grid[0] * grid[1] // 256
+    g = workload(n_off=n_off, grid=grid)
     times = []
     vals = None
     for _ in range(reps):
@@ -213,12 +214,16 @@ def oracle_sample(kernel, reps=1):
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    # about 11 s per 8 x 6 step on one core: smaller sub-grids when many steps are
+    # asked for, so that the whole run stays within a few minutes (targets/s is per target)
+    n = args.steps + args.warmup
+    grid = SAMPLE_GRID if n <= 8 else (6, 4) if n <= 16 else (4, 3)
     for _ in range(args.warmup):
-        oracle_sample(args.kernel)
-    g, _, nt, times = oracle_sample(args.kernel, reps=args.steps)
+        oracle_sample(args.kernel, grid=grid)
+    g, _, nt, times = oracle_sample(args.kernel, reps=args.steps, grid=grid)
     tot = sum(times)
     value = nt * args.steps / tot
-    sample = (f"oracle build + {args.kernel} evaluation of a {SAMPLE_GRID[0]}x{SAMPLE_GRID[1]} sub-grid "
+    sample = (f"oracle build + {args.kernel} evaluation of a {grid[0]}x{grid[1]} sub-grid "
               f"({nt} targets, {len(g['up_w'])} quadrature nodes) per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
