@@ -1846,25 +1846,33 @@ __global__ void k_tgt_ptpos(int npt, const int *__restrict__ pt_perm, int *__res
 }  // namespace
 
 // ------------------------------------------------------------------ tables (per geometry)
-struct EvalTables {
-    dbuf<double> logt;       // GqLogTable
-    dbuf<float> dlogt;       // GqDflLogTable
-    dbuf<double> binom;      // [64][64]
-    dbuf<double2> dtab;      // [121][32] delta^-k
-    dbuf<double> logtab;     // [121] log|delta|
-    dbuf<double2> tm2m;      // [4][kTN][kTN] M2M matrices
-    dbuf<double2> tl2l;      // [4][kTN][kTN] L2L matrices
+// Constant tables (log tables, binomials, same-level M2L offsets, M2M/L2L
+// quadrant matrices): built on the host once per device and kept for the
+// life of the process (about 200 KB); each geometry adds the target -> point
+// map of its current build.
+struct ConstTables {
+    const double *logt = nullptr;     // GqLogTable
+    const float *dlogt = nullptr;     // GqDflLogTable
+    const double *binom = nullptr;    // [64][64]
+    const double2 *dtab = nullptr;    // [121][32] delta^-k
+    const double *logtab = nullptr;   // [121] log|delta|
+    const double2 *tm2m = nullptr;    // [4][kTN][kTN] M2M matrices
+    const double2 *tl2l = nullptr;    // [4][kTN][kTN] L2L matrices
+};
+
+struct EvalTables : ConstTables {
     dbuf<int> tgt_ptpos;     // [nt] target -> sorted point index
 };
 
-static void make_tables(gq_geom *g, EvalTables &T) {
-    std::vector<double> bn(kBinN * kBinN, 0.0);
+static void host_const_tables(std::vector<double> &bn, std::vector<double2> &dt, std::vector<double> &lt,
+                              std::vector<double2> &tm, std::vector<double2> &tl) {
+    bn.assign(kBinN * kBinN, 0.0);
     for (int n = 0; n < kBinN; ++n) {
         bn[n * kBinN] = 1.0;
         for (int k = 1; k <= n; ++k) bn[n * kBinN + k] = bn[(n - 1) * kBinN + k - 1] + (k <= n - 1 ? bn[(n - 1) * kBinN + k] : 0.0);
     }
-    std::vector<double2> dt(121 * 32);
-    std::vector<double> lt(121, 0.0);
+    dt.assign(121 * 32, make_double2(0.0, 0.0));
+    lt.assign(121, 0.0);
     for (int dy = -5; dy <= 5; ++dy)
         for (int dx = -5; dx <= 5; ++dx) {
             int off = (dy + 5) * 11 + (dx + 5);
@@ -1878,74 +1886,84 @@ static void make_tables(gq_geom *g, EvalTables &T) {
             }
             lt[off] = n2 > 0 ? 0.5 * log(n2) : 0.0;
         }
-    static std::mutex mu;
-    static unsigned long long inited = 0;   // devices whose constant table is loaded
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        int dev = g->ctx->device;
-        if (dev < 64 && !(inited >> dev & 1ull)) {
-            std::vector<double> pc((GQ_MAX_PQBX + 1) * 33, 0.0);
-            for (int m = 0; m <= GQ_MAX_PQBX; ++m)
-                for (int k = 1; k <= 32; ++k) pc[m * 33 + k] = bn[(m + k - 1) * kBinN + (k - 1)];
-            GQ_CUDA(cudaMemcpyToSymbol(c_pascal, pc.data(), sizeof(double) * pc.size()));
-            inited |= 1ull << dev;
-        }
+    // translation matrices for the four child quadrants, in long double
+    tm.assign((size_t)4 * kTN * kTN, make_double2(0.0, 0.0));
+    tl.assign(tm.size(), make_double2(0.0, 0.0));
+    std::vector<long double> C((size_t)(2 * kTN) * (2 * kTN), 0.0L);
+    auto Cb = [&](int n, int k) -> long double & { return C[(size_t)n * (2 * kTN) + k]; };
+    for (int n = 0; n < 2 * kTN; ++n) {
+        Cb(n, 0) = 1.0L;
+        for (int k = 1; k <= n; ++k) Cb(n, k) = Cb(n - 1, k - 1) + (k <= n - 1 ? Cb(n - 1, k) : 0.0L);
     }
-    cudaStream_t st = g->ctx->stream;
+    for (int q = 0; q < 4; ++q) {
+        long double ex = (q & 1) ? 0.5L : -0.5L, ey = (q & 2) ? 0.5L : -0.5L;
+        std::vector<long double> pr(kTN + 1), pi(kTN + 1);   // eta^j
+        pr[0] = 1.0L;
+        pi[0] = 0.0L;
+        for (int j = 1; j <= kTN; ++j) {
+            pr[j] = pr[j - 1] * ex - pi[j - 1] * ey;
+            pi[j] = pr[j - 1] * ey + pi[j - 1] * ex;
+        }
+        for (int m = 0; m < kTN; ++m)
+            for (int k = 0; k < kTN; ++k) {
+                size_t i = ((size_t)q * kTN + m) * kTN + k;
+                if (m >= 1 && k == 0) tm[i] = make_double2((double)(-pr[m] / m), (double)(-pi[m] / m));
+                if (m >= 1 && k >= 1 && k <= m) {
+                    long double f = Cb(m - 1, k - 1) * ldexpl(1.0L, -k);
+                    tm[i] = make_double2((double)(f * pr[m - k]), (double)(f * pi[m - k]));
+                }
+                if (k >= m) {
+                    long double f = Cb(k, m) * ldexpl(1.0L, -m);
+                    tl[i] = make_double2((double)(f * pr[k - m]), (double)(f * pi[k - m]));
+                }
+            }
+    }
+}
+
+template <class T>
+static const T *upload_const(const T *h, size_t n) {
+    void *d = nullptr;
+    GQ_CUDA(cudaMalloc(&d, sizeof(T) * n));
+    GQ_CUDA(cudaMemcpy(d, h, sizeof(T) * n, cudaMemcpyHostToDevice));
+    return (const T *)d;
+}
+
+static const ConstTables &const_tables(int dev) {
+    static std::mutex mu;
+    static std::map<int, ConstTables> per_dev;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = per_dev.find(dev);
+    if (it != per_dev.end()) return it->second;
+    int cur = 0;
+    GQ_CUDA(cudaGetDevice(&cur));
+    GQ_CUDA(cudaSetDevice(dev));
+    std::vector<double> bn, lt;
+    std::vector<double2> dt, tm, tl;
+    host_const_tables(bn, dt, lt, tm, tl);
+    std::vector<double> pc((GQ_MAX_PQBX + 1) * 33, 0.0);
+    for (int m = 0; m <= GQ_MAX_PQBX; ++m)
+        for (int k = 1; k <= 32; ++k) pc[m * 33 + k] = bn[(m + k - 1) * kBinN + (k - 1)];
+    GQ_CUDA(cudaMemcpyToSymbol(c_pascal, pc.data(), sizeof(double) * pc.size()));
     GqLogTable LT;
     gq_log_table_host(&LT);
-    T.logt.alloc(kGqLogN);
-    GQ_CUDA(cudaMemcpyAsync(T.logt.p, &LT, sizeof(LT), cudaMemcpyHostToDevice, st));
     GqDflLogTable DT;
     gq_dfl_log_table_host(&DT);
-    T.dlogt.alloc(384);
-    GQ_CUDA(cudaMemcpyAsync(T.dlogt.p, &DT, sizeof(DT), cudaMemcpyHostToDevice, st));
-    T.binom.alloc(bn.size());
-    T.dtab.alloc(dt.size());
-    T.logtab.alloc(lt.size());
-    GQ_CUDA(cudaMemcpyAsync(T.binom.p, bn.data(), sizeof(double) * bn.size(), cudaMemcpyHostToDevice, st));
-    GQ_CUDA(cudaMemcpyAsync(T.dtab.p, dt.data(), sizeof(double2) * dt.size(), cudaMemcpyHostToDevice, st));
-    GQ_CUDA(cudaMemcpyAsync(T.logtab.p, lt.data(), sizeof(double) * lt.size(), cudaMemcpyHostToDevice, st));
-    {
-        // translation matrices for the four child quadrants, in long double
-        std::vector<double2> tm((size_t)4 * kTN * kTN, make_double2(0.0, 0.0)), tl(tm.size(), make_double2(0.0, 0.0));
-        std::vector<long double> C((size_t)(2 * kTN) * (2 * kTN), 0.0L);
-        auto Cb = [&](int n, int k) -> long double & { return C[(size_t)n * (2 * kTN) + k]; };
-        for (int n = 0; n < 2 * kTN; ++n) {
-            Cb(n, 0) = 1.0L;
-            for (int k = 1; k <= n; ++k) Cb(n, k) = Cb(n - 1, k - 1) + (k <= n - 1 ? Cb(n - 1, k) : 0.0L);
-        }
-        for (int q = 0; q < 4; ++q) {
-            long double ex = (q & 1) ? 0.5L : -0.5L, ey = (q & 2) ? 0.5L : -0.5L;
-            std::vector<long double> pr(kTN + 1), pi(kTN + 1);   // eta^j
-            pr[0] = 1.0L;
-            pi[0] = 0.0L;
-            for (int j = 1; j <= kTN; ++j) {
-                pr[j] = pr[j - 1] * ex - pi[j - 1] * ey;
-                pi[j] = pr[j - 1] * ey + pi[j - 1] * ex;
-            }
-            for (int m = 0; m < kTN; ++m)
-                for (int k = 0; k < kTN; ++k) {
-                    size_t i = ((size_t)q * kTN + m) * kTN + k;
-                    if (m >= 1 && k == 0) tm[i] = make_double2((double)(-pr[m] / m), (double)(-pi[m] / m));
-                    if (m >= 1 && k >= 1 && k <= m) {
-                        long double f = Cb(m - 1, k - 1) * ldexpl(1.0L, -k);
-                        tm[i] = make_double2((double)(f * pr[m - k]), (double)(f * pi[m - k]));
-                    }
-                    if (k >= m) {
-                        long double f = Cb(k, m) * ldexpl(1.0L, -m);
-                        tl[i] = make_double2((double)(f * pr[k - m]), (double)(f * pi[k - m]));
-                    }
-                }
-        }
-        T.tm2m.alloc(tm.size());
-        T.tl2l.alloc(tl.size());
-        GQ_CUDA(cudaMemcpyAsync(T.tm2m.p, tm.data(), sizeof(double2) * tm.size(), cudaMemcpyHostToDevice, st));
-        GQ_CUDA(cudaMemcpyAsync(T.tl2l.p, tl.data(), sizeof(double2) * tl.size(), cudaMemcpyHostToDevice, st));
-    }
+    ConstTables C;
+    C.logt = upload_const((const double *)&LT, kGqLogN);
+    C.dlogt = upload_const((const float *)&DT, 384);
+    C.binom = upload_const(bn.data(), bn.size());
+    C.dtab = upload_const(dt.data(), dt.size());
+    C.logtab = upload_const(lt.data(), lt.size());
+    C.tm2m = upload_const(tm.data(), tm.size());
+    C.tl2l = upload_const(tl.data(), tl.size());
+    GQ_CUDA(cudaSetDevice(cur));
+    return per_dev.emplace(dev, C).first->second;
+}
+
+static void make_tables(gq_geom *g, EvalTables &T) {
+    static_cast<ConstTables &>(T) = const_tables(g->ctx->device);
     T.tgt_ptpos.alloc(g->nt);
     if (g->npt) GQ_LAUNCH(g->ctx, k_tgt_ptpos, gq_blocks(g->npt, 256), 256, 0, g->npt, (const int *)g->pt_perm.p, T.tgt_ptpos.p);
-    GQ_CUDA(cudaStreamSynchronize(st));
 }
 
 // tables are owned by the geometry through this registry
