@@ -4,7 +4,8 @@ full loop -- features on the GPU, labels from the oracle on random star-
 shaped curves, training by the CUDA kernels, deployment on starfish curves at
 a requested accuracy of 1e-8 -- compared with the bound-driven orders: both
 must meet the accuracy against converged unaccelerated QBX (the oracle), and
-the learned orders must evaluate faster."""
+the learned orders must evaluate faster, and faster still with the
+mixed-precision tier of the same accuracy."""
 import numpy as np
 import pytest
 
@@ -116,11 +117,12 @@ def test_train_and_deploy_beats_bound_driven_orders():
     g = workloads.starfish_grid(4, 4, 64, n_off=1 << 16, on_surface="up", seed=1)
     q_fixed = 5
     results = {}
-    for mode in ("bound", "learned"):
-        geo = pkg.Geometry(g, pkg.params_default(p_qbx=q_fixed, p_fmm=0, n_max=32, eps=eps))
+    for mode in ("bound", "learned", "learned+mixed"):
+        prec = 1 if mode == "learned+mixed" else 0
+        geo = pkg.Geometry(g, pkg.params_default(p_qbx=q_fixed, p_fmm=0, n_max=32, eps=eps, precision=prec))
         geo.build()
         pb = geo.params.p_fmm
-        if mode == "learned":
+        if mode != "bound":
             p, q = geo.learned_orders(m, eps, margin_qbx=margin_q, margin_fmm=margin_f, q_ref=0, p_ref=P_REF,
                                       p_bound=pb)
         else:
@@ -150,6 +152,8 @@ def test_train_and_deploy_beats_bound_driven_orders():
         assert err <= eps, mode
     assert results["learned"][2] < results["bound"][2]
     assert results["learned"][1] < results["bound"][1]
+    # the learned orders with the mixed-precision tier of the same eps
+    assert results["learned+mixed"][1] < results["learned"][1]
 
 
 def test_centre_orders_truncate_each_expansion():
