@@ -1221,6 +1221,7 @@ struct SplitView {
     const float4 *lvl;   // per level l: [2l] = (rho, 1/rho), [2l+1] = (log rho, 1/rho^2)
     const float *logt;   // GqDflLogTable
     float H;             // root half-width (a power of two)
+    float fb;            // sources with |w|^2 < fb r^2 are taken in FP64 (fb >= 1)
 };
 
 __device__ __forceinline__ dflc dflc_add(dflc a, dflc b) { return dflc{dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
@@ -1339,7 +1340,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_split(EvalView E,
                     float4 y4 = X.s_rel[s];
                     dfl wx = dfl_add(dfl{y4.x, y4.y}, ex), wy = dfl_add(dfl{y4.z, y4.w}, ey);
                     dfl n2 = dfl_add(dfl_sqr(wx), dfl_sqr(wy));
-                    if (n2.hi < rc2) {
+                    if (n2.hi < rc2 * X.fb) {
                         used64 = true;
                         double2 yd = E.s_xy[s], sd = E.str[s];
                         double dx = yd.x - czd.x, dy = yd.y - czd.y;
@@ -1465,6 +1466,10 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points_split(EvalView E, 
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
     int tb = E.pt_beg[b], te = E.pt_end[b];
     double2 zb = box_centre(E.R, E.blev[b], E.bix[b], E.biy[b]);
+    // below eps = 1e-10, pairs closer than 1/8 of the box half-width go to FP64: a
+    // target that close to the curve sums large terms that cancel
+    const float hb = ldexpf(X.H, -E.blev[b]) * 0.125f;
+    const float near2 = X.fb > 1.0f ? hb * hb : 0x1p-100f;
     bool single = ne <= kNearRanges;
     if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
     for (int t0 = tb; t0 < te; t0 += kNearThreads / 32) {
@@ -1494,7 +1499,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points_split(EvalView E, 
                     float4 y4 = X.s_rel[s];
                     dfl wx = dfl_add(dfl{y4.x, y4.y}, ex), wy = dfl_add(dfl{y4.z, y4.w}, ey);
                     dfl n2 = dfl_add(dfl_sqr(wx), dfl_sqr(wy));
-                    if (n2.hi < 0x1p-100f) {
+                    if (n2.hi < near2) {
                         double2 yd = E.s_xy[s], td = E.sp_xy[t], sd = E.str[s];
                         double dx = yd.x - td.x, dy = yd.y - td.y, d2 = dx * dx + dy * dy;
                         if (d2 == 0.0) continue;
@@ -2050,7 +2055,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
               (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, g->strength.p);
     const bool f32 = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-6;
-    const bool split = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-10 && g->prm.eps < 1e-6;
+    const bool split = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-12 && g->prm.eps < 1e-6;
     MixedView X{};
     if (f32) {
         if (!g->mixed_ready) {
@@ -2105,6 +2110,9 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         }
         SX.s_rel = g->s_rel2; SX.str = g->str2; SX.c_rel = g->c_rel2; SX.c_r = g->c_r2; SX.p_rel = g->p_rel2;
         SX.M = g->M2; SX.lvl = g->lvl2; SX.logt = T.dlogt; SX.H = (float)g->root.H;
+        // below eps = 1e-10 the pairs with |r/w| > 1/2 also go to FP64: their rounding is
+        // amplified by |r/w|^m too, and the pair tier alone would leave about 5e-13
+        SX.fb = g->prm.eps < 1e-10 ? 4.0f : 1.0f;
     }
     mark(S_STR, st);
     GQ_CUDA(cudaEventRecord(g->ev_str, st));
@@ -2262,7 +2270,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
 // after another.
 void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, double *const *out) {
     const bool f32 = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-6;
-    const bool split = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-10 && g->prm.eps < 1e-6;
+    const bool split = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-12 && g->prm.eps < 1e-6;
     if (nd <= 1 || f32 || split || g->n_ctr_boxes == 0) {
         for (int d = 0; d < nd; ++d) gq_eval_all(g, kernel, dens[d], out[d], nullptr);
         return;
