@@ -87,8 +87,8 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
  *                 relative to the FP64 path).  In both tiers a source inside
  *                 a centre's expansion disk (|r/w| > 1, where rounding would
  *                 grow as |r/w|^m) is taken in FP64, below eps = 1e-10 also
- *                 a source with |r/w| > 1/2 and a source within 1/8 of the
- *                 box half-width of a point target; the List 3 far
+ *                 a source within 1/8 of the box half-width of a point
+ *                 target; the List 3 far
  *                 translation to centres (M2QBXL) runs in pairs when the tree
  *                 has at most 24 levels.  M2M, M2L, L2L, L2QBXL, P2M, P2L
  *                 and the final QBX evaluation stay FP64.  For eps < 1e-12

@@ -1222,6 +1222,7 @@ struct SplitView {
     const float *logt;   // GqDflLogTable
     float H;             // root half-width (a power of two)
     float fb;            // sources with |w|^2 < fb r^2 are taken in FP64 (fb >= 1)
+    bool near_pt;        // point-target pairs closer than 1/8 of the box half-width in FP64
 };
 
 __device__ __forceinline__ dflc dflc_add(dflc a, dflc b) { return dflc{dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
@@ -1469,7 +1470,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points_split(EvalView E, 
     // below eps = 1e-10, pairs closer than 1/8 of the box half-width go to FP64: a
     // target that close to the curve sums large terms that cancel
     const float hb = ldexpf(X.H, -E.blev[b]) * 0.125f;
-    const float near2 = X.fb > 1.0f ? hb * hb : 0x1p-100f;
+    const float near2 = X.near_pt ? hb * hb : 0x1p-100f;
     bool single = ne <= kNearRanges;
     if (single) load_ranges_f(E, b, zb, 0, ne, R, wsum);
     for (int t0 = tb; t0 < te; t0 += kNearThreads / 32) {
@@ -2110,9 +2111,11 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         }
         SX.s_rel = g->s_rel2; SX.str = g->str2; SX.c_rel = g->c_rel2; SX.c_r = g->c_r2; SX.p_rel = g->p_rel2;
         SX.M = g->M2; SX.lvl = g->lvl2; SX.logt = T.dlogt; SX.H = (float)g->root.H;
-        // below eps = 1e-10 the pairs with |r/w| > 1/2 also go to FP64: their rounding is
-        // amplified by |r/w|^m too, and the pair tier alone would leave about 5e-13
-        SX.fb = g->prm.eps < 1e-10 ? 4.0f : 1.0f;
+        // only the sources inside the disk go to FP64: widening that region to |r/w| > 1/2
+        // lowered the added D rounding on a small grid from 1.6e-13 to 1.45e-13 only, and
+        // its divergent FP64 lanes tripled the kernel time
+        SX.fb = 1.0f;
+        SX.near_pt = g->prm.eps < 1e-10;
     }
     mark(S_STR, st);
     GQ_CUDA(cudaEventRecord(g->ev_str, st));
