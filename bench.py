@@ -452,7 +452,7 @@ def run_gpu(args, rank, world, local):
         # the other measured rates on this GPU: FP32 FMA, and the FP64 tensor cores (an FP64
         # contraction would belong there only if they beat the FP64 FMA rate)
         others = {}
-        for what, name in ((1, "fp32_fma"), (2, "fp64_tensor_mma")):
+        for what, name in ((1, "fp32_fma"), (2, "fp64_tensor_mma"), (3, "fp64_fma_and_mma_together")):
             v = C.c_double()
             if L.gq_probe_fma_peak(ctx, what, C.byref(v)) == 0:
                 others[name] = v.value

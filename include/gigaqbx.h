@@ -340,7 +340,9 @@ gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out);
 /* Measurement helper: throughput of a dependent-chain-free FMA loop on the
  * context's device, in TFLOP/s (2 flops per FMA).  what = 0: FP64 FMA,
  * what = 1: FP32 FMA, what = 2: FP64 tensor-core MMA (warp-wide
- * mma.sync m8n8k4 FP64, 512 flops each).  Used as the measured peak of the
+ * mma.sync m8n8k4 FP64, 512 flops each), what = 3: both FP64 paths at once
+ * (half the warps each, equal flops; about the sum of the two rates if they
+ * issue to separate units).  Used as the measured peak of the
  * FP64/FP32 roofline and to decide whether a contraction should use the FP64
  * tensor cores; the paper has no counterpart.  Runs about 0.1 s of device work. */
 gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops);
@@ -354,7 +356,7 @@ gq_status gq_memory_release(void);
 /* Check helper for the FP64 logarithm and reciprocal the direct kernels use
  * (no counterpart in the paper): y[i] = f(x[i]) on the device, x and y device
  * arrays of n doubles; fn = 0: the table-driven logarithm, 1: CUDA's log,
- * 2: the Newton reciprocal, 3: IEEE division 1/x, 4: the double-FP32
+ * 2: the reciprocal (approximate seed + one third-order step), 3: IEEE division 1/x, 4: the double-FP32
  * logarithm of the split-precision kernels (x rounded to an FP32 pair,
  * x in [2^-126, 2^126]), 5: the double-FP32 reciprocal (same range). */
 gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y);

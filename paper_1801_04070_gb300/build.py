@@ -38,9 +38,9 @@ def _flags(src: str) -> list[str]:
 
 
 def _deps_mtime() -> float:
-    files = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "gq_internal.cuh"),
-                                                         os.path.join(ROOT, "include", "gigaqbx.h"),
-                                                         os.path.abspath(__file__)]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    files = [os.path.join(CSRC, s) for s in SOURCES] + headers + [os.path.join(ROOT, "include", "gigaqbx.h"),
+                                                                   os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files)
 
 

@@ -597,7 +597,7 @@ gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out) {
 }
 
 gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops) {
-    if (!ctx || !tflops || what < 0 || what > 2) return GQ_ERR_INVALID;
+    if (!ctx || !tflops || what < 0 || what > 3) return GQ_ERR_INVALID;
     return guarded(ctx, [&] { *tflops = gq_probe_fma(ctx, what); });
 }
 

@@ -104,10 +104,77 @@ double run_dmma(gq_ctx *ctx) {
     return best;
 }
 
+// Both FP64 paths at once: even warps run the FP64 FMA loop, odd warps the FP64
+// MMA loop, each sized to the same flop count (kChains * kIters * 32 FMAs
+// against kMma * kMmaIters MMAs of 256 multiply-adds).  The combined rate is
+// about the larger single rate if the two share one pipe and about their sum
+// if they issue to separate units.
+constexpr int kMixIters = kMma * kMmaIters * 256 / (kChains * 32);
+
+__global__ void k_fma_dmma_loop(double *out, double a, double b) {
+    const int warp = threadIdx.x >> 5;
+    double s = 0.0;
+    if ((warp & 1) == 0) {
+        double x[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = (double)(threadIdx.x + c) * 1e-3;
+        for (int i = 0; i < kMixIters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) s += x[c];
+    } else {
+        double aa = 1e-3 * (double)(threadIdx.x + 1), bb = 1e-7;
+        double c[kMma][2];
+#pragma unroll
+        for (int j = 0; j < kMma; ++j) c[j][0] = c[j][1] = 0.0;
+        for (int i = 0; i < kMmaIters; ++i) {
+#pragma unroll
+            for (int j = 0; j < kMma; ++j)
+                asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                             : "+d"(c[j][0]), "+d"(c[j][1])
+                             : "d"(aa), "d"(bb));
+        }
+#pragma unroll
+        for (int j = 0; j < kMma; ++j) s += c[j][0] + c[j][1];
+    }
+    if (s == -1.2345) out[0] = s;   // keeps the loops alive; never true for these inputs
+}
+
+double run_fma_dmma(gq_ctx *ctx) {
+    int dev = ctx->device, sms = 0;
+    GQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    dbuf<double> out;
+    out.alloc(1);
+    const int threads = 256;
+    const int blocks = sms * 8;
+    cudaEvent_t e0, e1;
+    GQ_CUDA(cudaEventCreate(&e0));
+    GQ_CUDA(cudaEventCreate(&e1));
+    GQ_LAUNCH(ctx, k_fma_dmma_loop, blocks, threads, 0, out.p, 0.999999, 1e-7);  // warm-up
+    double best = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+        GQ_CUDA(cudaEventRecord(e0, ctx->stream));
+        GQ_LAUNCH(ctx, k_fma_dmma_loop, blocks, threads, 0, out.p, 0.999999, 1e-7);
+        GQ_CUDA(cudaEventRecord(e1, ctx->stream));
+        GQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        GQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const double warps = (threads / 32) * (double)blocks;
+        double flops = warps / 2 * (2.0 * kChains * kMixIters * 32) + warps / 2 * (2.0 * 256 * kMma * kMmaIters);
+        double tf = flops / (ms * 1e-3) / 1e12;
+        if (tf > best) best = tf;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
 }  // namespace
 
 double gq_probe_fma(gq_ctx *ctx, int what) {
-    return what == 0 ? run<double>(ctx) : what == 1 ? run<float>(ctx) : run_dmma(ctx);
+    return what == 0 ? run<double>(ctx) : what == 1 ? run<float>(ctx) : what == 2 ? run_dmma(ctx) : run_fma_dmma(ctx);
 }
 
 namespace {

@@ -34,6 +34,7 @@ def test_log_matches_cuda_log():
     fin = np.isfinite(ref)
     assert np.array_equal(np.isfinite(mine), fin)
     err = np.abs(mine[fin] - ref[fin])
+    print(f"FP64 log: max error {(err / np.spacing(np.maximum(np.abs(ref[fin]), 1.0))).max():.2f} ulp of max(|log x|, 1)")
     # absolute error within a few ulp of max(|log x|, 1), i.e. of the terms it multiplies
     assert (err <= 4 * np.spacing(np.maximum(np.abs(ref[fin]), 1.0))).all(), err.max()
 
@@ -43,7 +44,9 @@ def test_reciprocal_matches_division():
     x = x[(x > 0) & np.isfinite(x)]
     x = np.concatenate([x, -x])
     mine, ref = _run(2, x), _run(3, x)
-    assert (np.abs(mine - ref) <= 2 * np.spacing(np.abs(ref))).all()
+    ulps = np.abs(mine - ref) / np.spacing(np.abs(ref))
+    print(f"FP64 reciprocal: max error {ulps.max():.2f} ulp, {np.mean(ulps > 0):.2e} of results not the IEEE quotient")
+    assert (ulps <= 2).all()
 
 
 def _split_inputs():
@@ -68,3 +71,29 @@ def test_split_reciprocal_matches_division():
     err = np.abs(mine - ref) / np.abs(ref)
     print(f"double-FP32 reciprocal: max relative error {err.max():.2e} (2^{np.log2(err.max()):.1f})")
     assert err.max() <= 2.0 ** -44
+
+
+def test_fma_probe_rates():
+    """The throughput probe behind the ALU roofline: every variant returns a
+    positive rate, FP32 beats FP64, the combined FP64 FMA + MMA run is at least
+    the slower of the two, and an unknown variant is rejected."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes as C
+
+    import paper_1801_04070_gb300 as pkg
+    import workloads
+    geo = pkg.Geometry(workloads.starfish_c1())
+    L = pkg.lib()
+    rates = []
+    for what in range(4):
+        v = C.c_double()
+        assert L.gq_probe_fma_peak(geo._ctx, what, C.byref(v)) == 0
+        assert v.value > 0
+        rates.append(v.value)
+    assert rates[1] > rates[0]
+    assert rates[3] >= 0.9 * min(rates[0], rates[2])
+    v = C.c_double()
+    assert L.gq_probe_fma_peak(geo._ctx, 4, C.byref(v)) != 0
+    print("probe TFLOP/s fp64 fma, fp32 fma, fp64 mma, fp64 fma+mma:", [round(r, 3) for r in rates])
