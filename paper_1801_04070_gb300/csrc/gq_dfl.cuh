@@ -110,6 +110,18 @@ __device__ __forceinline__ void dflc_acc(dflc &acc, dflc t) {
     dfl_acc(acc.re, t.re);
     dfl_acc(acc.im, t.im);
 }
+// acc += c a (c = ch + cl, a = ah + al) into a lazy accumulator: the product's
+// high part p = fl(ch ah) enters the running sum by a two-sum, its error
+// fma(ch, ah, -p) and the cross terms ch al + cl ah go to lo (12 FP32 operations).
+__device__ __forceinline__ void dfl_mac_lazy(dfl &acc, float ch, float cl, float ah, float al) {
+    float p = __fmul_rn(ch, ah);
+    float e = fmaf(ch, ah, -p);
+    e = fmaf(ch, al, e);
+    e = fmaf(cl, ah, e);
+    dfl s = dfl_two_sum(acc.hi, p);
+    acc.hi = s.hi;
+    acc.lo += s.lo + e;
+}
 
 // ---------------------------------------------------------------- logarithm
 // Tang's table-driven reduction (ACM TOMS 16(4), 1990) carried out in FP32

@@ -1654,6 +1654,75 @@ void dispatch_w_centres_split(gq_ctx *ctx, const EvalView &E, const SplitView &X
     }
 }
 
+// M2L (Stage 4) in FP32 pairs for the mixed tiers: the factored translation of
+// k_m2l -- At_k = A_k delta^-k, G_m = sum_k C(m+k-1, k-1) At_k, then
+// L_m += (-1)^m delta^-m (G_m - A_0/m) and L_0 += A_0 log(rho |delta|) + G_0 --
+// with the multipoles, delta^-k, the binomials and every product and sum in
+// pairs (about 2^-46 relative per operation; the G_m sums in lazy
+// accumulators).  Groups of G lanes, lane g the order index, as in k_m2l.
+// The binomial rows sit in shared memory with an odd row stride (in 8-byte
+// words), so that the G lanes of a group, each reading its own row, hit
+// distinct banks.
+template <int G>
+__global__ void k_m2l_split(EvalView E, SplitView X, int nwork, const int *__restrict__ work,
+                            const float4 *__restrict__ dtab2, const float2 *__restrict__ logtab2,
+                            const float2 *__restrict__ binom2, double2 *__restrict__ L) {
+    extern __shared__ float2 pasc2[];   // [P+1][RS]: C(m+k-1, k-1) as (hi, lo)
+    const int P = E.P, P1 = P + 1, RS = P1 | 1;
+    for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) {
+        int m = i / P1, k = i % P1;
+        pasc2[m * RS + k] = k >= 1 ? binom2[(m + k - 1) * kBinN + (k - 1)] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    int lane = threadIdx.x & 31, g = lane % G;
+    long long grp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    bool act = grp < nwork;
+    int b = act ? work[grp] : 0;
+    int beg = act ? E.loff[1][b] : 0, end = act ? E.loff[1][b + 1] : 0;
+    int n = end - beg, nmax = n;
+    for (int o = G; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    int l = E.blev[b], bx = E.bix[b], by = E.biy[b];
+    const float4 lv = X.lvl[2 * l + 1];
+    const dfl logrho{lv.x, lv.y};
+    float ih = g >= 1 ? __frcp_rn((float)g) : 0.f;
+    const dfl ig{ih, g >= 1 ? fmaf(-(float)g, ih, 1.0f) * ih : 0.f};   // 1/g
+    const dfl zero{0.f, 0.f};
+    dflc acc{zero, zero};
+    const float2 *prow = pasc2 + (g <= P ? g : 0) * RS;
+    for (int i = 0; i < nmax; ++i) {
+        bool valid = i < n;
+        int d = valid ? E.lidx[1][beg + i] : b;
+        int off = valid ? (by - E.biy[d] + 5) * 11 + (bx - E.bix[d] + 5) : 0;
+        dflc A = (valid && g <= P) ? dflc_ld(X.M[(size_t)d * P1 + g]) : dflc{zero, zero};
+        dflc tk = dflc_ld(dtab2[off * 32 + g]);                 // delta^-g
+        dflc At = g >= 1 ? dflc_mul(A, tk) : dflc{zero, zero};
+        dfl A0{__shfl_sync(0xffffffffu, A.re.hi, 0, G), __shfl_sync(0xffffffffu, A.re.lo, 0, G)};
+        dflc Gm{zero, zero};
+        for (int k = 1; k <= P; ++k) {
+            float xh = __shfl_sync(0xffffffffu, At.re.hi, k, G), xl = __shfl_sync(0xffffffffu, At.re.lo, k, G);
+            float yh = __shfl_sync(0xffffffffu, At.im.hi, k, G), yl = __shfl_sync(0xffffffffu, At.im.lo, k, G);
+            float2 c = prow[k];
+            dfl_mac_lazy(Gm.re, c.x, c.y, xh, xl);
+            dfl_mac_lazy(Gm.im, c.x, c.y, yh, yl);
+        }
+        if (!valid) continue;
+        Gm.re = dfl_two_sum(Gm.re.hi, Gm.re.lo);
+        Gm.im = dfl_two_sum(Gm.im.hi, Gm.im.lo);
+        if (g == 0) {
+            float2 lt = logtab2[off];
+            dflc_acc(acc, dflc{dfl_add(dfl_mul(A0, dfl_add(logrho, dfl{lt.x, lt.y})), Gm.re), Gm.im});
+        } else if (g <= P) {
+            dflc t{dfl_add(Gm.re, dfl_neg(dfl_mul(A0, ig))), Gm.im};
+            dflc sg = (g & 1) ? dflc{dfl_neg(tk.re), dfl_neg(tk.im)} : tk;
+            dflc_acc(acc, dflc_mul(sg, t));
+        }
+    }
+    if (act && g <= P) {
+        double2 *dst = L + (size_t)b * P1 + g;
+        *dst = make_double2(dst->x + dfl_to_double(acc.re), dst->y + dfl_to_double(acc.im));
+    }
+}
+
 template <int QQ>
 void launch_near_centres_split(gq_ctx *ctx, const EvalView &E, const SplitView &X, int nwork, const int *work,
                                double2 *Q) {
@@ -1864,6 +1933,9 @@ struct ConstTables {
     const double *logtab = nullptr;   // [121] log|delta|
     const double2 *tm2m = nullptr;    // [4][kTN][kTN] M2M matrices
     const double2 *tl2l = nullptr;    // [4][kTN][kTN] L2L matrices
+    const float4 *dtab2 = nullptr;    // dtab as FP32 pairs (re.hi, re.lo, im.hi, im.lo)
+    const float2 *logtab2 = nullptr;  // logtab as FP32 pairs
+    const float2 *binom2 = nullptr;   // binom as FP32 pairs
 };
 
 struct EvalTables : ConstTables {
@@ -1962,6 +2034,21 @@ static const ConstTables &const_tables(int dev) {
     C.logtab = upload_const(lt.data(), lt.size());
     C.tm2m = upload_const(tm.data(), tm.size());
     C.tl2l = upload_const(tl.data(), tl.size());
+    auto split = [](double x) {
+        float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    };
+    std::vector<float4> dt2(dt.size());
+    for (size_t i = 0; i < dt.size(); ++i) {
+        float2 a = split(dt[i].x), b = split(dt[i].y);
+        dt2[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    std::vector<float2> lt2(lt.size()), bn2(bn.size());
+    for (size_t i = 0; i < lt.size(); ++i) lt2[i] = split(lt[i]);
+    for (size_t i = 0; i < bn.size(); ++i) bn2[i] = split(bn[i]);
+    C.dtab2 = upload_const(dt2.data(), dt2.size());
+    C.logtab2 = upload_const(lt2.data(), lt2.size());
+    C.binom2 = upload_const(bn2.data(), bn2.size());
     GQ_CUDA(cudaSetDevice(cur));
     return per_dev.emplace(dev, C).first->second;
 }
@@ -2084,6 +2171,10 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     SplitView SX{};
     // List 3 far at centres runs in pairs in both mixed tiers (exact FP32 box offsets need l <= 23)
     const bool split_w = (split || f32) && g->nlev <= 24;
+    // M2L in pairs down to eps = 1e-10: its rounding, amplified by the binomial
+    // sums' cancellation (at most about 25x for the same-level offsets |delta| >= 4),
+    // stays near 1e-13 relative, below eps/5 there; at smaller eps M2L stays FP64
+    const bool m2l_split = (split || f32) && g->prm.eps >= 1e-10;
     if (split || f32) {
         if (!g->split_ready) {
             g->s_rel2.alloc(g->nsrc);
@@ -2170,15 +2261,27 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
                   g->M.p);
     }
     mark(S_M2M, st);
+    // multipoles as FP32 pairs for the pair M2L and the pair List 3 far kernels
+    if (split_w || m2l_split)
+        GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
+                  (const double2 *)g->M, g->M2.p);
     // Stage 4
     if (g->n_far_boxes) {
-        size_t sm = sizeof(double) * P1 * P1;
-        auto k16 = k_m2l<16>;
-        auto k32 = k_m2l<32>;
         int G = P1 <= 16 ? 16 : 32;
-        GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E,
-                  g->n_far_boxes, (const int *)g->far_boxes, (const double2 *)g->M, (const double2 *)T.dtab,
-                  (const double *)T.logtab, g->L.p);
+        if (m2l_split) {
+            size_t sm = sizeof(float2) * P1 * (P1 | 1);
+            auto k16 = k_m2l_split<16>;
+            auto k32 = k_m2l_split<32>;
+            GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E, SX,
+                      g->n_far_boxes, (const int *)g->far_boxes, T.dtab2, T.logtab2, T.binom2, g->L.p);
+        } else {
+            size_t sm = sizeof(double) * P1 * P1;
+            auto k16 = k_m2l<16>;
+            auto k32 = k_m2l<32>;
+            GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E,
+                      g->n_far_boxes, (const int *)g->far_boxes, (const double2 *)g->M, (const double2 *)T.dtab,
+                      (const double *)T.logtab, g->L.p);
+        }
     }
     mark(S_M2L, st);
     if (g->n_far_boxes) {
@@ -2196,9 +2299,6 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     if (f32)
         GQ_LAUNCH(ctx, k_to_float2, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
                   (const double2 *)g->M, g->M_f.p);
-    if (split_w)
-        GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
-                  (const double2 *)g->M, g->M2.p);
     mark(S_L2L, st);
     // Stage 5b
     if (g->nc && split_w) {

@@ -40,8 +40,9 @@ def test_mixed_split_tier_matches_oracle(kern, eps, bound):
     """1e-12 <= eps < 1e-6: power recurrences in double-FP32 pairs (about 48
     significant bits).  Pairs with sources near a centre amplify the rounding
     by |r/w|^m: those inside the disk are taken in FP64, and below eps = 1e-10
-    also those with |r/w| > 1/2.  Bound: eps/5 at the smallest eps of each
-    range (1e-10 and 1e-12)."""
+    also the point-target pairs closer than 1/8 of the box half-width.  M2L
+    runs in pairs at eps = 1e-8 and in FP64 at 1e-12.  Bound: eps/5 at the
+    smallest eps of each range (1e-10 and 1e-12)."""
     g = workloads.small_grid(3, 2, 24, 5000, seed=11, on_surface="up", p_qbx=8, p_fmm=15)
     geo = _geo(g, p_qbx=8, p_fmm=15, n_max=32, eps=eps, precision=1)
     v = geo.eval(kern, g["density"])
@@ -77,6 +78,31 @@ def test_mixed_split_tier_sampled_at_eps_orders(kern):
     err = np.abs(v[sel] - ref[sel]).max() / np.abs(ref[sel]).max()
     print(f"MIXED double-FP32 {kern} at p_qbx {prm.p_qbx} p_fmm {prm.p_fmm}: rel err vs FP64 oracle {err:.2e}")
     assert err <= 2e-11
+
+
+@pytest.mark.parametrize("kern", ["S", "D"])
+@pytest.mark.parametrize("eps,p_fmm", [(1e-6, 19), (1e-10, 30)])
+def test_pair_m2l_rounding(kern, eps, p_fmm):
+    """M2L in FP32 pairs (both mixed tiers, eps >= 1e-10): on a 4x4 starfish
+    grid, whose far field runs through several hundred thousand List 2
+    translations, the mixed evaluation at p_fmm up to 30 stays within eps/5 of
+    the FP64 path at the same orders; in the pair tier the QBX coefficients
+    (which carry the translated local expansions) also stay within eps/5 of the
+    FP64 ones, order by order."""
+    g = workloads.starfish_grid(4, 4, 64, n_off=1 << 16, on_surface="up", seed=1)
+    mixed = _geo(g, p_qbx=7, p_fmm=p_fmm, n_max=32, eps=eps, precision=1)
+    fp64 = _geo(g, p_qbx=7, p_fmm=p_fmm, n_max=32, eps=eps, precision=0)
+    v = mixed.eval(kern, g["density"])
+    qm = mixed.qbx_coefficients()
+    f = fp64.eval(kern, g["density"])
+    qf = fp64.qbx_coefficients()
+    added = np.abs(v - f).max() / np.abs(f).max()
+    qerr = max(np.abs(qm[:, m] - qf[:, m]).max() / np.abs(qf[:, m]).max() for m in range(qf.shape[1]))
+    print(f"pair M2L, eps {eps:.0e}, p_fmm {p_fmm}, {kern}: potential {added:.2e}, QBX coefficients {qerr:.2e} "
+          f"relative to the FP64 path")
+    assert added <= eps / 5
+    if eps < 1e-6:
+        assert qerr <= eps / 5
 
 
 def test_mixed_below_threshold_is_fp64():
