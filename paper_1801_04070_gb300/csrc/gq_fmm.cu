@@ -1654,6 +1654,110 @@ void dispatch_w_centres_split(gq_ctx *ctx, const EvalView &E, const SplitView &X
     }
 }
 
+// P2M (Stage 2) in FP32 pairs for the mixed tiers: the sums of k_p2m with the
+// box-relative source coordinates, the strengths, the powers of u and the lane
+// sums in pairs (lazy accumulators, normalised before the group butterfly).
+// Writes the pair multipoles M2 of the source leaves.
+template <int PM>
+__global__ void k_p2m_split(EvalView E, SplitView X, int nwork, const int *__restrict__ work,
+                            float4 *__restrict__ M2) {
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) / kP2MG, lane = threadIdx.x % kP2MG;
+    // whole groups leave together; the shuffles below stay inside a group
+    if (wid >= nwork) return;
+    int b = work[wid];
+    int l = E.blev[b], P = E.P;
+    const float irh = X.lvl[2 * l].z;   // 1/rho, a power of two: exact in FP32
+    const dfl zero{0.f, 0.f};
+    dflc acc[PM + 1];
+#pragma unroll
+    for (int k = 0; k <= PM; ++k) acc[k] = dflc{zero, zero};
+    for (int s = E.src_beg[b] + lane; s < E.src_end[b]; s += kP2MG) {
+        float4 y = X.s_rel[s];
+        dflc u{dfl{y.x * irh, y.y * irh}, dfl{y.z * irh, y.w * irh}};
+        dflc q = dflc_ld(X.str[s]);
+        dflc t;
+        if (E.kernel == GQ_D) {
+            t = dflc{dfl{q.re.hi * irh, q.re.lo * irh}, dfl{q.im.hi * irh, q.im.lo * irh}};
+        } else {
+            dfl_acc(acc[0].re, q.re);
+            t = dflc{dfl_mul(q.re, u.re), dfl_mul(q.re, u.im)};
+        }
+        dflc_acc(acc[1], t);
+#pragma unroll
+        for (int k = 2; k <= PM; ++k)
+            if (k <= P) {
+                t = dflc_mul(t, u);
+                dflc_acc(acc[k], t);
+            }
+    }
+    const unsigned gmask = ((1u << kP2MG) - 1u) << (threadIdx.x & 31 & ~(kP2MG - 1));
+#pragma unroll
+    for (int k = 0; k <= PM; ++k)
+        if (k <= P) {
+            dflc v{dfl_two_sum(acc[k].re.hi, acc[k].re.lo), dfl_two_sum(acc[k].im.hi, acc[k].im.lo)};
+            for (int o = kP2MG / 2; o > 0; o >>= 1) {
+                dflc w{dfl{__shfl_xor_sync(gmask, v.re.hi, o), __shfl_xor_sync(gmask, v.re.lo, o)},
+                       dfl{__shfl_xor_sync(gmask, v.im.hi, o), __shfl_xor_sync(gmask, v.im.lo, o)}};
+                v = dflc_add(v, w);
+            }
+            acc[k] = v;
+        }
+#pragma unroll
+    for (int k = 0; k <= PM; ++k)
+        if (k <= P && k % kP2MG == lane) {
+            dflc v = acc[k];
+            if (k >= 1) {
+                if (E.kernel == GQ_D) {
+                    v = dflc{dfl_neg(v.re), dfl_neg(v.im)};
+                } else {
+                    float ih = __frcp_rn((float)k);
+                    dfl mik{-ih, -(fmaf(-(float)k, ih, 1.0f) * ih)};   // -1/k
+                    v = dflc{dfl_mul(v.re, mik), dfl_mul(v.im, mik)};
+                }
+            }
+            M2[(size_t)b * (P + 1) + k] = make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo);
+        }
+}
+
+// M2M (Stage 2) in FP32 pairs: k_m2m_t with the quadrant matrices and the
+// multipoles in pairs, one thread per (parent, m), one lazy sum over children.
+__global__ void k_m2m_split(EvalView E, int lstart, int lend, const float4 *__restrict__ T2,
+                            float4 *__restrict__ M2) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int P1 = E.P + 1;
+    int b = lstart + (int)(t / P1), m = (int)(t % P1);
+    if (b >= lend) return;
+    int4 c4 = E.bchild[b];
+    int ch[4] = {c4.x, c4.y, c4.z, c4.w};
+    if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;  // leaf
+    if (E.sub_src[b] == 0) return;
+    const dfl zero{0.f, 0.f};
+    dflc acc{zero, zero};
+    for (int q = 0; q < 4; ++q) {
+        int c = ch[q];
+        if (c < 0 || E.sub_src[c] == 0) continue;
+        const float4 *A = M2 + (size_t)c * P1;
+        if (m == 0) {
+            dflc_acc(acc, dflc_ld(A[0]));
+            continue;
+        }
+        const float4 *Tq = T2 + ((size_t)q * kTN + m) * kTN;
+        dflc t0 = dflc_ld(__ldg(&Tq[0]));
+        dfl a0 = dflc_ld(A[0]).re;
+        dflc_acc(acc, dflc{dfl_mul(t0.re, a0), dfl_mul(t0.im, a0)});
+        for (int k = 1; k <= m; ++k) dflc_acc(acc, dflc_mul(dflc_ld(__ldg(&Tq[k])), dflc_ld(A[k])));
+    }
+    dfl re = dfl_two_sum(acc.re.hi, acc.re.lo), im = dfl_two_sum(acc.im.hi, acc.im.lo);
+    M2[(size_t)b * P1 + m] = make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+__global__ void k_from_dfl4(long long n, const float4 *__restrict__ in, double2 *__restrict__ out) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float4 v = in[j];
+    out[j] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
 // M2L (Stage 4) in FP32 pairs for the mixed tiers: the factored translation of
 // k_m2l -- At_k = A_k delta^-k, G_m = sum_k C(m+k-1, k-1) At_k, then
 // L_m += (-1)^m delta^-m (G_m - A_0/m) and L_0 += A_0 log(rho |delta|) + G_0 --
@@ -1936,6 +2040,7 @@ struct ConstTables {
     const float4 *dtab2 = nullptr;    // dtab as FP32 pairs (re.hi, re.lo, im.hi, im.lo)
     const float2 *logtab2 = nullptr;  // logtab as FP32 pairs
     const float2 *binom2 = nullptr;   // binom as FP32 pairs
+    const float4 *tm2m2 = nullptr;    // tm2m as FP32 pairs
 };
 
 struct EvalTables : ConstTables {
@@ -2049,6 +2154,12 @@ static const ConstTables &const_tables(int dev) {
     C.dtab2 = upload_const(dt2.data(), dt2.size());
     C.logtab2 = upload_const(lt2.data(), lt2.size());
     C.binom2 = upload_const(bn2.data(), bn2.size());
+    std::vector<float4> tm2(tm.size());
+    for (size_t i = 0; i < tm.size(); ++i) {
+        float2 a = split(tm[i].x), b = split(tm[i].y);
+        tm2[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    C.tm2m2 = upload_const(tm2.data(), tm2.size());
     GQ_CUDA(cudaSetDevice(cur));
     return per_dev.emplace(dev, C).first->second;
 }
@@ -2195,7 +2306,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
             g->split_ready = true;
         }
         g->M2.alloc((size_t)g->nbox * P1);
-        if (split) {
+        if (split || m2l_split) {
             g->str2.alloc(g->nsrc);
             if (g->nsrc) GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks(g->nsrc, 256), 256, 0, (long long)g->nsrc,
                                    (const double2 *)g->strength, g->str2.p);
@@ -2244,25 +2355,40 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     // ---- FMM passes on the context's stream
     mark(S_FMM, st);
     GQ_CUDA(cudaMemsetAsync(g->M.p, 0, sizeof(double2) * g->nbox * P1, st));
+    if (m2l_split) GQ_CUDA(cudaMemsetAsync(g->M2.p, 0, sizeof(float4) * g->nbox * P1, st));
     GQ_CUDA(cudaMemsetAsync(g->L.p, 0, sizeof(double2) * g->nbox * P1, st));
     GQ_CUDA(cudaMemsetAsync(g->Q.p, 0, sizeof(double2) * g->nc * Q1, st));
     if (g->npt) GQ_CUDA(cudaMemsetAsync(g->pot.p, 0, sizeof(double) * g->npt, st));
-    // Stage 2
+    // Stage 2 (in pairs wherever M2L runs in pairs: the multipoles then live in
+    // M2 and the FP64 copy is made from them for the FP64 consumers)
     if (g->n_leaf_src) {
-        auto k8 = k_p2m<8>;
-        auto k16 = k_p2m<16>;
-        auto k32 = k_p2m<GQ_MAX_PFMM>;
-        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * kP2MG, 128), 128, 0,
-                  E, g->n_leaf_src, (const int *)g->leaf_src_boxes, g->M.p);
+        if (m2l_split) {
+            auto k8 = k_p2m_split<8>;
+            auto k16 = k_p2m_split<16>;
+            auto k32 = k_p2m_split<GQ_MAX_PFMM>;
+            GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * kP2MG, 128),
+                      128, 0, E, SX, g->n_leaf_src, (const int *)g->leaf_src_boxes, g->M2.p);
+        } else {
+            auto k8 = k_p2m<8>;
+            auto k16 = k_p2m<16>;
+            auto k32 = k_p2m<GQ_MAX_PFMM>;
+            GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks((long long)g->n_leaf_src * kP2MG, 128),
+                      128, 0, E, g->n_leaf_src, (const int *)g->leaf_src_boxes, g->M.p);
+        }
     }
     for (int l = g->nlev - 2; l >= 0; --l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_m2m_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, (const double2 *)T.tm2m,
-                  g->M.p);
+        if (m2l_split)
+            GQ_LAUNCH(ctx, k_m2m_split, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, T.tm2m2, g->M2.p);
+        else
+            GQ_LAUNCH(ctx, k_m2m_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e,
+                      (const double2 *)T.tm2m, g->M.p);
     }
     mark(S_M2M, st);
-    // multipoles as FP32 pairs for the pair M2L and the pair List 3 far kernels
-    if (split_w || m2l_split)
+    if (m2l_split)
+        GQ_LAUNCH(ctx, k_from_dfl4, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
+                  (const float4 *)g->M2, g->M.p);
+    else if (split_w)   // multipoles as FP32 pairs for the pair List 3 far kernels
         GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
                   (const double2 *)g->M, g->M2.p);
     // Stage 4
