@@ -1751,6 +1751,91 @@ __global__ void k_m2m_split(EvalView E, int lstart, int lend, const float4 *__re
     M2[(size_t)b * P1 + m] = make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
+// L2L (Stage 7) in FP32 pairs: k_l2l_t with the quadrant matrices and the
+// local expansions in pairs, one thread per (child, m).
+__global__ void k_l2l_split(EvalView E, int lstart, int lend, const float4 *__restrict__ U2,
+                            float4 *__restrict__ L2) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int P1 = E.P + 1;
+    int c = lstart + (int)(t / P1), m = (int)(t % P1);
+    if (c >= lend || E.sub_tgt[c] == 0) return;
+    int p = E.bparent[c];
+    int q = (E.bix[c] & 1) | ((E.biy[c] & 1) << 1);
+    const float4 *B = L2 + (size_t)p * P1;
+    const float4 *Uq = U2 + ((size_t)q * kTN + m) * kTN;
+    float4 *dst = L2 + (size_t)c * P1 + m;
+    dflc acc = dflc_ld(*dst);
+    for (int k = m; k <= E.P; ++k) dflc_acc(acc, dflc_mul(dflc_ld(__ldg(&Uq[k])), dflc_ld(B[k])));
+    dfl re = dfl_two_sum(acc.re.hi, acc.re.lo), im = dfl_two_sum(acc.im.hi, acc.im.lo);
+    *dst = make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+// out += in as pairs (in FP64): folds the FP64 P2L terms into the pair locals
+__global__ void k_add_to_dfl4(long long n, const double2 *__restrict__ in, float4 *__restrict__ out) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float4 v = out[j];
+    dfl a = dfl_from_double(in[j].x), b = dfl_from_double(in[j].y);
+    dfl re = dfl_add(dfl{v.x, v.y}, a), im = dfl_add(dfl{v.z, v.w}, b);
+    out[j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+// L2QBXL (Stage 8) in FP32 pairs: the Taylor shift of k_l2qbxl_t on the
+// pair local expansions, with eta = (c - z_b)/rho and r/rho from the pair
+// box-relative centre coordinates and radius (scalings by the power of two
+// 1/rho exact), adding into the FP64 QBX coefficients.
+template <int PM, int QQ>
+__global__ void __launch_bounds__(128) k_l2qbxl_split(EvalView E, SplitView X, int nc,
+                                                      const int *__restrict__ ctr_box_of,
+                                                      const float4 *__restrict__ L2, double2 *__restrict__ Qout) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const int P = E.P;
+    int b = ctr_box_of[c];
+    const float irh = X.lvl[2 * E.blev[b]].z;   // 1/rho, a power of two
+    float4 c4 = X.c_rel[c], r4 = X.c_r[c];
+    dflc eta{dfl{c4.x * irh, c4.y * irh}, dfl{c4.z * irh, c4.w * irh}};
+    const float4 *B = L2 + (size_t)b * (P + 1);
+    const dfl zero{0.f, 0.f};
+    dflc bk[PM + 1];
+#pragma unroll
+    for (int k = 0; k <= PM; ++k) bk[k] = k <= P ? dflc_ld(B[k]) : dflc{zero, zero};
+#pragma unroll
+    for (int i = 0; i <= QQ; ++i)
+#pragma unroll
+        for (int k = PM - 1; k >= i; --k)
+            if (k < P) bk[k] = dflc_add(bk[k], dflc_mul(eta, bk[k + 1]));
+    const dfl sr{r4.x * irh, r4.y * irh};
+    dfl sm{1.f, 0.f};
+    double2 *dst = Qout + (size_t)c * (QQ + 1);
+#pragma unroll
+    for (int m = 0; m <= QQ; ++m) {
+        if (m <= P)
+            dst[m] = make_double2(dst[m].x + dfl_to_double(dfl_mul(bk[m].re, sm)),
+                                  dst[m].y + dfl_to_double(dfl_mul(bk[m].im, sm)));
+        sm = dfl_mul(sm, sr);
+    }
+}
+
+template <int PM>
+void launch_l2qbxl_split(gq_ctx *ctx, const EvalView &E, const SplitView &X, int nc, const int *owner,
+                         const float4 *L2, double2 *Q) {
+    switch (E.Q) {
+#define GQ_CASE(v) case v: GQ_LAUNCH(ctx, (k_l2qbxl_split<PM, v>), gq_blocks(nc, 128), 128, 0, E, X, nc, owner, L2, Q); break;
+        GQ_CASE(1) GQ_CASE(2) GQ_CASE(3) GQ_CASE(4) GQ_CASE(5) GQ_CASE(6) GQ_CASE(7) GQ_CASE(8)
+        GQ_CASE(9) GQ_CASE(10) GQ_CASE(11) GQ_CASE(12) GQ_CASE(13) GQ_CASE(14) GQ_CASE(15) GQ_CASE(16)
+#undef GQ_CASE
+        default: throw gq_error{GQ_ERR_INVALID, "p_qbx out of range"};
+    }
+}
+
+void dispatch_l2qbxl_split(gq_ctx *ctx, const EvalView &E, const SplitView &X, int nc, const int *owner,
+                           const float4 *L2, double2 *Q) {
+    if (E.P <= 8) launch_l2qbxl_split<8>(ctx, E, X, nc, owner, L2, Q);
+    else if (E.P <= 16) launch_l2qbxl_split<16>(ctx, E, X, nc, owner, L2, Q);
+    else launch_l2qbxl_split<GQ_MAX_PFMM>(ctx, E, X, nc, owner, L2, Q);
+}
+
 __global__ void k_from_dfl4(long long n, const float4 *__restrict__ in, double2 *__restrict__ out) {
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -1763,14 +1848,15 @@ __global__ void k_from_dfl4(long long n, const float4 *__restrict__ in, double2 
 // L_m += (-1)^m delta^-m (G_m - A_0/m) and L_0 += A_0 log(rho |delta|) + G_0 --
 // with the multipoles, delta^-k, the binomials and every product and sum in
 // pairs (about 2^-46 relative per operation; the G_m sums in lazy
-// accumulators).  Groups of G lanes, lane g the order index, as in k_m2l.
+// accumulators), adding into the pair local expansions L2.  Groups of G
+// lanes, lane g the order index, as in k_m2l.
 // The binomial rows sit in shared memory with an odd row stride (in 8-byte
 // words), so that the G lanes of a group, each reading its own row, hit
 // distinct banks.
 template <int G>
 __global__ void k_m2l_split(EvalView E, SplitView X, int nwork, const int *__restrict__ work,
                             const float4 *__restrict__ dtab2, const float2 *__restrict__ logtab2,
-                            const float2 *__restrict__ binom2, double2 *__restrict__ L) {
+                            const float2 *__restrict__ binom2, float4 *__restrict__ L2) {
     extern __shared__ float2 pasc2[];   // [P+1][RS]: C(m+k-1, k-1) as (hi, lo)
     const int P = E.P, P1 = P + 1, RS = P1 | 1;
     for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) {
@@ -1822,8 +1908,11 @@ __global__ void k_m2l_split(EvalView E, SplitView X, int nwork, const int *__res
         }
     }
     if (act && g <= P) {
-        double2 *dst = L + (size_t)b * P1 + g;
-        *dst = make_double2(dst->x + dfl_to_double(acc.re), dst->y + dfl_to_double(acc.im));
+        float4 *dst = L2 + (size_t)b * P1 + g;
+        float4 o = *dst;
+        dfl re = dfl_add(dfl{o.x, o.y}, dfl_two_sum(acc.re.hi, acc.re.lo));
+        dfl im = dfl_add(dfl{o.z, o.w}, dfl_two_sum(acc.im.hi, acc.im.lo));
+        *dst = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
 }
 
@@ -2041,6 +2130,7 @@ struct ConstTables {
     const float2 *logtab2 = nullptr;  // logtab as FP32 pairs
     const float2 *binom2 = nullptr;   // binom as FP32 pairs
     const float4 *tm2m2 = nullptr;    // tm2m as FP32 pairs
+    const float4 *tl2l2 = nullptr;    // tl2l as FP32 pairs
 };
 
 struct EvalTables : ConstTables {
@@ -2160,6 +2250,11 @@ static const ConstTables &const_tables(int dev) {
         tm2[i] = make_float4(a.x, a.y, b.x, b.y);
     }
     C.tm2m2 = upload_const(tm2.data(), tm2.size());
+    for (size_t i = 0; i < tl.size(); ++i) {
+        float2 a = split(tl[i].x), b = split(tl[i].y);
+        tm2[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    C.tl2l2 = upload_const(tm2.data(), tm2.size());
     GQ_CUDA(cudaSetDevice(cur));
     return per_dev.emplace(dev, C).first->second;
 }
@@ -2306,6 +2401,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
             g->split_ready = true;
         }
         g->M2.alloc((size_t)g->nbox * P1);
+        if (m2l_split) g->L2.alloc((size_t)g->nbox * P1);
         if (split || m2l_split) {
             g->str2.alloc(g->nsrc);
             if (g->nsrc) GQ_LAUNCH(ctx, k_to_dfl4, gq_blocks(g->nsrc, 256), 256, 0, (long long)g->nsrc,
@@ -2355,7 +2451,10 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     // ---- FMM passes on the context's stream
     mark(S_FMM, st);
     GQ_CUDA(cudaMemsetAsync(g->M.p, 0, sizeof(double2) * g->nbox * P1, st));
-    if (m2l_split) GQ_CUDA(cudaMemsetAsync(g->M2.p, 0, sizeof(float4) * g->nbox * P1, st));
+    if (m2l_split) {
+        GQ_CUDA(cudaMemsetAsync(g->M2.p, 0, sizeof(float4) * g->nbox * P1, st));
+        GQ_CUDA(cudaMemsetAsync(g->L2.p, 0, sizeof(float4) * g->nbox * P1, st));
+    }
     GQ_CUDA(cudaMemsetAsync(g->L.p, 0, sizeof(double2) * g->nbox * P1, st));
     GQ_CUDA(cudaMemsetAsync(g->Q.p, 0, sizeof(double2) * g->nc * Q1, st));
     if (g->npt) GQ_CUDA(cudaMemsetAsync(g->pot.p, 0, sizeof(double) * g->npt, st));
@@ -2399,7 +2498,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
             auto k16 = k_m2l_split<16>;
             auto k32 = k_m2l_split<32>;
             GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E, SX,
-                      g->n_far_boxes, (const int *)g->far_boxes, T.dtab2, T.logtab2, T.binom2, g->L.p);
+                      g->n_far_boxes, (const int *)g->far_boxes, T.dtab2, T.logtab2, T.binom2, g->L2.p);
         } else {
             size_t sm = sizeof(double) * P1 * P1;
             auto k16 = k_m2l<16>;
@@ -2416,12 +2515,22 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
                   (const int *)g->far_boxes, g->L.p);
     }
     mark(S_P2L, st);
-    // Stage 7
+    // Stage 7 (in pairs wherever M2L runs in pairs: the FP64 P2L terms are
+    // folded into the pair locals first, and the FP64 copy is made at the end)
+    if (m2l_split)
+        GQ_LAUNCH(ctx, k_add_to_dfl4, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
+                  (const double2 *)g->L, g->L2.p);
     for (int l = 1; l < g->nlev; ++l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_l2l_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, (const double2 *)T.tl2l,
-                  g->L.p);
+        if (m2l_split)
+            GQ_LAUNCH(ctx, k_l2l_split, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, T.tl2l2, g->L2.p);
+        else
+            GQ_LAUNCH(ctx, k_l2l_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e,
+                      (const double2 *)T.tl2l, g->L.p);
     }
+    if (m2l_split)
+        GQ_LAUNCH(ctx, k_from_dfl4, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
+                  (const float4 *)g->L2, g->L.p);
     if (f32)
         GQ_LAUNCH(ctx, k_to_float2, gq_blocks((long long)g->nbox * P1, 256), 256, 0, (long long)g->nbox * P1,
                   (const double2 *)g->M, g->M_f.p);
@@ -2447,7 +2556,10 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     mark(S_WP, st);
     // Stage 8
     if (g->nc)
-        dispatch_l2qbxl_t(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->L, g->Q.p);
+        if (m2l_split)
+            dispatch_l2qbxl_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, (const float4 *)g->L2, g->Q.p);
+        else
+            dispatch_l2qbxl_t(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->L, g->Q.p);
     if (g->npt)
         GQ_LAUNCH(ctx, k_l2p, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner, (const double2 *)g->L,
                   g->pot.p);

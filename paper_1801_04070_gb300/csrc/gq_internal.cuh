@@ -178,6 +178,7 @@ struct gq_geom {
     const double2 *qn_last = nullptr;   // direct coefficients of the last evaluation
     dbuf<float4> p_rel2;  // sorted point targets minus their leaf centre
     dbuf<float4> M2;      // multipoles
+    dbuf<float4> L2;      // local expansions
     dbuf<float4> lvl2;    // per level: (rho, 1/rho), (log rho, 1/rho^2)
 };
 

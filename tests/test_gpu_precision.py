@@ -82,9 +82,9 @@ def test_mixed_split_tier_sampled_at_eps_orders(kern):
 
 @pytest.mark.parametrize("kern", ["S", "D"])
 @pytest.mark.parametrize("eps,p_fmm", [(1e-6, 19), (1e-10, 30)])
-def test_pair_multipole_and_m2l_rounding(kern, eps, p_fmm):
-    """P2M, M2M and M2L in FP32 pairs (both mixed tiers, eps >= 1e-10): on a
-    4x4 starfish grid, whose far field runs through several hundred thousand
+def test_pair_fmm_passes_rounding(kern, eps, p_fmm):
+    """P2M, M2M, M2L, L2L and L2QBXL in FP32 pairs (both mixed tiers,
+    eps >= 1e-10): on a 4x4 starfish grid, whose far field runs through several hundred thousand
     List 2 translations, the mixed evaluation at p_fmm up to 30 stays within eps/5 of
     the FP64 path at the same orders; in the pair tier the QBX coefficients
     (which carry the translated local expansions) also stay within eps/5 of the
@@ -98,7 +98,7 @@ def test_pair_multipole_and_m2l_rounding(kern, eps, p_fmm):
     qf = fp64.qbx_coefficients()
     added = np.abs(v - f).max() / np.abs(f).max()
     qerr = max(np.abs(qm[:, m] - qf[:, m]).max() / np.abs(qf[:, m]).max() for m in range(qf.shape[1]))
-    print(f"pair P2M/M2M/M2L, eps {eps:.0e}, p_fmm {p_fmm}, {kern}: potential {added:.2e}, QBX coefficients {qerr:.2e} "
+    print(f"pair FMM passes, eps {eps:.0e}, p_fmm {p_fmm}, {kern}: potential {added:.2e}, QBX coefficients {qerr:.2e} "
           f"relative to the FP64 path")
     assert added <= eps / 5
     if eps < 1e-6:
