@@ -90,8 +90,10 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
  *                 a source within 1/8 of the box half-width of a point
  *                 target; the List 3 far
  *                 translation to centres (M2QBXL) runs in pairs when the tree
- *                 has at most 24 levels.  M2M, M2L, L2L, L2QBXL, P2M, P2L
- *                 and the final QBX evaluation stay FP64.  For eps < 1e-12
+ *                 has at most 24 levels.  For eps >= 1e-10 P2M, M2M, M2L,
+ *                 L2L and L2QBXL run in double-FP32 pairs too (measured
+ *                 3e-14 added to the potential at p_fmm 30).  P2L, L2P and
+ *                 the final QBX evaluation stay FP64.  For eps < 1e-12
  *                 MIXED runs as FP64.
  */
 typedef struct {
