@@ -514,14 +514,15 @@ def run_gpu(args, rank, world, local):
                "sample": (f"serial C oracle, build + {args.kernel} evaluation of a {SAMPLE_GRID[0]}x{SAMPLE_GRID[1]} "
                           f"sub-grid of the workload ({nts} targets), {times[0]:.1f} s")}
 
-    # ---- accuracy sweep: orders from eps, FP64 vs MIXED evaluation throughput
+    # ---- accuracy sweep: orders from eps, FP64 vs MIXED (FP64 translations) vs
+    # MIXED_FMM (translations in FP32 pairs too) evaluation throughput
     sweep = None
     if args.sweep and rank == 0:
         sweep = []
         for eps in (1e-4, 1e-6, 1e-8, 1e-10, 1e-12):
             row = {"eps": eps}
             ref = None
-            for prec, name in ((0, "fp64"), (1, "mixed")):
+            for prec, name in ((0, "fp64"), (1, "mixed"), (2, "mixed_fmm")):
                 pr = params_default(p_qbx=0, p_fmm=0, n_max=int(g["n_max"]), eps=eps, precision=prec)
                 sg = C.c_void_p()
                 chk(L.gq_geometry_create(ctx, C.byref(desc), C.byref(pr), C.byref(sg)))
@@ -545,7 +546,7 @@ def run_gpu(args, rank, world, local):
                 if ref is None:
                     ref = out
                 else:
-                    row["mixed_rel_err_vs_fp64_path"] = float((out - ref).abs().max() / ref.abs().max())
+                    row[name + "_rel_err_vs_fp64_path"] = float((out - ref).abs().max() / ref.abs().max())
                 L.gq_geometry_destroy(sg)
             sweep.append(row)
 

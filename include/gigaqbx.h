@@ -90,11 +90,13 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
  *                 a source within 1/8 of the box half-width of a point
  *                 target; the List 3 far
  *                 translation to centres (M2QBXL) runs in pairs when the tree
- *                 has at most 24 levels.  For eps >= 1e-10 P2M, M2M, M2L,
- *                 L2L and L2QBXL run in double-FP32 pairs too (measured
- *                 3e-14 added to the potential at p_fmm 30).  P2L, L2P and
- *                 the final QBX evaluation stay FP64.  For eps < 1e-12
- *                 MIXED runs as FP64.
+ *                 has at most 24 levels.  The translations M2M, M2L, L2L,
+ *                 L2QBXL, the P2M and P2L sums, L2P and the final QBX
+ *                 evaluation stay FP64.  For eps < 1e-12 MIXED runs as FP64.
+ *                 GQ_PREC_MIXED_FMM: MIXED, and for eps >= 1e-10 also P2M,
+ *                 M2M, M2L, L2L and L2QBXL in double-FP32 pairs (measured
+ *                 3e-14 added to the potential at p_fmm 30; an extension
+ *                 beyond the FP64 translations of MIXED).
  */
 typedef struct {
     int p_qbx, p_fmm, n_max;
@@ -107,7 +109,7 @@ typedef struct {
     int precision;
 } gq_params;
 
-enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1 };
+enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1, GQ_PREC_MIXED_FMM = 2 };
 
 /* Discretised curve (Sec. 2.1, 2.2.1).  Panel k owns base nodes
  * [k*nb, (k+1)*nb) and quadrature (upsampled) nodes [k*nu, (k+1)*nu).

@@ -13,7 +13,7 @@ _lock = threading.Lock()
 _lib = None
 
 GQ_S, GQ_D, GQ_SP = 0, 1, 2
-GQ_PREC_FP64, GQ_PREC_MIXED = 0, 1
+GQ_PREC_FP64, GQ_PREC_MIXED, GQ_PREC_MIXED_FMM = 0, 1, 2
 KERNELS = {"S": GQ_S, "D": GQ_D, "SP": GQ_SP}
 LISTS = ("U", "V", "WC", "WF", "XC", "XF")
 

@@ -94,7 +94,8 @@ void resolve_orders(gq_params &p) {
     GQ_REQUIRE(p.radius_factor > 0, GQ_ERR_INVALID, "radius_factor must be > 0");
     GQ_REQUIRE(p.assoc_slack >= 0, GQ_ERR_INVALID, "assoc_slack must be >= 0");
     GQ_REQUIRE(p.w3_demote >= 1, GQ_ERR_INVALID, "w3_demote must be >= 1");
-    GQ_REQUIRE(p.precision == GQ_PREC_FP64 || p.precision == GQ_PREC_MIXED, GQ_ERR_INVALID, "unknown precision");
+    GQ_REQUIRE(p.precision == GQ_PREC_FP64 || p.precision == GQ_PREC_MIXED || p.precision == GQ_PREC_MIXED_FMM,
+               GQ_ERR_INVALID, "unknown precision");
 }
 
 }  // namespace

@@ -2348,8 +2348,9 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     // A1
     GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
               (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, g->strength.p);
-    const bool f32 = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-6;
-    const bool split = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-12 && g->prm.eps < 1e-6;
+    const bool mixed = g->prm.precision == GQ_PREC_MIXED || g->prm.precision == GQ_PREC_MIXED_FMM;
+    const bool f32 = mixed && g->prm.eps >= 1e-6;
+    const bool split = mixed && g->prm.eps >= 1e-12 && g->prm.eps < 1e-6;
     MixedView X{};
     if (f32) {
         if (!g->mixed_ready) {
@@ -2377,10 +2378,12 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     SplitView SX{};
     // List 3 far at centres runs in pairs in both mixed tiers (exact FP32 box offsets need l <= 23)
     const bool split_w = (split || f32) && g->nlev <= 24;
-    // M2L in pairs down to eps = 1e-10: its rounding, amplified by the binomial
-    // sums' cancellation (at most about 25x for the same-level offsets |delta| >= 4),
-    // stays near 1e-13 relative, below eps/5 there; at smaller eps M2L stays FP64
-    const bool m2l_split = (split || f32) && g->prm.eps >= 1e-10;
+    // GQ_PREC_MIXED_FMM: the FMM passes (P2M, M2M, M2L, L2L, L2QBXL) in pairs down
+    // to eps = 1e-10: the M2L rounding, amplified by the binomial sums' cancellation
+    // (at most about 25x for the same-level offsets |delta| >= 4), stays near 1e-13
+    // relative, below eps/5 there; at smaller eps, and in GQ_PREC_MIXED, they stay FP64
+    const bool m2l_split =
+        g->prm.precision == GQ_PREC_MIXED_FMM && (split || f32) && g->prm.eps >= 1e-10;
     if (split || f32) {
         if (!g->split_ready) {
             g->s_rel2.alloc(g->nsrc);
@@ -2610,8 +2613,9 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
 // the evaluation per density.  The mixed-precision tiers evaluate one density
 // after another.
 void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, double *const *out) {
-    const bool f32 = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-6;
-    const bool split = g->prm.precision == GQ_PREC_MIXED && g->prm.eps >= 1e-12 && g->prm.eps < 1e-6;
+    const bool mixed = g->prm.precision == GQ_PREC_MIXED || g->prm.precision == GQ_PREC_MIXED_FMM;
+    const bool f32 = mixed && g->prm.eps >= 1e-6;
+    const bool split = mixed && g->prm.eps >= 1e-12 && g->prm.eps < 1e-6;
     if (nd <= 1 || f32 || split || g->n_ctr_boxes == 0) {
         for (int d = 0; d < nd; ++d) gq_eval_all(g, kernel, dens[d], out[d], nullptr);
         return;

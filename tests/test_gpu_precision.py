@@ -1,5 +1,6 @@
 """Precision modes (MIXED: FP32 direct sums when eps >= 1e-6, double-FP32
-power sums when 1e-12 <= eps < 1e-6) and the accuracy
+power sums when 1e-12 <= eps < 1e-6, FP64 translations; MIXED_FMM: the
+translations in double-FP32 pairs as well) and the accuracy
 sweep with orders chosen from the requested accuracy, checked against the
 FP64 oracle: O2 at the same orders (rounding of the mixed path) and O1,
 unaccelerated QBX at the same p_qbx (FMM + rounding error, the quantity the
@@ -83,14 +84,14 @@ def test_mixed_split_tier_sampled_at_eps_orders(kern):
 @pytest.mark.parametrize("kern", ["S", "D"])
 @pytest.mark.parametrize("eps,p_fmm", [(1e-6, 19), (1e-10, 30)])
 def test_pair_fmm_passes_rounding(kern, eps, p_fmm):
-    """P2M, M2M, M2L, L2L and L2QBXL in FP32 pairs (both mixed tiers,
-    eps >= 1e-10): on a 4x4 starfish grid, whose far field runs through several hundred thousand
+    """GQ_PREC_MIXED_FMM: P2M, M2M, M2L, L2L and L2QBXL in FP32 pairs on top
+    of either mixed tier (eps >= 1e-10): on a 4x4 starfish grid, whose far field runs through several hundred thousand
     List 2 translations, the mixed evaluation at p_fmm up to 30 stays within eps/5 of
     the FP64 path at the same orders; in the pair tier the QBX coefficients
     (which carry the translated local expansions) also stay within eps/5 of the
     FP64 ones, order by order."""
     g = workloads.starfish_grid(4, 4, 64, n_off=1 << 16, on_surface="up", seed=1)
-    mixed = _geo(g, p_qbx=7, p_fmm=p_fmm, n_max=32, eps=eps, precision=1)
+    mixed = _geo(g, p_qbx=7, p_fmm=p_fmm, n_max=32, eps=eps, precision=2)
     fp64 = _geo(g, p_qbx=7, p_fmm=p_fmm, n_max=32, eps=eps, precision=0)
     v = mixed.eval(kern, g["density"])
     qm = mixed.qbx_coefficients()
