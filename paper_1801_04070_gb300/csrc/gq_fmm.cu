@@ -73,9 +73,6 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src, int width) {
 __device__ __forceinline__ double2 shfl2_up(double2 v, int d, int width) {
     return make_double2(__shfl_up_sync(0xffffffffu, v.x, d, width), __shfl_up_sync(0xffffffffu, v.y, d, width));
 }
-__device__ __forceinline__ double2 shfl2_xor(double2 v, int m) {
-    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
-}
 // lane g of a group of `width` lanes receives u^g
 __device__ __forceinline__ double2 lane_powers(double2 u, int g, int width) {
     double2 v = g == 0 ? make_double2(1.0, 0.0) : u;
