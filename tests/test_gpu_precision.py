@@ -133,3 +133,14 @@ def test_accuracy_sweep(eps):
     err = np.abs(v[sel] - o1[sel]).max() / np.abs(o1[sel]).max()
     print(f"eps {eps:.0e}: p_qbx {prm.p_qbx} p_fmm {prm.p_fmm}: rel err vs unaccelerated QBX {err:.2e}")
     assert err <= max(eps, 1e-11)
+
+
+def test_unknown_precision_rejected():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_04070_gb300 import Geometry, params_default
+    from paper_1801_04070_gb300._lib import GigaQBXError
+    g = workloads.starfish_c1()
+    with pytest.raises(GigaQBXError):
+        Geometry(g, params_default(p_qbx=5, p_fmm=10, n_max=32, precision=3))
