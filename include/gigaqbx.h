@@ -311,7 +311,9 @@ gq_status gq_set_orders(gq_geom *g, int p_qbx, int p_fmm);
  * GQ_ERR_UNSUPPORTED and a message giving both sizes.
  *
  * density_dev and out_dev must be device memory (GQ_ERR_INVALID otherwise):
- * host inputs would need staging buffers.  The geometry must be built.
+ * host inputs would need staging buffers.  The geometry must be built.  The
+ * evaluation is the FP64 one whatever the geometry's precision mode (the
+ * mixed modes need buffers of their own).
  * The first call on a device sets the array up (looks up its device address
  * and writes the tables); make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents, so
