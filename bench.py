@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="also time 64 geometries of uneven size (2k-200k quadrature nodes, log-uniform) x 8 "
                          "densities: one CUDA-graph launch against one gq_eval after another")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="precision of the timed step: 0 FP64 (the benchmark), 1 MIXED, 2 MIXED_FMM at --eps "
+                         "with the workload's orders (profiling cases)")
+    ap.add_argument("--eps", type=float, default=1e-6, help="requested accuracy for --precision 1 or 2")
     ap.add_argument("--grid", type=int, nargs=2, default=[16, 16],
                     help="curves per row / column (the benchmark workload is 16 16; smaller grids are "
                          "profiling cases with the same per-curve sizes)")
@@ -369,7 +373,10 @@ def run_gpu(args, rank, world, local):
     g = workload(n_off=(1 << 20) * grid[0] * grid[1] // 256, grid=grid)
     nt = len(g["tgt_xy"])
     P, Q = int(g["p_fmm"]), int(g["p_qbx"])
-    prm = params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"]))
+    if args.precision == 0:
+        prm = params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"]))
+    else:
+        prm = params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"]), eps=args.eps, precision=args.precision)
     stream = torch.cuda.current_stream(dev)
 
     # device-resident inputs
@@ -559,13 +566,15 @@ def run_gpu(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64/f32 mixed", "data": "synthetic",
         "config": {"workload": g["name"], "kernel": args.kernel, "targets": nt,
                    "quadrature_nodes": int(len(g["up_w"])), "centres": int(info.ncentres),
                    "point_targets": int(info.npoint_targets), "boxes": int(info.nbox),
                    "p_qbx": Q, "p_fmm": P, "n_max": int(g["n_max"]), "t_f": 0.9,
                    "step": "gq_targets_set + gq_build + gq_eval", "l2": "flushed (256 MB write) between steps",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   **({} if args.precision == 0 else {"precision": ("MIXED", "MIXED_FMM")[args.precision - 1],
+                                                      "eps": args.eps})},
         "eval_only": {"value": world * nt / (statistics.mean(eval_ms) * 1e-3), "unit": UNIT,
                       "ms": statistics.mean(eval_ms)},
         "stages_ms": stage_report,
