@@ -412,7 +412,7 @@ static void w_farclose(const orc_state *s, int b, int d, boxlists *bl) {
     const obox *B = &s->box[b], *D = &s->box[d];
     if (D->sub_src == 0) return;
     if (sep_a_tcrb(s, D, B)) {
-        if (D->sub_src < s->p.w3_demote) collect_leaves(s, d, &bl->l[ORC_WC]);  /* Remark 1 */
+        if (GQ_ORC_MUT != 10 && D->sub_src < s->p.w3_demote) collect_leaves(s, d, &bl->l[ORC_WC]);  /* Remark 1 */
         else iv_push(&bl->l[ORC_WF], d);
         return;
     }
@@ -698,7 +698,7 @@ static cplx p2pot(int kernel, cplx t, cplx y, cplx str) {
 static void p2mpole(int kernel, int p, cplx c, cplx y, cplx str, cplx *a) {
     cplx w = y - c;
     if (kernel == ORC_D) {
-        for (int k = 1; k <= p; ++k) a[k] += -str * cpow_int(w, k - 1);
+        for (int k = 1; k <= p; ++k) a[k] += -str * cpow_int(w, GQ_ORC_MUT == 12 ? k : k - 1);
     } else {
         a[0] += str;
         for (int k = 1; k <= p; ++k) a[k] += -str * cpow_int(w, k) / (GQ_ORC_MUT == 3 ? 1 : k);
@@ -722,7 +722,7 @@ static void m2l(const double binom[128][128], int p_in, int p_out, cplx y, const
     for (int m = 1; m <= p_out; ++m) {
         double sg = (m % 2) ? -1.0 : 1.0;                    /* (-1)^m */
         acc = (GQ_ORC_MUT == 1 ? sg : -sg) * a[0] / (m * cpow_int(y, m));
-        for (int k = 1; k <= p_in; ++k) acc += sg * binom[m + k - 1][k - 1] * a[k] / cpow_int(y, m + k);
+        for (int k = 1; k <= p_in; ++k) acc += sg * binom[m + k - 1][GQ_ORC_MUT == 9 ? k : k - 1] * a[k] / cpow_int(y, m + k);
         out[m] += acc;
     }
 }
@@ -741,7 +741,7 @@ static cplx eval_local(int p, cplx c, const cplx *b, cplx t) {
 }
 static cplx eval_local_deriv(int p, cplx c, const cplx *b, cplx t) {
     cplx acc = 0;
-    for (int k = 1; k <= p; ++k) acc += (double)k * b[k] * cpow_int(t - c, k - 1);
+    for (int k = 1; k <= p; ++k) acc += (GQ_ORC_MUT == 11 ? 1.0 : (double)k) * b[k] * cpow_int(t - c, k - 1);
     return acc;
 }
 static cplx eval_mpole(int p, cplx c, const cplx *a, cplx t) {

@@ -23,6 +23,14 @@ CASES = {
     7: ("on-surface value the sum of the two sides, not their mean", "test_oracle_math.py",
         "test_unit_circle_closed_forms"),
     8: ("association threshold slack instead of slack^2", "test_oracle_lists.py", "test_association_bruteforce"),
+    9: ("M2L binomial C(m+k-1, k) for C(m+k-1, k-1) in the a_k terms (eq. m2l)", "test_oracle_math.py",
+        "test_lemma1_m2qbxl_bound"),
+    10: ("List 3 far boxes with few sources not demoted to List 3 close (Remark 1)", "test_oracle_lists.py",
+         "test_o2_lists_equal_bruteforce"),
+    11: ("S' without the factor m of the derivative of (t - c)^m", "test_oracle_neumann.py",
+         "test_unit_circle_neumann_closed_form"),
+    12: ("D multipole with w^k for w^(k-1) (eq. multipole)", "test_oracle_math.py",
+         "test_p2m_matches_direct_far_field"),
 }
 
 
