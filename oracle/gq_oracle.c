@@ -376,12 +376,12 @@ static inline int colleague2(const obox *a, const obox *b) { return a->level == 
 /* a < TCR(b): dist >= 3|a| + |b|(1 + t_f) */
 static inline int sep_a_tcrb(const orc_state *s, const obox *a, const obox *b) {
     int64_t tn = s->p.tf_num, td = s->p.tf_den;
-    return td * dcen(a, b) >= 3 * td * bh(a) + (td + tn) * bh(b);
+    return td * dcen(a, b) >= 3 * td * bh(a) + (GQ_ORC_MUT == 14 ? td : td + tn) * bh(b);
 }
 /* TCR(a) < b: dist >= 3|a|(1 + t_f) + |b| */
 static inline int sep_tcra_b(const orc_state *s, const obox *a, const obox *b) {
     int64_t tn = s->p.tf_num, td = s->p.tf_den;
-    return td * dcen(a, b) >= 3 * (td + tn) * bh(a) + td * bh(b);
+    return td * dcen(a, b) >= 3 * (GQ_ORC_MUT == 13 ? td : td + tn) * bh(a) + td * bh(b);
 }
 static inline int is_leaf(const obox *b) { return b->child[0] < 0 && b->child[1] < 0 && b->child[2] < 0 && b->child[3] < 0; }
 static int is_strict_desc(const orc_state *s, int d, int a) {

@@ -31,6 +31,10 @@ CASES = {
          "test_unit_circle_neumann_closed_form"),
     12: ("D multipole with w^k for w^(k-1) (eq. multipole)", "test_oracle_math.py",
          "test_p2m_matches_direct_far_field"),
+    13: ("TCR(a) < b tested without the factor (1 + t_f) on TCR(a) (Def. 8)", "test_oracle_lists.py",
+         "test_list_bounds_and_separation"),
+    14: ("a < TCR(b) tested without the factor (1 + t_f) on TCR(b) (Def. 5)", "test_oracle_lists.py",
+         "test_list_bounds_and_separation"),
 }
 
 
