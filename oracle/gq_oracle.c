@@ -266,8 +266,8 @@ static void root_and_keys(orc_state *s) {
             double hb = ldexp(s->H, -l);
             double bx = s->lo_x + (double)(2 * ix + 1) * hb;
             double by = s->lo_y + (double)(2 * iy + 1) * hb;
-            double d = fmax(fabs(s->c_xy[2 * c] - bx), fabs(s->c_xy[2 * c + 1] - by)) + s->c_r[c];
-            if (d <= hb * tcr_scale) lc = l; else break;
+            double d = fmax(fabs(s->c_xy[2 * c] - bx), fabs(s->c_xy[2 * c + 1] - by)) + (GQ_ORC_MUT == 16 ? 0.0 : s->c_r[c]);
+            if (d <= hb * (GQ_ORC_MUT == 15 ? 1.0 : tcr_scale)) lc = l; else break;
         }
         s->c_lc[c] = lc < 0 ? 0 : lc;
     }

@@ -35,6 +35,10 @@ CASES = {
          "test_list_bounds_and_separation"),
     14: ("a < TCR(b) tested without the factor (1 + t_f) on TCR(b) (Def. 5)", "test_oracle_lists.py",
          "test_list_bounds_and_separation"),
+    15: ("centre level from the box itself instead of its TCR (Sec. 4.3)", "test_oracle_lists.py",
+         "test_tree_invariants"),
+    16: ("centre level from the centre point, the disk radius left out (Sec. 4.3)", "test_oracle_lists.py",
+         "test_tree_invariants"),
 }
 
 
