@@ -74,7 +74,7 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
  *                 |t-c|/r when that ratio is <= assoc_slack (Sec. 2.2.2
  *                 reports up to 20% slack as harmless); otherwise it is an
  *                 ordinary FMM point target.
- *  eps          : requested accuracy (used for orders of 0 and by GQ_PREC_MIXED).
+ *  eps          : requested accuracy (used for orders of 0 and by the mixed modes).
  *  precision    : GQ_PREC_FP64 (default): every stage in FP64.
  *                 GQ_PREC_MIXED: a tier chosen from eps.
  *                 eps >= 1e-6: the direct interactions (Lists 1, 3 close,
@@ -97,6 +97,7 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
  *                 M2M, M2L, L2L and L2QBXL in double-FP32 pairs (measured
  *                 3e-14 added to the potential at p_fmm 30; an extension
  *                 beyond the FP64 translations of MIXED).
+ *                 Any other value: GQ_ERR_INVALID from gq_geometry_create.
  */
 typedef struct {
     int p_qbx, p_fmm, n_max;
