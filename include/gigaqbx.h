@@ -149,6 +149,15 @@ typedef struct {
 
 gq_status gq_params_default(gq_params *out);
 
+/* Host-only: the parameters gq_geometry_create will use for `in` -- orders
+ * of 0 filled in from eps (p_fmm: the smallest p with the idealised FMM
+ * error (1/2)^(p+1) <= eps, Sec. 4.1 and 5.1; p_qbx: the calibrated QBX
+ * truncation rule described under p_qbx above), clamped to [1, 30] and
+ * [1, 16] -- and the same validation.  `in` and `out` may alias.  Returns
+ * GQ_ERR_INVALID (and leaves `out` unchanged) for parameters that
+ * gq_geometry_create would reject; no context, no GPU work. */
+gq_status gq_params_resolve(const gq_params *in, gq_params *out);
+
 /* Context on `device`, ordering work on `cuda_stream` (a cudaStream_t; NULL
  * = the legacy default stream). */
 gq_status gq_create(int device, void *cuda_stream, gq_ctx **out);

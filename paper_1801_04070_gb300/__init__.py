@@ -19,6 +19,7 @@ from ._lib import (  # noqa: F401
     lib,
     library_path,
     params_default,
+    params_resolve,
 )
 
-__all__ = ["Batch", "Geometry", "MLP", "GigaQBXError", "params_default", "lib", "library_path", "GQ_S", "GQ_D", "GQ_SP"]
+__all__ = ["Batch", "Geometry", "MLP", "GigaQBXError", "params_default", "params_resolve", "lib", "library_path", "GQ_S", "GQ_D", "GQ_SP"]

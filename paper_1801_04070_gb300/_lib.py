@@ -66,6 +66,7 @@ def lib():
         vp, i32, st = C.c_void_p, C.c_int, C.c_int
         sig = {
             "gq_params_default": (st, [C.POINTER(Params)]),
+            "gq_params_resolve": (st, [C.POINTER(Params), C.POINTER(Params)]),
             "gq_create": (st, [i32, vp, C.POINTER(vp)]),
             "gq_destroy": (st, [vp]),
             "gq_last_error": (C.c_char_p, [vp]),
@@ -123,6 +124,16 @@ def params_default(**kw) -> Params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def params_resolve(p: Params) -> Params:
+    """The parameters a geometry built with `p` uses (orders from eps when
+    given as 0); raises GigaQBXError for parameters the library rejects."""
+    out = Params()
+    st = lib().gq_params_resolve(C.byref(p), C.byref(out))
+    if st != 0:
+        raise GigaQBXError(st, "invalid parameters")
+    return out
 
 
 def _ptr(a):

@@ -119,6 +119,18 @@ gq_status gq_params_default(gq_params *out) {
     return GQ_OK;
 }
 
+gq_status gq_params_resolve(const gq_params *in, gq_params *out) {
+    if (!in || !out) return GQ_ERR_INVALID;
+    gq_params p = *in;
+    try {
+        resolve_orders(p);
+    } catch (const gq_error &e) {
+        return e.code;
+    }
+    *out = p;
+    return GQ_OK;
+}
+
 gq_status gq_create(int device, void *cuda_stream, gq_ctx **out) {
     if (!out) return GQ_ERR_INVALID;
     *out = nullptr;
