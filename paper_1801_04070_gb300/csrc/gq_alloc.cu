@@ -31,10 +31,19 @@ int size_class(size_t bytes, size_t *cap) {
     return c;
 }
 
+// Frees the cached blocks of one device.  Devices without cached blocks are
+// not touched: selecting a device that does not exist would leave an error
+// for the next launch check to find, and selecting one that does would start
+// a context on it.
 void release_device_locked(Pool &P, int dev) {
+    bool any = false;
+    for (int c = 0; c < kClasses && !any; ++c) any = !P.free_list[dev][c].empty();
+    if (!any) return;
     int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(dev);
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) {
+        (void)cudaGetLastError();   // clear it: the blocks stay cached
+        return;
+    }
     for (int c = 0; c < kClasses; ++c) {
         for (void *p : P.free_list[dev][c]) {
             cudaFree(p);

@@ -45,6 +45,10 @@ def test_host_entry_points(libpath):
     assert L.gq_build(None) == -1
     assert L.gq_eval(None, 0, None, None, None) == -1
     assert L.gq_last_error(None) == b"null context"
+    n = C.c_int64(-1)
+    assert L.gq_memory_cached(C.byref(n)) == 0 and n.value >= 0
+    assert L.gq_memory_cached(None) == -1
+    assert L.gq_memory_release() == 0       # nothing cached without a GPU: touches no device
 
 
 def test_create_without_gpu_fails_cleanly(libpath):
