@@ -159,7 +159,12 @@ gq_status gq_params_default(gq_params *out);
 gq_status gq_params_resolve(const gq_params *in, gq_params *out);
 
 /* Context on `device`, ordering work on `cuda_stream` (a cudaStream_t; NULL
- * = the legacy default stream). */
+ * = the legacy default stream).  gq_create, gq_geometry_create, gq_build and
+ * the batch calls make `device` the calling thread's current device; the
+ * other calls that launch work (gq_targets_set, gq_eval, gq_eval_noalloc,
+ * gq_gmres, the learned-order calls) expect it to be current already, as it
+ * is when one thread drives one GPU, and leave the device selection alone so
+ * that they can be recorded into a caller's stream capture. */
 gq_status gq_create(int device, void *cuda_stream, gq_ctx **out);
 gq_status gq_destroy(gq_ctx *ctx);
 const char *gq_last_error(const gq_ctx *ctx);

@@ -143,6 +143,7 @@ gq_status gq_create(int device, void *cuda_stream, gq_ctx **out) {
         return GQ_ERR_CUDA;
     }
     if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
         delete ctx;
         return GQ_ERR_CUDA;
     }
