@@ -133,9 +133,9 @@ static void form_centres(orc_state *s) {
     s->c_lc = malloc(sizeof(int) * s->nc);
     for (int i = 0; i < s->nbase; ++i) {
         int panel = i / s->g.nb;
-        double r = s->p.radius_factor * s->panel_len[panel];
+        double r = (GQ_ORC_MUT == 17 ? 0.5 : 1.0) * s->p.radius_factor * s->panel_len[panel];
         for (int side = 0; side < 2; ++side) {
-            double sg = side ? 1.0 : -1.0;
+            double sg = (side ? 1.0 : -1.0) * (GQ_ORC_MUT == 18 ? -1.0 : 1.0);
             int c = 2 * i + side;
             s->c_xy[2 * c] = s->base_xy[2 * i] + sg * r * s->base_n[2 * i];
             s->c_xy[2 * c + 1] = s->base_xy[2 * i + 1] + sg * r * s->base_n[2 * i + 1];

@@ -187,6 +187,29 @@ def test_unit_circle_closed_forms(circle, which):
         assert np.abs(v - ref).max() < 2e-8, (kern, np.abs(v - ref).max())
 
 
+@pytest.mark.parametrize("n_panels", [16, 32, 48])
+def test_unit_circle_centres(n_panels):
+    """Centre placement (Sec. 2.2.2) on the unit circle, where every panel of
+    n equal panels has arc length 2 pi / n: with centres half a panel length
+    off the curve (the workload's radius), centre 2i lies on the ray of base
+    node i at distance 1 - pi/n (interior) and centre 2i+1 at 1 + pi/n
+    (exterior), both with radius pi/n.  Fixes the reading of the expansion
+    radius (full arc length times 1/2, not half of the half-length h_k)."""
+    g = workloads.unit_circle(n_panels)
+    o = oracle.Oracle(g, oracle.default_params(p_qbx=4, p_fmm=8))
+    xy, r, _ = o.centres()
+    nb = len(g["base_xy"])
+    assert len(r) == 2 * nb
+    h = np.pi / n_panels
+    assert np.abs(r - h).max() < 1e-13
+    th = np.arctan2(g["base_xy"][:, 1], g["base_xy"][:, 0])
+    for side, rad in ((0, 1.0 - h), (1, 1.0 + h)):
+        c = xy[side::2]
+        assert np.abs(np.hypot(c[:, 0], c[:, 1]) - rad).max() < 1e-13, side
+        ang = np.angle(np.exp(1j * (np.arctan2(c[:, 1], c[:, 0]) - th)))
+        assert np.abs(ang).max() < 1e-12, side
+
+
 def test_unit_circle_qbx_order_convergence():
     """Error of on/near-surface values drops with the QBX order (truncation
     error, eq. qbx-truncation-estimate)."""

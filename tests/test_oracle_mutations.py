@@ -39,6 +39,10 @@ CASES = {
          "test_tree_invariants"),
     16: ("centre level from the centre point, the disk radius left out (Sec. 4.3)", "test_oracle_lists.py",
          "test_tree_invariants"),
+    17: ("expansion radius from half the panel length, radius_factor x h_k with h_k = arc/2 (Sec. 2.2.2)",
+         "test_oracle_math.py", "test_unit_circle_centres"),
+    18: ("centre 2i on the exterior side, 2i+1 on the interior (Sec. 2.2.2 ordering)", "test_oracle_math.py",
+         "test_unit_circle_centres"),
 }
 
 
