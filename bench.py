@@ -160,11 +160,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- algorithmic work model
-def work_model(geo, p, q):
+LOG_FLOPS = 7   # FP64 flops of one table-driven logarithm as the kernels run it: 3 FMAs + 1 add
+
+
+def work_model(geo, p, q, kernel="S"):
     """Units per launch of each stage (pairs), from the exported lists.  Flop
     weights: direct to centres 14q + 20 per (source, centre) pair, direct to
-    points 10 per pair, M2L 8(p+1)^2 per List 2 pair, List 3 far to centres
-    8(p+1)(q+1) per (box, centre)."""
+    points 10 per pair plus, for S, one logarithm (LOG_FLOPS), M2L 8(p+1)^2 per
+    List 2 pair, List 3 far to centres 8(p+1)(q+1) per (box, centre)."""
     bx = geo.boxes()
     L = geo.lists()
     nsrc, nctr, ntgt = bx["nsrc"].astype(np.int64), bx["nctr"].astype(np.int64), bx["ntgt"].astype(np.int64)
@@ -184,7 +187,8 @@ def work_model(geo, p, q):
     wf_ctr = int((wf * nctr).sum())
     return {
         5: dict(name="k_near_centres", units=pairs_ctr, flops_per_unit=14 * q + 20, unit="(source, centre) pair"),
-        6: dict(name="k_near_points", units=pairs_pt, flops_per_unit=10, unit="(source, point) pair"),
+        6: dict(name="k_near_points", units=pairs_pt, flops_per_unit=10 + (LOG_FLOPS if kernel == "S" else 0),
+                unit="(source, point) pair"),
         2: dict(name="k_m2l", units=v_pairs, flops_per_unit=8 * (p + 1) ** 2, unit="List 2 pair"),
         7: dict(name="k_w_centres", units=wf_ctr, flops_per_unit=8 * (p + 1) * (q + 1), unit="(List 3 far box, centre)"),
     }
@@ -195,46 +199,78 @@ STAGE_NAMES = ["upsample", "p2m_m2m", "m2l", "p2l", "l2l", "near_centres", "near
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(kernel, reps=1, grid=SAMPLE_GRID):
-    """The CPU oracle (serial C, FP64) on a sub-grid of the workload (8 x 6 by
-    default): same per-curve discretisation, density recipe and target density
-    (the sub-grid's share of the curves and of the off-surface targets).  Build
-    + evaluation timed."""
+def cpu_model():
+    """The host CPU's model name (lscpu), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(kernel, reps=1, grid=SAMPLE_GRID, threads=1, g=None):
+    """The CPU oracle (plain C, FP64) on a grid of the workload (a sub-grid
+    has the same per-curve discretisation, density recipe and target density:
+    its share of the curves and of the off-surface targets).  Build +
+    evaluation timed.  threads > 1 runs the oracle's evaluation loops on that
+    many cores (the same results bit for bit; the tree build stays serial)."""
     import oracle
-    n_off = (1 << 20) * grid[0] * grid[1] // 256
-    g = workload(n_off=n_off, grid=grid)
+    if g is None:
+        n_off = (1 << 20) * grid[0] * grid[1] // 256
+        g = workload(n_off=n_off, grid=grid)
+    used = oracle.set_threads(threads)
     times = []
     vals = None
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        o = oracle.Oracle(g, oracle.default_params(g))
-        vals = o.eval(kernel, g["density"])
-        times.append(time.perf_counter() - t0)
+    try:
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            o = oracle.Oracle(g, oracle.default_params(g))
+            vals = o.eval(kernel, g["density"])
+            times.append(time.perf_counter() - t0)
+            del o
+    finally:
+        oracle.set_threads(1)
     nt = len(g["tgt_xy"])
-    return g, vals, nt, times
+    return g, vals, nt, times, used
+
+
+def host_cores():
+    import oracle
+    return max(1, min(os.cpu_count() or 1, oracle.max_threads()))
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    # about 11 s per 8 x 6 step on one core: smaller sub-grids when many steps are
+    # the oracle on all host cores: the full workload takes about 7-11 s a step
+    # (serial tree build + parallel evaluation); smaller sub-grids when many steps are
     # asked for, so that the whole run stays within a few minutes (targets/s is per target)
+    cores = host_cores()
     n = args.steps + args.warmup
-    grid = SAMPLE_GRID if n <= 8 else (6, 4) if n <= 16 else (4, 3)
+    grid = (16, 16) if n <= 10 else SAMPLE_GRID if n <= 24 else (4, 3)
+    g = workload(n_off=(1 << 20) * grid[0] * grid[1] // 256, grid=grid)
     for _ in range(args.warmup):
-        oracle_sample(args.kernel, grid=grid)
-    g, _, nt, times = oracle_sample(args.kernel, reps=args.steps, grid=grid)
+        oracle_sample(args.kernel, threads=cores, g=g)
+    g, _, nt, times, used = oracle_sample(args.kernel, reps=args.steps, threads=cores, g=g)
     tot = sum(times)
     value = nt * args.steps / tot
-    sample = (f"oracle build + {args.kernel} evaluation of a {grid[0]}x{grid[1]} sub-grid "
+    full = grid == (16, 16)
+    sample = (f"oracle build (serial) + {args.kernel} evaluation ({used} OpenMP threads) of "
+              f"{'the whole workload' if full else f'a {grid[0]}x{grid[1]} sub-grid'} "
               f"({nt} targets, {len(g['up_w'])} quadrature nodes) per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "starfish-grid16x16x64x16-p8-15 (sub-grid sample)",
-                                             "kernel": args.kernel, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic",
+            "config": {"workload": g["name"] + ("" if full else " (sub-grid sample)"),
+                       "kernel": args.kernel, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -440,7 +476,7 @@ def run_gpu(args, rank, world, local):
     info = TreeInfo()
     chk(L.gq_tree_info_get(geom, C.byref(info)))
     wrap.info, wrap.nbox, wrap.nc, wrap.npt, wrap.nsrc = info, info.nbox, info.ncentres, info.npoint_targets, info.nsources
-    model = work_model(wrap, P, Q)
+    model = work_model(wrap, P, Q, args.kernel)
     wrap._geom = wrap._ctx = None     # borrowed handles: released below, not by the wrapper
     dom = int(np.argmax(stage_ms))
     peak = C.c_double()
@@ -463,11 +499,17 @@ def run_gpu(args, rank, world, local):
             v = C.c_double()
             if L.gq_probe_fma_peak(ctx, what, C.byref(v)) == 0:
                 others[name] = v.value
+        per_kernel = {}
+        for i, mm in model.items():
+            a = mm["units"] * mm["flops_per_unit"] / (stage_ms[i] * 1e-3) / 1e12
+            per_kernel[mm["name"]] = {"achieved": a, "frac": a / peak.value, "ms_per_launch": float(stage_ms[i]),
+                                      "units_per_launch": mm["units"], "flops_per_unit": mm["flops_per_unit"],
+                                      "unit_of_work": mm["unit"]}
         roof = {"bound": "alu", "kernel": m["name"], "achieved": achieved, "peak": peak.value,
                 "unit": "TFLOP/s", "frac": achieved / peak.value, "traffic": traffic,
                 "peak_source": peak_src, "units_per_launch": m["units"], "unit_of_work": m["unit"],
                 "flops_per_unit": m["flops_per_unit"], "ms_per_launch": stage_ms[dom],
-                "other_measured_tflops": others}
+                "other_measured_tflops": others, "kernels": per_kernel}
     stage_report = {STAGE_NAMES[i]: round(float(stage_ms[i]), 4) for i in range(11)}
     for i, m in model.items():
         stage_report[STAGE_NAMES[i] + "_tflops"] = m["units"] * m["flops_per_unit"] / (stage_ms[i] * 1e-3) / 1e12
@@ -507,19 +549,32 @@ def run_gpu(args, rank, world, local):
         e2e = {"value": world * nt * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * tot / args.steps}
 
-    # ---- CPU oracle baseline and accuracy on the same sample (rank 0, N = 1)
+    # ---- CPU oracle baseline (rank 0, N = 1): the whole workload on all host cores,
+    # and a single-core figure on a sub-grid; the GPU result is compared with the
+    # oracle at every target of the whole workload
     cpu = None
     rel_err = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        gs, ref, nts, times = oracle_sample(args.kernel)
-        sgeo = Geometry(gs, params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"])), device=local)
-        sgeo.build()
-        v = sgeo.eval(args.kernel, gs["density"])
-        rel_err = float(np.abs(v - ref).max() / np.abs(ref).max())
-        sgeo.close()
-        cpu = {"value": nts / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": (f"serial C oracle, build + {args.kernel} evaluation of a {SAMPLE_GRID[0]}x{SAMPLE_GRID[1]} "
-                          f"sub-grid of the workload ({nts} targets), {times[0]:.1f} s")}
+        cores = host_cores()
+        _, ref, nts, times, used = oracle_sample(args.kernel, threads=cores, g=g)
+        gpu_vals = np.empty(nt)
+        geo_full = C.c_void_p()
+        chk(L.gq_geometry_create(ctx, C.byref(desc), C.byref(prm), C.byref(geo_full)))
+        chk(L.gq_targets_set(geo_full, nt, d_txy.data_ptr(), d_ton.data_ptr()))
+        chk(L.gq_build(geo_full))
+        chk(L.gq_eval(geo_full, kern, d_mu.data_ptr(), d_out.data_ptr(), None))
+        torch.cuda.synchronize()
+        gpu_vals[:] = d_out.cpu().numpy()
+        L.gq_geometry_destroy(geo_full)
+        rel_err = float(np.abs(gpu_vals - ref).max() / np.abs(ref).max())
+        gs, _, nts1, times1, _ = oracle_sample(args.kernel)
+        cpu = {"value": nts / times[0], "unit": UNIT, "cores": used, "kind": "oracle",
+               "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+               "sample": (f"C oracle, build (serial) + {args.kernel} evaluation ({used} OpenMP threads) of the whole "
+                          f"workload ({nts} targets), {times[0]:.1f} s"),
+               "single_core": {"value": nts1 / times1[0], "unit": UNIT, "cores": 1,
+                               "sample": (f"the same oracle on one core, a {SAMPLE_GRID[0]}x{SAMPLE_GRID[1]} sub-grid "
+                                          f"({nts1} targets), {times1[0]:.1f} s")}}
 
     # ---- accuracy sweep: orders from eps, FP64 vs MIXED (FP64 translations) vs
     # MIXED_FMM (translations in FP32 pairs too) evaluation throughput

@@ -77,12 +77,13 @@ enum { GQ_S = 0, GQ_D = 1, GQ_SP = 2 };
  *  eps          : requested accuracy (used for orders of 0 and by the mixed modes).
  *  precision    : GQ_PREC_FP64 (default): every stage in FP64.
  *                 GQ_PREC_MIXED: a tier chosen from eps.
- *                 eps >= 1e-6: the direct interactions (Lists 1, 3 close,
+ *                 eps >= 5e-6: the direct interactions (Lists 1, 3 close,
  *                 4 close to centres and to point targets) and the List 3
  *                 far multipole evaluation at point targets run in FP32 on
  *                 coordinates taken relative to box centres, with FP64 sums
- *                 across lanes (rounding about 1e-7 relative, below eps/5).
- *                 1e-12 <= eps < 1e-6: the same steps run in double-FP32
+ *                 across lanes (rounding 4e-8 .. 3e-7 relative measured,
+ *                 the larger for D; below eps/5).
+ *                 1e-12 <= eps < 5e-6: the same steps run in double-FP32
  *                 pairs (about 48 significant bits; measured 1e-15 .. 2e-13
  *                 relative to the FP64 path).  In both tiers a source inside
  *                 a centre's expansion disk (|r/w| > 1, where rounding would
@@ -198,15 +199,32 @@ gq_status gq_build(gq_geom *g);
  * out: [ntargets] potential values (host or device).  stats may be NULL. */
 gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *out, gq_stats *stats);
 
+/* The layer-potential operator at the base nodes, as an integral equation
+ * applies it (Sec. 1: the exterior Neumann problem leads to the second-kind
+ * equation -mu/2 + S' mu = g; Sec. 4 states the evaluation of S mu for a
+ * density given at the nodes):
+ *     out[i] = identity * mu[i] + (K mu)(x_i),   K = S, D or S' (kernel),
+ * x_i the base node i, evaluated two-sided from its two centres 2i and 2i+1
+ * and averaged (the principal value on the curve, eq. qbx).  identity = -0.5
+ * with kernel GQ_SP gives the exterior Neumann operator; 0 gives K alone.
+ * Stages 2-8 run as in gq_eval on the geometry's current build; the targets
+ * given to gq_targets_set play no part in the result beyond the tree they
+ * shaped (their point-target stages are skipped), so the values equal those
+ * of gq_eval with the base nodes as on-surface targets on the same tree.
+ * mu: [npanels*nb] density at the base nodes (host or device).
+ * out: [npanels*nb] (host or device).  GQ_ERR_STATE before gq_build,
+ * GQ_ERR_INVALID for a null pointer or an unknown kernel.  Runs in the
+ * geometry's precision mode. */
+gq_status gq_apply(gq_geom *g, int kernel, double identity, const double *mu, double *out);
+
 /* Exterior Neumann problem (Sec. 1): with u = S mu outside the curve and the
  * normal derivative g prescribed on it, solve the second-kind equation
  *     -mu/2 + S' mu = g
- * for mu at the base nodes by restarted GMRES(restart) from mu = 0.  S' is
- * evaluated by gq_eval(GQ_SP) (two-sided QBX, principal value); the Arnoldi
+ * for mu at the base nodes by restarted GMRES(restart) from mu = 0.  The
+ * operator is gq_apply(GQ_SP, identity -0.5) (two-sided QBX, principal value),
+ * on whatever targets the geometry was built with; the Arnoldi
  * vectors and their orthogonalisation (classical Gram-Schmidt, twice) are
- * FP64 device work.  The targets must be the base nodes, on-surface, in
- * order (gq_targets_set with xy = base nodes, on_surface_node[i] = i), else
- * GQ_ERR_STATE.  rhs: [npanels*nb] g (host or device).  mu: [npanels*nb]
+ * FP64 device work.  rhs: [npanels*nb] g (host or device).  mu: [npanels*nb]
  * solution (host or device).  Stops when the residual estimate drops below
  * tol * |rhs| or after maxit iterations; *iters receives the iteration count
  * and *resid the true relative residual |rhs - A mu| / |rhs| (either may be
@@ -318,7 +336,7 @@ gq_status gq_set_orders(gq_geom *g, int p_qbx, int p_fmm);
  * after start-up.  The paper has no counterpart; it is a deployment variant.
  *
  * Working memory comes from one fixed device array inside the library
- * (16 MiB, of which 128 KiB hold translation tables); every GPU that loads
+ * (16 MiB, of which 256 KiB hold translation tables); every GPU that loads
  * the library keeps that array until the process exits.  Problems whose
  * working set (quadrature nodes x 16 B + 2 x boxes x (p_fmm+1) x 16 B +
  * centres x (p_qbx+1) x 16 B + point targets x 8 B + targets x 4 B, each
@@ -329,8 +347,11 @@ gq_status gq_set_orders(gq_geom *g, int p_qbx, int p_fmm);
  * host inputs would need staging buffers.  The geometry must be built.  The
  * evaluation is the FP64 one whatever the geometry's precision mode (the
  * mixed modes need buffers of their own).
- * The first call on a device sets the array up (looks up its device address
- * and writes the tables); make that first call before any stream capture.
+ * The context's device must be the calling thread's current device
+ * (GQ_ERR_STATE otherwise).  The first call on a device sets the array up
+ * (looks up its device address, writes the tables and waits for the copies
+ * with a device synchronisation); make that first call before any stream
+ * capture.  The kernels are those of gq_eval in FP64 mode.
  * All calls share the one array and it keeps the last call's contents, so
  * calls whose device work overlaps (different streams or contexts) race;
  * order them on one stream.  No memory is allocated or freed by this call. */

@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
@@ -70,6 +70,10 @@ def lib():
                       "orc_npoint_targets"):
                 getattr(L, f).argtypes = [C.c_void_p]
                 getattr(L, f).restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = C.c_int
+            L.orc_max_threads.argtypes = []
+            L.orc_max_threads.restype = C.c_int
             L.orc_list_size.restype = C.c_int64
             L.orc_list_size.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_list.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
@@ -92,6 +96,18 @@ def lib():
             L.orc_op_eval_mpole.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's evaluation loops (1 = serial, the default).
+    Every output is summed by one thread in the serial order, so the results
+    are the same bits for any count.  Returns the count in effect."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def max_threads() -> int:
+    """Processors the oracle's OpenMP runtime sees."""
+    return int(lib().orc_max_threads())
 
 
 def _p(a):

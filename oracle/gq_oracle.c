@@ -7,6 +7,12 @@
  * Compile with -ffp-contract=off: the decisions that feed integer results
  * (keys, centre levels, association) must round every operation separately.
  *
+ * Threads: built with -fopenmp, the evaluation loops (O1 and Stages 2-8 of
+ * O2) run over boxes, centres and targets in parallel (orc_set_threads);
+ * every output is still summed by one thread in the serial order, so the
+ * results are bit for bit those of one thread.  The tree and lists stay
+ * serial.
+ *
  * GQ_ORC_MUT (default 0) plants one deliberate mistake when compiled with
  * -DGQ_ORC_MUT=k; tests/test_oracle_mutations.py builds such variants to show
  * that the pins catch each of them.  Normal builds never set it.
@@ -35,6 +41,28 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* number of threads for the evaluation loops (1 = serial) */
+static int g_threads = 1;
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
 
 typedef double complex cplx;
 
@@ -754,6 +782,7 @@ static cplx eval_mpole(int p, cplx c, const cplx *a, cplx t) {
 static void final_values(orc_state *s, int kernel, const int *target_mask, const cplx *Q,
                          const cplx *pot_pt, double *value) {
     int q = s->p.p_qbx;
+#pragma omp parallel for schedule(static) num_threads(g_threads)
     for (int t = 0; t < s->g.ntargets; ++t) {
         if (target_mask && !target_mask[t]) continue;
         cplx tt = pt(s->tgt_xy, t);
@@ -801,6 +830,7 @@ int orc_eval(orc_state *s, int kernel, const double *density_base, const int *ta
 
     /* Stage 2: multipoles, leaves then postorder M2M (children have larger indices) */
     cplx *M = calloc((size_t)s->nbox * P1, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic, 64) num_threads(g_threads)
     for (int b = 0; b < s->nbox; ++b) {
         obox *B = &s->box[b];
         cplx cb = B->cx + I * B->cy;
@@ -815,7 +845,13 @@ int orc_eval(orc_state *s, int kernel, const double *density_base, const int *ta
     }
     /* Stages 4, 6b, 7: box local expansions, top down (parents first) */
     cplx *L = calloc((size_t)s->nbox * P1, sizeof(cplx));
-    for (int b = 0; b < s->nbox; ++b) {
+    /* boxes are numbered level by level: one level at a time, a box's parent
+     * (previous level) is complete before the box reads it */
+    for (int lb = 0; lb < s->nbox;) {
+        int le = lb;
+        while (le < s->nbox && s->box[le].level == s->box[lb].level) ++le;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
+    for (int b = lb; b < le; ++b) {
         if (!need_far[b]) continue;
         obox *B = &s->box[b];
         cplx cb = B->cx + I * B->cy;
@@ -832,10 +868,13 @@ int orc_eval(orc_state *s, int kernel, const double *density_base, const int *ta
             for (int j = 0; j < D->src.n; ++j) { int i = D->src.v[j]; p2local(kin, p, cb, pt(s->up_xy, i), str[i], L + b * P1); }
         }
     }
+        lb = le;
+    }
     /* Stages 3, 5, 6a, 8 for centres and point targets */
     cplx *Q = calloc((size_t)s->nc * Q1 + 1, sizeof(cplx));
     cplx *pot = calloc((size_t)s->npt + 1, sizeof(cplx));
     const int near_lists[3] = {ORC_U, ORC_WC, ORC_XC};
+#pragma omp parallel for schedule(dynamic, 4) num_threads(g_threads)
     for (int b = 0; b < s->nbox; ++b) {
         if (!need_box[b]) continue;
         obox *B = &s->box[b];
@@ -902,11 +941,13 @@ int orc_direct(orc_state *s, int kernel, const double *density_base, const int *
     mark_needed(s, target_mask, need_c, need_p);
     cplx *Q = calloc((size_t)s->nc * Q1 + 1, sizeof(cplx));
     cplx *pot = calloc((size_t)s->npt + 1, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
     for (int c = 0; c < s->nc; ++c) {
         if (!need_c[c]) continue;
         cplx cc = pt(s->c_xy, c);
         for (int i = 0; i < s->nsrc; ++i) p2local(kin, q, cc, pt(s->up_xy, i), str[i], Q + c * Q1);
     }
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
     for (int k = 0; k < s->npt; ++k) {
         if (!need_p[k]) continue;
         cplx tt = pt(s->tgt_xy, s->pt_tgt[k]), acc = 0;

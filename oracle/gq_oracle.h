@@ -83,6 +83,12 @@ void orc_upsample(const orc_state *s, const double *mu_base, double *mu_up);
  * value[nt] receives the result (unselected entries untouched).  qbx_out
  * (may be NULL) receives [nc][p_qbx+1] complex coefficients (interleaved
  * re,im) for the centres that were needed. */
+/* Threads of the evaluation loops (OpenMP builds; 1 = serial, the default).
+ * Results do not depend on it.  Returns the count in effect. */
+int orc_set_threads(int n);
+/* Processors OpenMP sees (1 without OpenMP). */
+int orc_max_threads(void);
+
 int orc_eval(orc_state *s, int kernel, const double *density_base, const int *target_mask,
              double *value, double *qbx_out);
 /* O1: direct QBX / direct point sums, same conventions. */

@@ -78,6 +78,7 @@ def lib():
             "gq_build": (st, [vp]),
             "gq_eval": (st, [vp, i32, vp, vp, C.POINTER(Stats)]),
             "gq_eval_noalloc": (st, [vp, i32, vp, vp]),
+            "gq_apply": (st, [vp, i32, C.c_double, vp, vp]),
             "gq_gmres": (st, [vp, vp, C.c_double, i32, i32, vp, C.POINTER(i32), C.POINTER(C.c_double)]),
             "gq_context_launches": (st, [vp, C.POINTER(C.c_int64)]),
             "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
@@ -236,9 +237,20 @@ class Geometry:
         self._check(self.L.gq_eval(self._geom, k, _ptr(density), _ptr(out), C.byref(st)))
         return (out, st) if stats else out
 
+    def apply(self, kernel, mu, out=None, identity=0.0):
+        """identity * mu + K mu at the base nodes (gq_apply), K = S, D or SP
+        evaluated two-sided.  mu / out: numpy (host) or torch CUDA tensors."""
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        if isinstance(mu, np.ndarray):
+            mu = np.ascontiguousarray(mu, np.float64)
+        if out is None:
+            out = np.empty(self.nbase, np.float64)
+        self._check(self.L.gq_apply(self._geom, k, float(identity), _ptr(mu), _ptr(out)))
+        return out
+
     def gmres(self, rhs, tol=1e-10, maxit=500, restart=50, mu=None):
-        """Solve -mu/2 + S' mu = rhs at the base nodes (targets must be the base
-        nodes, on-surface, in order).  Returns (mu, iterations, relative residual)."""
+        """Solve -mu/2 + S' mu = rhs at the base nodes (the operator is
+        gq_apply).  Returns (mu, iterations, relative residual)."""
         if isinstance(rhs, np.ndarray):
             rhs = np.ascontiguousarray(rhs, np.float64)
         if mu is None:

@@ -298,6 +298,33 @@ gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *ou
     });
 }
 
+gq_status gq_apply(gq_geom *g, int kernel, double identity, const double *mu, double *out) {
+    if (!g || !mu || !out) return GQ_ERR_INVALID;
+    if (kernel != GQ_S && kernel != GQ_D && kernel != GQ_SP) return GQ_ERR_INVALID;
+    return guarded(g->ctx, [&] {
+        GQ_REQUIRE(g->built, GQ_ERR_STATE, "gq_apply before gq_build");
+        cudaStream_t st = g->ctx->stream;
+        const double *dens = mu;
+        if (!is_device_ptr(mu)) {
+            g->dens_dev.alloc(g->nbase);
+            GQ_CUDA(cudaMemcpyAsync(g->dens_dev.p, mu, sizeof(double) * g->nbase, cudaMemcpyDefault, st));
+            dens = g->dens_dev.p;
+        }
+        bool out_dev = is_device_ptr(out);
+        double *o = out;
+        dbuf<double> stage;
+        if (!out_dev) {
+            stage.alloc(g->nbase);
+            o = stage.p;
+        }
+        gq_eval_all(g, kernel, dens, o, nullptr, nullptr, &identity);
+        if (!out_dev) {
+            GQ_CUDA(cudaMemcpyAsync(out, o, sizeof(double) * g->nbase, cudaMemcpyDefault, st));
+            GQ_CUDA(cudaStreamSynchronize(st));
+        }
+    });
+}
+
 gq_status gq_eval_noalloc(gq_geom *g, int kernel, const double *density_dev, double *out_dev) {
     if (!g || !density_dev || (!out_dev && g->nt > 0)) return GQ_ERR_INVALID;
     if (kernel != GQ_S && kernel != GQ_D && kernel != GQ_SP) return GQ_ERR_INVALID;
@@ -314,8 +341,6 @@ gq_status gq_gmres(gq_geom *g, const double *rhs, double tol, int maxit, int res
     if (!g || !rhs || !mu || !(tol > 0) || maxit < 1 || restart < 1 || restart > 1000) return GQ_ERR_INVALID;
     return guarded(g->ctx, [&] {
         GQ_REQUIRE(g->built, GQ_ERR_STATE, "gq_gmres before gq_build");
-        GQ_REQUIRE(g->targets_are_base_nodes, GQ_ERR_STATE,
-                   "gq_gmres needs the targets to be the base nodes, on-surface, in order");
         cudaStream_t st = g->ctx->stream;
         dbuf<double> b, x;
         const double *bd = rhs;

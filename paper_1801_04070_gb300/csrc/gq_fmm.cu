@@ -33,6 +33,10 @@
 namespace {
 
 constexpr double kInv2Pi = 0.15915494309189533576888376337251;
+// MIXED: FP32 direct sums from this accuracy up.  Their rounding, measured up
+// to 3e-7 relative (D on a single starfish, where the double-layer terms
+// cancel most), stays below eps/5 = 1e-6 here; smaller eps use FP32 pairs.
+constexpr double kF32TierEps = 5e-6;
 constexpr int kBinN = 64;   // binomial table C(n, k), n, k < 64
 
 // C(m+k-1, k-1) for m <= GQ_MAX_PQBX, k <= 32: the real matrix of the factored
@@ -58,6 +62,7 @@ struct EvalView {
     const double *binom;   // [kBinN][kBinN]
     const int *qc;         // per-centre QBX order (sorted centres) or nullptr: all use Q
     const double *logt;    // GqLogTable
+    const unsigned int *qexp;   // largest biased exponent of the S strengths (k_strengths)
 };
 
 __device__ __forceinline__ double box_rho(const RootInfo &R, int l) { return ldexp(R.H, -l); }
@@ -65,7 +70,6 @@ __device__ __forceinline__ double2 box_centre(const RootInfo &R, int l, int ix, 
     double h = ldexp(R.H, -l);
     return make_double2(R.lo_x + (double)(2 * ix + 1) * h, R.lo_y + (double)(2 * iy + 1) * h);
 }
-__device__ __forceinline__ double bin(const EvalView &E, int n, int k) { return E.binom[n * kBinN + k]; }
 
 __device__ __forceinline__ double2 shfl2(double2 v, int src, int width) {
     return make_double2(__shfl_sync(0xffffffffu, v.x, src, width), __shfl_sync(0xffffffffu, v.y, src, width));
@@ -86,17 +90,27 @@ __device__ __forceinline__ double2 lane_powers(double2 u, int g, int width) {
 // ------------------------------------------------------------------ A1: upsample + strengths
 __global__ void k_strengths(int nsrc, int nu, int nb, const int *__restrict__ src_perm, const double *__restrict__ interp,
                             const double *__restrict__ dens, const double *__restrict__ s_w,
-                            const double2 *__restrict__ s_n, int kernel, double2 *__restrict__ str) {
+                            const double2 *__restrict__ s_n, int kernel, double2 *__restrict__ str,
+                            unsigned int *__restrict__ qexp) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nsrc) return;
-    int id = src_perm[j];
-    int panel = id / nu, jj = id - panel * nu;
-    const double *row = interp + (size_t)jj * nb;
-    const double *mu_b = dens + (size_t)panel * nb;
-    double mu = 0.0;
-    for (int i = 0; i < nb; ++i) mu += row[i] * mu_b[i];
-    double wm = s_w[j] * mu;
-    str[j] = kernel == GQ_D ? cscale(s_n[j], wm) : make_double2(wm, 0.0);
+    unsigned int ex = 0;
+    if (j < nsrc) {
+        int id = src_perm[j];
+        int panel = id / nu, jj = id - panel * nu;
+        const double *row = interp + (size_t)jj * nb;
+        const double *mu_b = dens + (size_t)panel * nb;
+        double mu = 0.0;
+        for (int i = 0; i < nb; ++i) mu += row[i] * mu_b[i];
+        double wm = s_w[j] * mu;
+        str[j] = kernel == GQ_D ? cscale(s_n[j], wm) : make_double2(wm, 0.0);
+        ex = (unsigned int)(((unsigned long long)__double_as_longlong(wm) >> 52) & 0x7ff);
+    }
+    // the largest exponent of w mu (qexp cleared before the launch): the direct
+    // kernels scale their FP32 copies of the strengths by it
+    if (qexp) {
+        ex = __reduce_max_sync(0xffffffffu, ex);
+        if ((threadIdx.x & 31) == 0 && ex) atomicMax(qexp, ex);
+    }
 }
 
 // ------------------------------------------------------------------ Stage 2: P2M
@@ -155,43 +169,6 @@ __global__ void k_p2m(EvalView E, int nwork, const int *__restrict__ work, doubl
             if (k >= 1) v = E.kernel == GQ_D ? make_double2(-v.x, -v.y) : cscale(v, -1.0 / k);
             M[(size_t)b * (P + 1) + k] = v;
         }
-}
-
-// ------------------------------------------------------------------ Stage 2: M2M, one thread per (parent, m)
-__global__ void k_m2m(EvalView E, int lstart, int lend, double2 *__restrict__ M) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int P1 = E.P + 1;
-    int b = lstart + (int)(t / P1), m = (int)(t % P1);
-    if (b >= lend) return;
-    int4 c4 = E.bchild[b];
-    int ch[4] = {c4.x, c4.y, c4.z, c4.w};
-    if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;  // leaf
-    if (E.sub_src[b] == 0) return;
-    int l = E.blev[b];
-    double2 zp = box_centre(E.R, l, E.bix[b], E.biy[b]);
-    double rho = box_rho(E.R, l);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int q = 0; q < 4; ++q) {
-        int c = ch[q];
-        if (c < 0 || E.sub_src[c] == 0) continue;
-        double2 zc = box_centre(E.R, l + 1, E.bix[c], E.biy[c]);
-        double2 eta = make_double2((zc.x - zp.x) / rho, (zc.y - zp.y) / rho);
-        const double2 *A = M + (size_t)c * P1;
-        if (m == 0) {
-            acc = cadd(acc, A[0]);
-            continue;
-        }
-        // sum_{k=1}^{m} C(m-1,k-1) A_k 2^-k eta^(m-k), k descending so the power grows
-        double2 pw = make_double2(1.0, 0.0), s = make_double2(0.0, 0.0);
-        for (int k = m; k >= 1; --k) {
-            s = cadd(s, cscale(cmul(A[k], pw), bin(E, m - 1, k - 1) * ldexp(1.0, -k)));
-            pw = cmul(pw, eta);
-        }
-        // pw = eta^m
-        s = csub(s, cscale(pw, A[0].x / m));
-        acc = cadd(acc, s);
-    }
-    M[(size_t)b * P1 + m] = acc;
 }
 
 // M2M and L2L with the translation matrices tabulated: with box-scaled
@@ -340,25 +317,6 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
     }
 }
 
-// ------------------------------------------------------------------ Stage 7: L2L, one thread per (child, m)
-__global__ void k_l2l(EvalView E, int lstart, int lend, double2 *__restrict__ L) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int P1 = E.P + 1;
-    int c = lstart + (int)(t / P1), m = (int)(t % P1);
-    if (c >= lend || E.sub_tgt[c] == 0) return;
-    int p = E.bparent[c];
-    int l = E.blev[c];
-    double rho_p = box_rho(E.R, l - 1);
-    double2 zp = box_centre(E.R, l - 1, E.bix[p], E.biy[p]);
-    double2 zc = box_centre(E.R, l, E.bix[c], E.biy[c]);
-    double2 eta = make_double2((zc.x - zp.x) / rho_p, (zc.y - zp.y) / rho_p);
-    const double2 *B = L + (size_t)p * P1;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = E.P; k >= m; --k) acc = cadd(cmul(acc, eta), cscale(B[k], bin(E, k, m)));
-    double2 *dst = L + (size_t)c * P1 + m;
-    *dst = cadd(*dst, cscale(acc, ldexp(1.0, -m)));
-}
-
 // ------------------------------------------------------------------ Stages 3, 5a, 6a: direct near field
 // One block per target box; the box's List 1, 3 close and 4 close source
 // ranges are flattened into shared memory; each warp takes one target and its
@@ -458,6 +416,9 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
     __shared__ int wsum[kNearThreads / 32];
     __shared__ double lt[kGqLogN];
     for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
+    // FP32 strengths are rebased to the largest one: q = qf * 2^(qe - 1023)
+    const int qe = KERNEL == GQ_D ? 1023 : (int)*E.qexp;
+    const double qscale = gq_pow2_biased(qe);
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
@@ -473,6 +434,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
         double2 acc[QQ + 1];
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) acc[m] = make_double2(0.0, 0.0);
+        float acc0f = 0.0f;   // S: FP32 tails of the logarithms, strengths rebased by qe
         for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
             if (!single) {
                 __syncthreads();
@@ -508,7 +470,9 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                         // last term: a multiply-add into the sum (t is not needed again)
                         if (qc >= QQ) acc[QQ] = cfma(t, u, acc[QQ]);
                     } else {
-                        acc[0].x += st.x * gq_log_half(n2, lt);
+                        float tail;
+                        acc[0].x = fma(st.x, gq_log_half_split(n2, lt, tail), acc[0].x);
+                        acc0f = fmaf(gq_f32_rebased(st.x, qe), tail, acc0f);
                         double2 t = make_double2(st.x * u.x, st.x * u.y);
                         acc[1] = cadd(acc[1], t);
 #pragma unroll
@@ -522,6 +486,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
                 }
             }
         }
+        if (KERNEL != GQ_D) acc[0].x = fma((double)acc0f, qscale, acc[0].x);
         double vals[2 * (QQ + 1)];
 #pragma unroll
         for (int m = 0; m <= QQ; ++m) {
@@ -553,6 +518,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
     __shared__ int wsum[kNearThreads / 32];
     __shared__ double lt[kGqLogN];
     for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
+    const int qe = KERNEL == GQ_D ? 1023 : (int)*E.qexp;
+    const double qscale = gq_pow2_biased(qe);
     int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
@@ -564,6 +531,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
         bool valid = t < te;
         double2 tz = valid ? E.sp_xy[t] : make_double2(0.0, 0.0);
         double acc = 0.0;
+        float accf = 0.0f;
         for (int e0 = 0; e0 < ne; e0 += kNearRanges) {
             if (!single) {
                 __syncthreads();
@@ -578,12 +546,18 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
                     double2 y = E.s_xy[s], st = E.str[s];
                     double wx = y.x - tz.x, wy = y.y - tz.y;
                     double n2 = wx * wx + wy * wy;
-                    if (n2 == 0.0) continue;
-                    if (KERNEL == GQ_D) acc += (st.x * wx + st.y * wy) * gq_rcp(n2);
-                    else acc += st.x * gq_log_half(n2, lt);
+                    if (KERNEL == GQ_D) {
+                        if (n2 == 0.0) continue;   // coincident source skipped
+                        acc += (st.x * wx + st.y * wy) * gq_rcp(n2);
+                    } else {                       // a coincident source gives log term 0
+                        float tail;
+                        acc = fma(st.x, gq_log_half_split(n2, lt, tail), acc);
+                        accf = fmaf(gq_f32_rebased(st.x, qe), tail, accf);
+                    }
                 }
             }
         }
+        if (KERNEL != GQ_D) acc = fma((double)accf, qscale, acc);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (valid && lane == 0) pot[t] = acc;
     }
@@ -595,74 +569,10 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
 // v = rho_d / y, s = r / y and At_k = A_k v^k:
 //   Q_0 += A_0 log|y| + sum_k At_k
 //   Q_m += (-1)^m s^m (sum_k C(m+k-1,k-1) At_k - A_0/m),   1 <= m <= q.
-template <int PM>
-__global__ void k_w_centres(EvalView E, int nc, const int *__restrict__ ctr_box_of, const double2 *__restrict__ M,
-                            double2 *__restrict__ Qout) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
-    int b = ctr_box_of[c];
-    int beg = E.loff[3][b], end = E.loff[3][b + 1];
-    if (beg == end) return;
-    const int P = E.P, P1 = P + 1, Qn = E.Q;
-    double2 cz = E.sc_xy[c];
-    double rc = E.sc_r[c];
-    double2 acc[GQ_MAX_PQBX + 1];
-#pragma unroll
-    for (int m = 0; m <= GQ_MAX_PQBX; ++m) acc[m] = make_double2(0.0, 0.0);
-    for (int i = beg; i < end; ++i) {
-        int d = E.lidx[3][i];
-        int l = E.blev[d];
-        double rho = box_rho(E.R, l);
-        double2 zd = box_centre(E.R, l, E.bix[d], E.biy[d]);
-        double2 y = make_double2(cz.x - zd.x, cz.y - zd.y);
-        double n2 = y.x * y.x + y.y * y.y, inv = gq_rcp(n2);
-        double2 yinv = make_double2(y.x * inv, -y.y * inv);
-        double2 v = cscale(yinv, rho), sv = cscale(yinv, rc);
-        const double2 *A = M + (size_t)d * P1;
-        double A0 = A[0].x;
-        double2 At[PM + 1];
-        double2 vk = v, sum = make_double2(0.0, 0.0);
-#pragma unroll
-        for (int k = 1; k <= PM; ++k) {
-            At[k] = make_double2(0.0, 0.0);
-            if (k <= P) {
-                At[k] = cmul(A[k], vk);
-                sum = cadd(sum, At[k]);
-                vk = cmul(vk, v);
-            }
-        }
-        acc[0].x += A0 * gq_log_half(n2, E.logt) + sum.x;
-        acc[0].y += sum.y;
-        double2 sm = make_double2(1.0, 0.0);
-#pragma unroll
-        for (int m = 1; m <= GQ_MAX_PQBX; ++m) {
-            if (m <= Qn) {
-                sm = cmul(sm, sv);
-                double2 G = make_double2(0.0, 0.0);
-#pragma unroll
-                for (int k = 1; k <= PM; ++k)
-                    if (k <= P) {
-                        double cc = c_pascal[m][k];
-                        G.x += cc * At[k].x;
-                        G.y += cc * At[k].y;
-                    }
-                G.x -= A0 * (1.0 / m);   // m is a constant here: the reciprocal folds
-                double2 t = cmul(sm, G);
-                if (m & 1) acc[m] = csub(acc[m], t);
-                else acc[m] = cadd(acc[m], t);
-            }
-        }
-    }
-    double2 *dst = Qout + (size_t)c * (Qn + 1);
-#pragma unroll
-    for (int m = 0; m <= GQ_MAX_PQBX; ++m)
-        if (m <= Qn) dst[m] = cadd(dst[m], acc[m]);
-}
-
-// The same M2QBXL with the QBX order a template parameter and the loops
-// exchanged: k outer, m inner, so that At_k = A_k v^k is used as soon as it is
-// formed (no array of p+1 terms) and G_m = sum_k C(m+k-1, k-1) At_k
-// accumulates in q+1 registers; (-r/y)^m carries the sign (-1)^m.
+// The QBX order is a template parameter and the loops run k outer, m inner,
+// so that At_k = A_k v^k is used as soon as it is formed (no array of p+1
+// terms) and G_m = sum_k C(m+k-1, k-1) At_k accumulates in q+1 registers;
+// (-r/y)^m carries the sign (-1)^m.
 template <int PM, int QQ>
 __global__ void __launch_bounds__(128) k_w_centres_q(EvalView E, int nc, const int *__restrict__ ctr_box_of,
                                                      const double2 *__restrict__ M, double2 *__restrict__ Qout) {
@@ -768,29 +678,6 @@ __global__ void k_w_points(EvalView E, int npt, const int *__restrict__ pt_owner
 }
 
 // ------------------------------------------------------------------ Stage 8
-// L2QBXL: thread per (centre, m): Q_m += (r/rho)^m sum_{k>=m} C(k,m) L_k eta^(k-m)
-__global__ void k_l2qbxl(EvalView E, int nc, const int *__restrict__ ctr_box_of, const double2 *__restrict__ L,
-                         double2 *__restrict__ Qout) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int Q1 = E.Q + 1;
-    int c = (int)(t / Q1), m = (int)(t % Q1);
-    if (c >= nc) return;
-    int b = ctr_box_of[c];
-    int l = E.blev[b];
-    double rho = box_rho(E.R, l);
-    double2 zb = box_centre(E.R, l, E.bix[b], E.biy[b]);
-    double2 cz = E.sc_xy[c];
-    double2 eta = make_double2((cz.x - zb.x) / rho, (cz.y - zb.y) / rho);
-    const double2 *B = L + (size_t)b * (E.P + 1);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = E.P; k >= m; --k) acc = cadd(cmul(acc, eta), cscale(B[k], bin(E, k, m)));
-    double s = E.sc_r[c] / rho, sm = 1.0;
-    for (int i = 0; i < m; ++i) sm *= s;
-    double2 *dst = Qout + (size_t)c * Q1 + m;
-    *dst = cadd(*dst, cscale(acc, sm));
-}
-
-// L2P: thread per point target
 // L2QBXL by a Taylor shift, one thread per centre: with the box-scaled local
 // expansion sum_k L_k z^k, z = (x - z_b)/rho, and eta = (c - z_b)/rho, the
 // coefficients of the shifted polynomial in zeta = z - eta come from q+1
@@ -845,6 +732,7 @@ void dispatch_l2qbxl_t(gq_ctx *ctx, const EvalView &E, int nc, const int *owner,
     else launch_l2qbxl_t<GQ_MAX_PFMM>(ctx, E, nc, owner, L, Q);
 }
 
+// L2P: one thread per point target, Horner in the box-scaled variable
 __global__ void k_l2p(EvalView E, int npt, const int *__restrict__ pt_owner, const double2 *__restrict__ L,
                       double *__restrict__ pot) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -904,6 +792,41 @@ __global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, 
         }
     }
     out[t] = sum / nside;
+}
+
+// the operator at the base nodes (gq_apply): base node i is evaluated from its
+// two centres 2i, 2i+1 and averaged, as an on-surface target of gq_eval would
+// be (eq. qbx; principal value), and identity * mu_i is added
+__global__ void k_final_base(int nbase, int kernel, int Q, const int *__restrict__ qcs, const int *__restrict__ ctr_pos,
+                             const double *__restrict__ base_xy, const double *__restrict__ base_n,
+                             const double2 *__restrict__ sc_xy, const double *__restrict__ sc_r,
+                             const double2 *__restrict__ Qc, const double2 *__restrict__ Qc2, double identity,
+                             const double *__restrict__ mu, double *__restrict__ out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nbase) return;
+    double2 tz = make_double2(base_xy[2 * t], base_xy[2 * t + 1]);
+    double sum = 0.0;
+    for (int sd = 0; sd < 2; ++sd) {
+        int cp = ctr_pos[2 * t + sd];
+        double2 cz = sc_xy[cp];
+        double r = sc_r[cp];
+        double2 zeta = make_double2((tz.x - cz.x) / r, (tz.y - cz.y) / r);
+        const double2 *B = Qc + (size_t)cp * (Q + 1);
+        const double2 *B2 = Qc2 ? Qc2 + (size_t)cp * (Q + 1) : nullptr;
+        const int q = qcs ? qcs[cp] : Q;
+        auto coef = [&](int m) { return B2 ? cadd(B[m], B2[m]) : B[m]; };
+        if (kernel == GQ_SP) {
+            double2 h = cscale(coef(q), (double)q);
+            for (int m = q - 1; m >= 1; --m) h = cfma(h, zeta, cscale(coef(m), (double)m));
+            double2 n = make_double2(base_n[2 * t], base_n[2 * t + 1]);
+            sum += -kInv2Pi * cmul(n, h).x / r;
+        } else {
+            double2 h = coef(q);
+            for (int m = q - 1; m >= 0; --m) h = cfma(h, zeta, coef(m));
+            sum += -kInv2Pi * h.x;
+        }
+    }
+    out[t] = identity * mu[t] + sum / 2;
 }
 
 __global__ void k_export_qbx(int nc, int Q, const int *__restrict__ ctr_perm, const double *__restrict__ sc_r,
@@ -2286,7 +2209,10 @@ static EvalTables &get_tables(gq_geom *g) {
 }
 
 void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *stt,
-                 const double2 *qn_pre) {
+                 const double2 *qn_pre, const double *apply_identity) {
+    // apply_identity != null: the operator at the base nodes (gq_apply); the
+    // point-target stages are skipped and out_dev has one value per base node
+    const bool at_base = apply_identity != nullptr;
     gq_ctx *ctx = g->ctx;
     cudaStream_t st = ctx->stream;
     EvalTables &T = get_tables(g);
@@ -2309,6 +2235,8 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
 
     g->strength.alloc(g->nsrc);
     E.str = g->strength;
+    g->qexp.alloc(1);
+    E.qexp = g->qexp;
     g->M.alloc((size_t)g->nbox * P1);
     g->L.alloc((size_t)g->nbox * P1);
     g->Q.alloc((size_t)g->nc * Q1);    // List 3 far + box-local part of the QBX coefficients
@@ -2343,11 +2271,13 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     int64_t l0 = ctx->launches;
 
     // A1
+    GQ_CUDA(cudaMemsetAsync(g->qexp.p, 0, sizeof(unsigned int), st));
     GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
-              (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, g->strength.p);
+              (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, g->strength.p,
+              g->qexp.p);
     const bool mixed = g->prm.precision == GQ_PREC_MIXED || g->prm.precision == GQ_PREC_MIXED_FMM;
-    const bool f32 = mixed && g->prm.eps >= 1e-6;
-    const bool split = mixed && g->prm.eps >= 1e-12 && g->prm.eps < 1e-6;
+    const bool f32 = mixed && g->prm.eps >= kF32TierEps;
+    const bool split = mixed && g->prm.eps >= 1e-12 && g->prm.eps < kF32TierEps;
     MixedView X{};
     if (f32) {
         if (!g->mixed_ready) {
@@ -2427,7 +2357,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         else if (!qn_pre) dispatch_near_centres(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
     }
     mark(N_CTR, s2);
-    if (g->n_pt_boxes) {
+    if (g->n_pt_boxes && !at_base) {
         if (f32) {
             auto kd = k_near_points_f32<GQ_D>;
             auto ks = k_near_points_f32<GQ_S>;
@@ -2457,7 +2387,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     }
     GQ_CUDA(cudaMemsetAsync(g->L.p, 0, sizeof(double2) * g->nbox * P1, st));
     GQ_CUDA(cudaMemsetAsync(g->Q.p, 0, sizeof(double2) * g->nc * Q1, st));
-    if (g->npt) GQ_CUDA(cudaMemsetAsync(g->pot.p, 0, sizeof(double) * g->npt, st));
+    if (g->npt && !at_base) GQ_CUDA(cudaMemsetAsync(g->pot.p, 0, sizeof(double) * g->npt, st));
     // Stage 2 (in pairs wherever M2L runs in pairs: the multipoles then live in
     // M2 and the FP64 copy is made from them for the FP64 consumers)
     if (g->n_leaf_src) {
@@ -2542,7 +2472,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         dispatch_w_centres_q(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->M, g->Q.p);
     }
     mark(S_WC, st);
-    if (g->npt) {
+    if (g->npt && !at_base) {
         if (f32)
             GQ_LAUNCH(ctx, k_w_points_f32, gq_blocks(g->npt, 128), 128, 0, E, X, g->npt, (const int *)g->pt_owner,
                       g->pot.p);
@@ -2560,7 +2490,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
             dispatch_l2qbxl_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, (const float4 *)g->L2, g->Q.p);
         else
             dispatch_l2qbxl_t(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->L, g->Q.p);
-    if (g->npt)
+    if (g->npt && !at_base)
         GQ_LAUNCH(ctx, k_l2p, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner, (const double2 *)g->L,
                   g->pot.p);
     mark(S_L2Q, st);
@@ -2571,7 +2501,13 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     const bool use_pre = qn_pre && !f32 && !split;
     const double2 *qn_use = use_pre ? qn_pre : (const double2 *)g->Qn;
     g->qn_last = qn_use;
-    if (g->nt)
+    if (at_base) {
+        if (g->nbase)
+            GQ_LAUNCH(ctx, k_final_base, gq_blocks(g->nbase, 256), 256, 0, g->nbase, kernel, Qn, E.qc,
+                      (const int *)g->ctr_pos, (const double *)g->base_xy, (const double *)g->base_n,
+                      (const double2 *)g->sc_xy, (const double *)g->sc_r, (const double2 *)g->Q, qn_use,
+                      *apply_identity, dens_dev, out_dev);
+    } else if (g->nt)
         GQ_LAUNCH(ctx, k_final, gq_blocks(g->nt, 256), 256, 0, g->nt, kernel, Qn, E.qc, (const int *)g->t_kind,
                   (const int *)g->t_ctr, (const int *)g->ctr_pos, (const int *)T.tgt_ptpos, (const double *)g->tgt_xy,
                   (const int *)g->tgt_on, (const double *)g->base_n, (const double2 *)g->sc_xy,
@@ -2611,8 +2547,8 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
 // after another.
 void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, double *const *out) {
     const bool mixed = g->prm.precision == GQ_PREC_MIXED || g->prm.precision == GQ_PREC_MIXED_FMM;
-    const bool f32 = mixed && g->prm.eps >= 1e-6;
-    const bool split = mixed && g->prm.eps >= 1e-12 && g->prm.eps < 1e-6;
+    const bool f32 = mixed && g->prm.eps >= kF32TierEps;
+    const bool split = mixed && g->prm.eps >= 1e-12 && g->prm.eps < kF32TierEps;
     if (nd <= 1 || f32 || split || g->n_ctr_boxes == 0) {
         for (int d = 0; d < nd; ++d) gq_eval_all(g, kernel, dens[d], out[d], nullptr);
         return;
@@ -2628,7 +2564,7 @@ void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, do
         if (g->nsrc)
             GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
                       (const double *)g->interp, dens[d], (const double *)g->s_w, (const double2 *)g->s_n, kin,
-                      g->strm.p + d * sstride);
+                      g->strm.p + d * sstride, (unsigned int *)nullptr);
     EvalView E{};
     E.R = g->root;
     E.P = g->prm.p_fmm;
@@ -2672,10 +2608,23 @@ void gq_export_qbx_impl(gq_geom *g, double *host) {
 // device memory at call time.  Its working memory (source strengths, box
 // multipole and local expansions, QBX coefficients, point-target potentials,
 // translation tables) lives in one file-scope device array of fixed size.
+// It launches the kernels gq_eval launches in FP64 mode, with the direct and
+// List 3 far/local parts of the QBX coefficients summed in one array.
 namespace {
 
 constexpr size_t kNoAllocBytes = size_t(16) << 20;   // 16 MiB per device, held until exit
-constexpr size_t kNoAllocTableBytes = size_t(128) << 10;
+constexpr size_t kNoAllocTableBytes = size_t(256) << 10;
+// table offsets inside the array (bytes)
+constexpr size_t kNaBinom = 0;                  // [64][64] doubles, 32 KiB
+constexpr size_t kNaDtab = 32768;               // [121][32] double2, 61,952 B
+constexpr size_t kNaLogtab = 98304;             // [121] doubles
+constexpr size_t kNaLogt = 99328;               // GqLogTable
+constexpr size_t kNaM2M = 131072;               // [4][kTN][kTN] double2, 61,504 B
+constexpr size_t kNaL2L = 196608;               // [4][kTN][kTN] double2
+constexpr size_t kNaQexp = 261888;              // one unsigned int, written by every call
+static_assert(kNaLogt + sizeof(double) * kGqLogN <= kNaM2M, "log table overlaps the M2M matrices");
+static_assert(kNaL2L + sizeof(double2) * 4 * kTN * kTN <= kNaQexp, "tables exceed their region");
+static_assert(kNaQexp + 256 <= kNoAllocTableBytes, "exponent slot outside the table region");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -2686,55 +2635,39 @@ struct NoAllocDevice {
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[64];
 
-void host_tables(std::vector<double> &bn, std::vector<double2> &dt, std::vector<double> &lt) {
-    bn.assign(kBinN * kBinN, 0.0);
-    for (int n = 0; n < kBinN; ++n) {
-        bn[n * kBinN] = 1.0;
-        for (int k = 1; k <= n; ++k) bn[n * kBinN + k] = bn[(n - 1) * kBinN + k - 1] + (k <= n - 1 ? bn[(n - 1) * kBinN + k] : 0.0);
-    }
-    dt.assign(121 * 32, make_double2(0.0, 0.0));
-    lt.assign(121, 0.0);
-    for (int dy = -5; dy <= 5; ++dy)
-        for (int dx = -5; dx <= 5; ++dx) {
-            int off = (dy + 5) * 11 + (dx + 5);
-            double re = 2.0 * dx, im = 2.0 * dy, n2 = re * re + im * im;
-            double ir = n2 > 0 ? re / n2 : 0.0, ii = n2 > 0 ? -im / n2 : 0.0;
-            double pr = 1.0, pi = 0.0;
-            for (int k = 0; k < 32; ++k) {
-                dt[off * 32 + k] = make_double2(pr, pi);
-                double nr = pr * ir - pi * ii, ni = pr * ii + pi * ir;
-                pr = nr;
-                pi = ni;
-            }
-            lt[off] = n2 > 0 ? 0.5 * log(n2) : 0.0;
-        }
-}
-
-// Once per device, with that device current: resolve the device address of
-// the scratch array (host code cannot use the symbol itself) and store the
-// read-only translation tables at its start.
+// Once per device, with that device current (checked): resolve the device
+// address of the scratch array (host code cannot use the symbol itself) and
+// store the read-only translation tables at its start.  The copies finish
+// before the slot is marked ready, so no later launch on any stream can read
+// a partly written table.
 NoAllocDevice &noalloc_setup(int dev) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     GQ_REQUIRE(dev >= 0 && dev < 64, GQ_ERR_UNSUPPORTED, "gq_eval_noalloc: device index >= 64");
+    int cur = -1;
+    GQ_CUDA(cudaGetDevice(&cur));
+    GQ_REQUIRE(cur == dev, GQ_ERR_STATE, "gq_eval_noalloc: the context's device must be the current device");
     NoAllocDevice &D = g_noalloc_dev[dev];
     if (D.ready) return D;
     void *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) throw gq_error{GQ_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)};
     std::vector<double> bn, lt;
-    std::vector<double2> dt;
-    host_tables(bn, dt, lt);
+    std::vector<double2> dt, tm, tl;
+    host_const_tables(bn, dt, lt, tm, tl);
     unsigned char *base = (unsigned char *)ptr;
-    GQ_CUDA(cudaMemcpy(base, bn.data(), sizeof(double) * bn.size(), cudaMemcpyHostToDevice));
-    GQ_CUDA(cudaMemcpy(base + 32768, dt.data(), sizeof(double2) * dt.size(), cudaMemcpyHostToDevice));
-    GQ_CUDA(cudaMemcpy(base + 32768 + 65536, lt.data(), sizeof(double) * lt.size(), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(base + kNaBinom, bn.data(), sizeof(double) * bn.size(), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(base + kNaDtab, dt.data(), sizeof(double2) * dt.size(), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(base + kNaLogtab, lt.data(), sizeof(double) * lt.size(), cudaMemcpyHostToDevice));
     GqLogTable LT;
     gq_log_table_host(&LT);
-    GQ_CUDA(cudaMemcpy(base + 32768 + 65536 + 1024, &LT, sizeof(LT), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(base + kNaLogt, &LT, sizeof(LT), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(base + kNaM2M, tm.data(), sizeof(double2) * tm.size(), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(base + kNaL2L, tl.data(), sizeof(double2) * tl.size(), cudaMemcpyHostToDevice));
     std::vector<double> pc((GQ_MAX_PQBX + 1) * 33, 0.0);
     for (int m = 0; m <= GQ_MAX_PQBX; ++m)
         for (int k = 1; k <= 32; ++k) pc[m * 33 + k] = bn[(m + k - 1) * kBinN + (k - 1)];
     GQ_CUDA(cudaMemcpyToSymbol(c_pascal, pc.data(), sizeof(double) * pc.size()));
+    GQ_CUDA(cudaDeviceSynchronize());
     D.base = base;
     D.ready = true;
     return D;
@@ -2762,9 +2695,12 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
                                                " bytes of scratch, the fixed array holds " +
                                                std::to_string(gq_noalloc_capacity())};
     NoAllocDevice &D = noalloc_setup(ctx->device);
-    const double *binom = (const double *)D.base;
-    const double2 *dtab = (const double2 *)(D.base + 32768);
-    const double *logtab = (const double *)(D.base + 32768 + 65536);
+    const double *binom = (const double *)(D.base + kNaBinom);
+    const double2 *dtab = (const double2 *)(D.base + kNaDtab);
+    const double *logtab = (const double *)(D.base + kNaLogtab);
+    const double2 *tm2m = (const double2 *)(D.base + kNaM2M);
+    const double2 *tl2l = (const double2 *)(D.base + kNaL2L);
+    unsigned int *qexp = (unsigned int *)(D.base + kNaQexp);
     unsigned char *w = D.base + kNoAllocTableBytes;
     int P = g->prm.p_fmm, Qn = g->prm.p_qbx, P1 = P + 1, Q1 = Qn + 1;
     double2 *str = (double2 *)w;  w += align256(sizeof(double2) * g->nsrc);
@@ -2787,15 +2723,17 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
     for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
     E.binom = binom;
     E.qc = g->has_qc ? (const int *)g->q_ctr.p : nullptr;
-    E.logt = (const double *)(D.base + 32768 + 65536 + 1024);
+    E.logt = (const double *)(D.base + kNaLogt);
+    E.qexp = qexp;
 
     // the array keeps the previous call's contents: clear the accumulators
     GQ_CUDA(cudaMemsetAsync(M, 0, sizeof(double2) * g->nbox * P1, st));
     GQ_CUDA(cudaMemsetAsync(L, 0, sizeof(double2) * g->nbox * P1, st));
     GQ_CUDA(cudaMemsetAsync(Qc, 0, sizeof(double2) * g->nc * Q1, st));
     if (g->npt) GQ_LAUNCH(ctx, k_tgt_ptpos, gq_blocks(g->npt, 256), 256, 0, g->npt, (const int *)g->pt_perm.p, ptpos);
+    GQ_CUDA(cudaMemsetAsync(qexp, 0, sizeof(unsigned int), st));
     GQ_LAUNCH(ctx, k_strengths, gq_blocks(g->nsrc, 256), 256, 0, g->nsrc, g->nu, g->nb, (const int *)g->src_perm,
-              (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, str);
+              (const double *)g->interp, dens_dev, (const double *)g->s_w, (const double2 *)g->s_n, kin, str, qexp);
     if (g->n_leaf_src) {
         auto k8 = k_p2m<8>;
         auto k16 = k_p2m<16>;
@@ -2805,7 +2743,7 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
     }
     for (int l = g->nlev - 2; l >= 0; --l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_m2m, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, M);
+        GQ_LAUNCH(ctx, k_m2m_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, tm2m, M);
     }
     if (g->n_far_boxes) {
         size_t sm = sizeof(double) * P1 * P1;
@@ -2819,8 +2757,9 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
     }
     for (int l = 1; l < g->nlev; ++l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_l2l, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, L);
+        GQ_LAUNCH(ctx, k_l2l_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, tl2l, L);
     }
+    // the direct part writes the coefficients, the List 3 far and local parts add to them
     if (g->n_ctr_boxes) dispatch_near_centres(ctx, E, g->n_ctr_boxes, g->ctr_boxes, Qc);
     if (g->n_pt_boxes) {
         auto kd = k_near_points<GQ_D>;
@@ -2829,13 +2768,8 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
                   (const int *)g->pt_boxes, pot);
     }
     if (g->nc) {
-        auto k8 = k_w_centres<8>;
-        auto k16 = k_w_centres<16>;
-        auto k32 = k_w_centres<GQ_MAX_PFMM>;
-        GQ_LAUNCH(ctx, (P <= 8 ? k8 : P <= 16 ? k16 : k32), gq_blocks(g->nc, 128), 128, 0, E, g->nc,
-                  (const int *)g->ctr_owner, (const double2 *)M, Qc);
-        GQ_LAUNCH(ctx, k_l2qbxl, gq_blocks((long long)g->nc * Q1, 128), 128, 0, E, g->nc, (const int *)g->ctr_owner,
-                  (const double2 *)L, Qc);
+        dispatch_w_centres_q(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)M, Qc);
+        dispatch_l2qbxl_t(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)L, Qc);
     }
     if (g->npt) {
         GQ_LAUNCH(ctx, k_w_points, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,

@@ -68,10 +68,10 @@ __global__ void k_scale(int n, double a, double *__restrict__ x) {
 struct Solver {
     gq_geom *g;
     int n;
-    dbuf<double> tmp, hdev;
-    void apply(const double *v, double *out) {   // out = -v/2 + S' v
-        gq_eval_all(g, GQ_SP, v, tmp.p, nullptr);
-        GQ_LAUNCH(g->ctx, k_axpby, gq_blocks(n, kT), kT, 0, n, -0.5, v, 1.0, (const double *)tmp.p, out);
+    dbuf<double> hdev;
+    void apply(const double *v, double *out) {   // out = -v/2 + S' v at the base nodes (gq_apply)
+        const double minus_half = -0.5;
+        gq_eval_all(g, GQ_SP, v, out, nullptr, nullptr, &minus_half);
     }
     std::vector<double> dots(const double *V, int k, const double *w) {
         GQ_LAUNCH(g->ctx, k_multidot, k, 1024, 0, n, k, V, w, hdev.p);
@@ -94,7 +94,6 @@ int gq_gmres_impl(gq_geom *g, const double *rhs_dev, double tol, int maxit, int 
     Solver S;
     S.g = g;
     S.n = n;
-    S.tmp.alloc(n);
     S.hdev.alloc(m + 2);
     dbuf<double> V, w, r;
     V.alloc((size_t)(m + 1) * n);

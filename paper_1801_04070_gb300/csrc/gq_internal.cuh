@@ -145,6 +145,7 @@ struct gq_geom {
     dbuf<int> far_boxes;       int n_far_boxes = 0;  // boxes with V or X far entries
     // evaluation buffers
     dbuf<double2> strength;          // sorted sources: S -> (q, 0), D -> d
+    dbuf<unsigned int> qexp;         // largest biased exponent of the strengths (one value)
     dbuf<double2> M, L;              // [nbox][p_fmm+1] box-scaled expansions
     dbuf<double2> Q;                 // [nc][p_qbx+1] r-scaled QBX coefficients (sorted centres): far part
     dbuf<double2> Qn;                // the same, direct part
@@ -201,7 +202,7 @@ void gq_radix_sort_pairs32(gq_ctx *ctx, uint32_t *keys, int *vals, long long n, 
 void gq_build_all(gq_geom *g);                 // gq_tree.cu
 void gq_build_lists(gq_geom *g);               // gq_lists.cu
 void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *st,
-                 const double2 *qn_pre = nullptr);                                          // gq_fmm.cu
+                 const double2 *qn_pre = nullptr, const double *apply_identity = nullptr);  // gq_fmm.cu
 void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, double *const *out);
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu

@@ -57,6 +57,46 @@ __device__ __forceinline__ double gq_log_half(double x, const double *__restrict
 
 __device__ __forceinline__ double gq_log(double x, const double *__restrict__ T) { return 2.0 * gq_log_half(x, T); }
 
+// FP32 copy of x built from its bits with integer operations only (no FP64
+// conversion instruction): the leading 24 significant bits (truncated, so
+// relative error below 2^-23), with the exponent lowered so that
+// x = f * 2^(ebias - 1023).  Values with |f| below 2^-126 (and zeros,
+// subnormals) give 0; the caller keeps |x| <= 2^(ebias - 1023 + 127).
+__device__ __forceinline__ float gq_f32_rebased(double x, int ebias) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
+    int e = (int)((hi >> 20) & 0x7ff) - ebias + 127;
+    unsigned int f = (hi & 0x80000000u) | ((unsigned int)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return e > 0 ? __uint_as_float(f) : 0.0f;
+}
+
+// (1/2) log x as h + tail with fewer FP64 instructions: log1p(r)/2 =
+// r/2 - r^2/4 + r^3 (1/6 - r/8); the first two terms and the table terms stay
+// in FP64 (h, two FMAs after r), the tail, below 2^-32 in magnitude, is formed
+// in FP32 from r's FP32 copy (relative error about 2^-21, so below 2^-53
+// absolute).  The caller sums tails in FP32 and adds them once at the end.
+// x = 0 gives h = 0 and tail = 0 (a coincident source contributes nothing).
+__device__ __forceinline__ double gq_log_half_split(double x, const double *__restrict__ T, float &tail) {
+    long long bits = __double_as_longlong(x);
+    unsigned long long e = (unsigned long long)bits >> 52;
+    if (e - 23ull > 2000ull) {                                 // rare: see gq_log_half
+        tail = 0.0f;
+        return x == 0.0 ? 0.0 : 0.5 * log(x);
+    }
+    int j = (int)((bits >> 43) & (kGqLogJ - 1));
+    double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    double r = fma(m, T[j], -1.0);
+    float rf = gq_f32_rebased(r, 1023);
+    tail = rf * rf * (rf * fmaf(rf, -0.125f, 0.16666667f));
+    double u = fma(r, -0.25, 0.5);
+    return fma(r, u, T[2 * kGqLogJ + (int)e] + T[kGqLogJ + j]);
+}
+
+// 2^(e - 1023) for a biased exponent 1 <= e <= 2046 (0 for e = 0)
+__device__ __forceinline__ double gq_pow2_biased(int e) {
+    return e > 0 ? __longlong_as_double((long long)e << 52) : 0.0;
+}
+
 // ---------------------------------------------------------------- reciprocal
 // 1/x from the hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64,
 // which works on the upper mantissa bits; no conversions through FP32) refined

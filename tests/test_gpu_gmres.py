@@ -67,14 +67,26 @@ def test_starfish_known_solution_and_oracle_parity():
     assert np.abs(mu - mu_o).max() <= 1e-9 * np.abs(mu_o).max()
 
 
-def test_requires_base_node_targets():
-    from paper_1801_04070_gb300 import GigaQBXError
+def test_any_target_set():
+    """The GMRES operator is gq_apply at the base nodes, so the solve does not
+    depend on the targets the geometry was built with: with off-surface point
+    targets (a deeper tree) the solution agrees with the base-node build to
+    the FMM accuracy, and gq_apply(SP, -1/2) of it reproduces rhs."""
     g = workloads.starfish_c1()
-    geo, p = _geo(g)
-    geo.set_targets(g["base_xy"][:10], np.arange(10, dtype=np.int32))
+    geo, p = _geo(g, p_qbx=8, p_fmm=20)
+    x = g["base_xy"][:, 0] + 1j * g["base_xy"][:, 1]
+    nrm = g["base_n"][:, 0] + 1j * g["base_n"][:, 1]
+    rhs = (nrm * (-1.0 / (x - 0.1 - 0.2j) ** 2)).real
+    mu0, _, res0 = geo.gmres(rhs, tol=1e-12, maxit=300, restart=60)
+    rng = np.random.default_rng(5)
+    t = rng.uniform(-1.5, 1.5, size=(3000, 2))
+    geo.set_targets(t, -np.ones(len(t), np.int32))
     geo.build()
-    with pytest.raises(GigaQBXError):
-        geo.gmres(np.ones(len(g["base_xy"])))
+    mu1, _, res1 = geo.gmres(rhs, tol=1e-12, maxit=300, restart=60)
+    assert res0 < 1e-11 and res1 < 1e-11
+    assert np.abs(mu1 - mu0).max() <= 1e-9 * np.abs(mu0).max()
+    r = geo.apply("SP", mu1, identity=-0.5)
+    assert np.abs(r - rhs).max() <= 1e-10 * np.abs(rhs).max()
 
 
 def test_batched_gmres_equals_individual_solves():

@@ -196,3 +196,22 @@ def test_invalid_on_surface_index_leaves_no_targets():
     v = geo.eval("S", g["density"])
     assert np.isfinite(v).all() and len(v) == len(on)
     geo.close()
+
+
+@pytest.mark.parametrize("scale_exp", [-100, 0, 100])
+def test_density_scaling_is_exact(scale_exp):
+    """The potentials are linear in the density.  A power-of-two scale 2^k
+    scales every FP64 operation exactly, and the direct kernels' FP32 copies
+    of the strengths are rebased to the largest strength of the call.  So
+    S and D of 2^k mu are 2^k times those of mu, bit for bit, even where
+    2^k takes the strengths far outside FP32's range.  The oracle agrees at
+    1e-12."""
+    g = workloads.small_grid(2, 2, 16, 3000, seed=7)
+    geo, orc = _make(g, p_qbx=5, p_fmm=10)
+    mu = g["density"]
+    for kern in ("S", "D"):
+        base = geo.eval(kern, mu)
+        v = geo.eval(kern, np.ldexp(mu, scale_exp))
+        assert np.array_equal(v, np.ldexp(base, scale_exp)), kern
+        ref = orc.eval(kern, mu)
+        assert np.abs(base - ref).max() <= TOL * np.abs(ref).max(), kern

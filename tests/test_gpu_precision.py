@@ -1,5 +1,5 @@
-"""Precision modes (MIXED: FP32 direct sums when eps >= 1e-6, double-FP32
-power sums when 1e-12 <= eps < 1e-6, FP64 translations; MIXED_FMM: the
+"""Precision modes (MIXED: FP32 direct sums when eps >= 5e-6, double-FP32
+power sums when 1e-12 <= eps < 5e-6, FP64 translations; MIXED_FMM: the
 translations in double-FP32 pairs as well) and the accuracy
 sweep with orders chosen from the requested accuracy, checked against the
 FP64 oracle: O2 at the same orders (rounding of the mixed path) and O1,
@@ -27,18 +27,18 @@ def _geo(g, **kw):
 @pytest.mark.parametrize("kern", ["S", "D"])
 def test_mixed_fp32_tier_matches_oracle(kern):
     g = workloads.small_grid(3, 2, 24, 5000, seed=11, on_surface="up", p_qbx=8, p_fmm=15)
-    geo = _geo(g, p_qbx=8, p_fmm=15, n_max=32, eps=1e-6, precision=1)
+    geo = _geo(g, p_qbx=8, p_fmm=15, n_max=32, eps=5e-6, precision=1)
     v = geo.eval(kern, g["density"])
     ref = oracle.Oracle(g, oracle.default_params(g)).eval(kern, g["density"])
     err = np.abs(v - ref).max() / np.abs(ref).max()
     print(f"MIXED (FP32 direct) {kern}: rel err vs FP64 oracle {err:.2e}")
-    assert err <= 2e-7          # <= eps/5 at the FP32 tier threshold eps = 1e-6
+    assert err <= 1e-6          # <= eps/5 at the FP32 tier threshold eps = 5e-6
 
 
 @pytest.mark.parametrize("kern", ["S", "D"])
 @pytest.mark.parametrize("eps,bound", [(1e-8, 2e-11), (1e-12, 2e-13)])
 def test_mixed_split_tier_matches_oracle(kern, eps, bound):
-    """1e-12 <= eps < 1e-6: power recurrences in double-FP32 pairs (about 48
+    """1e-12 <= eps < 5e-6: power recurrences in double-FP32 pairs (about 48
     significant bits).  Pairs with sources near a centre amplify the rounding
     by |r/w|^m: those inside the disk are taken in FP64, and below eps = 1e-10
     also the point-target pairs closer than 1/8 of the box half-width.  M2L
@@ -82,7 +82,7 @@ def test_mixed_split_tier_sampled_at_eps_orders(kern):
 
 
 @pytest.mark.parametrize("kern", ["S", "D"])
-@pytest.mark.parametrize("eps,p_fmm", [(1e-6, 19), (1e-10, 30)])
+@pytest.mark.parametrize("eps,p_fmm", [(1e-5, 16), (1e-6, 19), (1e-10, 30)])
 def test_pair_fmm_passes_rounding(kern, eps, p_fmm):
     """GQ_PREC_MIXED_FMM: P2M, M2M, M2L, L2L and L2QBXL in FP32 pairs on top
     of either mixed tier (eps >= 1e-10): on a 4x4 starfish grid, whose far field runs through several hundred thousand
@@ -102,7 +102,7 @@ def test_pair_fmm_passes_rounding(kern, eps, p_fmm):
     print(f"pair FMM passes, eps {eps:.0e}, p_fmm {p_fmm}, {kern}: potential {added:.2e}, QBX coefficients {qerr:.2e} "
           f"relative to the FP64 path")
     assert added <= eps / 5
-    if eps < 1e-6:
+    if eps < 5e-6:
         assert qerr <= eps / 5
 
 

@@ -275,3 +275,21 @@ def test_fmm_converges_to_direct_qbx(c1):
         # coefficients m >= 1 agree too (constant term: only its real part is defined)
         assert np.abs(q2[:, 1:] - q1[:, 1:]).max() < 1e-10 * np.abs(q1[:, 1:]).max()
         assert np.abs(q2[:, 0].real - q1[:, 0].real).max() < 1e-10 * np.abs(q1[:, 0].real).max()
+
+
+def test_threads_do_not_change_results(c1):
+    """The OpenMP evaluation loops sum every output in the serial order: O1
+    and O2 values and QBX coefficients are the same bits for 1 and 4 threads."""
+    g = workloads.small_grid(2, 2, 16, 3000, seed=7)
+    o = oracle.Oracle(g, oracle.default_params(p_qbx=5, p_fmm=10))
+    mu = np.random.default_rng(2).normal(size=len(g["density"]))
+    res = {}
+    for nt in (1, 4):
+        oracle.set_threads(nt)
+        try:
+            res[nt] = [o.eval(k, mu, want_qbx=True) for k in ("S", "D")] + [o.direct("S", mu)]
+        finally:
+            oracle.set_threads(1)
+    for a, b in zip(res[1], res[4]):
+        for x, y in zip(a if isinstance(a, tuple) else (a,), b if isinstance(b, tuple) else (b,)):
+            assert np.array_equal(x, y)
