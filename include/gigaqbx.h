@@ -109,9 +109,21 @@ typedef struct {
     double assoc_slack;
     double eps;
     int precision;
+    int m2l;
 } gq_params;
 
 enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1, GQ_PREC_MIXED_FMM = 2 };
+
+/* m2l: how the List 2 translations (Stage 4, Sec. 3.1 eq. m2l) run in FP64
+ *   GQ_M2L_AUTO (default): on the BF16 tensor cores with FP64 accuracy when
+ *     p_fmm <= 15 and the translations are FP64 (GQ_PREC_FP64, GQ_PREC_MIXED;
+ *     GQ_PREC_MIXED_FMM keeps its FP32-pair M2L): every multipole and
+ *     translation entry is split exactly into eleven 5-bit digits (54 bits) at
+ *     a shared exponent, digit products accumulate exactly in FP32 tensor
+ *     memory and are recombined in 64-bit integers (measured within a few
+ *     units of 1e-15 of the FP64 M2L); otherwise FP64 FMAs.
+ *   GQ_M2L_FP64: always the FP64 FMA kernel. */
+enum { GQ_M2L_AUTO = 0, GQ_M2L_FP64 = 1 };
 
 /* Discretised curve (Sec. 2.1, 2.2.1).  Panel k owns base nodes
  * [k*nb, (k+1)*nb) and quadrature (upsampled) nodes [k*nu, (k+1)*nu).
@@ -379,6 +391,19 @@ gq_status gq_export_qbx(gq_geom *g, double *coeffs);
 /* Number of kernels this context has launched so far (all calls). */
 gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out);
 
+/* Device memory the library keeps cached for reuse (bytes), and a call that
+ * returns all of it to the driver (call when no library work is in flight).
+ * Buffers of live geometries are not affected. */
+gq_status gq_memory_cached(int64_t *bytes);
+gq_status gq_memory_release(void);
+
+/* ======================================================================
+ * Diagnostics.  Measurement and self-check helpers used by the tests and
+ * the benchmark; they are not part of the method and the paper has no
+ * counterpart.  Each runs a small amount of device work on the context's
+ * device.
+ * ==================================================================== */
+
 /* Measurement helper: throughput of a dependent-chain-free FMA loop on the
  * context's device, in TFLOP/s (2 flops per FMA).  what = 0: FP64 FMA,
  * what = 1: FP32 FMA, what = 2: FP64 tensor-core MMA (warp-wide
@@ -389,12 +414,6 @@ gq_status gq_context_launches(const gq_ctx *ctx, int64_t *out);
  * tensor cores; the paper has no counterpart.  Runs about 0.1 s of device work. */
 gq_status gq_probe_fma_peak(gq_ctx *ctx, int what, double *tflops);
 
-/* Device memory the library keeps cached for reuse (bytes), and a call that
- * returns all of it to the driver (call when no library work is in flight).
- * Buffers of live geometries are not affected. */
-gq_status gq_memory_cached(int64_t *bytes);
-gq_status gq_memory_release(void);
-
 /* Check helper for the FP64 logarithm and reciprocal the direct kernels use
  * (no counterpart in the paper): y[i] = f(x[i]) on the device, x and y device
  * arrays of n doubles; fn = 0: the table-driven logarithm, 1: CUDA's log,
@@ -402,6 +421,15 @@ gq_status gq_memory_release(void);
  * logarithm of the split-precision kernels (x rounded to an FP32 pair,
  * x in [2^-126, 2^126]), 5: the double-FP32 reciprocal (same range). */
 gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y);
+
+/* Tensor-core check: D[128][32] = A[128][K] * B[32][K]^T on one CTA by K/16
+ * chained tcgen05.mma (BF16 inputs, FP32 accumulation in tensor memory), as
+ * the tensor-core M2L uses them.  a, b: host arrays of BF16 bit patterns,
+ * row-major; d: host [128][32] floats.  K a multiple of 16 in [16, 256]
+ * (GQ_ERR_INVALID otherwise).  swap = 1 exchanges the leading and stride
+ * byte offsets of the shared-memory descriptors (a layout check).
+ * GQ_ERR_TIMEOUT if the bounded completion wait gave up. */
+gq_status gq_probe_umma(gq_ctx *ctx, int K, const uint16_t *a, const uint16_t *b, int swap, float *d);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ class Params(C.Structure):
     _fields_ = [("p_qbx", C.c_int), ("p_fmm", C.c_int), ("n_max", C.c_int),
                 ("tf_num", C.c_int), ("tf_den", C.c_int), ("w3_demote", C.c_int),
                 ("max_level", C.c_int), ("radius_factor", C.c_double),
-                ("assoc_slack", C.c_double), ("eps", C.c_double), ("precision", C.c_int)]
+                ("assoc_slack", C.c_double), ("eps", C.c_double), ("precision", C.c_int), ("m2l", C.c_int)]
 
 
 class GeometryDesc(C.Structure):
@@ -83,6 +83,7 @@ def lib():
             "gq_context_launches": (st, [vp, C.POINTER(C.c_int64)]),
             "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
             "gq_probe_math": (st, [vp, i32, i32, vp, vp]),
+            "gq_probe_umma": (st, [vp, i32, vp, vp, i32, vp]),
             "gq_memory_cached": (st, [C.POINTER(C.c_int64)]),
             "gq_memory_release": (st, []),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),

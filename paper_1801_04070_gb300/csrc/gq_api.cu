@@ -96,6 +96,7 @@ void resolve_orders(gq_params &p) {
     GQ_REQUIRE(p.w3_demote >= 1, GQ_ERR_INVALID, "w3_demote must be >= 1");
     GQ_REQUIRE(p.precision == GQ_PREC_FP64 || p.precision == GQ_PREC_MIXED || p.precision == GQ_PREC_MIXED_FMM,
                GQ_ERR_INVALID, "unknown precision");
+    GQ_REQUIRE(p.m2l == GQ_M2L_AUTO || p.m2l == GQ_M2L_FP64, GQ_ERR_INVALID, "unknown m2l mode");
 }
 
 }  // namespace
@@ -116,6 +117,7 @@ gq_status gq_params_default(gq_params *out) {
     out->assoc_slack = 1.2;
     out->eps = 0.0;
     out->precision = GQ_PREC_FP64;
+    out->m2l = GQ_M2L_AUTO;
     return GQ_OK;
 }
 
@@ -264,8 +266,10 @@ gq_status gq_build(gq_geom *g) {
         gq_tables_release(g);
         g->mixed_ready = false;
         g->split_ready = false;
+        g->tc_ready = false;
         gq_form_centres(g);
         gq_build_all(g);
+        if (gq_m2l_tc_supported(g)) gq_m2l_tc_build(g);   // tiles of the tensor-core M2L
         GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
         g->built = true;
     });
@@ -294,6 +298,7 @@ gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *ou
         if (!out_dev && g->nt) {
             GQ_CUDA(cudaMemcpyAsync(out, o, sizeof(double) * g->nt, cudaMemcpyDefault, st));
             GQ_CUDA(cudaStreamSynchronize(st));
+            GQ_REQUIRE(gq_m2l_tc_error(g) == 0, GQ_ERR_TIMEOUT, "tensor-core M2L: a bounded wait gave up");
         }
     });
 }
@@ -649,6 +654,14 @@ gq_status gq_memory_cached(int64_t *bytes) {
 gq_status gq_memory_release(void) {
     gq_dev_release_cache();
     return GQ_OK;
+}
+
+gq_status gq_probe_umma(gq_ctx *ctx, int K, const uint16_t *a, const uint16_t *b, int swap, float *d) {
+    if (!ctx || !a || !b || !d) return GQ_ERR_INVALID;
+    return guarded(ctx, [&] {
+        GQ_CUDA(cudaSetDevice(ctx->device));
+        gq_probe_umma_impl(ctx, K, a, b, swap, d);
+    });
 }
 
 gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y) {

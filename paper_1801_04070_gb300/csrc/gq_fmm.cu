@@ -2429,6 +2429,8 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
             auto k32 = k_m2l_split<32>;
             GQ_LAUNCH(ctx, (G == 16 ? k16 : k32), gq_blocks((long long)g->n_far_boxes * G, 128), 128, sm, E, SX,
                       g->n_far_boxes, (const int *)g->far_boxes, T.dtab2, T.logtab2, T.binom2, g->L2.p);
+        } else if (gq_m2l_tc_supported(g)) {
+            gq_m2l_tc(g, (const double2 *)g->M, g->L.p);   // FP64-accurate, on the tensor cores
         } else {
             size_t sm = sizeof(double) * P1 * P1;
             auto k16 = k_m2l<16>;
@@ -2517,6 +2519,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     ctx->launches += ctx2.launches;
     if (timed) {
         GQ_CUDA(cudaEventSynchronize(ev[S_END]));
+        GQ_REQUIRE(gq_m2l_tc_error(g) == 0, GQ_ERR_TIMEOUT, "tensor-core M2L: a bounded wait gave up");
         auto el = [&](int a, int b2) {
             float ms = 0;
             GQ_CUDA(cudaEventElapsedTime(&ms, ev[a], ev[b2]));

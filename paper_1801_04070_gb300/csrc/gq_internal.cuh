@@ -181,6 +181,12 @@ struct gq_geom {
     dbuf<float4> M2;      // multipoles
     dbuf<float4> L2;      // local expansions
     dbuf<float4> lvl2;    // per level: (rho, 1/rho), (log rho, 1/rho^2)
+    // tensor-core M2L (gq_m2l_tc.cu): tiles of the current build, multipole digits
+    bool tc_ready = false;
+    int tc_ntiles = 0;
+    dbuf<int> tc_tile_box, tc_slot_src, tc_tile_q, tc_err, tc_bexp, tc_lexp;
+    dbuf<unsigned> tc_tile_mask;
+    dbuf<uint16_t> tc_mdig;
 };
 
 // ------------------------------------------------------------------ launch helpers
@@ -207,7 +213,12 @@ void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, do
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
 void gq_probe_math_impl(gq_ctx *ctx, int fn, int n, const double *x_dev, double *y_dev);
+void gq_probe_umma_impl(gq_ctx *ctx, int K, const uint16_t *A_host, const uint16_t *B_host, int swap, float *D_host);
 void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double *out_dev);  // gq_fmm.cu
+bool gq_m2l_tc_supported(const gq_geom *g);                                                  // gq_m2l_tc.cu
+void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L);
+void gq_m2l_tc_build(gq_geom *g);
+int gq_m2l_tc_error(gq_geom *g);
 struct gq_mlp;
 int gq_mlp_param_count();                                                                   // gq_learned.cu
 gq_mlp *gq_mlp_new(gq_ctx *ctx, uint64_t seed);

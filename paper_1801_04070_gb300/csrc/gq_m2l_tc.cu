@@ -1,0 +1,619 @@
+// gq_m2l_tc.cu -- Stage 4 (M2L over List 2, Sec. 3.1 eq. m2l, Sec. 4.4) on
+// the BF16 tensor cores with FP64 accuracy, by exact digit splitting.
+//
+// With box-scaled coefficients (M_k = a_k / rho^k, L_m = beta_m rho^m) a List 2
+// translation between same-level boxes depends only on their offset
+// delta = (z_b - z_d) / rho = 2 (tx - sx) + 2i (ty - sy) (index differences):
+//     L_m += sum_k T_delta[m][k] M_k,
+//     T[0][0] = log|delta|, T[0][k] = delta^-k,
+//     T[m][0] = -(-1)^m delta^-m / m, T[m][k] = (-1)^m C(m+k-1, k-1) delta^-(m+k),
+// plus M_0 log rho for m = 0 (added in FP64).  In real form T is a 32 x 32
+// matrix per offset (p_fmm <= 15).  A target box b in quadrant (bx & 1, by & 1)
+// of its parent has its List 2 boxes among 75 offsets of a 10 x 10 window, so
+// for 128 target boxes of one quadrant
+//     L[128 x 32] = sum over window slots s of  Mg_s[128 x 32] * T_s^T,
+// Mg_s holding row b's List 2 multipole at slot s (or zeros): one GEMM with
+// K = 100 slots x 32, accumulated across slots in tensor memory.
+//
+// FP64 accuracy: every multipole entry is a 54-bit fixed-point integer at the
+// largest exponent of its tree level, every T entry one at the largest
+// exponent of its output column (over all offsets), both written as 11
+// balanced base-32 digits in [-16, 16] -- exact in BF16.  Digit products
+// (|.| <= 256) summed over at most 100 x 32 terms and 11 digit pairs stay
+// below 2^24, so the FP32 accumulators hold exact integers; the sums for
+// digit levels w = i + j <= 11 (i, j the digit indices) go to 12 accumulators
+// and are recombined in 64-bit integers, converted to FP64 once.  Emulated on
+// random multipoles this gives about 4e-15 of max|L| (the FP64 sum itself
+// carries about 1e-16 per term).
+//
+// One CTA (128 threads) per SM walks tiles of 128 target boxes; per occupied
+// slot, all threads stage the 11 multipole digit tiles (cp.async, 16 bytes)
+// and the 11 translation digit tiles into one of two shared-memory stages,
+// and thread 0 issues the MMAs (128 x N x 16, N up to 256: the 11 translation
+// digits are stacked along N so that digit pair (i, j) lands in the
+// accumulator columns of level i + j) and commits them to the stage's
+// mbarrier; the next slot is staged while they run.  Thread r then reads row
+// r's 12 x 32 accumulators (tcgen05.ld), recombines them and adds L_m.
+#include <math.h>
+
+#include <mutex>
+#include <vector>
+
+#include "gq_internal.cuh"
+#include "gq_tc.cuh"
+
+namespace {
+
+constexpr int kTcND = 11;          // digits per operand
+constexpr int kTcLev = 12;         // accumulated digit levels w = 0 .. 11
+constexpr int kTcBits = 54;        // fixed-point bits
+constexpr int kTcSlots = 100;      // 10 x 10 window of List 2 offsets
+constexpr int kTcRows = 128;       // target boxes per tile (MMA M)
+constexpr int kTcK = 32;           // real multipole terms per box (16 complex)
+constexpr int kTcN = 32;           // real outputs per box
+constexpr uint32_t kTileA = kTcRows * kTcK * 2;          // bytes per multipole digit tile (8 KiB)
+constexpr uint32_t kTileB = kTcN * kTcK * 2;             // bytes per translation digit tile (2 KiB)
+constexpr uint32_t kStage = kTcND * (kTileA + kTileB);   // 112,640 bytes
+constexpr uint64_t kWaitNs = 2000000000ull;              // bounded waits: 2 s
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0) : "memory");
+}
+
+// balanced base-32 digits of |X| <= 2^54, most significant first
+__host__ __device__ inline void tc_digits(long long X, int (&d)[kTcND]) {
+    for (int j = kTcND - 1; j >= 1; --j) {
+        int r = (int)(X & 31);
+        if (r >= 16) r -= 32;
+        d[j] = r;
+        X = (X - r) / 32;
+    }
+    d[0] = (int)X;
+}
+
+__host__ __device__ inline uint16_t bf16_of_small_int(int v) {
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+}
+
+// ---------------------------------------------------------------- per-eval: multipole digits
+// largest biased exponent of box b's 32 real multipole terms (a warp per box)
+__global__ void k_tc_boxexp(int nbox, int P, const double2 *__restrict__ M, int *__restrict__ bexp) {
+    int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, kk = threadIdx.x & 31;
+    if (b >= nbox) return;
+    int k = kk >> 1;
+    double x = 0.0;
+    if (k <= P) {
+        double2 v = M[(size_t)b * (P + 1) + k];
+        x = (kk & 1) ? v.y : v.x;
+    }
+    unsigned e = (unsigned)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (kk == 0) bexp[b] = (int)e;
+}
+
+// largest exponent per level (one block per level)
+__global__ void k_tc_levexp(const int *__restrict__ level_start, const int *__restrict__ bexp, int *__restrict__ lexp) {
+    __shared__ int red[32];
+    int l = blockIdx.x;
+    int s = level_start[l], e = level_start[l + 1];
+    int m = 0;
+    for (int b = s + threadIdx.x; b < e; b += blockDim.x) m = max(m, bexp[b]);
+    m = __reduce_max_sync(0xffffffffu, (unsigned)m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        v = __reduce_max_sync(0xffffffffu, (unsigned)v);
+        if (threadIdx.x == 0) lexp[l] = v;
+    }
+}
+
+// 11 BF16 digits of every real multipole term at its level's exponent:
+// mdig[b][i][kk], term kk = 2k + (0 re, 1 im)
+__global__ void k_tc_digits(int nbox, int P, const int *__restrict__ blev, const int *__restrict__ lexp,
+                            const double2 *__restrict__ M, uint16_t *__restrict__ mdig) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int b = (int)(t >> 5), kk = (int)(t & 31);
+    if (b >= nbox) return;
+    int k = kk >> 1;
+    double x = 0.0;
+    if (k <= P) {
+        double2 v = M[(size_t)b * (P + 1) + k];
+        x = (kk & 1) ? v.y : v.x;
+    }
+    int le = lexp[blev[b]];
+    int d[kTcND];
+    if (le == 0) {
+        for (int i = 0; i < kTcND; ++i) d[i] = 0;
+    } else {
+        // |x| < 2^(le - 1022): X = round(x 2^(54 - (le - 1022))), |X| <= 2^54
+        long long X = __double2ll_rn(ldexp(x, kTcBits - (le - 1022)));
+        tc_digits(X, d);
+    }
+    uint16_t *dst = mdig + (size_t)b * kTcND * kTcK + kk;
+#pragma unroll
+    for (int i = 0; i < kTcND; ++i) dst[i * kTcK] = bf16_of_small_int(d[i]);
+}
+
+// ---------------------------------------------------------------- per-build: tiles
+__global__ void k_tc_flags(int nbox, int q, const int *__restrict__ voff, const int *__restrict__ bix,
+                           const int *__restrict__ biy, int *__restrict__ flag) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    flag[b] = voff[b + 1] > voff[b] && ((bix[b] & 1) | ((biy[b] & 1) << 1)) == q;
+}
+
+// window slot of List 2 box d seen from b (quadrant q), or -1 outside the window
+__device__ __forceinline__ int tc_slot(int q, int bx, int by, int dx_, int dy_) {
+    int sx = dx_ - bx + 4 + (q & 1), sy = dy_ - by + 4 + (q >> 1);
+    return (sx < 0 || sx > 9 || sy < 0 || sy > 9) ? -1 : sy * 10 + sx;
+}
+
+// Sort key of a target box: which of the quadrant's first 64 List 2 window
+// slots (row-major, the 5 x 5 block of the box's 2-colleagues skipped) it
+// uses.  Boxes with similar keys share slots, so sorted tiles touch fewer.
+__global__ void k_tc_keys(int nbox, int q, const int *__restrict__ flag, const int *__restrict__ pos,
+                          const int *__restrict__ voff, const int *__restrict__ vidx, const int *__restrict__ bix,
+                          const int *__restrict__ biy, uint64_t *__restrict__ key, int *__restrict__ val,
+                          int *__restrict__ err) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox || !flag[b]) return;
+    const int qx = q & 1, qy = q >> 1;
+    uint64_t k = 0;
+    for (int e = voff[b]; e < voff[b + 1]; ++e) {
+        int d = vidx[e];
+        int s = tc_slot(q, bix[b], biy[b], bix[d], biy[d]);
+        if (s < 0) {
+            atomicExch(err, 2);
+            continue;
+        }
+        int sx = s % 10, sy = s / 10;
+        // valid-slot index: inner 5 x 5 block at columns/rows [2 + q., 6 + q.]
+        int rows_inner = min(max(sy - (2 + qy), 0), 5);
+        int in_row = (sy >= 2 + qy && sy <= 6 + qy) ? min(max(sx - (2 + qx), 0), 5) : 0;
+        int c = s - 5 * rows_inner - in_row;
+        if (c < 64) k |= 1ull << (63 - c);
+    }
+    key[pos[b]] = k;
+    val[pos[b]] = b;
+}
+
+__global__ void k_tc_fill(int n, int row0, const int *__restrict__ sorted_box, int q, const int *__restrict__ voff,
+                          const int *__restrict__ vidx, const int *__restrict__ bix, const int *__restrict__ biy,
+                          int *__restrict__ tile_box, int *__restrict__ slot_src, unsigned *__restrict__ tile_mask) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = sorted_box[i];
+    int row = row0 + i;
+    tile_box[row] = b;
+    for (int e = voff[b]; e < voff[b + 1]; ++e) {
+        int d = vidx[e];
+        int s = tc_slot(q, bix[b], biy[b], bix[d], biy[d]);
+        if (s < 0) continue;   // reported by k_tc_keys
+        slot_src[(size_t)row * kTcSlots + s] = d;
+        atomicOr(&tile_mask[(row / kTcRows) * 4 + (s >> 5)], 1u << (s & 31));
+    }
+}
+
+// ---------------------------------------------------------------- the tensor-core M2L
+struct TcArgs {
+    int ntiles, P;
+    const int *tile_box, *tile_q, *slot_src;
+    const unsigned *tile_mask;
+    const uint16_t *mdig, *tdig;
+    const int *fexp;     // [32] column exponents (|T[n][.]| < 2^fexp[n])
+    const int *lexp;     // per level: largest biased exponent of the multipoles
+    const int *blev, *voff, *vidx;
+    const double2 *M;
+    double2 *L;
+    double logH, ln2;    // log rho_l = logH - l log 2
+    int *err;
+};
+
+constexpr int kTcThreads = 160;   // warps 0-3: staging and epilogue (row = thread), warp 4: MMA issue
+
+__device__ __forceinline__ int next_slot(const unsigned *mask, int s) {
+    for (++s; s < kTcSlots; ++s)
+        if ((mask[s >> 5] >> (s & 31)) & 1u) return s;
+    return kTcSlots;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t full[2], empty[2], accfull, accfree;
+    __shared__ uint32_t tslot;
+    __shared__ unsigned smask[2][4];
+    __shared__ int sq[2];
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) gqtc::tmem_alloc(&tslot, 512);
+    if (tid == 0) {
+        gqtc::mbar_init(&full[0], 2 * kTcRows);   // per staging thread: one arrive + one cp.async arrive
+        gqtc::mbar_init(&full[1], 2 * kTcRows);
+        gqtc::mbar_init(&empty[0], 1);
+        gqtc::mbar_init(&empty[1], 1);
+        gqtc::mbar_init(&accfull, 1);
+        gqtc::mbar_init(&accfree, kTcRows);
+        abort_flag = 0;
+    }
+    gqtc::fence_before_sync();
+    __syncthreads();
+    gqtc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    const uint32_t sbase = gqtc::smem_u32(sm);
+    int it = 0;       // tiles done by this CTA
+    uint32_t g = 0;   // slots staged / consumed so far (both roles count the same slots)
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+        if (tid < 4) smask[it & 1][tid] = a.tile_mask[tile * 4 + tid];
+        if (tid == 4) sq[it & 1] = a.tile_q[tile];
+        // every thread passes this barrier once per tile; a wait that gave up
+        // (abort_flag) ends the loop for all of them together
+        if (__syncthreads_or(abort_flag)) break;
+        const unsigned *mask = smask[it & 1];
+        if (warp == 4) {
+            // ---------------- MMA issue (one thread)
+            if ((tid & 31) == 0) {
+                bool ok = it == 0 || gqtc::mbar_wait_abortable(&accfree, (uint32_t)((it - 1) & 1), kWaitNs, &abort_flag);
+                gqtc::fence_after_sync();
+                bool first = true;
+                for (int s = next_slot(mask, -1); s < kTcSlots; s = next_slot(mask, s), ++g) {
+                    const int st = g & 1;
+                    if (ok) ok = gqtc::mbar_wait_abortable(&full[st], (g >> 1) & 1, kWaitNs, &abort_flag);
+                    if (!ok) continue;   // count the remaining slots only
+                    gqtc::fence_smem_to_async();
+                    gqtc::fence_after_sync();
+                    const uint32_t sA = sbase + st * kStage, sB = sA + kTcND * kTileA;
+#pragma unroll 1
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const bool init = first && ks == 0;
+#pragma unroll 1
+                        for (int i = 0; i < kTcND; ++i) {
+                            const int jmax = min(kTcND - 1, kTcLev - 1 - i);
+                            const uint64_t ad = gqtc::smem_desc(sA + i * kTileA + ks * 256, 128, 512);
+                            // digit groups [j0, j1] stacked along N; the first MMAs of a tile
+                            // overwrite the levels not written yet (i = 0: 0..10; i = 1: 11)
+                            int gj[3][3], ng = 0;
+                            gj[ng][0] = 0; gj[ng][1] = min(jmax, 7); gj[ng][2] = (init && i == 0) ? 0 : 1; ++ng;
+                            if (jmax >= 8) {
+                                if (init && i == 1) {
+                                    gj[ng][0] = 8; gj[ng][1] = 9; gj[ng][2] = 1; ++ng;
+                                    gj[ng][0] = 10; gj[ng][1] = 10; gj[ng][2] = 0; ++ng;
+                                } else {
+                                    gj[ng][0] = 8; gj[ng][1] = jmax; gj[ng][2] = (init && i == 0) ? 0 : 1; ++ng;
+                                }
+                            }
+                            for (int x = 0; x < ng; ++x) {
+                                const int j0 = gj[x][0], j1 = gj[x][1];
+                                const uint64_t bd = gqtc::smem_desc(sB + j0 * kTileB + ks * 256, 128, 512);
+                                gqtc::mma_bf16(tmem + (uint32_t)((i + j0) * 32), ad, bd,
+                                               gqtc::idesc_bf16_f32(128, 32 * (j1 - j0 + 1)), (uint32_t)gj[x][2]);
+                            }
+                        }
+                    }
+                    gqtc::mma_commit(&empty[st]);
+                    first = false;
+                }
+                if (ok) gqtc::mma_commit(&accfull);
+            } else {
+                for (int s = next_slot(mask, -1); s < kTcSlots; s = next_slot(mask, s)) ++g;
+            }
+        } else {
+            // ---------------- staging (row = tid) and epilogue
+            const size_t row = (size_t)tile * kTcRows + tid;
+            const uint32_t rowoff = (uint32_t)(((tid >> 3) * 4) << 7) + (uint32_t)((tid & 7) << 4);
+            const int qx = sq[it & 1] & 1, qy = sq[it & 1] >> 1;
+            bool ok = true;
+            int s = next_slot(mask, -1);
+            int d = s < kTcSlots ? a.slot_src[row * kTcSlots + s] : -1;
+            for (; s < kTcSlots; ++g) {
+                const int sn = next_slot(mask, s);
+                const int dn = sn < kTcSlots ? a.slot_src[row * kTcSlots + sn] : -1;   // prefetch
+                const int st = g & 1;
+                if (ok && g >= 2) ok = gqtc::mbar_wait_abortable(&empty[st], ((g >> 1) - 1) & 1, kWaitNs, &abort_flag);
+                if (ok) {
+                    const uint32_t sA = sbase + st * kStage, sB = sA + kTcND * kTileA;
+#pragma unroll
+                    for (int i = 0; i < kTcND; ++i)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const uint32_t dst = sA + i * kTileA + rowoff + (c << 7);
+                            if (d >= 0) cp_async16(dst, a.mdig + ((size_t)d * kTcND + i) * kTcK + c * 8);
+                            else st_shared_zero16(dst);
+                        }
+                    const int dx = (s % 10) - 4 - qx, dy = (s / 10) - 4 - qy;
+                    const uint16_t *tsrc = a.tdig + (size_t)((-dy + 5) * 11 + (-dx + 5)) * kTcND * (kTileB / 2);
+                    for (int c = tid; c < (int)(kTcND * kTileB / 16); c += kTcRows) cp_async16(sB + c * 16, tsrc + c * 8);
+                    gqtc::mbar_arrive(&full[st]);            // orders the zero stores
+                    gqtc::mbar_arrive_cp_async(&full[st]);   // fires when this thread's copies have landed
+                }
+                s = sn;
+                d = dn;
+            }
+            if (ok) ok = gqtc::mbar_wait_abortable(&accfull, (uint32_t)(it & 1), kWaitNs, &abort_flag);
+            // tcgen05.ld is warp-collective: the warp decides together
+            if (__all_sync(0xffffffffu, ok)) {
+                gqtc::fence_after_sync();
+                long long shi[kTcN], slo[kTcN];
+#pragma unroll
+                for (int n = 0; n < kTcN; ++n) shi[n] = slo[n] = 0;
+                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+                for (int w = 0; w < kTcLev; ++w) {
+                    uint32_t v[32];
+                    gqtc::tmem_ld32(lane_base + (uint32_t)(w * 32), v);
+                    gqtc::tmem_ld_wait();
+                    if (w <= 5) {
+                        const int sh = 5 * (5 - w);
+#pragma unroll
+                        for (int n = 0; n < kTcN; ++n) shi[n] += (long long)__float2int_rn(__uint_as_float(v[n])) << sh;
+                    } else {
+                        const int sh = 5 * (11 - w);
+#pragma unroll
+                        for (int n = 0; n < kTcN; ++n) slo[n] += (long long)__float2int_rn(__uint_as_float(v[n])) << sh;
+                    }
+                }
+                gqtc::fence_before_sync();
+                gqtc::mbar_arrive(&accfree);   // the accumulators may be overwritten now
+                const int b = a.tile_box[row];
+                if (b >= 0) {
+                    const int l = a.blev[b];
+                    const int E = a.lexp[l] - 1022;   // |M| < 2^E at this level
+                    const int P1 = a.P + 1;
+                    double2 *Lb = a.L + (size_t)b * P1;
+                    double m0 = 0.0;                   // sum of M_0 over the List 2 boxes (the log rho term)
+                    for (int e = a.voff[b]; e < a.voff[b + 1]; ++e) m0 += a.M[(size_t)a.vidx[e] * P1].x;
+                    const double logrho = a.logH - l * a.ln2;
+#pragma unroll
+                    for (int n = 0; n < kTcN; ++n) {
+                        const int m = n >> 1;
+                        if (m > a.P) continue;
+                        const int F = a.fexp[n];
+                        // value = 2^(E+F-108) sum_w acc_w 2^(5 (20 - w)) = 2^(E+F-33) shi + 2^(E+F-63) slo
+                        double v = fma((double)shi[n], ldexp(1.0, E + F - 33), (double)slo[n] * ldexp(1.0, E + F - 63));
+                        if (n == 0) v += m0 * logrho;
+                        if (n & 1) Lb[m].y += v;
+                        else Lb[m].x += v;
+                    }
+                }
+            } else if (!ok) {
+                abort_flag = 1;
+            }
+        }
+    }
+    // a role that gave up has set abort_flag; wait for this thread's copies before leaving
+    cp_async_wait_all();
+    if (abort_flag && tid == 0) atomicExch(a.err, 1);
+    gqtc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) gqtc::tmem_free(tmem, 512);
+}
+
+// ---------------------------------------------------------------- constant tables
+struct TcConst {
+    uint16_t *tdig = nullptr;   // [121 offsets][11 digits][32 x 32 tile order]
+    int *fexp = nullptr;        // [32]
+};
+
+void host_tc_tables(std::vector<uint16_t> &tdig, std::vector<int> &fexp) {
+    const int P1 = 16;
+    std::vector<long double> C(64 * 64, 0.0L);
+    for (int n = 0; n < 64; ++n) {
+        C[n * 64] = 1.0L;
+        for (int k = 1; k <= n; ++k) C[n * 64 + k] = C[(n - 1) * 64 + k - 1] + (k <= n - 1 ? C[(n - 1) * 64 + k] : 0.0L);
+    }
+    // real-form matrices B[off][n][kk]: n = 2m + c', kk = 2k + c
+    std::vector<long double> B((size_t)121 * 32 * 32, 0.0L);
+    for (int ty = -5; ty <= 5; ++ty)
+        for (int tx = -5; tx <= 5; ++tx) {
+            const int off = (ty + 5) * 11 + (tx + 5);
+            if (tx >= -2 && tx <= 2 && ty >= -2 && ty <= 2) continue;   // never a List 2 offset
+            long double dr = 2.0L * tx, di = 2.0L * ty, n2 = dr * dr + di * di;
+            long double ir = dr / n2, ii = -di / n2;   // 1 / delta
+            std::vector<long double> pr(2 * P1 + 1), pi(2 * P1 + 1);   // delta^-j
+            pr[0] = 1.0L;
+            pi[0] = 0.0L;
+            for (int j = 1; j <= 2 * P1; ++j) {
+                pr[j] = pr[j - 1] * ir - pi[j - 1] * ii;
+                pi[j] = pr[j - 1] * ii + pi[j - 1] * ir;
+            }
+            for (int m = 0; m < P1; ++m)
+                for (int k = 0; k < P1; ++k) {
+                    long double tr, ti;
+                    if (m == 0 && k == 0) {
+                        tr = 0.5L * logl(n2);
+                        ti = 0.0L;
+                    } else if (m == 0) {
+                        tr = pr[k];
+                        ti = pi[k];
+                    } else if (k == 0) {
+                        long double s = ((m & 1) ? 1.0L : -1.0L) / m;   // -(-1)^m / m
+                        tr = s * pr[m];
+                        ti = s * pi[m];
+                    } else {
+                        long double s = ((m & 1) ? -1.0L : 1.0L) * C[(m + k - 1) * 64 + (k - 1)];
+                        tr = s * pr[m + k];
+                        ti = s * pi[m + k];
+                    }
+                    long double *Bo = &B[(size_t)off * 1024];
+                    Bo[(2 * m) * 32 + 2 * k] = tr;
+                    Bo[(2 * m) * 32 + 2 * k + 1] = -ti;
+                    Bo[(2 * m + 1) * 32 + 2 * k] = ti;
+                    Bo[(2 * m + 1) * 32 + 2 * k + 1] = tr;
+                }
+        }
+    fexp.assign(32, -1074);
+    for (int n = 0; n < 32; ++n) {
+        long double mx = 0.0L;
+        for (int off = 0; off < 121; ++off)
+            for (int kk = 0; kk < 32; ++kk) mx = fmaxl(mx, fabsl(B[(size_t)off * 1024 + n * 32 + kk]));
+        int e = 0;
+        frexpl(mx, &e);   // mx < 2^e
+        fexp[n] = e;
+    }
+    tdig.assign((size_t)121 * kTcND * 1024, 0);
+    for (int off = 0; off < 121; ++off)
+        for (int n = 0; n < 32; ++n)
+            for (int kk = 0; kk < 32; ++kk) {
+                long double v = B[(size_t)off * 1024 + n * 32 + kk];
+                long long X = llroundl(ldexpl(v, kTcBits - fexp[n]));
+                int d[kTcND];
+                tc_digits(X, d);
+                GQ_REQUIRE(d[0] >= -16 && d[0] <= 16, GQ_ERR_CUDA, "tensor-core M2L: translation digit out of range");
+                const uint32_t o = gqtc::tile_offset(n, kk, 32) / 2;
+                for (int j = 0; j < kTcND; ++j) tdig[((size_t)off * kTcND + j) * 1024 + o] = bf16_of_small_int(d[j]);
+            }
+}
+
+const TcConst &tc_const(int dev) {
+    static std::mutex mu;
+    static TcConst per_dev[64];
+    static bool ready[64] = {};
+    GQ_REQUIRE(dev >= 0 && dev < 64, GQ_ERR_UNSUPPORTED, "device index >= 64");
+    std::lock_guard<std::mutex> lk(mu);
+    if (ready[dev]) return per_dev[dev];
+    std::vector<uint16_t> tdig;
+    std::vector<int> fexp;
+    host_tc_tables(tdig, fexp);
+    int cur = 0;
+    GQ_CUDA(cudaGetDevice(&cur));
+    GQ_CUDA(cudaSetDevice(dev));
+    TcConst T;
+    GQ_CUDA(cudaMalloc(&T.tdig, sizeof(uint16_t) * tdig.size()));
+    GQ_CUDA(cudaMalloc(&T.fexp, sizeof(int) * fexp.size()));
+    GQ_CUDA(cudaMemcpy(T.tdig, tdig.data(), sizeof(uint16_t) * tdig.size(), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaMemcpy(T.fexp, fexp.data(), sizeof(int) * fexp.size(), cudaMemcpyHostToDevice));
+    GQ_CUDA(cudaSetDevice(cur));
+    per_dev[dev] = T;
+    ready[dev] = true;
+    return per_dev[dev];
+}
+
+}  // namespace
+
+bool gq_m2l_tc_supported(const gq_geom *g) { return g->prm.p_fmm <= 15 && g->prm.m2l == GQ_M2L_AUTO; }
+
+// Tiles of the current build (once per build; synchronises the stream):
+// per quadrant, the target boxes with a nonempty List 2 sorted by their slot
+// pattern, 128 per tile.
+void gq_m2l_tc_build(gq_geom *g) {
+    gq_ctx *ctx = g->ctx;
+    cudaStream_t st = ctx->stream;
+    const int nbox = g->nbox;
+    dbuf<int> flag, tmp;
+    dbuf<int> posq[4];
+    flag.alloc(nbox);
+    tmp.alloc(gq_scan_tmp_size(nbox));
+    int cnt[4], row0[4], total_rows = 0;
+    for (int q = 0; q < 4; ++q) {
+        posq[q].alloc((size_t)nbox + 1);
+        GQ_LAUNCH(ctx, k_tc_flags, gq_blocks(nbox, 256), 256, 0, nbox, q, (const int *)g->list_off[1].p,
+                  (const int *)g->bix.p, (const int *)g->biy.p, flag.p);
+        gq_exclusive_scan(ctx, flag.p, posq[q].p, nbox, tmp.p);
+        GQ_CUDA(cudaMemcpyAsync(&cnt[q], posq[q].p + nbox, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    GQ_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < 4; ++q) {
+        row0[q] = total_rows;
+        total_rows += (cnt[q] + kTcRows - 1) / kTcRows * kTcRows;
+    }
+    g->tc_ntiles = total_rows / kTcRows;
+    g->tc_tile_box.alloc((size_t)total_rows);
+    g->tc_slot_src.alloc((size_t)total_rows * kTcSlots);
+    g->tc_tile_mask.alloc((size_t)g->tc_ntiles * 4);
+    g->tc_tile_q.alloc((size_t)g->tc_ntiles);
+    g->tc_err.alloc(1);
+    if (total_rows) {
+        GQ_CUDA(cudaMemsetAsync(g->tc_tile_box.p, 0xff, sizeof(int) * total_rows, st));
+        GQ_CUDA(cudaMemsetAsync(g->tc_slot_src.p, 0xff, sizeof(int) * (size_t)total_rows * kTcSlots, st));
+        GQ_CUDA(cudaMemsetAsync(g->tc_tile_mask.p, 0, sizeof(unsigned) * g->tc_ntiles * 4, st));
+    }
+    GQ_CUDA(cudaMemsetAsync(g->tc_err.p, 0, sizeof(int), st));
+    std::vector<int> tq(g->tc_ntiles);
+    dbuf<uint64_t> key;
+    dbuf<int> val;
+    for (int q = 0; q < 4; ++q) {
+        for (int t = row0[q] / kTcRows; t < (row0[q] + (cnt[q] + kTcRows - 1) / kTcRows * kTcRows) / kTcRows; ++t)
+            tq[t] = q;
+        if (!cnt[q]) continue;
+        key.alloc(cnt[q]);
+        val.alloc(cnt[q]);
+        GQ_LAUNCH(ctx, k_tc_flags, gq_blocks(nbox, 256), 256, 0, nbox, q, (const int *)g->list_off[1].p,
+                  (const int *)g->bix.p, (const int *)g->biy.p, flag.p);
+        GQ_LAUNCH(ctx, k_tc_keys, gq_blocks(nbox, 256), 256, 0, nbox, q, (const int *)flag.p, (const int *)posq[q].p,
+                  (const int *)g->list_off[1].p, (const int *)g->list_idx[1].p, (const int *)g->bix.p,
+                  (const int *)g->biy.p, key.p, val.p, g->tc_err.p);
+        gq_radix_sort_pairs(ctx, key.p, val.p, cnt[q], 64);
+        GQ_LAUNCH(ctx, k_tc_fill, gq_blocks(cnt[q], 256), 256, 0, cnt[q], row0[q], (const int *)val.p, q,
+                  (const int *)g->list_off[1].p, (const int *)g->list_idx[1].p, (const int *)g->bix.p,
+                  (const int *)g->biy.p, g->tc_tile_box.p, g->tc_slot_src.p, g->tc_tile_mask.p);
+    }
+    if (g->tc_ntiles)
+        GQ_CUDA(cudaMemcpyAsync(g->tc_tile_q.p, tq.data(), sizeof(int) * g->tc_ntiles, cudaMemcpyHostToDevice, st));
+    int herr = 0;
+    GQ_CUDA(cudaMemcpyAsync(&herr, g->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GQ_CUDA(cudaStreamSynchronize(st));
+    GQ_REQUIRE(herr == 0, GQ_ERR_UNSUPPORTED, "tensor-core M2L: a List 2 entry outside the 10 x 10 offset window");
+    g->tc_ready = true;
+}
+
+// M2L of the current multipoles M into L (added) on the tensor cores.
+void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L) {
+    gq_ctx *ctx = g->ctx;
+    if (!g->tc_ready) gq_m2l_tc_build(g);
+    if (g->tc_ntiles == 0) return;
+    const TcConst &T = tc_const(ctx->device);
+    const int nbox = g->nbox, P = g->prm.p_fmm;
+    g->tc_bexp.alloc(nbox);
+    g->tc_lexp.alloc(g->nlev);
+    g->tc_mdig.alloc((size_t)nbox * kTcND * kTcK);
+    GQ_LAUNCH(ctx, k_tc_boxexp, gq_blocks((long long)nbox * 32, 256), 256, 0, nbox, P, M, g->tc_bexp.p);
+    GQ_LAUNCH(ctx, k_tc_levexp, g->nlev, 256, 0, (const int *)g->level_start.p, (const int *)g->tc_bexp.p,
+              g->tc_lexp.p);
+    GQ_LAUNCH(ctx, k_tc_digits, gq_blocks((long long)nbox * 32, 256), 256, 0, nbox, P, (const int *)g->blev.p,
+              (const int *)g->tc_lexp.p, M, g->tc_mdig.p);
+    TcArgs a;
+    a.ntiles = g->tc_ntiles;
+    a.P = P;
+    a.tile_box = g->tc_tile_box;
+    a.tile_q = g->tc_tile_q;
+    a.slot_src = g->tc_slot_src;
+    a.tile_mask = g->tc_tile_mask;
+    a.mdig = g->tc_mdig;
+    a.tdig = T.tdig;
+    a.fexp = T.fexp;
+    a.lexp = g->tc_lexp;
+    a.blev = g->blev;
+    a.voff = g->list_off[1];
+    a.vidx = g->list_idx[1];
+    a.M = M;
+    a.L = L;
+    a.logH = log(g->root.H);
+    a.ln2 = log(2.0);
+    a.err = g->tc_err;
+    static bool attr_set[64] = {};
+    int dev = ctx->device;
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        GQ_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * kStage)));
+        attr_set[dev] = true;
+    }
+    int sms = 0;
+    GQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int grid = g->tc_ntiles < sms ? g->tc_ntiles : sms;
+    GQ_LAUNCH(ctx, k_m2l_tc, grid, kTcThreads, 2 * kStage, a);
+}
+
+// nonzero when a tensor-core M2L wait gave up (reads the device flag; synchronises)
+int gq_m2l_tc_error(gq_geom *g) {
+    if (!g->tc_ready || !g->tc_err.p) return 0;
+    int h = 0;
+    GQ_CUDA(cudaMemcpyAsync(&h, g->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, g->ctx->stream));
+    GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
+    return h;
+}

@@ -3,6 +3,7 @@
 #include "gq_internal.cuh"
 #include "gq_dfl.cuh"
 #include "gq_math.cuh"
+#include "gq_tc.cuh"
 
 namespace {
 
@@ -171,6 +172,63 @@ double run_fma_dmma(gq_ctx *ctx) {
     return best;
 }
 
+
+// ---------------------------------------------------------------- tensor-core check
+// One CTA of 128 threads: D[128][32] = A[128][K] * B[32][K]^T with BF16 A and
+// B (given as raw bit patterns) and FP32 accumulation in tensor memory, by
+// K/16 chained tcgen05.mma of shape 128 x 32 x 16.  Used to check the
+// descriptor encodings and that integer-valued products accumulate exactly
+// (the precondition of the split-digit FP64 emulation).  lbo_sbo_swap = 1
+// exchanges the two byte offsets of the shared-memory descriptors (both
+// choices address only inside the staged tiles).  *err = 1 if the
+// completion wait gave up.
+__global__ void __launch_bounds__(128) k_umma_probe(const uint16_t *__restrict__ A, const uint16_t *__restrict__ B,
+                                                    int K, int lbo_sbo_swap, float *__restrict__ D,
+                                                    int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    unsigned char *sa = sm;                         // 128 x K
+    unsigned char *sb = sm + (size_t)128 * K * 2;   // 32 x K
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) gqtc::tmem_alloc(&tslot, 32);
+    if (tid == 0) gqtc::mbar_init(&bar, 1);
+    for (int i = tid; i < 128 * K; i += 128)
+        *(uint16_t *)(sa + gqtc::tile_offset(i / K, i % K, K)) = A[i];
+    for (int i = tid; i < 32 * K; i += 128)
+        *(uint16_t *)(sb + gqtc::tile_offset(i / K, i % K, K)) = B[i];
+    gqtc::fence_smem_to_async();
+    gqtc::fence_before_sync();
+    __syncthreads();
+    gqtc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    if (tid == 0) {
+        const uint32_t idesc = gqtc::idesc_bf16_f32(128, 32);
+        const uint32_t kstride = (uint32_t)(K / 8) * 128;
+        const uint32_t lbo = lbo_sbo_swap ? kstride : 128u, sbo = lbo_sbo_swap ? 128u : kstride;
+        for (int ks = 0; ks < K / 16; ++ks) {
+            uint64_t ad = gqtc::smem_desc(gqtc::smem_u32(sa) + ks * 256, lbo, sbo);
+            uint64_t bd = gqtc::smem_desc(gqtc::smem_u32(sb) + ks * 256, lbo, sbo);
+            gqtc::mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+        }
+        gqtc::mma_commit(&bar);
+    }
+    bool ok = gqtc::mbar_wait(&bar, 0, 2000000000ull);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && (tid & 31) == 0) atomicExch(err, 1);
+    gqtc::fence_after_sync();
+    if (ok) {
+        uint32_t v[32];
+        gqtc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+        gqtc::tmem_ld_wait();
+        const int row = warp * 32 + (tid & 31);
+        for (int j = 0; j < 32; ++j) D[row * 32 + j] = __uint_as_float(v[j]);
+    }
+    gqtc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) gqtc::tmem_free(tmem, 32);
+}
+
 }  // namespace
 
 double gq_probe_fma(gq_ctx *ctx, int what) {
@@ -205,3 +263,27 @@ void gq_probe_math_impl(gq_ctx *ctx, int fn, int n, const double *x_dev, double 
     GQ_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
+
+void gq_probe_umma_impl(gq_ctx *ctx, int K, const uint16_t *A_host, const uint16_t *B_host, int swap, float *D_host) {
+    GQ_REQUIRE(K >= 16 && K <= 256 && K % 16 == 0, GQ_ERR_INVALID, "gq_probe_umma: K must be a multiple of 16 in [16, 256]");
+    dbuf<uint16_t> a, b;
+    dbuf<float> d;
+    dbuf<int> err;
+    a.alloc((size_t)128 * K);
+    b.alloc((size_t)32 * K);
+    d.alloc(128 * 32);
+    err.alloc(1);
+    cudaStream_t st = ctx->stream;
+    GQ_CUDA(cudaMemcpyAsync(a.p, A_host, sizeof(uint16_t) * 128 * K, cudaMemcpyHostToDevice, st));
+    GQ_CUDA(cudaMemcpyAsync(b.p, B_host, sizeof(uint16_t) * 32 * K, cudaMemcpyHostToDevice, st));
+    GQ_CUDA(cudaMemsetAsync(d.p, 0, sizeof(float) * 128 * 32, st));
+    GQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    size_t smem = (size_t)160 * K * 2;
+    GQ_CUDA(cudaFuncSetAttribute(k_umma_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GQ_LAUNCH(ctx, k_umma_probe, 1, 128, smem, (const uint16_t *)a.p, (const uint16_t *)b.p, K, swap, d.p, err.p);
+    int herr = 0;
+    GQ_CUDA(cudaMemcpyAsync(D_host, d.p, sizeof(float) * 128 * 32, cudaMemcpyDeviceToHost, st));
+    GQ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GQ_CUDA(cudaStreamSynchronize(st));
+    GQ_REQUIRE(herr == 0, GQ_ERR_TIMEOUT, "gq_probe_umma: tensor-core completion wait gave up");
+}
