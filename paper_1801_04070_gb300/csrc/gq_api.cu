@@ -298,7 +298,11 @@ gq_status gq_eval(gq_geom *g, int kernel, const double *density_base, double *ou
         if (!out_dev && g->nt) {
             GQ_CUDA(cudaMemcpyAsync(out, o, sizeof(double) * g->nt, cudaMemcpyDefault, st));
             GQ_CUDA(cudaStreamSynchronize(st));
-            GQ_REQUIRE(gq_m2l_tc_error(g) == 0, GQ_ERR_TIMEOUT, "tensor-core M2L: a bounded wait gave up");
+            {
+            int tce = gq_m2l_tc_error(g);
+            GQ_REQUIRE(tce != 2, GQ_ERR_UNSUPPORTED, "tensor-core M2L: a List 2 entry outside the offset window");
+            GQ_REQUIRE(tce == 0, GQ_ERR_TIMEOUT, "tensor-core M2L: a bounded wait gave up");
+        }
         }
     });
 }

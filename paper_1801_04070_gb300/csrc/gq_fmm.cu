@@ -2519,7 +2519,11 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     ctx->launches += ctx2.launches;
     if (timed) {
         GQ_CUDA(cudaEventSynchronize(ev[S_END]));
-        GQ_REQUIRE(gq_m2l_tc_error(g) == 0, GQ_ERR_TIMEOUT, "tensor-core M2L: a bounded wait gave up");
+        {
+            int tce = gq_m2l_tc_error(g);
+            GQ_REQUIRE(tce != 2, GQ_ERR_UNSUPPORTED, "tensor-core M2L: a List 2 entry outside the offset window");
+            GQ_REQUIRE(tce == 0, GQ_ERR_TIMEOUT, "tensor-core M2L: a bounded wait gave up");
+        }
         auto el = [&](int a, int b2) {
             float ms = 0;
             GQ_CUDA(cudaEventElapsedTime(&ms, ev[a], ev[b2]));

@@ -183,8 +183,7 @@ struct gq_geom {
     dbuf<float4> lvl2;    // per level: (rho, 1/rho), (log rho, 1/rho^2)
     // tensor-core M2L (gq_m2l_tc.cu): tiles of the current build, multipole digits
     bool tc_ready = false;
-    int tc_ntiles = 0;
-    dbuf<int> tc_tile_box, tc_slot_src, tc_tile_q, tc_err, tc_bexp, tc_lexp;
+    dbuf<int> tc_tile_box, tc_slot_src, tc_tile_q, tc_err, tc_bexp, tc_lexp, tc_counter, tc_ntiles_dev, tc_cnt;
     dbuf<unsigned> tc_tile_mask;
     dbuf<uint16_t> tc_mdig;
 };

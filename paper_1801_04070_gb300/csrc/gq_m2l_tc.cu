@@ -143,30 +143,30 @@ __global__ void k_tc_digits(int nbox, int P, const int *__restrict__ blev, const
 }
 
 // ---------------------------------------------------------------- per-build: tiles
-__global__ void k_tc_flags(int nbox, int q, const int *__restrict__ voff, const int *__restrict__ bix,
-                           const int *__restrict__ biy, int *__restrict__ flag) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbox) return;
-    flag[b] = voff[b + 1] > voff[b] && ((bix[b] & 1) | ((biy[b] & 1) << 1)) == q;
-}
-
 // window slot of List 2 box d seen from b (quadrant q), or -1 outside the window
 __device__ __forceinline__ int tc_slot(int q, int bx, int by, int dx_, int dy_) {
     int sx = dx_ - bx + 4 + (q & 1), sy = dy_ - by + 4 + (q >> 1);
     return (sx < 0 || sx > 9 || sy < 0 || sy > 9) ? -1 : sy * 10 + sx;
 }
 
-// Sort key of a target box: which of the quadrant's first 64 List 2 window
-// slots (row-major, the 5 x 5 block of the box's 2-colleagues skipped) it
-// uses.  Boxes with similar keys share slots, so sorted tiles touch fewer.
-__global__ void k_tc_keys(int nbox, int q, const int *__restrict__ flag, const int *__restrict__ pos,
-                          const int *__restrict__ voff, const int *__restrict__ vidx, const int *__restrict__ bix,
-                          const int *__restrict__ biy, uint64_t *__restrict__ key, int *__restrict__ val,
-                          int *__restrict__ err) {
+constexpr uint32_t kNoTile = 0xffffffffu;
+
+// Sort key of every box: quadrant in bits 30-31, then which of the quadrant's
+// first 29 List 2 window slots (row-major, the 5 x 5 block of the box's
+// 2-colleagues skipped) it uses; boxes without List 2 get kNoTile (sorted
+// last).  Boxes with similar keys share slots, so sorted tiles touch fewer.
+__global__ void k_tc_keys(int nbox, const int *__restrict__ voff, const int *__restrict__ vidx,
+                          const int *__restrict__ bix, const int *__restrict__ biy, uint32_t *__restrict__ key,
+                          int *__restrict__ val, int *__restrict__ cnt, int *__restrict__ err) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbox || !flag[b]) return;
-    const int qx = q & 1, qy = q >> 1;
-    uint64_t k = 0;
+    if (b >= nbox) return;
+    val[b] = b;
+    if (voff[b + 1] == voff[b]) {
+        key[b] = kNoTile;
+        return;
+    }
+    const int q = (bix[b] & 1) | ((biy[b] & 1) << 1), qx = q & 1, qy = q >> 1;
+    uint32_t k = 0;
     for (int e = voff[b]; e < voff[b + 1]; ++e) {
         int d = vidx[e];
         int s = tc_slot(q, bix[b], biy[b], bix[d], biy[d]);
@@ -175,36 +175,49 @@ __global__ void k_tc_keys(int nbox, int q, const int *__restrict__ flag, const i
             continue;
         }
         int sx = s % 10, sy = s / 10;
-        // valid-slot index: inner 5 x 5 block at columns/rows [2 + q., 6 + q.]
         int rows_inner = min(max(sy - (2 + qy), 0), 5);
         int in_row = (sy >= 2 + qy && sy <= 6 + qy) ? min(max(sx - (2 + qx), 0), 5) : 0;
-        int c = s - 5 * rows_inner - in_row;
-        if (c < 64) k |= 1ull << (63 - c);
+        int c = s - 5 * rows_inner - in_row;   // index among the quadrant's valid slots
+        if (c < 29) k |= 1u << (28 - c);   // bit 29 stays clear: no key equals kNoTile
     }
-    key[pos[b]] = k;
-    val[pos[b]] = b;
+    key[b] = ((uint32_t)q << 30) | k;
+    atomicAdd(&cnt[q], 1);
 }
 
-__global__ void k_tc_fill(int n, int row0, const int *__restrict__ sorted_box, int q, const int *__restrict__ voff,
-                          const int *__restrict__ vidx, const int *__restrict__ bix, const int *__restrict__ biy,
-                          int *__restrict__ tile_box, int *__restrict__ slot_src, unsigned *__restrict__ tile_mask) {
+// Rows in sorted order; each quadrant starts a new tile (padded to 128 rows).
+__global__ void k_tc_fill(int nbox, const uint32_t *__restrict__ key, const int *__restrict__ sorted_box,
+                          const int *__restrict__ cnt, const int *__restrict__ voff, const int *__restrict__ vidx,
+                          const int *__restrict__ bix, const int *__restrict__ biy, int *__restrict__ tile_box,
+                          int *__restrict__ tile_q, int *__restrict__ slot_src, unsigned *__restrict__ tile_mask,
+                          int *__restrict__ ntiles) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int b = sorted_box[i];
-    int row = row0 + i;
+    int start[4], row0[4], rows = 0, seen = 0;
+    for (int q = 0; q < 4; ++q) {
+        start[q] = seen;
+        row0[q] = rows;
+        seen += cnt[q];
+        rows += (cnt[q] + kTcRows - 1) / kTcRows * kTcRows;
+    }
+    if (i == 0) *ntiles = rows / kTcRows;
+    if (i >= nbox || key[i] == kNoTile) return;
+    const int q = (int)(key[i] >> 30);
+    const int b = sorted_box[i];
+    const int row = row0[q] + (i - start[q]), tile = row / kTcRows;
     tile_box[row] = b;
+    tile_q[tile] = q;
     for (int e = voff[b]; e < voff[b + 1]; ++e) {
         int d = vidx[e];
         int s = tc_slot(q, bix[b], biy[b], bix[d], biy[d]);
         if (s < 0) continue;   // reported by k_tc_keys
-        slot_src[(size_t)row * kTcSlots + s] = d;
-        atomicOr(&tile_mask[(row / kTcRows) * 4 + (s >> 5)], 1u << (s & 31));
+        slot_src[((size_t)tile * kTcSlots + s) * kTcRows + (row % kTcRows)] = d;
+        atomicOr(&tile_mask[tile * 4 + (s >> 5)], 1u << (s & 31));
     }
 }
 
 // ---------------------------------------------------------------- the tensor-core M2L
 struct TcArgs {
-    int ntiles, P;
+    const int *ntiles;   // device: number of tiles of the current build
+    int P;
     const int *tile_box, *tile_q, *slot_src;
     const unsigned *tile_mask;
     const uint16_t *mdig, *tdig;
@@ -215,6 +228,7 @@ struct TcArgs {
     double2 *L;
     double logH, ln2;    // log rho_l = logH - l log 2
     int *err;
+    int *next_tile;      // dynamic tile counter (zero at launch)
 };
 
 constexpr int kTcThreads = 160;   // warps 0-3: staging and epilogue (row = thread), warp 4: MMA issue
@@ -231,6 +245,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     __shared__ uint32_t tslot;
     __shared__ unsigned smask[2][4];
     __shared__ int sq[2];
+    __shared__ int stile[2];
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5;
     if (warp == 0) gqtc::tmem_alloc(&tslot, 512);
@@ -250,11 +265,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     const uint32_t sbase = gqtc::smem_u32(sm);
     int it = 0;       // tiles done by this CTA
     uint32_t g = 0;   // slots staged / consumed so far (both roles count the same slots)
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+    bool zero_row[2] = {false, false};   // staging: this thread's row of stage s holds zeros
+    for (;; ++it) {
+        // tiles are taken from a shared counter (their slot counts differ), one
+        // per CTA at a time; every thread passes the barrier below once per
+        // tile, and a wait that gave up (abort_flag) ends the loop for all
+        if (tid == 0) stile[it & 1] = atomicAdd(a.next_tile, 1);
+        __syncthreads();
+        const int tile = stile[it & 1];
+        if (tile >= *a.ntiles) break;
         if (tid < 4) smask[it & 1][tid] = a.tile_mask[tile * 4 + tid];
         if (tid == 4) sq[it & 1] = a.tile_q[tile];
-        // every thread passes this barrier once per tile; a wait that gave up
-        // (abort_flag) ends the loop for all of them together
         if (__syncthreads_or(abort_flag)) break;
         const unsigned *mask = smask[it & 1];
         if (warp == 4) {
@@ -310,31 +331,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             const uint32_t rowoff = (uint32_t)(((tid >> 3) * 4) << 7) + (uint32_t)((tid & 7) << 4);
             const int qx = sq[it & 1] & 1, qy = sq[it & 1] >> 1;
             bool ok = true;
+            // slot sources of this tile, [slot][row]: a warp's loads are contiguous;
+            // prefetched two slots ahead
+            const int *ssrc = a.slot_src + (size_t)tile * kTcSlots * kTcRows + tid;
             int s = next_slot(mask, -1);
-            int d = s < kTcSlots ? a.slot_src[row * kTcSlots + s] : -1;
+            int s1 = next_slot(mask, s);
+            int d = s < kTcSlots ? ssrc[s * kTcRows] : -1;
+            int d1 = s1 < kTcSlots ? ssrc[s1 * kTcRows] : -1;
             for (; s < kTcSlots; ++g) {
-                const int sn = next_slot(mask, s);
-                const int dn = sn < kTcSlots ? a.slot_src[row * kTcSlots + sn] : -1;   // prefetch
+                const int s2 = next_slot(mask, s1);
+                const int d2 = s2 < kTcSlots ? ssrc[s2 * kTcRows] : -1;
                 const int st = g & 1;
                 if (ok && g >= 2) ok = gqtc::mbar_wait_abortable(&empty[st], ((g >> 1) - 1) & 1, kWaitNs, &abort_flag);
                 if (ok) {
                     const uint32_t sA = sbase + st * kStage, sB = sA + kTcND * kTileA;
+                    if (d >= 0 || !zero_row[st]) {   // a row already zero in this stage stays zero
 #pragma unroll
-                    for (int i = 0; i < kTcND; ++i)
+                        for (int i = 0; i < kTcND; ++i)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const uint32_t dst = sA + i * kTileA + rowoff + (c << 7);
-                            if (d >= 0) cp_async16(dst, a.mdig + ((size_t)d * kTcND + i) * kTcK + c * 8);
-                            else st_shared_zero16(dst);
-                        }
+                            for (int c = 0; c < 4; ++c) {
+                                const uint32_t dst = sA + i * kTileA + rowoff + (c << 7);
+                                if (d >= 0) cp_async16(dst, a.mdig + ((size_t)d * kTcND + i) * kTcK + c * 8);
+                                else st_shared_zero16(dst);
+                            }
+                        zero_row[st] = d < 0;
+                    }
                     const int dx = (s % 10) - 4 - qx, dy = (s / 10) - 4 - qy;
                     const uint16_t *tsrc = a.tdig + (size_t)((-dy + 5) * 11 + (-dx + 5)) * kTcND * (kTileB / 2);
                     for (int c = tid; c < (int)(kTcND * kTileB / 16); c += kTcRows) cp_async16(sB + c * 16, tsrc + c * 8);
                     gqtc::mbar_arrive(&full[st]);            // orders the zero stores
                     gqtc::mbar_arrive_cp_async(&full[st]);   // fires when this thread's copies have landed
                 }
-                s = sn;
-                d = dn;
+                s = s1;
+                s1 = s2;
+                d = d1;
+                d1 = d2;
             }
             if (ok) ok = gqtc::mbar_wait_abortable(&accfull, (uint32_t)(it & 1), kWaitNs, &abort_flag);
             // tcgen05.ld is warp-collective: the warp decides together
@@ -499,67 +530,38 @@ const TcConst &tc_const(int dev) {
 
 bool gq_m2l_tc_supported(const gq_geom *g) { return g->prm.p_fmm <= 15 && g->prm.m2l == GQ_M2L_AUTO; }
 
-// Tiles of the current build (once per build; synchronises the stream):
-// per quadrant, the target boxes with a nonempty List 2 sorted by their slot
-// pattern, 128 per tile.
+// Tiles of the current build: the target boxes with a nonempty List 2,
+// grouped by quadrant and sorted by slot pattern, 128 per tile.  Device work
+// only (no host read); the tile count stays on the device.
 void gq_m2l_tc_build(gq_geom *g) {
     gq_ctx *ctx = g->ctx;
     cudaStream_t st = ctx->stream;
     const int nbox = g->nbox;
-    dbuf<int> flag, tmp;
-    dbuf<int> posq[4];
-    flag.alloc(nbox);
-    tmp.alloc(gq_scan_tmp_size(nbox));
-    int cnt[4], row0[4], total_rows = 0;
-    for (int q = 0; q < 4; ++q) {
-        posq[q].alloc((size_t)nbox + 1);
-        GQ_LAUNCH(ctx, k_tc_flags, gq_blocks(nbox, 256), 256, 0, nbox, q, (const int *)g->list_off[1].p,
-                  (const int *)g->bix.p, (const int *)g->biy.p, flag.p);
-        gq_exclusive_scan(ctx, flag.p, posq[q].p, nbox, tmp.p);
-        GQ_CUDA(cudaMemcpyAsync(&cnt[q], posq[q].p + nbox, sizeof(int), cudaMemcpyDeviceToHost, st));
-    }
-    GQ_CUDA(cudaStreamSynchronize(st));
-    for (int q = 0; q < 4; ++q) {
-        row0[q] = total_rows;
-        total_rows += (cnt[q] + kTcRows - 1) / kTcRows * kTcRows;
-    }
-    g->tc_ntiles = total_rows / kTcRows;
-    g->tc_tile_box.alloc((size_t)total_rows);
-    g->tc_slot_src.alloc((size_t)total_rows * kTcSlots);
-    g->tc_tile_mask.alloc((size_t)g->tc_ntiles * 4);
-    g->tc_tile_q.alloc((size_t)g->tc_ntiles);
+    const size_t max_tiles = ((size_t)nbox + kTcRows - 1) / kTcRows + 4, max_rows = max_tiles * kTcRows;
+    g->tc_tile_box.alloc(max_rows);
+    g->tc_slot_src.alloc(max_rows * kTcSlots);
+    g->tc_tile_mask.alloc(max_tiles * 4);
+    g->tc_tile_q.alloc(max_tiles);
     g->tc_err.alloc(1);
-    if (total_rows) {
-        GQ_CUDA(cudaMemsetAsync(g->tc_tile_box.p, 0xff, sizeof(int) * total_rows, st));
-        GQ_CUDA(cudaMemsetAsync(g->tc_slot_src.p, 0xff, sizeof(int) * (size_t)total_rows * kTcSlots, st));
-        GQ_CUDA(cudaMemsetAsync(g->tc_tile_mask.p, 0, sizeof(unsigned) * g->tc_ntiles * 4, st));
-    }
-    GQ_CUDA(cudaMemsetAsync(g->tc_err.p, 0, sizeof(int), st));
-    std::vector<int> tq(g->tc_ntiles);
-    dbuf<uint64_t> key;
+    g->tc_ntiles_dev.alloc(1);
+    g->tc_cnt.alloc(4);
+    dbuf<uint32_t> key;
     dbuf<int> val;
-    for (int q = 0; q < 4; ++q) {
-        for (int t = row0[q] / kTcRows; t < (row0[q] + (cnt[q] + kTcRows - 1) / kTcRows * kTcRows) / kTcRows; ++t)
-            tq[t] = q;
-        if (!cnt[q]) continue;
-        key.alloc(cnt[q]);
-        val.alloc(cnt[q]);
-        GQ_LAUNCH(ctx, k_tc_flags, gq_blocks(nbox, 256), 256, 0, nbox, q, (const int *)g->list_off[1].p,
-                  (const int *)g->bix.p, (const int *)g->biy.p, flag.p);
-        GQ_LAUNCH(ctx, k_tc_keys, gq_blocks(nbox, 256), 256, 0, nbox, q, (const int *)flag.p, (const int *)posq[q].p,
-                  (const int *)g->list_off[1].p, (const int *)g->list_idx[1].p, (const int *)g->bix.p,
-                  (const int *)g->biy.p, key.p, val.p, g->tc_err.p);
-        gq_radix_sort_pairs(ctx, key.p, val.p, cnt[q], 64);
-        GQ_LAUNCH(ctx, k_tc_fill, gq_blocks(cnt[q], 256), 256, 0, cnt[q], row0[q], (const int *)val.p, q,
-                  (const int *)g->list_off[1].p, (const int *)g->list_idx[1].p, (const int *)g->bix.p,
-                  (const int *)g->biy.p, g->tc_tile_box.p, g->tc_slot_src.p, g->tc_tile_mask.p);
-    }
-    if (g->tc_ntiles)
-        GQ_CUDA(cudaMemcpyAsync(g->tc_tile_q.p, tq.data(), sizeof(int) * g->tc_ntiles, cudaMemcpyHostToDevice, st));
-    int herr = 0;
-    GQ_CUDA(cudaMemcpyAsync(&herr, g->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GQ_CUDA(cudaStreamSynchronize(st));
-    GQ_REQUIRE(herr == 0, GQ_ERR_UNSUPPORTED, "tensor-core M2L: a List 2 entry outside the 10 x 10 offset window");
+    key.alloc(nbox);
+    val.alloc(nbox);
+    GQ_CUDA(cudaMemsetAsync(g->tc_tile_box.p, 0xff, sizeof(int) * max_rows, st));
+    GQ_CUDA(cudaMemsetAsync(g->tc_slot_src.p, 0xff, sizeof(int) * max_rows * kTcSlots, st));
+    GQ_CUDA(cudaMemsetAsync(g->tc_tile_mask.p, 0, sizeof(unsigned) * max_tiles * 4, st));
+    GQ_CUDA(cudaMemsetAsync(g->tc_err.p, 0, sizeof(int), st));
+    GQ_CUDA(cudaMemsetAsync(g->tc_cnt.p, 0, sizeof(int) * 4, st));
+    GQ_LAUNCH(ctx, k_tc_keys, gq_blocks(nbox, 256), 256, 0, nbox, (const int *)g->list_off[1].p,
+              (const int *)g->list_idx[1].p, (const int *)g->bix.p, (const int *)g->biy.p, key.p, val.p, g->tc_cnt.p,
+              g->tc_err.p);
+    gq_radix_sort_pairs32(ctx, key.p, val.p, nbox, 32);
+    GQ_LAUNCH(ctx, k_tc_fill, gq_blocks(nbox, 256), 256, 0, nbox, (const uint32_t *)key.p, (const int *)val.p,
+              (const int *)g->tc_cnt.p, (const int *)g->list_off[1].p, (const int *)g->list_idx[1].p,
+              (const int *)g->bix.p, (const int *)g->biy.p, g->tc_tile_box.p, g->tc_tile_q.p, g->tc_slot_src.p,
+              g->tc_tile_mask.p, g->tc_ntiles_dev.p);
     g->tc_ready = true;
 }
 
@@ -567,7 +569,6 @@ void gq_m2l_tc_build(gq_geom *g) {
 void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L) {
     gq_ctx *ctx = g->ctx;
     if (!g->tc_ready) gq_m2l_tc_build(g);
-    if (g->tc_ntiles == 0) return;
     const TcConst &T = tc_const(ctx->device);
     const int nbox = g->nbox, P = g->prm.p_fmm;
     g->tc_bexp.alloc(nbox);
@@ -579,7 +580,7 @@ void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L) {
     GQ_LAUNCH(ctx, k_tc_digits, gq_blocks((long long)nbox * 32, 256), 256, 0, nbox, P, (const int *)g->blev.p,
               (const int *)g->tc_lexp.p, M, g->tc_mdig.p);
     TcArgs a;
-    a.ntiles = g->tc_ntiles;
+    a.ntiles = g->tc_ntiles_dev;
     a.P = P;
     a.tile_box = g->tc_tile_box;
     a.tile_q = g->tc_tile_q;
@@ -597,6 +598,9 @@ void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L) {
     a.logH = log(g->root.H);
     a.ln2 = log(2.0);
     a.err = g->tc_err;
+    g->tc_counter.alloc(1);
+    GQ_CUDA(cudaMemsetAsync(g->tc_counter.p, 0, sizeof(int), ctx->stream));
+    a.next_tile = g->tc_counter;
     static bool attr_set[64] = {};
     int dev = ctx->device;
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
@@ -605,11 +609,12 @@ void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L) {
     }
     int sms = 0;
     GQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int grid = g->tc_ntiles < sms ? g->tc_ntiles : sms;
+    int grid = sms;   // persistent: each CTA takes tiles from the counter until none is left
     GQ_LAUNCH(ctx, k_m2l_tc, grid, kTcThreads, 2 * kStage, a);
 }
 
-// nonzero when a tensor-core M2L wait gave up (reads the device flag; synchronises)
+// the device error flag of the tensor-core M2L (synchronises): 0 none, 1 a
+// bounded wait gave up, 2 a List 2 entry outside the offset window
 int gq_m2l_tc_error(gq_geom *g) {
     if (!g->tc_ready || !g->tc_err.p) return 0;
     int h = 0;
