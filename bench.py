@@ -189,7 +189,8 @@ def work_model(geo, p, q, kernel="S"):
         5: dict(name="k_near_centres", units=pairs_ctr, flops_per_unit=14 * q + 20, unit="(source, centre) pair"),
         6: dict(name="k_near_points", units=pairs_pt, flops_per_unit=10 + (LOG_FLOPS if kernel == "S" else 0),
                 unit="(source, point) pair"),
-        2: dict(name="k_m2l", units=v_pairs, flops_per_unit=8 * (p + 1) ** 2, unit="List 2 pair"),
+        2: dict(name="k_m2l_tc" if p <= 15 else "k_m2l", units=v_pairs, flops_per_unit=8 * (p + 1) ** 2,
+                unit="List 2 pair (FP64-equivalent flops of the translation)"),
         7: dict(name="k_w_centres", units=wf_ctr, flops_per_unit=8 * (p + 1) * (q + 1), unit="(List 3 far box, centre)"),
     }
 
@@ -500,11 +501,19 @@ def run_gpu(args, rank, world, local):
             if L.gq_probe_fma_peak(ctx, what, C.byref(v)) == 0:
                 others[name] = v.value
         per_kernel = {}
+        # FP64 instructions per unit measured by ncu (profiles/fp64_inst.json): the FP64 pipe
+        # issues one instruction per slot whatever its kind, at the measured FMA peak / 2
+        fi = os.path.join(ROOT, "profiles", "fp64_inst.json")
+        inst = json.load(open(fi)) if os.path.exists(fi) else {}
         for i, mm in model.items():
             a = mm["units"] * mm["flops_per_unit"] / (stage_ms[i] * 1e-3) / 1e12
             per_kernel[mm["name"]] = {"achieved": a, "frac": a / peak.value, "ms_per_launch": float(stage_ms[i]),
                                       "units_per_launch": mm["units"], "flops_per_unit": mm["flops_per_unit"],
                                       "unit_of_work": mm["unit"]}
+            if args.kernel == "S" and mm["name"] in inst:
+                rate = mm["units"] * inst[mm["name"]] / (stage_ms[i] * 1e-3) / 1e12
+                per_kernel[mm["name"]]["fp64_inst_per_unit"] = inst[mm["name"]]
+                per_kernel[mm["name"]]["fp64_issue_frac"] = rate / (peak.value / 2)
         roof = {"bound": "alu", "kernel": m["name"], "achieved": achieved, "peak": peak.value,
                 "unit": "TFLOP/s", "frac": achieved / peak.value, "traffic": traffic,
                 "peak_source": peak_src, "units_per_launch": m["units"], "unit_of_work": m["unit"],
