@@ -55,7 +55,7 @@ class _Params(C.Structure):
     _fields_ = [("p_qbx", C.c_int), ("p_fmm", C.c_int), ("n_max", C.c_int),
                 ("tf_num", C.c_int), ("tf_den", C.c_int), ("w3_demote", C.c_int),
                 ("max_level", C.c_int), ("radius_factor", C.c_double),
-                ("assoc_slack", C.c_double)]
+                ("assoc_slack", C.c_double), ("level_restrict", C.c_int)]
 
 
 def lib():
@@ -116,7 +116,7 @@ def _p(a):
 
 def default_params(g: dict | None = None, **kw) -> dict:
     p = dict(p_qbx=5, p_fmm=10, n_max=32, tf_num=9, tf_den=10, w3_demote=15,
-             max_level=30, radius_factor=0.5, assoc_slack=1.2)
+             max_level=30, radius_factor=0.5, assoc_slack=1.2, level_restrict=0)
     if g is not None:
         for k in ("p_qbx", "p_fmm", "n_max"):
             if k in g:
@@ -144,7 +144,8 @@ class Oracle:
                      _p(a["tgt_xy"]), _p(a["tgt_onsurf"]))
         pr = self.params
         prm = _Params(pr["p_qbx"], pr["p_fmm"], pr["n_max"], pr["tf_num"], pr["tf_den"],
-                      pr["w3_demote"], pr["max_level"], pr["radius_factor"], pr["assoc_slack"])
+                      pr["w3_demote"], pr["max_level"], pr["radius_factor"], pr["assoc_slack"],
+                      int(pr.get("level_restrict", 0)))
         self.h = self.L.orc_create(C.byref(geom), C.byref(prm))
         self.nt = len(a["tgt_xy"])
         self.nsrc = int(g["npanels"]) * int(g["nu"])

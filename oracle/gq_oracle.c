@@ -102,6 +102,9 @@ struct orc_state {
     int64_t *s_kx, *s_ky, *c_kx, *c_ky, *p_kx, *p_ky;
     /* tree */
     int nbox, capbox; obox *box;
+    /* level restriction: boxes subdivided regardless of their particle count,
+     * keys (level << 60) | morton(ix, iy), sorted */
+    uint64_t *forced; int nforced;
     int *src_owner, *ctr_owner, *pt_owner;
     /* lists */
     csr L[ORC_NLISTS], LB[ORC_NLISTS];
@@ -145,7 +148,7 @@ void orc_destroy(orc_state *s) {
     free(s->c_xy); free(s->c_r); free(s->c_lc); free(s->t_kind); free(s->t_ctr); free(s->pt_tgt); free(s->tgt_pt);
     free(s->s_kx); free(s->s_ky); free(s->c_kx); free(s->c_ky); free(s->p_kx); free(s->p_ky);
     for (int b = 0; b < s->nbox; ++b) { iv_free(&s->box[b].src); iv_free(&s->box[b].ctr); iv_free(&s->box[b].tgt); }
-    free(s->box); free(s->src_owner); free(s->ctr_owner); free(s->pt_owner);
+    free(s->box); free(s->src_owner); free(s->ctr_owner); free(s->pt_owner); free(s->forced);
     free_lists(s->L); free_lists(s->LB);
     free(s);
 }
@@ -326,6 +329,20 @@ static int quadrant(int64_t kx, int64_t ky, int child_level) {
     return (int)((kx >> sh) & 1) | (int)(((ky >> sh) & 1) << 1);
 }
 
+static uint64_t morton2(int64_t ix, int64_t iy) {
+    uint64_t k = 0;
+    for (int i = 0; i < KEYBITS; ++i) k |= (((uint64_t)ix >> i) & 1) << (2 * i) | (((uint64_t)iy >> i) & 1) << (2 * i + 1);
+    return k;
+}
+static uint64_t box_key(int level, int64_t ix, int64_t iy) { return ((uint64_t)level << 60) | morton2(ix, iy); }
+static int cmp_u64(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : x > y;
+}
+static int key_in(const uint64_t *keys, int n, uint64_t k) {
+    return n > 0 && bsearch(&k, keys, n, sizeof(uint64_t), cmp_u64) != NULL;
+}
+
 static void build_tree(orc_state *s) {
     new_box(s, 0, 0, 0, -1);
     for (int i = 0; i < s->nsrc; ++i) iv_push(&s->box[0].src, i);
@@ -338,7 +355,9 @@ static void build_tree(orc_state *s) {
             if (lev >= s->p.max_level) continue;
             int elig = s->box[b].src.n + s->box[b].tgt.n;
             for (int k = 0; k < s->box[b].ctr.n; ++k) if (s->c_lc[s->box[b].ctr.v[k]] > lev) elig++;
-            if (elig <= s->p.n_max) continue;
+            if (elig <= s->p.n_max &&
+                !(elig > 0 && key_in(s->forced, s->nforced, box_key(lev, s->box[b].ix, s->box[b].iy))))
+                continue;
             int cl = lev + 1;
             int cnt[4] = {0, 0, 0, 0};
             for (int k = 0; k < s->box[b].src.n; ++k) { int i = s->box[b].src.v[k]; cnt[quadrant(s->s_kx[i], s->s_ky[i], cl)]++; }
@@ -629,11 +648,72 @@ int orc_lists_bruteforce(orc_state *s) {
     return 0;
 }
 
+static void free_tree(orc_state *s) {
+    for (int b = 0; b < s->nbox; ++b) { iv_free(&s->box[b].src); iv_free(&s->box[b].ctr); iv_free(&s->box[b].tgt); }
+    free(s->box); s->box = NULL; s->nbox = s->capbox = 0;
+    free(s->src_owner); free(s->ctr_owner); free(s->pt_owner);
+    s->src_owner = s->ctr_owner = s->pt_owner = NULL;
+}
+
+/* Level restriction (Sec. 4.6, remark on level-restricted quadtrees: adjacent
+ * leaves' levels differ by at most one).  Reading: a leaf a at level l is in
+ * violation when some box at level l + 2 touches it (closed squares
+ * intersect; a deeper box touching a has such an ancestor).  A leaf in
+ * violation that owns a particle eligible for children (and l < max_level) is
+ * subdivided as in Stage 1 -- empty children pruned, centres moving only when
+ * their disk fits the child's TCR -- by rebuilding the tree from the root
+ * with the subdivision forced; repeat until no such leaf is left.  A leaf with
+ * no particle eligible for children cannot be refined and keeps its
+ * violation.  Candidates: the 20 level-(l+2) positions around a, looked up
+ * among the existing boxes. */
+static int balance_pass(orc_state *s) {
+    int maxl = 0;
+    for (int b = 0; b < s->nbox; ++b) if (s->box[b].level > maxl) maxl = s->box[b].level;
+    uint64_t *keys = malloc(sizeof(uint64_t) * (size_t)(s->nbox > 0 ? s->nbox : 1));
+    for (int b = 0; b < s->nbox; ++b) keys[b] = box_key(s->box[b].level, s->box[b].ix, s->box[b].iy);
+    qsort(keys, s->nbox, sizeof(uint64_t), cmp_u64);
+    int nnew = 0;
+    uint64_t *add = malloc(sizeof(uint64_t) * (size_t)(s->nbox > 0 ? s->nbox : 1));
+    for (int b = 0; b < s->nbox; ++b) {
+        const obox *B = &s->box[b];
+        int leaf = B->child[0] < 0 && B->child[1] < 0 && B->child[2] < 0 && B->child[3] < 0;
+        int l = B->level;
+        if (!leaf || l + 2 > maxl || l >= s->p.max_level) continue;
+        int elig = B->src.n + B->tgt.n;
+        for (int k = 0; k < B->ctr.n; ++k) if (s->c_lc[B->ctr.v[k]] > l) elig++;
+        if (elig == 0) continue;
+        int viol = 0;
+        int64_t n2 = (int64_t)1 << (l + 2);
+        for (int64_t Y = 4 * B->iy - 1; Y <= 4 * B->iy + 4 && !viol; ++Y)
+            for (int64_t X = 4 * B->ix - 1; X <= 4 * B->ix + 4 && !viol; ++X) {
+                if (X < 0 || Y < 0 || X >= n2 || Y >= n2) continue;
+                if (X >= 4 * B->ix && X < 4 * B->ix + 4 && Y >= 4 * B->iy && Y < 4 * B->iy + 4) continue;
+                if (GQ_ORC_MUT == 19 && (X < 4 * B->ix || X > 4 * B->ix + 3) && (Y < 4 * B->iy || Y > 4 * B->iy + 3))
+                    continue;   /* planted mistake: corner neighbours ignored */
+                if (key_in(keys, s->nbox, box_key(l + 2, X, Y))) viol = 1;
+            }
+        if (viol) add[nnew++] = box_key(l, B->ix, B->iy);
+    }
+    free(keys);
+    if (nnew) {
+        s->forced = realloc(s->forced, sizeof(uint64_t) * (s->nforced + nnew));
+        memcpy(s->forced + s->nforced, add, sizeof(uint64_t) * nnew);
+        s->nforced += nnew;
+        qsort(s->forced, s->nforced, sizeof(uint64_t), cmp_u64);
+    }
+    free(add);
+    return nnew;
+}
+
 int orc_build(orc_state *s) {
     form_centres(s);
     associate(s);
     root_and_keys(s);
     build_tree(s);
+    while (s->p.level_restrict && balance_pass(s) > 0) {
+        free_tree(s);
+        build_tree(s);
+    }
     build_lists_o2(s);
     return 0;
 }

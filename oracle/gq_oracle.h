@@ -48,6 +48,7 @@ typedef struct {
     int max_level;                /* <= 30 */
     double radius_factor;         /* expansion radius = radius_factor * panel length */
     double assoc_slack;           /* off-surface target joins a centre if |t-c|/r <= slack */
+    int level_restrict;           /* 1: balance the tree (Sec. 4.6, level-restriction remark) */
 } orc_params;
 
 enum { ORC_U = 0, ORC_V = 1, ORC_WC = 2, ORC_WF = 3, ORC_XC = 4, ORC_XF = 5, ORC_NLISTS = 6 };

@@ -43,6 +43,8 @@ CASES = {
          "test_oracle_math.py", "test_unit_circle_centres"),
     18: ("centre 2i on the exterior side, 2i+1 on the interior (Sec. 2.2.2 ordering)", "test_oracle_math.py",
          "test_unit_circle_centres"),
+    19: ("level restriction blind to boxes touching only at a corner (Sec. 4.6 remark)",
+         "test_oracle_level_restrict.py", "test_balanced_tree_has_no_violation"),
 }
 
 
