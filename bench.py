@@ -621,6 +621,58 @@ def run_gpu(args, rank, world, local):
                 L.gq_geometry_destroy(sg)
             sweep.append(row)
 
+    # ---- level-restricted tree (Sec. 4.6 remark): the same workload with the
+    # balanced tree; build and evaluation times, tree size and List 3 sizes of
+    # leaves against the plain tree
+    restricted = None
+    if args.sweep and rank == 0 and args.precision == 0:
+        def tree_stats(gh):
+            bx = gh.boxes()
+            Lh = gh.lists()
+            leaf = np.ones(len(bx["level"]), bool)
+            leaf[bx["parent"][bx["parent"] >= 0]] = False
+            w3 = np.diff(Lh["WC"][0]) + np.diff(Lh["WF"][0])
+            return int(len(bx["level"])), int(w3[leaf].max()), int(sum(len(Lh[k][1]) for k in Lh))
+
+        out_plain = d_out.clone()
+        res = {}
+        for lr in (0, 1):
+            pr = params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"]), level_restrict=lr)
+            sg = C.c_void_p()
+            chk(L.gq_geometry_create(ctx, C.byref(desc), C.byref(pr), C.byref(sg)))
+            chk(L.gq_targets_set(sg, nt, d_txy.data_ptr(), d_ton.data_ptr()))
+            bms = []
+            for _ in range(3):
+                b0 = torch.cuda.Event(enable_timing=True)
+                b1 = torch.cuda.Event(enable_timing=True)
+                b0.record(stream)
+                chk(L.gq_build(sg))
+                b1.record(stream)
+                b1.synchronize()
+                bms.append(b0.elapsed_time(b1))
+            sst = Stats()
+            ems = []
+            for _ in range(3):
+                flush.zero_()
+                chk(L.gq_eval(sg, kern, d_mu.data_ptr(), d_out.data_ptr(), C.byref(sst)))
+                ems.append(sst.ms_total)
+            gh = Geometry.__new__(Geometry)
+            gh.L, gh._ctx, gh._geom, gh.nt = L, ctx, sg, nt
+            ti = TreeInfo()
+            chk(L.gq_tree_info_get(sg, C.byref(ti)))
+            gh.info, gh.nbox, gh.nc, gh.npt, gh.nsrc = ti, ti.nbox, ti.ncentres, ti.npoint_targets, ti.nsources
+            nb, w3max, nlist = tree_stats(gh)
+            gh._geom = gh._ctx = None
+            res[lr] = {"build_ms": statistics.median(bms), "eval_ms": statistics.median(ems), "boxes": nb,
+                       "list3_max_per_leaf": w3max, "list_entries": nlist,
+                       "stages_ms": {STAGE_NAMES[i]: round(float(sst.ms_stage[i]), 3) for i in range(11)}}
+            if lr == 1:
+                res[lr]["max_rel_diff_vs_plain_tree"] = float((d_out - out_plain).abs().max() / out_plain.abs().max())
+            L.gq_geometry_destroy(sg)
+        restricted = {"plain": res[0], "level_restricted": res[1],
+                      "eval_targets_per_s": nt / (res[1]["eval_ms"] * 1e-3)}
+        d_out.copy_(out_plain)
+
     batched = run_batched(args, dev, stream) if args.batched else None
 
     L.gq_geometry_destroy(geom)
@@ -644,6 +696,7 @@ def run_gpu(args, rank, world, local):
         "stages_ms": stage_report,
         "rel_err_vs_oracle": rel_err,
         "precision_sweep": sweep,
+        "level_restricted": restricted,
         "batched": batched,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -110,6 +110,7 @@ typedef struct {
     double eps;
     int precision;
     int m2l;
+    int level_restrict;
 } gq_params;
 
 enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1, GQ_PREC_MIXED_FMM = 2 };
@@ -124,6 +125,17 @@ enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1, GQ_PREC_MIXED_FMM = 2 };
  *     units of 1e-15 of the FP64 M2L); otherwise FP64 FMAs.
  *   GQ_M2L_FP64: always the FP64 FMA kernel. */
 enum { GQ_M2L_AUTO = 0, GQ_M2L_FP64 = 1 };
+
+/* level_restrict = 1: a level-restricted tree (Sec. 4.6, remark on
+ * level-restricted quadtrees: adjacent leaves differ by at most one level),
+ * which bounds List 3 of every leaf.  After Stage 1, a leaf that owns a
+ * particle eligible for children (and is above max_level) is subdivided as in
+ * Stage 1 (empty children pruned, centres moving only when their disk fits
+ * the child's TCR) while some box two or more levels deeper touches it (closed
+ * squares intersect); the tree is rebuilt with those subdivisions forced until
+ * none is left.  A leaf with no particle eligible for children cannot be
+ * refined and keeps its contact.  0 (default): the tree of Stage 1 alone.
+ * Other values: GQ_ERR_INVALID. */
 
 /* Discretised curve (Sec. 2.1, 2.2.1).  Panel k owns base nodes
  * [k*nb, (k+1)*nb) and quadrature (upsampled) nodes [k*nu, (k+1)*nu).

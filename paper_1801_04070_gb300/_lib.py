@@ -28,7 +28,8 @@ class Params(C.Structure):
     _fields_ = [("p_qbx", C.c_int), ("p_fmm", C.c_int), ("n_max", C.c_int),
                 ("tf_num", C.c_int), ("tf_den", C.c_int), ("w3_demote", C.c_int),
                 ("max_level", C.c_int), ("radius_factor", C.c_double),
-                ("assoc_slack", C.c_double), ("eps", C.c_double), ("precision", C.c_int), ("m2l", C.c_int)]
+                ("assoc_slack", C.c_double), ("eps", C.c_double), ("precision", C.c_int), ("m2l", C.c_int),
+                ("level_restrict", C.c_int)]
 
 
 class GeometryDesc(C.Structure):

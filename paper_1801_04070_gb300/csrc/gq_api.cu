@@ -97,6 +97,7 @@ void resolve_orders(gq_params &p) {
     GQ_REQUIRE(p.precision == GQ_PREC_FP64 || p.precision == GQ_PREC_MIXED || p.precision == GQ_PREC_MIXED_FMM,
                GQ_ERR_INVALID, "unknown precision");
     GQ_REQUIRE(p.m2l == GQ_M2L_AUTO || p.m2l == GQ_M2L_FP64, GQ_ERR_INVALID, "unknown m2l mode");
+    GQ_REQUIRE(p.level_restrict == 0 || p.level_restrict == 1, GQ_ERR_INVALID, "level_restrict must be 0 or 1");
 }
 
 }  // namespace
@@ -118,6 +119,7 @@ gq_status gq_params_default(gq_params *out) {
     out->eps = 0.0;
     out->precision = GQ_PREC_FP64;
     out->m2l = GQ_M2L_AUTO;
+    out->level_restrict = 0;
     return GQ_OK;
 }
 

@@ -206,6 +206,10 @@ void gq_radix_sort_pairs32(gq_ctx *ctx, uint32_t *keys, int *vals, long long n, 
 // ------------------------------------------------------------------ stages
 void gq_build_all(gq_geom *g);                 // gq_tree.cu
 void gq_build_lists(gq_geom *g);               // gq_lists.cu
+// Keys (level << 60) | Morton key of the leaves that violate the level
+// restriction (a box two levels deeper touches them) and own a particle
+// eligible for children (belig[b] > 0); synchronises the stream.
+void gq_balance_violations(gq_geom *g, const int *belig, std::vector<uint64_t> &out);
 void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *st,
                  const double2 *qn_pre = nullptr, const double *apply_identity = nullptr);  // gq_fmm.cu
 void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, double *const *out);

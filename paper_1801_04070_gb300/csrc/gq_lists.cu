@@ -99,6 +99,42 @@ __device__ __forceinline__ int wlook(const TreeView &T, int b, int dx, int dy) {
     return T.win[(size_t)b * 25 + (dy + 2) * 5 + dx + 2];
 }
 
+// Level restriction (Sec. 4.6 remark): leaf b is in violation when a box two
+// levels deeper touches it; such a box is a grandchild of one of b's eight
+// same-level neighbours (its level-l ancestor touches b and is not b).
+__global__ void k_balance_check(int nbox, int max_level, const int *__restrict__ blev, const int *__restrict__ bix,
+                                const int *__restrict__ biy, const int4 *__restrict__ bchild,
+                                const uint64_t *__restrict__ bkey, const int *__restrict__ win,
+                                const int *__restrict__ belig, uint64_t *__restrict__ out, int *__restrict__ nout) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int4 c = bchild[b];
+    if (c.x >= 0 || c.y >= 0 || c.z >= 0 || c.w >= 0) return;   // not a leaf
+    const int l = blev[b];
+    if (belig[b] <= 0 || l >= max_level) return;
+    IBox me{l, bix[b], biy[b]};
+    bool viol = false;
+    for (int dy = -1; dy <= 1 && !viol; ++dy)
+        for (int dx = -1; dx <= 1 && !viol; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            int n = win[(size_t)b * 25 + (dy + 2) * 5 + dx + 2];
+            if (n < 0) continue;
+            int4 nc = bchild[n];
+            int ch[4] = {nc.x, nc.y, nc.z, nc.w};
+            for (int q = 0; q < 4 && !viol; ++q) {
+                if (ch[q] < 0) continue;
+                int4 gc = bchild[ch[q]];
+                int gg[4] = {gc.x, gc.y, gc.z, gc.w};
+                for (int r = 0; r < 4; ++r)
+                    if (gg[r] >= 0 && adjacent(IBox{l + 2, bix[gg[r]], biy[gg[r]]}, me)) {
+                        viol = true;
+                        break;
+                    }
+            }
+        }
+    if (viol) out[atomicAdd(nout, 1)] = ((uint64_t)l << 60) | bkey[b];
+}
+
 enum { LU = 0, LV = 1, LWC = 2, LWF = 3, LXC = 4, LXF = 5 };
 // stack modes
 enum { M_OWN = 0, M_COLL = 1, M_FARCLOSE = 2, M_LEAVES_WC = 3 };
@@ -282,6 +318,34 @@ __global__ void k_lists(TreeView T, int nbox, int fill, const int *__restrict__ 
 }
 
 }  // namespace
+
+void gq_balance_violations(gq_geom *g, const int *belig, std::vector<uint64_t> &out) {
+    gq_ctx *ctx = g->ctx;
+    cudaStream_t st = ctx->stream;
+    int nbox = g->nbox;
+    dbuf<int> win, n;
+    dbuf<uint64_t> keys;
+    win.alloc((size_t)nbox * 25);
+    keys.alloc(nbox);
+    n.alloc(1);
+    for (int l = 0; l < g->nlev; ++l) {
+        int s0 = g->level_start_h[l], s1 = g->level_start_h[l + 1];
+        GQ_LAUNCH(ctx, k_windows, gq_blocks(s1 - s0, kT), kT, 0, s0, s1, (const int *)g->bparent.p,
+                  (const int *)g->bix.p, (const int *)g->biy.p, (const int4 *)g->bchild.p, win.p);
+    }
+    GQ_CUDA(cudaMemsetAsync(n.p, 0, sizeof(int), st));
+    GQ_LAUNCH(ctx, k_balance_check, gq_blocks(nbox, kT), kT, 0, nbox, g->prm.max_level, (const int *)g->blev.p,
+              (const int *)g->bix.p, (const int *)g->biy.p, (const int4 *)g->bchild.p, (const uint64_t *)g->bkey.p,
+              (const int *)win.p, belig, keys.p, n.p);
+    int h = 0;
+    GQ_CUDA(cudaMemcpyAsync(&h, n.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GQ_CUDA(cudaStreamSynchronize(st));
+    out.resize(h);
+    if (h) {
+        GQ_CUDA(cudaMemcpyAsync(out.data(), keys.p, sizeof(uint64_t) * h, cudaMemcpyDeviceToHost, st));
+        GQ_CUDA(cudaStreamSynchronize(st));
+    }
+}
 
 void gq_build_lists(gq_geom *g) {
     gq_ctx *ctx = g->ctx;

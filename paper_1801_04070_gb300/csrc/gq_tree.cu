@@ -299,17 +299,31 @@ __device__ int lower_bound_prefix(const uint64_t *K, int lo, int hi, int shift, 
 
 // For each box at level l: subdivide if it holds more than n_max particles
 // eligible for level l+1; a child exists if its quadrant holds one.
+// forced: sorted keys (level << 60) | Morton key of boxes subdivided whatever
+// their count (level restriction); belig[j]: the count, kept for the balance check
+__device__ bool key_forced(const uint64_t *forced, int n, uint64_t k) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (forced[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return lo < n && forced[lo] == k;
+}
+
 __global__ void k_subdivide(int nl, int l, int max_level, int n_max, const uint64_t *__restrict__ K,
                             const int *__restrict__ P, const uint64_t *__restrict__ bkey, const int *__restrict__ bbeg,
                             const int *__restrict__ bend, int *__restrict__ nchild, int4 *__restrict__ cbeg,
-                            int4 *__restrict__ cend) {
+                            int4 *__restrict__ cend, const uint64_t *__restrict__ forced, int nforced,
+                            int *__restrict__ belig) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nl) return;
     int beg = bbeg[j], end = bend[j];
     int S = P[end] - P[beg];
+    belig[j] = S;
     int cnt = 0;
     int cb[4] = {-1, -1, -1, -1}, ce[4] = {-1, -1, -1, -1};
-    if (S > n_max && l < max_level) {
+    bool sub = S > n_max || (S > 0 && nforced > 0 && key_forced(forced, nforced, ((uint64_t)l << 60) | bkey[j]));
+    if (sub && l < max_level) {
         int shift = 2 * (GQ_KEYBITS - (l + 1));
         uint64_t base = bkey[j] << 2;
         int bnd[5];
@@ -608,7 +622,7 @@ static RootInfo make_root(const Ext &e) {
 
 struct LevelBufs {
     dbuf<uint64_t> key;
-    dbuf<int> beg, end, par;
+    dbuf<int> beg, end, par, elig;
     dbuf<int4> child;
     int n = 0;
 };
@@ -669,92 +683,122 @@ void gq_build_all(gq_geom *g) {
     GQ_LAUNCH(ctx, k_gather_int, gq_blocks(N, kT), kT, 0, N, (const int *)V.p, (const int *)elig0.p, elig.p);
 
     pt.mark("keys_sort");
-    // ---- level-by-level subdivision
-    std::vector<std::unique_ptr<LevelBufs>> lv;
-    lv.emplace_back(new LevelBufs);
-    lv[0]->n = 1;
-    lv[0]->key.alloc(1);
-    lv[0]->beg.alloc(1);
-    lv[0]->end.alloc(1);
-    lv[0]->par.alloc(1);
-    {
-        uint64_t k0 = 0;
-        int b0 = 0, e0 = (int)N, p0 = -1;
-        GQ_CUDA(cudaMemcpyAsync(lv[0]->key.p, &k0, sizeof(k0), cudaMemcpyHostToDevice, st));
-        GQ_CUDA(cudaMemcpyAsync(lv[0]->beg.p, &b0, sizeof(int), cudaMemcpyHostToDevice, st));
-        GQ_CUDA(cudaMemcpyAsync(lv[0]->end.p, &e0, sizeof(int), cudaMemcpyHostToDevice, st));
-        GQ_CUDA(cudaMemcpyAsync(lv[0]->par.p, &p0, sizeof(int), cudaMemcpyHostToDevice, st));
-        GQ_CUDA(cudaStreamSynchronize(st));
-    }
+    // ---- level-by-level subdivision (a lambda: the level restriction runs it
+    // again with the subdivisions it forces)
+    std::vector<int> lstart;
+    dbuf<int> belig;   // per box: particles eligible for its children
     dbuf<int> flag, P, scan_tmp, owner, nchild, coff, ctmp;
     dbuf<int4> cbeg, cend;
-    flag.alloc(N);
-    P.alloc(N + 1);
-    scan_tmp.alloc(gq_scan_tmp_size(N));
-    owner.alloc(N);
-    GQ_LAUNCH(ctx, k_fill_int, gq_blocks(N, kT), kT, 0, N, 0, owner.p);
-    std::vector<int> lstart = {0, 1};
-    for (int l = 0;; ++l) {
-        LevelBufs &cur = *lv[l];
-        int nl = cur.n;
-        GQ_LAUNCH(ctx, k_flags_level, gq_blocks(N, kT), kT, 0, N, (const int *)elig.p, l, flag.p);
-        gq_exclusive_scan(ctx, flag.p, P.p, N, scan_tmp.p);
-        nchild.alloc(nl);
-        coff.alloc(nl + 1);
-        cbeg.alloc(nl);
-        cend.alloc(nl);
-        ctmp.alloc(gq_scan_tmp_size(nl));
-        GQ_LAUNCH(ctx, k_subdivide, gq_blocks(nl, kT), kT, 0, nl, l, g->prm.max_level, g->prm.n_max,
-                  (const uint64_t *)K.p, (const int *)P.p, (const uint64_t *)cur.key.p, (const int *)cur.beg.p,
-                  (const int *)cur.end.p, nchild.p, cbeg.p, cend.p);
-        gq_exclusive_scan(ctx, nchild.p, coff.p, nl, ctmp.p);
-        int total = 0;
-        GQ_CUDA(cudaMemcpyAsync(&total, coff.p + nl, sizeof(int), cudaMemcpyDeviceToHost, st));
-        GQ_CUDA(cudaStreamSynchronize(st));
-        cur.child.alloc(nl);
+    auto build_levels = [&](const uint64_t *forced, int nforced) {
+        // ---- level-by-level subdivision
+        std::vector<std::unique_ptr<LevelBufs>> lv;
         lv.emplace_back(new LevelBufs);
-        LevelBufs &nxt = *lv[l + 1];
-        nxt.n = total;
-        nxt.key.alloc(total);
-        nxt.beg.alloc(total);
-        nxt.end.alloc(total);
-        nxt.par.alloc(total);
-        int next_start = lstart[l + 1];
-        GQ_LAUNCH(ctx, k_emit_children, gq_blocks(nl, kT), kT, 0, nl, next_start, (const uint64_t *)cur.key.p,
-                  (const int *)coff.p, (const int4 *)cbeg.p, (const int4 *)cend.p, lstart[l], cur.child.p, nxt.key.p,
-                  nxt.beg.p, nxt.end.p, nxt.par.p);
-        GQ_LAUNCH(ctx, k_own_update, gq_blocks(N, kT), kT, 0, N, l, lstart[l], lstart[l + 1], (const uint64_t *)K.p,
-                  (const int *)elig.p, (const int4 *)cur.child.p, owner.p);
-        if (total == 0) {
-            lv.pop_back();
-            break;
+        lv[0]->n = 1;
+        lv[0]->key.alloc(1);
+        lv[0]->beg.alloc(1);
+        lv[0]->end.alloc(1);
+        lv[0]->par.alloc(1);
+        {
+            uint64_t k0 = 0;
+            int b0 = 0, e0 = (int)N, p0 = -1;
+            GQ_CUDA(cudaMemcpyAsync(lv[0]->key.p, &k0, sizeof(k0), cudaMemcpyHostToDevice, st));
+            GQ_CUDA(cudaMemcpyAsync(lv[0]->beg.p, &b0, sizeof(int), cudaMemcpyHostToDevice, st));
+            GQ_CUDA(cudaMemcpyAsync(lv[0]->end.p, &e0, sizeof(int), cudaMemcpyHostToDevice, st));
+            GQ_CUDA(cudaMemcpyAsync(lv[0]->par.p, &p0, sizeof(int), cudaMemcpyHostToDevice, st));
+            GQ_CUDA(cudaStreamSynchronize(st));
         }
-        lstart.push_back(lstart[l + 1] + total);
-    }
-    g->nlev = (int)lv.size();
-    g->nbox = lstart[g->nlev];
-    g->level_start_h.assign(lstart.begin(), lstart.begin() + g->nlev + 1);
-    g->level_start.alloc(g->nlev + 1);
-    GQ_CUDA(cudaMemcpyAsync(g->level_start.p, g->level_start_h.data(), sizeof(int) * (g->nlev + 1),
-                            cudaMemcpyHostToDevice, st));
+        flag.alloc(N);
+        P.alloc(N + 1);
+        scan_tmp.alloc(gq_scan_tmp_size(N));
+        owner.alloc(N);
+        GQ_LAUNCH(ctx, k_fill_int, gq_blocks(N, kT), kT, 0, N, 0, owner.p);
+        lstart = {0, 1};
+        for (int l = 0;; ++l) {
+            LevelBufs &cur = *lv[l];
+            int nl = cur.n;
+            GQ_LAUNCH(ctx, k_flags_level, gq_blocks(N, kT), kT, 0, N, (const int *)elig.p, l, flag.p);
+            gq_exclusive_scan(ctx, flag.p, P.p, N, scan_tmp.p);
+            nchild.alloc(nl);
+            coff.alloc(nl + 1);
+            cbeg.alloc(nl);
+            cend.alloc(nl);
+            ctmp.alloc(gq_scan_tmp_size(nl));
+            cur.elig.alloc(nl);
+            GQ_LAUNCH(ctx, k_subdivide, gq_blocks(nl, kT), kT, 0, nl, l, g->prm.max_level, g->prm.n_max,
+                      (const uint64_t *)K.p, (const int *)P.p, (const uint64_t *)cur.key.p, (const int *)cur.beg.p,
+                      (const int *)cur.end.p, nchild.p, cbeg.p, cend.p, forced, nforced, cur.elig.p);
+            gq_exclusive_scan(ctx, nchild.p, coff.p, nl, ctmp.p);
+            int total = 0;
+            GQ_CUDA(cudaMemcpyAsync(&total, coff.p + nl, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GQ_CUDA(cudaStreamSynchronize(st));
+            cur.child.alloc(nl);
+            lv.emplace_back(new LevelBufs);
+            LevelBufs &nxt = *lv[l + 1];
+            nxt.n = total;
+            nxt.key.alloc(total);
+            nxt.beg.alloc(total);
+            nxt.end.alloc(total);
+            nxt.par.alloc(total);
+            int next_start = lstart[l + 1];
+            GQ_LAUNCH(ctx, k_emit_children, gq_blocks(nl, kT), kT, 0, nl, next_start, (const uint64_t *)cur.key.p,
+                      (const int *)coff.p, (const int4 *)cbeg.p, (const int4 *)cend.p, lstart[l], cur.child.p, nxt.key.p,
+                      nxt.beg.p, nxt.end.p, nxt.par.p);
+            GQ_LAUNCH(ctx, k_own_update, gq_blocks(N, kT), kT, 0, N, l, lstart[l], lstart[l + 1], (const uint64_t *)K.p,
+                      (const int *)elig.p, (const int4 *)cur.child.p, owner.p);
+            if (total == 0) {
+                lv.pop_back();
+                break;
+            }
+            lstart.push_back(lstart[l + 1] + total);
+        }
+        g->nlev = (int)lv.size();
+        g->nbox = lstart[g->nlev];
+        g->level_start_h.assign(lstart.begin(), lstart.begin() + g->nlev + 1);
+        g->level_start.alloc(g->nlev + 1);
+        GQ_CUDA(cudaMemcpyAsync(g->level_start.p, g->level_start_h.data(), sizeof(int) * (g->nlev + 1),
+                                cudaMemcpyHostToDevice, st));
 
-    pt.mark("levels");
-    // ---- final box arrays
-    int nbox = g->nbox;
-    g->bkey.alloc(nbox);
-    g->blev.alloc(nbox);
-    g->bix.alloc(nbox);
-    g->biy.alloc(nbox);
-    g->bparent.alloc(nbox);
-    g->bchild.alloc(nbox);
-    for (int l = 0; l < g->nlev; ++l) {
-        LevelBufs &B = *lv[l];
-        GQ_LAUNCH(ctx, k_box_final, gq_blocks(B.n, kT), kT, 0, B.n, lstart[l], l, (const uint64_t *)B.key.p,
-                  (const int *)B.par.p, (const int4 *)B.child.p, g->bkey.p, g->blev.p, g->bix.p, g->biy.p,
-                  g->bparent.p, g->bchild.p);
+        pt.mark("levels");
+        // ---- final box arrays
+        int nbox = g->nbox;
+        belig.alloc(nbox);
+        g->bkey.alloc(nbox);
+        g->blev.alloc(nbox);
+        g->bix.alloc(nbox);
+        g->biy.alloc(nbox);
+        g->bparent.alloc(nbox);
+        g->bchild.alloc(nbox);
+        for (int l = 0; l < g->nlev; ++l) {
+            LevelBufs &B = *lv[l];
+            GQ_LAUNCH(ctx, k_box_final, gq_blocks(B.n, kT), kT, 0, B.n, lstart[l], l, (const uint64_t *)B.key.p,
+                      (const int *)B.par.p, (const int4 *)B.child.p, g->bkey.p, g->blev.p, g->bix.p, g->biy.p,
+                      g->bparent.p, g->bchild.p);
+            GQ_CUDA(cudaMemcpyAsync(belig.p + lstart[l], B.elig.p, sizeof(int) * B.n, cudaMemcpyDeviceToDevice, st));
+        }
+    };
+    build_levels(nullptr, 0);
+    if (g->prm.level_restrict) {
+        // Sec. 4.6 level restriction: subdivide, and rebuild, while a leaf owning a
+        // particle eligible for children touches a box two levels deeper
+        std::vector<uint64_t> forced;
+        dbuf<uint64_t> dforced;
+        for (int it = 0;; ++it) {
+            std::vector<uint64_t> add;
+            gq_balance_violations(g, belig.p, add);
+            if (add.empty()) break;
+            GQ_REQUIRE(it < 64, GQ_ERR_UNSUPPORTED, "level restriction did not converge");
+            forced.insert(forced.end(), add.begin(), add.end());
+            std::sort(forced.begin(), forced.end());
+            forced.erase(std::unique(forced.begin(), forced.end()), forced.end());
+            dforced.alloc(forced.size());
+            GQ_CUDA(cudaMemcpyAsync(dforced.p, forced.data(), sizeof(uint64_t) * forced.size(),
+                                    cudaMemcpyHostToDevice, st));
+            build_levels(dforced.p, (int)forced.size());
+        }
     }
 
     pt.mark("box_arrays");
+    const int nbox = g->nbox;
     // ---- per-type arrays
     dbuf<int> pos;
     pos.alloc(N + 1);
