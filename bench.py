@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false",
                     help="skip the FP64 vs MIXED evaluation sweep at eps = 1e-4 ... 1e-12 (orders from eps)")
-    ap.add_argument("--batched", action="store_true",
-                    help="also time 64 geometries of uneven size (2k-200k quadrature nodes, log-uniform) x 8 "
-                         "densities: one CUDA-graph launch against one gq_eval after another")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 64 geometries of uneven size (2k-200k quadrature nodes, log-uniform) x 8 "
+                         "densities: the persistent launch and the graph branches against one gq_eval after "
+                         "another, and the batched exterior Neumann solves")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="precision of the timed step: 0 FP64 (the benchmark), 1 MIXED, 2 MIXED_FMM at --eps "
                          "with the workload's orders (profiling cases)")
@@ -319,14 +320,15 @@ def run_batched(args, dev, stream):
                 geo.eval(kern, d[j], o[j])
 
     b = Batch(geos)
-    b.eval(kern, dens, outs)            # eager pass, autotune, capture
+    b.eval(kern, dens, outs)            # eager pass, autotune, capture (persistent launch)
     torch.cuda.synchronize()
     ref = [o.clone() for o in outs]
     sequential()
     torch.cuda.synchronize()
     diff = max(float((a - c).abs().max() / c.abs().max()) for a, c in zip(ref, outs))
     res = {}
-    for name, fn in (("graph", lambda: b.eval(kern, dens, outs)), ("sequential", sequential)):
+
+    def timed3(fn):
         fn()
         torch.cuda.synchronize()
         t = []
@@ -338,8 +340,14 @@ def run_batched(args, dev, stream):
             e1.record(stream)
             e1.synchronize()
             t.append(e0.elapsed_time(e1))
-        res[name] = statistics.mean(t)
-    streams = b.streams()
+        return statistics.mean(t)
+
+    res["persistent"] = timed3(lambda: b.eval(kern, dens, outs))
+    tile, streams = b.persistent_tile(), b.streams()
+    b.mode(1)
+    res["graph"] = timed3(lambda: b.eval(kern, dens, outs))
+    graph_streams = b.streams()
+    res["sequential"] = timed3(sequential)
     b.close()
     for geo in geos:
         geo.close()
@@ -389,10 +397,13 @@ def run_batched(args, dev, stream):
         geo.close()
     return {"workload": f"{len(items)} starfish arrays, {min(nsrc)}-{max(nsrc)} quadrature nodes "
                         f"(log-uniform), {dens[0].shape[0]} densities each, p_qbx 8, p_fmm 15, {kern}",
-            "targets_x_densities": ntot, "graph_ms": res["graph"], "sequential_ms": res["sequential"],
+            "targets_x_densities": ntot, "persistent_ms": res["persistent"], "graph_ms": res["graph"],
+            "sequential_ms": res["sequential"],
+            "persistent_targets_per_s": ntot / (res["persistent"] * 1e-3),
             "graph_targets_per_s": ntot / (res["graph"] * 1e-3),
             "sequential_targets_per_s": ntot / (res["sequential"] * 1e-3),
-            "streams": streams, "max_rel_diff_vs_sequential": diff, "gmres": gmres}
+            "persistent_tile": tile, "persistent_streams": streams, "graph_streams": graph_streams,
+            "max_rel_diff_vs_sequential": diff, "gmres": gmres}
 
 
 # ---------------------------------------------------------------- GPU arm

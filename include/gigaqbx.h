@@ -281,6 +281,29 @@ gq_status gq_batch_eval(gq_batch *b, int kernel, int ndens, const double *const 
 /* Streams the autotuner chose for the captured graph (0 before the first gq_batch_eval). */
 gq_status gq_batch_streams(const gq_batch *b, int *streams);
 
+/* How gq_batch_eval evaluates (the next call recaptures):
+ *   mode 0 (default): when every geometry is FP64 with the same p_qbx (5 or
+ *     8), the graph's per-geometry branches run only the strengths and the
+ *     FMM passes (Stages 2, 4, 5b, 6b, 7, 8) of each density into buffers of
+ *     their own, and one persistent launch then takes work items from a
+ *     counter for all geometries and densities: the direct part of the QBX
+ *     coefficients for 4, 2 or 1 densities of a tile of target boxes, the
+ *     direct potential at point targets, and the final sums (eq. qbx) of 256
+ *     targets.  Every direct item precedes every final item; a final item
+ *     waits, boundedly, for its geometry's direct items (a counter in global
+ *     memory); a wait that runs out makes the call return GQ_ERR_TIMEOUT.
+ *     The autotuner picks the branch streams and then the target boxes per
+ *     direct item (1, 2, 4).  The call synchronises the stream to read the
+ *     wait status.  Other configurations use the branches of mode 1.
+ *   mode 1: every evaluation in the per-geometry branches (as described at
+ *     gq_batch_eval).
+ * The results equal those of mode 1 to rounding of the final sums (the same
+ * kernels' arithmetic). */
+gq_status gq_batch_mode(gq_batch *b, int mode);
+/* Target boxes per direct item of the persistent launch in use (0: the
+ * captured graph does not use the persistent launch). */
+gq_status gq_batch_persistent(const gq_batch *b, int *tile);
+
 /* Exterior Neumann solves (Sec. 1, as gq_gmres) for every geometry of the
  * batch at once: restarted GMRES(restart) from mu = 0 on each geometry in
  * lockstep, where each Arnoldi step applies S' to all geometries by one replay
@@ -442,6 +465,14 @@ gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y);
  * byte offsets of the shared-memory descriptors (a layout check).
  * GQ_ERR_TIMEOUT if the bounded completion wait gave up. */
 gq_status gq_probe_umma(gq_ctx *ctx, int K, const uint16_t *a, const uint16_t *b, int swap, float *d);
+
+/* Check of the persistent batch launch's bounded waits: wait_ns bounds every
+ * dependency wait (default 1 s); stall_geom >= 0 makes that geometry's final
+ * items wait for one direct item more than exist (a count nothing reaches),
+ * so their waits run out, gq_batch_eval returns GQ_ERR_TIMEOUT and the other
+ * items still complete; -1 restores normal operation.  The next gq_batch_eval
+ * recaptures.  GQ_ERR_INVALID for wait_ns <= 0 or a geometry index out of range. */
+gq_status gq_batch_wait_test(gq_batch *b, int64_t wait_ns, int stall_geom);
 
 #ifdef __cplusplus
 }

@@ -103,6 +103,9 @@ def lib():
             "gq_batch_destroy": (st, [vp]),
             "gq_batch_eval": (st, [vp, i32, i32, C.POINTER(vp), C.POINTER(vp)]),
             "gq_batch_streams": (st, [vp, C.POINTER(i32)]),
+            "gq_batch_mode": (st, [vp, i32]),
+            "gq_batch_persistent": (st, [vp, C.POINTER(i32)]),
+            "gq_batch_wait_test": (st, [vp, C.c_int64, i32]),
             "gq_batch_gmres": (st, [vp, C.POINTER(vp), C.c_double, i32, i32, C.POINTER(vp), C.POINTER(i32),
                                     C.POINTER(C.c_double)]),
             "gq_export_root": (st, [vp, vp]),
@@ -353,6 +356,22 @@ class Batch:
         if st != 0:
             raise GigaQBXError(st, self.L.gq_last_error(self._ctx).decode())
         return outs
+
+    def mode(self, mode):
+        """0: persistent launch where supported (default), 1: graph branches only."""
+        st = self.L.gq_batch_mode(self._b, int(mode))
+        if st != 0:
+            raise GigaQBXError(st, self.L.gq_last_error(self._ctx).decode())
+
+    def persistent_tile(self):
+        t = C.c_int()
+        self.L.gq_batch_persistent(self._b, C.byref(t))
+        return t.value
+
+    def wait_test(self, wait_ns, stall_geom):
+        st = self.L.gq_batch_wait_test(self._b, int(wait_ns), int(stall_geom))
+        if st != 0:
+            raise GigaQBXError(st, self.L.gq_last_error(self._ctx).decode())
 
     def streams(self):
         s = C.c_int()

@@ -427,6 +427,22 @@ gq_status gq_batch_streams(const gq_batch *b, int *streams) {
     return GQ_OK;
 }
 
+gq_status gq_batch_mode(gq_batch *b, int mode) {
+    if (!b || (mode != 0 && mode != 1)) return GQ_ERR_INVALID;
+    return guarded(gq_batch_ctx(b), [&] { gq_batch_config_impl(b, mode, 0, -1); });
+}
+
+gq_status gq_batch_persistent(const gq_batch *b, int *tile) {
+    if (!b || !tile) return GQ_ERR_INVALID;
+    *tile = gq_batch_persistent_tile(b);
+    return GQ_OK;
+}
+
+gq_status gq_batch_wait_test(gq_batch *b, int64_t wait_ns, int stall_geom) {
+    if (!b || wait_ns <= 0 || stall_geom < -1 || stall_geom >= gq_batch_size(b)) return GQ_ERR_INVALID;
+    return guarded(gq_batch_ctx(b), [&] { gq_batch_config_impl(b, 0, (long long)wait_ns, stall_geom); });
+}
+
 gq_status gq_centre_features(gq_geom *g, float *features) {
     if (!g || !features) return GQ_ERR_INVALID;
     return guarded(g->ctx, [&] {

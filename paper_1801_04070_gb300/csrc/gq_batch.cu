@@ -32,6 +32,17 @@ struct gq_batch {
     std::vector<double *> out;
     double tuned_ms = 0.0;
     int64_t kernels_per_replay = 0;
+    // persistent path: the direct parts and final sums of all geometries and
+    // densities in one launch after the per-geometry FMM branches
+    int mode = 0;                          // 0: persistent where supported, 1: graph branches only
+    bool persistent = false;               // the captured graph uses the persistent launch
+    int tile = 1;                          // target boxes per direct item (tuned)
+    unsigned long long wait_ns = 1000000000ull;   // bound of each dependency wait
+    int stall_geom = -1;                   // test hook: that geometry's final items can never start
+    std::map<int, gq_bplan *> plans;       // per tile
+    ~gq_batch() {
+        for (auto &kv : plans) gq_bplan_free(kv.second);
+    }
 };
 
 namespace {
@@ -155,6 +166,86 @@ cudaGraphExec_t capture(gq_batch *b, int kernel, int ndens, const double *const 
     return exec;
 }
 
+// Persistent variant: branch i records geometry i's strengths and FMM passes
+// (gq_bplan_fmm); after the join, one persistent launch on the origin stream
+// does every direct part and final sum (gq_bplan_persistent).
+cudaGraphExec_t capture_persistent(gq_batch *b, gq_bplan *P, int S, int64_t *kernels) {
+    cudaStream_t origin;
+    GQ_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+    std::vector<cudaStream_t> st(S);
+    std::vector<gq_ctx> sctx(S);
+    for (int s = 0; s < S; ++s) {
+        GQ_CUDA(cudaStreamCreateWithFlags(&st[s], cudaStreamNonBlocking));
+        sctx[s].device = b->ctx->device;
+        sctx[s].stream = st[s];
+    }
+    gq_ctx octx;
+    octx.device = b->ctx->device;
+    octx.stream = origin;
+    std::vector<int> order(b->geoms.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return cost_of(b->geoms[a]) > cost_of(b->geoms[c]); });
+    std::vector<double> load(S, 0.0);
+    std::vector<int> assign(b->geoms.size());
+    for (int i : order) {
+        int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        assign[i] = s;
+        load[s] += cost_of(b->geoms[i]);
+    }
+    int sms = 0;
+    GQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx->device));
+    cudaGraph_t graph = nullptr;
+    cudaEvent_t fork;
+    std::vector<cudaEvent_t> joins(S);
+    GQ_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int s = 0; s < S; ++s) GQ_CUDA(cudaEventCreateWithFlags(&joins[s], cudaEventDisableTiming));
+    std::vector<gq_ctx *> saved(b->geoms.size(), nullptr);
+    GQ_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+    try {
+        GQ_CUDA(cudaEventRecord(fork, origin));
+        for (int s = 0; s < S; ++s) GQ_CUDA(cudaStreamWaitEvent(st[s], fork, 0));
+        for (size_t i = 0; i < b->geoms.size(); ++i) {
+            gq_geom *g = b->geoms[i];
+            saved[i] = g->ctx;
+            g->ctx = &sctx[assign[i]];
+            gq_bplan_fmm(P, (int)i);
+            g->ctx = saved[i];
+        }
+        for (int s = 0; s < S; ++s) {
+            GQ_CUDA(cudaEventRecord(joins[s], st[s]));
+            GQ_CUDA(cudaStreamWaitEvent(origin, joins[s], 0));
+        }
+        gq_bplan_persistent(P, &octx, sms, b->wait_ns);
+        GQ_CUDA(cudaStreamEndCapture(origin, &graph));
+    } catch (...) {
+        for (size_t i = 0; i < b->geoms.size(); ++i)
+            if (saved[i]) b->geoms[i]->ctx = saved[i];
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(origin, &dummy);
+        if (dummy) cudaGraphDestroy(dummy);
+        throw;
+    }
+    int64_t launched = octx.launches;
+    for (auto &c : sctx) launched += c.launches;
+    *kernels = launched;
+    cudaGraphExec_t exec = nullptr;
+    GQ_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    cudaGraphDestroy(graph);
+    cudaEventDestroy(fork);
+    for (auto e : joins) cudaEventDestroy(e);
+    for (auto x : st) cudaStreamDestroy(x);
+    cudaStreamDestroy(origin);
+    return exec;
+}
+
+gq_bplan *plan_for(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out, int tile) {
+    auto it = b->plans.find(tile);
+    if (it != b->plans.end()) return it->second;
+    gq_bplan *P = gq_bplan_new(b->ctx, kernel, ndens, b->geoms, dens, out, tile, b->stall_geom);
+    b->plans[tile] = P;
+    return P;
+}
+
 double time_replays(gq_batch *b, cudaGraphExec_t exec) {
     cudaStream_t st = b->ctx->stream;
     cudaEvent_t e0, e1;
@@ -186,16 +277,29 @@ void gq_batch_free(gq_batch *b) {
     delete b;
 }
 
+static void drop_capture(gq_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    for (auto &kv : b->plans) gq_bplan_free(kv.second);
+    b->plans.clear();
+}
+
+void gq_batch_config_impl(gq_batch *b, int mode, long long wait_ns, int stall_geom) {
+    drop_capture(b);
+    b->mode = mode;
+    if (wait_ns > 0) b->wait_ns = (unsigned long long)wait_ns;
+    b->stall_geom = stall_geom;
+}
+
+int gq_batch_persistent_tile(const gq_batch *b) { return b->persistent ? b->tile : 0; }
+
 void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out) {
     gq_ctx *ctx = b->ctx;
     size_t n = b->geoms.size();
     bool same = b->exec && b->kernel == kernel && b->ndens == ndens && b->dens.size() == n;
     for (size_t i = 0; same && i < n; ++i) same = b->dens[i] == dens[i] && b->out[i] == out[i];
     if (!same) {
-        if (b->exec) {
-            cudaGraphExecDestroy(b->exec);
-            b->exec = nullptr;
-        }
+        drop_capture(b);
         // eager pass: sizes every buffer and table so that capture allocates nothing
         for (size_t i = 0; i < n; ++i) {
             gq_geom *g = b->geoms[i];
@@ -205,41 +309,73 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
             g->ctx = saved;
         }
         GQ_CUDA(cudaStreamSynchronize(ctx->stream));
-        std::string key = shape_key(b, kernel, ndens);
-        int S = 0;
+        b->persistent = b->mode == 0 && gq_bplan_supported(b->geoms, kernel);
+        std::string key = (b->persistent ? "P" : "") + shape_key(b, kernel, ndens);
+        int S = 0, tile = 1;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             if (g_tune.empty()) load_cache_file();
             auto it = g_tune.find(key);
-            if (it != g_tune.end()) S = it->second;
+            if (it != g_tune.end()) {
+                S = it->second % 100;
+                tile = b->persistent ? it->second / 100 : 1;
+            }
         }
-        if (S <= 0) {
+        auto time_config = [&](int streams, int t) {
+            int64_t kn = 0;
+            cudaGraphExec_t ex = b->persistent
+                                     ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, t), streams, &kn)
+                                     : capture(b, kernel, ndens, dens, out, streams, &kn);
+            double ms = time_replays(b, ex);
+            cudaGraphExecDestroy(ex);
+            return ms;
+        };
+        if (S <= 0 || tile <= 0) {
+            // streams for the per-geometry branches first, then (persistent
+            // path) the target boxes per direct item with those streams
             double best = 1e300;
+            tile = 1;
             for (int cand : {1, 2, 4, 8, 16}) {
                 if (cand > (int)n && cand != 1) break;
-                int64_t kn = 0;
-                cudaGraphExec_t ex = capture(b, kernel, ndens, dens, out, cand, &kn);
-                double ms = time_replays(b, ex);
-                cudaGraphExecDestroy(ex);
+                double ms = time_config(cand, 1);
                 if (ms < best) {
                     best = ms;
                     S = cand;
                 }
             }
+            if (b->persistent)
+                for (int t : {2, 4}) {
+                    double ms = time_config(S, t);
+                    if (ms < best) {
+                        best = ms;
+                        tile = t;
+                    }
+                }
             b->tuned_ms = best;
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tune[key] = S;
+            g_tune[key] = tile * 100 + S;
             save_cache_file();
         }
-        b->exec = capture(b, kernel, ndens, dens, out, S, &b->kernels_per_replay);
+        b->exec = b->persistent ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, tile), S,
+                                                     &b->kernels_per_replay)
+                                : capture(b, kernel, ndens, dens, out, S, &b->kernels_per_replay);
+        b->tile = tile;
         b->kernel = kernel;
         b->ndens = ndens;
         b->streams = S;
         b->dens.assign(dens, dens + n);
         b->out.assign(out, out + n);
+        if (b->persistent) {   // the tuning replays ran the dependency waits too
+            for (auto &kv : b->plans)
+                GQ_REQUIRE(gq_bplan_error(kv.second) == 0, GQ_ERR_TIMEOUT,
+                           "batched evaluation: a bounded dependency wait gave up");
+        }
     }
     GQ_CUDA(cudaGraphLaunch(b->exec, ctx->stream));
     ctx->launches += b->kernels_per_replay;
+    if (b->persistent)
+        GQ_REQUIRE(gq_bplan_error(b->plans[b->tile]) == 0, GQ_ERR_TIMEOUT,
+                   "batched evaluation: a bounded dependency wait gave up");
 }
 
 int gq_batch_streams(const gq_batch *b) { return b->streams; }

@@ -26,6 +26,8 @@
 #include <map>
 #include <mutex>
 
+#include <memory>
+
 #include "gq_internal.cuh"
 #include "gq_dfl.cuh"
 #include "gq_math.cuh"
@@ -33,6 +35,12 @@
 namespace {
 
 constexpr double kInv2Pi = 0.15915494309189533576888376337251;
+
+__device__ __forceinline__ unsigned long long gqtc_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 // MIXED: FP32 direct sums from this accuracy up.  Their rounding, measured up
 // to 3e-7 relative (D on a single starfish, where the double-layer terms
 // cancel most), stays below eps/5 = 1e-6 here; smaller eps use FP32 pairs.
@@ -63,6 +71,7 @@ struct EvalView {
     const int *qc;         // per-centre QBX order (sorted centres) or nullptr: all use Q
     const double *logt;    // GqLogTable
     const unsigned int *qexp;   // largest biased exponent of the S strengths (k_strengths)
+    int nwork_ctr;              // boxes owning centres (batched items)
 };
 
 __device__ __forceinline__ double box_rho(const RootInfo &R, int l) { return ldexp(R.H, -l); }
@@ -511,16 +520,13 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres(EvalView E, int n
 }
 
 // potential at point targets: S: sum q log|t - y| (coincident sources skipped), D: Re sum d/(y - t)
+// Body for target box b (a block of kNearThreads); lt holds the log table
+// (S) in shared memory, loaded by the caller.
 template <int KERNEL>
-__global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nwork, const int *__restrict__ work,
-                                                               double *__restrict__ pot) {
-    __shared__ NearRanges R;
-    __shared__ int wsum[kNearThreads / 32];
-    __shared__ double lt[kGqLogN];
-    for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
+__device__ void near_points_box(const EvalView &E, int b, const double2 *__restrict__ str, double *__restrict__ pot,
+                                NearRanges &R, int *wsum, const double *lt) {
     const int qe = KERNEL == GQ_D ? 1023 : (int)*E.qexp;
     const double qscale = gq_pow2_biased(qe);
-    int b = work[blockIdx.x];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
     int tb = E.pt_beg[b], te = E.pt_end[b];
@@ -543,7 +549,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
                 for (int v = lane; v < T; v += 32) {
                     while (R.pre[r + 1] <= v) ++r;
                     int s = R.beg[r] + (v - R.pre[r]);
-                    double2 y = E.s_xy[s], st = E.str[s];
+                    double2 y = E.s_xy[s], st = str[s];
                     double wx = y.x - tz.x, wy = y.y - tz.y;
                     double n2 = wx * wx + wy * wy;
                     if (KERNEL == GQ_D) {
@@ -561,6 +567,16 @@ __global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nw
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (valid && lane == 0) pot[t] = acc;
     }
+}
+
+template <int KERNEL>
+__global__ void __launch_bounds__(kNearThreads) k_near_points(EvalView E, int nwork, const int *__restrict__ work,
+                                                               double *__restrict__ pot) {
+    __shared__ NearRanges R;
+    __shared__ int wsum[kNearThreads / 32];
+    __shared__ double lt[kGqLogN];
+    for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
+    near_points_box<KERNEL>(E, work[blockIdx.x], E.str, pot, R, wsum, lt);
 }
 
 // ------------------------------------------------------------------ Stage 5b: List 3 far
@@ -750,16 +766,14 @@ __global__ void k_l2p(EvalView E, int npt, const int *__restrict__ pt_owner, con
 }
 
 // final values at the targets (eq. qbx; two-sided targets average both centres)
-__global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, const int *__restrict__ kind,
-                        const int *__restrict__ ctr,
-                        const int *__restrict__ ctr_pos, const int *__restrict__ tgt_ptpos,
-                        const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on,
-                        const double *__restrict__ base_n, const double2 *__restrict__ sc_xy,
-                        const double *__restrict__ sc_r, const double2 *__restrict__ Qc,
-                        const double2 *__restrict__ Qc2, const double *__restrict__ pot, const double *__restrict__ pot2,
-                        double *__restrict__ out) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
+__device__ __forceinline__ void final_target(int t, int kernel, int Q, const int *__restrict__ qcs,
+                                             const int *__restrict__ kind, const int *__restrict__ ctr,
+                                             const int *__restrict__ ctr_pos, const int *__restrict__ tgt_ptpos,
+                                             const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on,
+                                             const double *__restrict__ base_n, const double2 *__restrict__ sc_xy,
+                                             const double *__restrict__ sc_r, const double2 *__restrict__ Qc,
+                                             const double2 *__restrict__ Qc2, const double *__restrict__ pot,
+                                             const double *__restrict__ pot2, double *__restrict__ out) {
     int k = kind[t];
     if (k == 0) {
         int j = tgt_ptpos[t];
@@ -792,6 +806,20 @@ __global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, 
         }
     }
     out[t] = sum / nside;
+}
+
+__global__ void k_final(int nt, int kernel, int Q, const int *__restrict__ qcs, const int *__restrict__ kind,
+                        const int *__restrict__ ctr,
+                        const int *__restrict__ ctr_pos, const int *__restrict__ tgt_ptpos,
+                        const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on,
+                        const double *__restrict__ base_n, const double2 *__restrict__ sc_xy,
+                        const double *__restrict__ sc_r, const double2 *__restrict__ Qc,
+                        const double2 *__restrict__ Qc2, const double *__restrict__ pot, const double *__restrict__ pot2,
+                        double *__restrict__ out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    final_target(t, kernel, Q, qcs, kind, ctr, ctr_pos, tgt_ptpos, tgt_xy, tgt_on, base_n, sc_xy, sc_r, Qc, Qc2, pot,
+                 pot2, out);
 }
 
 // the operator at the base nodes (gq_apply): base node i is evaluated from its
@@ -1881,15 +1909,9 @@ void dispatch_near_centres_f32(gq_ctx *ctx, const EvalView &E, const MixedView &
 // coefficient arrays [nc][q+1], qstride apart.  Same layout and sums as
 // k_near_centres otherwise.
 template <int QQ, int KERNEL, int ND>
-__global__ void __launch_bounds__(kNearThreads) k_near_centres_multi(EvalView E, int nwork, const int *__restrict__ work,
-                                                                      const double2 *__restrict__ strm, long long sstride,
-                                                                      double2 *__restrict__ Qm, long long qstride) {
-    __shared__ NearRanges R;
-    __shared__ int wsum[kNearThreads / 32];
-    __shared__ double lt[KERNEL == GQ_D ? 1 : kGqLogN];
-    if (KERNEL != GQ_D)
-        for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
-    int b = work[blockIdx.x];
+__device__ void near_centres_multi_box(const EvalView &E, int b, const double2 *__restrict__ strm, long long sstride,
+                                       double2 *__restrict__ Qm, long long qstride, NearRanges &R, int *wsum,
+                                       const double *lt) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int ne = (E.loff[0][b + 1] - E.loff[0][b]) + (E.loff[2][b + 1] - E.loff[2][b]) + (E.loff[4][b + 1] - E.loff[4][b]);
     int cb = E.ctr_beg[b], ce = E.ctr_end[b];
@@ -1986,6 +2008,19 @@ __global__ void __launch_bounds__(kNearThreads) k_near_centres_multi(EvalView E,
     }
 }
 
+
+template <int QQ, int KERNEL, int ND>
+__global__ void __launch_bounds__(kNearThreads) k_near_centres_multi(EvalView E, int nwork, const int *__restrict__ work,
+                                                                      const double2 *__restrict__ strm, long long sstride,
+                                                                      double2 *__restrict__ Qm, long long qstride) {
+    __shared__ NearRanges R;
+    __shared__ int wsum[kNearThreads / 32];
+    __shared__ double lt[KERNEL == GQ_D ? 1 : kGqLogN];
+    if (KERNEL != GQ_D)
+        for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = E.logt[i];
+    near_centres_multi_box<QQ, KERNEL, ND>(E, work[blockIdx.x], strm, sstride, Qm, qstride, R, wsum, lt);
+}
+
 template <int QQ, int ND>
 void launch_near_centres_multi(gq_ctx *ctx, const EvalView &E, int nwork, const int *work, const double2 *strm,
                                long long sstride, double2 *Qm, long long qstride) {
@@ -2029,6 +2064,115 @@ void dispatch_near_centres(gq_ctx *ctx, const EvalView &E, int nwork, const int 
 __global__ void k_tgt_ptpos(int npt, const int *__restrict__ pt_perm, int *__restrict__ out) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < npt) out[pt_perm[j]] = j;
+}
+
+
+// ------------------------------------------------------------------ persistent batched evaluation
+// One launch covers the direct interactions and the final sums of every
+// geometry and density of a batch (the FMM passes run before it, per
+// geometry).  Work items, taken in order from a counter by CTAs of
+// kNearThreads threads:
+//   NEAR4/NEAR2/NEAR1 (geometry, first box, first density): the direct part of
+//     the QBX coefficients (Stages 3, 5a, 6a) of `tile` target boxes for 4, 2
+//     or 1 densities at once (per-pair geometry and powers shared);
+//   NEARPT (geometry, box, density): the direct potential at point targets;
+//   FINAL (geometry, first target, density): eq. qbx at 256 targets.
+// All NEAR/NEARPT items precede every FINAL item.  A FINAL item first waits
+// until its geometry's direct items are done (a per-geometry counter; the
+// items it waits for were taken earlier by running CTAs and wait for nothing,
+// so the wait ends); the wait is bounded by limit_ns, after which the kernel
+// sets *err and skips the item (later waits return at once).
+enum { BI_NEAR4 = 0, BI_NEAR2 = 1, BI_NEAR1 = 2, BI_NEARPT = 3, BI_FINAL = 4 };
+
+struct BatchItem {
+    int type, geom, a, b;
+};
+
+struct BatchGeomDev {
+    EvalView E;
+    const int *ctr_boxes, *pt_boxes;
+    int tile;                          // target boxes per NEAR item
+    const double2 *strm;               // [nd][nsrc] strengths
+    long long sstride;
+    double2 *Qn;                       // [nd][nc][q+1] direct parts
+    const double2 *Qf;                 // [nd][nc][q+1] far parts (FMM passes)
+    long long qstride;
+    double *potn;                      // [nd][npt] direct point potentials
+    const double *potf;                // [nd][npt] far point potentials
+    long long pstride;
+    const unsigned int *qexp;          // [nd] largest strength exponent per density
+    double *out;                       // [nd][nt]
+    int nt, kernel, items;             // items: NEAR + NEARPT items of this geometry
+    const int *kind, *ctr, *ctr_pos, *tgt_ptpos, *tgt_on;
+    const double *tgt_xy, *base_n;
+};
+
+template <int QQ, int KERNEL>
+__global__ void __launch_bounds__(kNearThreads) k_batch_persistent(const BatchGeomDev *__restrict__ G,
+                                                                    const BatchItem *__restrict__ items, int nitems,
+                                                                    const double *__restrict__ logt, int *next,
+                                                                    int *done, unsigned long long limit_ns,
+                                                                    int *err) {
+    __shared__ NearRanges R;
+    __shared__ int wsum[kNearThreads / 32];
+    __shared__ double lt[KERNEL == GQ_D ? 1 : kGqLogN];
+    __shared__ int sitem, sok;
+    if (KERNEL != GQ_D)
+        for (int i = threadIdx.x; i < kGqLogN; i += kNearThreads) lt[i] = logt[i];
+    for (;;) {
+        if (threadIdx.x == 0) sitem = atomicAdd(next, 1);
+        __syncthreads();
+        const int it = sitem;
+        __syncthreads();   // every thread has the item before thread 0 takes the next
+        if (it >= nitems) break;
+        const BatchItem I = items[it];
+        const BatchGeomDev &g = G[I.geom];
+        if (I.type <= BI_NEAR1) {
+            const int n0 = I.a, n1 = min(I.a + g.tile, g.E.nwork_ctr);
+            for (int j = n0; j < n1; ++j) {
+                const int b = g.ctr_boxes[j];
+                const double2 *st = g.strm + I.b * g.sstride;
+                double2 *q = g.Qn + I.b * g.qstride;
+                if (I.type == BI_NEAR4) near_centres_multi_box<QQ, KERNEL, 4>(g.E, b, st, g.sstride, q, g.qstride, R, wsum, lt);
+                else if (I.type == BI_NEAR2) near_centres_multi_box<QQ, KERNEL, 2>(g.E, b, st, g.sstride, q, g.qstride, R, wsum, lt);
+                else near_centres_multi_box<QQ, KERNEL, 1>(g.E, b, st, g.sstride, q, g.qstride, R, wsum, lt);
+                __syncthreads();
+            }
+        } else if (I.type == BI_NEARPT) {
+            EvalView E = g.E;
+            E.qexp = g.qexp + I.b;
+            near_points_box<KERNEL>(E, g.pt_boxes[I.a], g.strm + I.b * g.sstride, g.potn + I.b * g.pstride, R, wsum,
+                                    lt);
+            __syncthreads();
+        } else {
+            if (threadIdx.x == 0) {
+                const volatile int *dv = done + I.geom;
+                const unsigned long long t0 = gqtc_globaltimer();
+                int ok = 1;
+                while (*dv < g.items) {
+                    if (*(volatile int *)err || gqtc_globaltimer() - t0 > limit_ns) {
+                        atomicExch(err, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __threadfence();
+                sok = ok;
+            }
+            __syncthreads();
+            const int t = I.a + threadIdx.x;
+            if (sok && t < g.nt)
+                final_target(t, g.kernel, g.E.Q, g.E.qc, g.kind, g.ctr, g.ctr_pos, g.tgt_ptpos, g.tgt_xy, g.tgt_on,
+                             g.base_n, g.E.sc_xy, g.E.sc_r, g.Qf + I.b * g.qstride, g.Qn + I.b * g.qstride,
+                             g.potf + I.b * g.pstride, g.potn + I.b * g.pstride, g.out + (size_t)I.b * g.nt);
+            continue;
+        }
+        // a direct item is done: every thread's writes are visible device-wide
+        // before the count moves
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(done + I.geom, 1);
+    }
 }
 
 }  // namespace
@@ -2209,10 +2353,14 @@ static EvalTables &get_tables(gq_geom *g) {
 }
 
 void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *stt,
-                 const double2 *qn_pre, const double *apply_identity) {
+                 const double2 *qn_pre, const double *apply_identity, const EvalFar *far) {
     // apply_identity != null: the operator at the base nodes (gq_apply); the
-    // point-target stages are skipped and out_dev has one value per base node
+    // point-target stages are skipped and out_dev has one value per base node.
+    // far != null: strengths and the FMM passes only, their parts of the QBX
+    // coefficients and point potentials written to far->Q, far->pot (the
+    // batched evaluation does the direct parts and the final sums itself).
     const bool at_base = apply_identity != nullptr;
+    const bool fmm_only = far != nullptr;
     gq_ctx *ctx = g->ctx;
     cudaStream_t st = ctx->stream;
     EvalTables &T = get_tables(g);
@@ -2243,6 +2391,8 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     g->Qn.alloc((size_t)g->nc * Q1);   // direct part
     g->pot.alloc(g->npt);
     g->potn.alloc(g->npt);
+    double2 *Qb = fmm_only ? far->Q : g->Q.p;      // after the allocations: the
+    double *potb = fmm_only ? far->pot : g->pot.p; // first call sets the pointers
     if (!g->s2) {
         GQ_CUDA(cudaStreamCreateWithFlags(&g->s2, cudaStreamNonBlocking));
         GQ_CUDA(cudaEventCreateWithFlags(&g->ev_str, cudaEventDisableTiming));
@@ -2351,13 +2501,13 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     // ---- Stages 3, 5a, 6a (direct interactions) on the second stream
     GQ_CUDA(cudaStreamWaitEvent(s2, g->ev_str, 0));
     mark(N_BEG, s2);
-    if (g->n_ctr_boxes) {
+    if (g->n_ctr_boxes && !fmm_only) {
         if (f32) dispatch_near_centres_f32(&ctx2, E, X, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
         else if (split) dispatch_near_centres_split(&ctx2, E, SX, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
         else if (!qn_pre) dispatch_near_centres(&ctx2, E, g->n_ctr_boxes, g->ctr_boxes, g->Qn.p);
     }
     mark(N_CTR, s2);
-    if (g->n_pt_boxes && !at_base) {
+    if (g->n_pt_boxes && !at_base && !fmm_only) {
         if (f32) {
             auto kd = k_near_points_f32<GQ_D>;
             auto ks = k_near_points_f32<GQ_S>;
@@ -2386,8 +2536,8 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         GQ_CUDA(cudaMemsetAsync(g->L2.p, 0, sizeof(float4) * g->nbox * P1, st));
     }
     GQ_CUDA(cudaMemsetAsync(g->L.p, 0, sizeof(double2) * g->nbox * P1, st));
-    GQ_CUDA(cudaMemsetAsync(g->Q.p, 0, sizeof(double2) * g->nc * Q1, st));
-    if (g->npt && !at_base) GQ_CUDA(cudaMemsetAsync(g->pot.p, 0, sizeof(double) * g->npt, st));
+    GQ_CUDA(cudaMemsetAsync(Qb, 0, sizeof(double2) * g->nc * Q1, st));
+    if (g->npt && !at_base) GQ_CUDA(cudaMemsetAsync(potb, 0, sizeof(double) * g->npt, st));
     // Stage 2 (in pairs wherever M2L runs in pairs: the multipoles then live in
     // M2 and the FP64 copy is made from them for the FP64 consumers)
     if (g->n_leaf_src) {
@@ -2469,32 +2619,32 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     mark(S_L2L, st);
     // Stage 5b
     if (g->nc && split_w) {
-        dispatch_w_centres_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, g->Q.p);
+        dispatch_w_centres_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, Qb);
     } else if (g->nc) {
-        dispatch_w_centres_q(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->M, g->Q.p);
+        dispatch_w_centres_q(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->M, Qb);
     }
     mark(S_WC, st);
     if (g->npt && !at_base) {
         if (f32)
             GQ_LAUNCH(ctx, k_w_points_f32, gq_blocks(g->npt, 128), 128, 0, E, X, g->npt, (const int *)g->pt_owner,
-                      g->pot.p);
+                      potb);
         else if (split_w)
             GQ_LAUNCH(ctx, k_w_points_split, gq_blocks(g->npt, 128), 128, 0, E, SX, g->npt, (const int *)g->pt_owner,
-                      g->pot.p);
+                      potb);
         else
             GQ_LAUNCH(ctx, k_w_points, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner,
-                      (const double2 *)g->M, g->pot.p);
+                      (const double2 *)g->M, potb);
     }
     mark(S_WP, st);
     // Stage 8
     if (g->nc)
         if (m2l_split)
-            dispatch_l2qbxl_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, (const float4 *)g->L2, g->Q.p);
+            dispatch_l2qbxl_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, (const float4 *)g->L2, Qb);
         else
-            dispatch_l2qbxl_t(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->L, g->Q.p);
+            dispatch_l2qbxl_t(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->L, Qb);
     if (g->npt && !at_base)
         GQ_LAUNCH(ctx, k_l2p, gq_blocks(g->npt, 128), 128, 0, E, g->npt, (const int *)g->pt_owner, (const double2 *)g->L,
-                  g->pot.p);
+                  potb);
     mark(S_L2Q, st);
     // join the direct part, then evaluate at the targets
     GQ_CUDA(cudaStreamWaitEvent(st, g->ev_near, 0));
@@ -2503,7 +2653,9 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     const bool use_pre = qn_pre && !f32 && !split;
     const double2 *qn_use = use_pre ? qn_pre : (const double2 *)g->Qn;
     g->qn_last = qn_use;
-    if (at_base) {
+    if (fmm_only) {
+        // the direct parts and the final sums are the caller's
+    } else if (at_base) {
         if (g->nbase)
             GQ_LAUNCH(ctx, k_final_base, gq_blocks(g->nbase, 256), 256, 0, g->nbase, kernel, Qn, E.qc,
                       (const int *)g->ctr_pos, (const double *)g->base_xy, (const double *)g->base_n,
@@ -2546,6 +2698,191 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     }
     g->have_eval = true;
     g->last_kernel = kernel;
+}
+
+// the evaluation views a batch item needs
+static void gq_batch_geom_view(gq_geom *g, int kernel, BatchGeomDev &out) {
+    EvalTables &T = get_tables(g);
+    EvalView E{};
+    E.R = g->root;
+    E.P = g->prm.p_fmm;
+    E.Q = g->prm.p_qbx;
+    E.kernel = kernel == GQ_SP ? GQ_S : kernel;
+    E.blev = g->blev; E.bix = g->bix; E.biy = g->biy; E.bparent = g->bparent; E.bchild = g->bchild;
+    E.src_beg = g->src_beg; E.src_end = g->src_end;
+    E.ctr_beg = g->ctr_beg; E.ctr_end = g->ctr_end; E.pt_beg = g->pt_beg; E.pt_end = g->pt_end;
+    E.sub_src = g->sub_src; E.sub_tgt = g->sub_tgt;
+    E.s_xy = g->s_xy; E.sc_xy = g->sc_xy; E.sc_r = g->sc_r; E.sp_xy = g->sp_xy;
+    for (int i = 0; i < 6; ++i) { E.loff[i] = g->list_off[i]; E.lidx[i] = g->list_idx[i]; }
+    E.binom = T.binom;
+    E.qc = g->has_qc ? (const int *)g->q_ctr.p : nullptr;
+    E.logt = T.logt;
+    E.nwork_ctr = g->n_ctr_boxes;
+    out.E = E;
+    out.ctr_boxes = g->ctr_boxes;
+    out.pt_boxes = g->pt_boxes;
+    out.kernel = kernel;
+    out.nt = g->nt;
+    out.kind = g->t_kind;
+    out.ctr = g->t_ctr;
+    out.ctr_pos = g->ctr_pos;
+    out.tgt_ptpos = T.tgt_ptpos;
+    out.tgt_on = g->tgt_on;
+    out.tgt_xy = g->tgt_xy;
+    out.base_n = g->base_n;
+}
+
+// ------------------------------------------------------------------ persistent batch plan
+struct gq_bplan {
+    gq_ctx *ctx = nullptr;
+    int kernel = 0, ndens = 0, q = 0, tile = 1;
+    std::vector<gq_geom *> geoms;
+    std::vector<const double *> dens;
+    std::vector<double *> out;
+    std::vector<std::unique_ptr<dbuf<double2>>> strm, Qn, Qf;
+    std::vector<std::unique_ptr<dbuf<double>>> potn, potf;
+    std::vector<std::unique_ptr<dbuf<unsigned int>>> qexp;
+    dbuf<BatchGeomDev> G;
+    dbuf<BatchItem> items;
+    int nitems = 0;
+    dbuf<int> next, done, err;
+    const double *logt = nullptr;
+};
+
+bool gq_bplan_supported(const std::vector<gq_geom *> &geoms, int kernel) {
+    if (geoms.empty() || (kernel != GQ_S && kernel != GQ_D && kernel != GQ_SP)) return false;
+    const int q = geoms[0]->prm.p_qbx;
+    if (q != 5 && q != 8) return false;
+    for (auto *g : geoms)
+        if (g->prm.precision != GQ_PREC_FP64 || g->prm.p_qbx != q || !g->built) return false;
+    return true;
+}
+
+// Buffers, device descriptors and the item list for `kernel` and `ndens`
+// densities of every geometry; tile target boxes per direct item.  The
+// geometries' evaluation tables must exist (an eager evaluation has run).
+// stall_geom >= 0 makes that geometry's final items wait for one item more
+// than exist (a test of the bounded wait).
+gq_bplan *gq_bplan_new(gq_ctx *ctx, int kernel, int ndens, const std::vector<gq_geom *> &geoms,
+                       const double *const *dens, double *const *out, int tile, int stall_geom) {
+    std::unique_ptr<gq_bplan> P(new gq_bplan);
+    P->ctx = ctx;
+    P->kernel = kernel;
+    P->ndens = ndens;
+    P->q = geoms[0]->prm.p_qbx;
+    P->tile = tile;
+    P->geoms = geoms;
+    P->dens.assign(dens, dens + geoms.size());
+    P->out.assign(out, out + geoms.size());
+    const int Q1 = P->q + 1;
+    std::vector<BatchGeomDev> hG(geoms.size());
+    std::vector<BatchItem> near, fin;
+    for (size_t i = 0; i < geoms.size(); ++i) {
+        gq_geom *g = geoms[i];
+        P->strm.emplace_back(new dbuf<double2>);
+        P->Qn.emplace_back(new dbuf<double2>);
+        P->Qf.emplace_back(new dbuf<double2>);
+        P->potn.emplace_back(new dbuf<double>);
+        P->potf.emplace_back(new dbuf<double>);
+        P->qexp.emplace_back(new dbuf<unsigned int>);
+        const long long ss = g->nsrc, qs = (long long)g->nc * Q1, ps = g->npt > 0 ? g->npt : 1;
+        P->strm[i]->alloc((size_t)ndens * ss);
+        P->Qn[i]->alloc((size_t)ndens * qs);
+        P->Qf[i]->alloc((size_t)ndens * qs);
+        P->potn[i]->alloc((size_t)ndens * ps);
+        P->potf[i]->alloc((size_t)ndens * ps);
+        P->qexp[i]->alloc(ndens);
+        BatchGeomDev &G = hG[i];
+        gq_batch_geom_view(g, kernel, G);
+        if (i == 0) P->logt = G.E.logt;
+        G.tile = tile;
+        G.strm = P->strm[i]->p;
+        G.sstride = ss;
+        G.Qn = P->Qn[i]->p;
+        G.Qf = P->Qf[i]->p;
+        G.qstride = qs;
+        G.potn = P->potn[i]->p;
+        G.potf = P->potf[i]->p;
+        G.pstride = ps;
+        G.qexp = P->qexp[i]->p;
+        G.out = out[i];
+        int items = 0;
+        for (int j = 0; j < g->n_ctr_boxes; j += tile) {
+            int d0 = 0;
+            for (; d0 + 4 <= ndens; d0 += 4, ++items) near.push_back({BI_NEAR4, (int)i, j, d0});
+            for (; d0 + 2 <= ndens; d0 += 2, ++items) near.push_back({BI_NEAR2, (int)i, j, d0});
+            for (; d0 < ndens; ++d0, ++items) near.push_back({BI_NEAR1, (int)i, j, d0});
+        }
+        for (int j = 0; j < g->n_pt_boxes; ++j)
+            for (int d = 0; d < ndens; ++d, ++items) near.push_back({BI_NEARPT, (int)i, j, d});
+        for (int d = 0; d < ndens; ++d)
+            for (int t = 0; t < g->nt; t += kNearThreads) fin.push_back({BI_FINAL, (int)i, t, d});
+        G.items = items + ((int)i == stall_geom ? 1 : 0);
+    }
+    std::vector<BatchItem> all(near);
+    all.insert(all.end(), fin.begin(), fin.end());   // every direct item before every final item
+    P->nitems = (int)all.size();
+    P->G.alloc(hG.size());
+    P->items.alloc(all.size());
+    P->next.alloc(1);
+    P->done.alloc(geoms.size());
+    P->err.alloc(1);
+    cudaStream_t st = ctx->stream;
+    GQ_CUDA(cudaMemcpyAsync(P->G.p, hG.data(), sizeof(BatchGeomDev) * hG.size(), cudaMemcpyHostToDevice, st));
+    if (!all.empty())
+        GQ_CUDA(cudaMemcpyAsync(P->items.p, all.data(), sizeof(BatchItem) * all.size(), cudaMemcpyHostToDevice, st));
+    GQ_CUDA(cudaMemsetAsync(P->err.p, 0, sizeof(int), st));
+    GQ_CUDA(cudaStreamSynchronize(st));
+    return P.release();
+}
+
+void gq_bplan_free(gq_bplan *P) { delete P; }
+
+// Record geometry i's evaluations without their direct parts: strengths and
+// the FMM passes of every density into the plan's far buffers (on g->ctx).
+void gq_bplan_fmm(gq_bplan *P, int i) {
+    gq_geom *g = P->geoms[i];
+    const int Q1 = P->q + 1;
+    cudaStream_t st = g->ctx->stream;
+    for (int d = 0; d < P->ndens; ++d) {
+        EvalFar far{P->Qf[i]->p + (size_t)d * g->nc * Q1, P->potf[i]->p + (size_t)d * (g->npt > 0 ? g->npt : 1)};
+        gq_eval_all(g, P->kernel, P->dens[i] + (size_t)d * g->nbase, nullptr, nullptr, nullptr, nullptr, &far);
+        if (g->nsrc)
+            GQ_CUDA(cudaMemcpyAsync(P->strm[i]->p + (size_t)d * g->nsrc, g->strength.p, sizeof(double2) * g->nsrc,
+                                    cudaMemcpyDeviceToDevice, st));
+        GQ_CUDA(cudaMemcpyAsync(P->qexp[i]->p + d, g->qexp.p, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
+    }
+}
+
+// Record the persistent launch (counters cleared first) on ctx's stream.
+void gq_bplan_persistent(gq_bplan *P, gq_ctx *ctx, int grid, unsigned long long limit_ns) {
+    cudaStream_t st = ctx->stream;
+    GQ_CUDA(cudaMemsetAsync(P->next.p, 0, sizeof(int), st));
+    GQ_CUDA(cudaMemsetAsync(P->done.p, 0, sizeof(int) * P->geoms.size(), st));
+    const int kin = P->kernel == GQ_SP ? GQ_S : P->kernel;
+#define GQ_BP(QV)                                                                                                 \
+    if (P->q == QV) {                                                                                             \
+        auto ks = k_batch_persistent<QV, GQ_S>;                                                                   \
+        auto kd = k_batch_persistent<QV, GQ_D>;                                                                   \
+        GQ_LAUNCH(ctx, (kin == GQ_D ? kd : ks), grid, kNearThreads, 0, (const BatchGeomDev *)P->G.p,             \
+                  (const BatchItem *)P->items.p, P->nitems, P->logt, P->next.p, P->done.p, limit_ns, P->err.p);   \
+        return;                                                                                                   \
+    }
+    GQ_BP(5)
+    GQ_BP(8)
+#undef GQ_BP
+    throw gq_error{GQ_ERR_UNSUPPORTED, "persistent batch: p_qbx not compiled"};
+}
+
+// the device error word (synchronises): nonzero when a bounded wait gave up;
+// cleared by the read
+int gq_bplan_error(gq_bplan *P) {
+    int h = 0;
+    cudaStream_t st = P->ctx->stream;
+    GQ_CUDA(cudaMemcpyAsync(&h, P->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GQ_CUDA(cudaMemsetAsync(P->err.p, 0, sizeof(int), st));
+    GQ_CUDA(cudaStreamSynchronize(st));
+    return h;
 }
 
 // Several densities on one geometry: the direct part of the QBX coefficients

@@ -210,14 +210,30 @@ void gq_build_lists(gq_geom *g);               // gq_lists.cu
 // restriction (a box two levels deeper touches them) and own a particle
 // eligible for children (belig[b] > 0); synchronises the stream.
 void gq_balance_violations(gq_geom *g, const int *belig, std::vector<uint64_t> &out);
+// far parts of one evaluation for the batched path (see gq_eval_all)
+struct EvalFar {
+    double2 *Q;     // [nc][p_qbx+1] QBX coefficients from List 3 far and the box locals
+    double *pot;    // [npt] point potentials from List 3 far and the box locals
+};
 void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev, gq_stats *st,
-                 const double2 *qn_pre = nullptr, const double *apply_identity = nullptr);  // gq_fmm.cu
+                 const double2 *qn_pre = nullptr, const double *apply_identity = nullptr,
+                 const EvalFar *far = nullptr);                                            // gq_fmm.cu
 void gq_eval_multi(gq_geom *g, int kernel, int nd, const double *const *dens, double *const *out);
 void gq_export_qbx_impl(gq_geom *g, double *host);  // gq_fmm.cu
 double gq_probe_fma(gq_ctx *ctx, int what);         // gq_probe.cu
 void gq_probe_math_impl(gq_ctx *ctx, int fn, int n, const double *x_dev, double *y_dev);
 void gq_probe_umma_impl(gq_ctx *ctx, int K, const uint16_t *A_host, const uint16_t *B_host, int swap, float *D_host);
 void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double *out_dev);  // gq_fmm.cu
+// persistent batched evaluation (gq_fmm.cu): direct parts and final sums of
+// all geometries and densities in one launch after per-geometry FMM passes
+struct gq_bplan;
+bool gq_bplan_supported(const std::vector<gq_geom *> &geoms, int kernel);
+gq_bplan *gq_bplan_new(gq_ctx *ctx, int kernel, int ndens, const std::vector<gq_geom *> &geoms,
+                       const double *const *dens, double *const *out, int tile, int stall_geom);
+void gq_bplan_free(gq_bplan *P);
+void gq_bplan_fmm(gq_bplan *P, int i);
+void gq_bplan_persistent(gq_bplan *P, gq_ctx *ctx, int grid, unsigned long long limit_ns);
+int gq_bplan_error(gq_bplan *P);
 bool gq_m2l_tc_supported(const gq_geom *g);                                                  // gq_m2l_tc.cu
 void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L);
 void gq_m2l_tc_build(gq_geom *g);
@@ -241,6 +257,8 @@ gq_batch *gq_batch_new(gq_ctx *ctx, int n, gq_geom *const *geoms);              
 void gq_batch_free(gq_batch *b);
 void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out);
 int gq_batch_streams(const gq_batch *b);
+void gq_batch_config_impl(gq_batch *b, int mode, long long wait_ns, int stall_geom);
+int gq_batch_persistent_tile(const gq_batch *b);
 gq_ctx *gq_batch_ctx(const gq_batch *b);
 int gq_batch_size(const gq_batch *b);
 gq_geom *gq_batch_geom(const gq_batch *b, int i);
