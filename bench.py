@@ -342,6 +342,9 @@ def run_batched(args, dev, stream):
             t.append(e0.elapsed_time(e1))
         return statistics.mean(t)
 
+    res["auto"] = timed3(lambda: b.eval(kern, dens, outs))
+    auto_pick = "persistent" if b.persistent_tile() > 0 else "graph"
+    b.mode(0)
     res["persistent"] = timed3(lambda: b.eval(kern, dens, outs))
     tile, streams = b.persistent_tile(), b.streams()
     b.mode(1)
@@ -397,7 +400,9 @@ def run_batched(args, dev, stream):
         geo.close()
     return {"workload": f"{len(items)} starfish arrays, {min(nsrc)}-{max(nsrc)} quadrature nodes "
                         f"(log-uniform), {dens[0].shape[0]} densities each, p_qbx 8, p_fmm 15, {kern}",
-            "targets_x_densities": ntot, "persistent_ms": res["persistent"], "graph_ms": res["graph"],
+            "targets_x_densities": ntot, "auto_ms": res["auto"], "auto_pick": auto_pick,
+            "auto_targets_per_s": ntot / (res["auto"] * 1e-3),
+            "persistent_ms": res["persistent"], "graph_ms": res["graph"],
             "sequential_ms": res["sequential"],
             "persistent_targets_per_s": ntot / (res["persistent"] * 1e-3),
             "graph_targets_per_s": ntot / (res["graph"] * 1e-3),

@@ -358,7 +358,8 @@ class Batch:
         return outs
 
     def mode(self, mode):
-        """0: persistent launch where supported (default), 1: graph branches only."""
+        """0: persistent launch where supported, 1: graph branches only,
+        2 (default): whichever of the two the autotuner measures faster."""
         st = self.L.gq_batch_mode(self._b, int(mode))
         if st != 0:
             raise GigaQBXError(st, self.L.gq_last_error(self._ctx).decode())

@@ -428,7 +428,7 @@ gq_status gq_batch_streams(const gq_batch *b, int *streams) {
 }
 
 gq_status gq_batch_mode(gq_batch *b, int mode) {
-    if (!b || (mode != 0 && mode != 1)) return GQ_ERR_INVALID;
+    if (!b || mode < 0 || mode > 2) return GQ_ERR_INVALID;
     return guarded(gq_batch_ctx(b), [&] { gq_batch_config_impl(b, mode, 0, -1); });
 }
 

@@ -34,14 +34,14 @@ struct gq_batch {
     int64_t kernels_per_replay = 0;
     // persistent path: the direct parts and final sums of all geometries and
     // densities in one launch after the per-geometry FMM branches
-    int mode = 0;                          // 0: persistent where supported, 1: graph branches only
+    int mode = 2;                          // 0: persistent where supported, 1: graph branches, 2: the faster
     bool persistent = false;               // the captured graph uses the persistent launch
     int tile = 1;                          // target boxes per direct item (tuned)
     unsigned long long wait_ns = 1000000000ull;   // bound of each dependency wait
     int stall_geom = -1;                   // test hook: that geometry's final items can never start
-    std::map<int, gq_bplan *> plans;       // per tile
+    gq_bplan *plan = nullptr;              // buffers and items of the persistent launch
     ~gq_batch() {
-        for (auto &kv : plans) gq_bplan_free(kv.second);
+        if (plan) gq_bplan_free(plan);
     }
 };
 
@@ -239,11 +239,11 @@ cudaGraphExec_t capture_persistent(gq_batch *b, gq_bplan *P, int S, int64_t *ker
 }
 
 gq_bplan *plan_for(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out, int tile) {
-    auto it = b->plans.find(tile);
-    if (it != b->plans.end()) return it->second;
-    gq_bplan *P = gq_bplan_new(b->ctx, kernel, ndens, b->geoms, dens, out, tile, b->stall_geom);
-    b->plans[tile] = P;
-    return P;
+    if (!b->plan)
+        b->plan = gq_bplan_new(b->ctx, kernel, ndens, b->geoms, dens, out, tile, b->stall_geom);
+    else if (gq_bplan_tile(b->plan) != tile)
+        gq_bplan_retile(b->plan, tile);
+    return b->plan;
 }
 
 double time_replays(gq_batch *b, cudaGraphExec_t exec) {
@@ -280,8 +280,8 @@ void gq_batch_free(gq_batch *b) {
 static void drop_capture(gq_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
-    for (auto &kv : b->plans) gq_bplan_free(kv.second);
-    b->plans.clear();
+    if (b->plan) gq_bplan_free(b->plan);
+    b->plan = nullptr;
 }
 
 void gq_batch_config_impl(gq_batch *b, int mode, long long wait_ns, int stall_geom) {
@@ -309,52 +309,82 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
             g->ctx = saved;
         }
         GQ_CUDA(cudaStreamSynchronize(ctx->stream));
-        b->persistent = b->mode == 0 && gq_bplan_supported(b->geoms, kernel);
-        std::string key = (b->persistent ? "P" : "") + shape_key(b, kernel, ndens);
+        // candidates: the persistent launch (mode 0, or mode 2 where supported)
+        // and the graph branches (mode 1, mode 2, or where the persistent
+        // launch is not supported)
+        const bool can_p = b->mode != 1 && gq_bplan_supported(b->geoms, kernel);
+        const bool try_g = b->mode != 0 || !can_p;
+        std::string key = std::string(b->mode == 2 ? "A" : (can_p ? "P" : "")) + shape_key(b, kernel, ndens);
         int S = 0, tile = 1;
+        bool pers = can_p && !try_g;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             if (g_tune.empty()) load_cache_file();
             auto it = g_tune.find(key);
             if (it != g_tune.end()) {
                 S = it->second % 100;
-                tile = b->persistent ? it->second / 100 : 1;
+                tile = (it->second / 100) % 100;
+                pers = can_p && (!try_g || (it->second / 10000) == 1);
             }
         }
-        auto time_config = [&](int streams, int t) {
+        auto time_config = [&](bool p, int streams, int t) {
             int64_t kn = 0;
-            cudaGraphExec_t ex = b->persistent
-                                     ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, t), streams, &kn)
-                                     : capture(b, kernel, ndens, dens, out, streams, &kn);
+            cudaGraphExec_t ex = p ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, t), streams, &kn)
+                                   : capture(b, kernel, ndens, dens, out, streams, &kn);
             double ms = time_replays(b, ex);
             cudaGraphExecDestroy(ex);
             return ms;
         };
         if (S <= 0 || tile <= 0) {
-            // streams for the per-geometry branches first, then (persistent
-            // path) the target boxes per direct item with those streams
+            // per path: streams for the per-geometry branches first, then (the
+            // persistent launch) the target boxes per direct item with those
+            // streams; the faster path wins
             double best = 1e300;
-            tile = 1;
-            for (int cand : {1, 2, 4, 8, 16}) {
-                if (cand > (int)n && cand != 1) break;
-                double ms = time_config(cand, 1);
-                if (ms < best) {
-                    best = ms;
-                    S = cand;
-                }
-            }
-            if (b->persistent)
-                for (int t : {2, 4}) {
-                    double ms = time_config(S, t);
-                    if (ms < best) {
-                        best = ms;
-                        tile = t;
+            for (int path = 0; path < 2; ++path) {
+                const bool p = path == 0;
+                if (p ? !can_p : !try_g) continue;
+                double pbest = 1e300;
+                int pS = 1, pt = 1;
+                for (int cand : {1, 2, 4, 8, 16}) {
+                    if (cand > (int)n && cand != 1) break;
+                    double ms = time_config(p, cand, 1);
+                    if (ms < pbest) {
+                        pbest = ms;
+                        pS = cand;
                     }
                 }
+                if (p)
+                    for (int t : {2, 4}) {
+                        double ms = time_config(p, pS, t);
+                        if (ms < pbest) {
+                            pbest = ms;
+                            pt = t;
+                        }
+                    }
+                {   // each path's winner also serves a later call in mode 0 or 1
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    g_tune[std::string(p ? "P" : "") + shape_key(b, kernel, ndens)] = (p ? 10000 : 0) + pt * 100 + pS;
+                }
+                if (pbest < best) {
+                    best = pbest;
+                    S = pS;
+                    tile = pt;
+                    pers = p;
+                }
+            }
             b->tuned_ms = best;
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tune[key] = tile * 100 + S;
+            g_tune[key] = (pers ? 10000 : 0) + tile * 100 + S;
             save_cache_file();
+        }
+        b->persistent = pers;
+        if (b->plan) {   // the tuning replays of the persistent launch ran its waits
+            const int e = gq_bplan_error(b->plan);
+            if (!pers) {
+                gq_bplan_free(b->plan);
+                b->plan = nullptr;
+            }
+            GQ_REQUIRE(e == 0, GQ_ERR_TIMEOUT, "batched evaluation: a bounded dependency wait gave up");
         }
         b->exec = b->persistent ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, tile), S,
                                                      &b->kernels_per_replay)
@@ -365,16 +395,11 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
         b->streams = S;
         b->dens.assign(dens, dens + n);
         b->out.assign(out, out + n);
-        if (b->persistent) {   // the tuning replays ran the dependency waits too
-            for (auto &kv : b->plans)
-                GQ_REQUIRE(gq_bplan_error(kv.second) == 0, GQ_ERR_TIMEOUT,
-                           "batched evaluation: a bounded dependency wait gave up");
-        }
     }
     GQ_CUDA(cudaGraphLaunch(b->exec, ctx->stream));
     ctx->launches += b->kernels_per_replay;
     if (b->persistent)
-        GQ_REQUIRE(gq_bplan_error(b->plans[b->tile]) == 0, GQ_ERR_TIMEOUT,
+        GQ_REQUIRE(gq_bplan_error(b->plan) == 0, GQ_ERR_TIMEOUT,
                    "batched evaluation: a bounded dependency wait gave up");
 }
 

@@ -2735,8 +2735,9 @@ static void gq_batch_geom_view(gq_geom *g, int kernel, BatchGeomDev &out) {
 // ------------------------------------------------------------------ persistent batch plan
 struct gq_bplan {
     gq_ctx *ctx = nullptr;
-    int kernel = 0, ndens = 0, q = 0, tile = 1;
+    int kernel = 0, ndens = 0, q = 0, tile = 1, stall_geom = -1;
     std::vector<gq_geom *> geoms;
+    std::vector<BatchGeomDev> hG;
     std::vector<const double *> dens;
     std::vector<double *> out;
     std::vector<std::unique_ptr<dbuf<double2>>> strm, Qn, Qf;
@@ -2758,11 +2759,45 @@ bool gq_bplan_supported(const std::vector<gq_geom *> &geoms, int kernel) {
     return true;
 }
 
-// Buffers, device descriptors and the item list for `kernel` and `ndens`
-// densities of every geometry; tile target boxes per direct item.  The
-// geometries' evaluation tables must exist (an eager evaluation has run).
-// stall_geom >= 0 makes that geometry's final items wait for one item more
-// than exist (a test of the bounded wait).
+// The item list for `tile` target boxes per direct item (uploaded; the
+// stream is synchronised, so no launch reads the old list afterwards).
+// Every direct item precedes every final item.
+void gq_bplan_retile(gq_bplan *P, int tile) {
+    std::vector<BatchItem> near, fin;
+    for (size_t i = 0; i < P->geoms.size(); ++i) {
+        gq_geom *g = P->geoms[i];
+        int items = 0;
+        for (int j = 0; j < g->n_ctr_boxes; j += tile) {
+            int d0 = 0;
+            for (; d0 + 4 <= P->ndens; d0 += 4, ++items) near.push_back({BI_NEAR4, (int)i, j, d0});
+            for (; d0 + 2 <= P->ndens; d0 += 2, ++items) near.push_back({BI_NEAR2, (int)i, j, d0});
+            for (; d0 < P->ndens; ++d0, ++items) near.push_back({BI_NEAR1, (int)i, j, d0});
+        }
+        for (int j = 0; j < g->n_pt_boxes; ++j)
+            for (int d = 0; d < P->ndens; ++d, ++items) near.push_back({BI_NEARPT, (int)i, j, d});
+        for (int d = 0; d < P->ndens; ++d)
+            for (int t = 0; t < g->nt; t += kNearThreads) fin.push_back({BI_FINAL, (int)i, t, d});
+        P->hG[i].tile = tile;
+        P->hG[i].items = items + ((int)i == P->stall_geom ? 1 : 0);
+    }
+    std::vector<BatchItem> all(near);
+    all.insert(all.end(), fin.begin(), fin.end());
+    P->tile = tile;
+    P->nitems = (int)all.size();
+    P->items.alloc(all.size());
+    cudaStream_t st = P->ctx->stream;
+    GQ_CUDA(cudaStreamSynchronize(st));
+    GQ_CUDA(cudaMemcpyAsync(P->G.p, P->hG.data(), sizeof(BatchGeomDev) * P->hG.size(), cudaMemcpyHostToDevice, st));
+    if (!all.empty())
+        GQ_CUDA(cudaMemcpyAsync(P->items.p, all.data(), sizeof(BatchItem) * all.size(), cudaMemcpyHostToDevice, st));
+    GQ_CUDA(cudaStreamSynchronize(st));
+}
+
+// Buffers and device descriptors for `kernel` and `ndens` densities of every
+// geometry, and the item list for `tile`.  The geometries' evaluation tables
+// must exist (an eager evaluation has run).  stall_geom >= 0 makes that
+// geometry's final items wait for one item more than exist (a test of the
+// bounded wait).
 gq_bplan *gq_bplan_new(gq_ctx *ctx, int kernel, int ndens, const std::vector<gq_geom *> &geoms,
                        const double *const *dens, double *const *out, int tile, int stall_geom) {
     std::unique_ptr<gq_bplan> P(new gq_bplan);
@@ -2770,13 +2805,12 @@ gq_bplan *gq_bplan_new(gq_ctx *ctx, int kernel, int ndens, const std::vector<gq_
     P->kernel = kernel;
     P->ndens = ndens;
     P->q = geoms[0]->prm.p_qbx;
-    P->tile = tile;
+    P->stall_geom = stall_geom;
     P->geoms = geoms;
     P->dens.assign(dens, dens + geoms.size());
     P->out.assign(out, out + geoms.size());
     const int Q1 = P->q + 1;
-    std::vector<BatchGeomDev> hG(geoms.size());
-    std::vector<BatchItem> near, fin;
+    P->hG.resize(geoms.size());
     for (size_t i = 0; i < geoms.size(); ++i) {
         gq_geom *g = geoms[i];
         P->strm.emplace_back(new dbuf<double2>);
@@ -2792,10 +2826,9 @@ gq_bplan *gq_bplan_new(gq_ctx *ctx, int kernel, int ndens, const std::vector<gq_
         P->potn[i]->alloc((size_t)ndens * ps);
         P->potf[i]->alloc((size_t)ndens * ps);
         P->qexp[i]->alloc(ndens);
-        BatchGeomDev &G = hG[i];
+        BatchGeomDev &G = P->hG[i];
         gq_batch_geom_view(g, kernel, G);
         if (i == 0) P->logt = G.E.logt;
-        G.tile = tile;
         G.strm = P->strm[i]->p;
         G.sstride = ss;
         G.Qn = P->Qn[i]->p;
@@ -2806,35 +2839,17 @@ gq_bplan *gq_bplan_new(gq_ctx *ctx, int kernel, int ndens, const std::vector<gq_
         G.pstride = ps;
         G.qexp = P->qexp[i]->p;
         G.out = out[i];
-        int items = 0;
-        for (int j = 0; j < g->n_ctr_boxes; j += tile) {
-            int d0 = 0;
-            for (; d0 + 4 <= ndens; d0 += 4, ++items) near.push_back({BI_NEAR4, (int)i, j, d0});
-            for (; d0 + 2 <= ndens; d0 += 2, ++items) near.push_back({BI_NEAR2, (int)i, j, d0});
-            for (; d0 < ndens; ++d0, ++items) near.push_back({BI_NEAR1, (int)i, j, d0});
-        }
-        for (int j = 0; j < g->n_pt_boxes; ++j)
-            for (int d = 0; d < ndens; ++d, ++items) near.push_back({BI_NEARPT, (int)i, j, d});
-        for (int d = 0; d < ndens; ++d)
-            for (int t = 0; t < g->nt; t += kNearThreads) fin.push_back({BI_FINAL, (int)i, t, d});
-        G.items = items + ((int)i == stall_geom ? 1 : 0);
     }
-    std::vector<BatchItem> all(near);
-    all.insert(all.end(), fin.begin(), fin.end());   // every direct item before every final item
-    P->nitems = (int)all.size();
-    P->G.alloc(hG.size());
-    P->items.alloc(all.size());
+    P->G.alloc(P->hG.size());
     P->next.alloc(1);
     P->done.alloc(geoms.size());
     P->err.alloc(1);
-    cudaStream_t st = ctx->stream;
-    GQ_CUDA(cudaMemcpyAsync(P->G.p, hG.data(), sizeof(BatchGeomDev) * hG.size(), cudaMemcpyHostToDevice, st));
-    if (!all.empty())
-        GQ_CUDA(cudaMemcpyAsync(P->items.p, all.data(), sizeof(BatchItem) * all.size(), cudaMemcpyHostToDevice, st));
-    GQ_CUDA(cudaMemsetAsync(P->err.p, 0, sizeof(int), st));
-    GQ_CUDA(cudaStreamSynchronize(st));
+    GQ_CUDA(cudaMemsetAsync(P->err.p, 0, sizeof(int), ctx->stream));
+    gq_bplan_retile(P.get(), tile);
     return P.release();
 }
+
+int gq_bplan_tile(const gq_bplan *P) { return P->tile; }
 
 void gq_bplan_free(gq_bplan *P) { delete P; }
 

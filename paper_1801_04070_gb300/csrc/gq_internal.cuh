@@ -231,6 +231,8 @@ bool gq_bplan_supported(const std::vector<gq_geom *> &geoms, int kernel);
 gq_bplan *gq_bplan_new(gq_ctx *ctx, int kernel, int ndens, const std::vector<gq_geom *> &geoms,
                        const double *const *dens, double *const *out, int tile, int stall_geom);
 void gq_bplan_free(gq_bplan *P);
+void gq_bplan_retile(gq_bplan *P, int tile);
+int gq_bplan_tile(const gq_bplan *P);
 void gq_bplan_fmm(gq_bplan *P, int i);
 void gq_bplan_persistent(gq_bplan *P, gq_ctx *ctx, int grid, unsigned long long limit_ns);
 int gq_bplan_error(gq_bplan *P);

@@ -72,6 +72,7 @@ def test_stalled_wait_times_out_and_recovers():
     torch, Batch, gs, geos, dens, outs = _setup(5, 2, seed=3)
     from paper_1801_04070_gb300 import GigaQBXError
     b = Batch(geos)
+    b.mode(0)
     b.eval("S", dens, outs)
     torch.cuda.synchronize()
     ref = [o.clone() for o in outs]
@@ -90,4 +91,22 @@ def test_stalled_wait_times_out_and_recovers():
     torch.cuda.synchronize()
     for a, c in zip(outs, ref):
         assert torch.equal(a, c)
+    b.close()
+
+
+def test_default_mode_takes_the_faster_path():
+    """The default mode times the persistent launch and the graph branches and
+    keeps one of them; its results agree with both to 1e-12."""
+    torch, Batch, gs, geos, dens, outs = _setup(8, 2, seed=5)
+    b = Batch(geos)
+    b.eval("D", dens, outs)
+    torch.cuda.synchronize()
+    auto = [o.clone() for o in outs]
+    assert b.persistent_tile() in (0, 1, 2, 4)
+    for m in (0, 1):
+        b.mode(m)
+        b.eval("D", dens, outs)
+        torch.cuda.synchronize()
+        for a, c in zip(auto, outs):
+            assert (a - c).abs().max().item() <= 1e-12 * c.abs().max().item(), m
     b.close()
