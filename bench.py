@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false",
                     help="skip the FP64 vs MIXED evaluation sweep at eps = 1e-4 ... 1e-12 (orders from eps)")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="skip the learned order selection (training on the oracle labels, deployment at eps 1e-8)")
+    ap.add_argument("--learned-curves", type=int, default=2000,
+                    help="training curves (of tests/golden/order_labels.npz) for the learned order selection")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64 geometries of uneven size (2k-200k quadrature nodes, log-uniform) x 8 "
                          "densities: the persistent launch and the graph branches against one gq_eval after "
@@ -411,6 +415,126 @@ def run_batched(args, dev, stream):
             "max_rel_diff_vs_sequential": diff, "gmres": gmres}
 
 
+# ---------------------------------------------------------------- learned order selection
+LABELS = os.path.join(ROOT, "tests", "golden", "order_labels.npz")
+LEARNED_EPS = 1e-8
+
+
+def order_labels():
+    """Oracle labels of the order-selection training set (written by
+    tests/golden/make_order_labels.py): [n_centres, 2] float32 and metadata."""
+    with np.load(LABELS) as f:
+        meta = json.loads(str(f["meta"]))
+        y = -f["codes"].astype(np.float32) / meta["codes_per_decade"]
+    return y, meta
+
+
+def run_learned(args, dev, g, flush):
+    """Train the order-selection network on the oracle labels (features on the
+    GPU, one geometry per training curve), then evaluate the workload at eps =
+    1e-8 with the bound-driven orders, the learned FMM order (one p_fmm for
+    the tree, the bound-driven order as cap and fallback; p_qbx from eps), the
+    same with the mixed-precision tier of that eps, and per-centre learned
+    QBX orders on top (the labels are one-sided truncation errors at the
+    centre's base node, which overstate the two-sided on-surface error, so
+    these orders are conservative).  Returns
+    the report and, per mode, the outputs at a sample of targets of each kind
+    (the CPU leg compares them with the oracle's direct QBX)."""
+    import workloads
+    from paper_1801_04070_gb300 import MLP, Geometry, params_default
+    y, meta = order_labels()
+    per = int(meta["centres_per_curve"])
+    ncur = min(args.learned_curves, int(meta["n_curves"]))
+    curves = workloads.order_training_curves(int(meta["n_curves"]), int(meta["curve_seed"]))
+    t0 = time.perf_counter()
+    X = []
+    for i in range(ncur):
+        gi = workloads.order_training_problem(curves[i], i)
+        geo = Geometry(gi, params_default(p_qbx=int(meta["q_ref"]), p_fmm=int(meta["p_ref"]), n_max=32),
+                       device=dev.index)
+        geo.build()
+        X.append(geo.features())
+        geo.close()
+    t_feat = time.perf_counter() - t0
+    hold = max(1, ncur // 20)
+    ntr = ncur - hold
+    Xtr = np.concatenate(X[:ntr]).astype(np.float32)
+    Ytr = y[:ntr * per]
+    Xs = X[ntr:]
+    Ys = [y[i * per:(i + 1) * per] for i in range(ntr, ncur)]
+    geo0 = Geometry(workloads.order_training_problem(curves[0], 0), device=dev.index)
+    m = MLP(geo0, seed=7)
+    t0 = time.perf_counter()
+    epochs = 20
+    loss = m.train(Xtr, Ytr, epochs=epochs, batch=1024, lr=1e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    Xv, Yv = np.concatenate(Xs), np.concatenate(Ys)
+    pv = m.predict(Xv)
+    r2 = [float(1 - ((pv[:, k] - Yv[:, k]) ** 2).mean() / Yv[:, k].var()) for k in (0, 1)]
+    # margins from the held-out curves: the upper tail of the QBX residuals (per
+    # centre); for the one FMM order, the largest excess of a curve's worst
+    # measured error over its worst prediction
+    margin_q = float(np.quantile(Yv[:, 0] - pv[:, 0], 0.995)) + 0.25
+    margin_f = max(float(yy[:, 1].max() - m.predict(xx)[:, 1].max()) for xx, yy in zip(Xs, Ys)) + 0.5
+
+    nt = len(g["tgt_xy"])
+    rng = np.random.default_rng(12)
+    modes = {}
+    sample = {}
+    mask = None
+    for mode in ("bound", "learned", "learned+mixed", "learned per-centre"):
+        prec = 1 if mode == "learned+mixed" else 0
+        geo = Geometry(g, params_default(p_qbx=0, p_fmm=0, n_max=int(g["n_max"]), eps=LEARNED_EPS, precision=prec),
+                       device=dev.index)
+        geo.build()
+        pb, qb = geo.params.p_fmm, geo.params.p_qbx
+        sel_ms = None
+        if mode == "bound":
+            p, q = pb, qb
+            kind, _ = geo.association()
+            mask = np.zeros(nt, np.int32)
+            for k in (0, 1, 2):
+                ids = np.nonzero(kind == k)[0]
+                if len(ids):
+                    mask[rng.choice(ids, min(200, len(ids)), replace=False)] = 1
+        else:
+            ts = time.perf_counter()
+            # "learned": the tree's FMM order from the network, the QBX order from eps;
+            # "learned per-centre": each centre's QBX order from the network as well
+            q_ref = int(meta["q_ref"]) if mode == "learned per-centre" else 0
+            p, q = geo.learned_orders(m, LEARNED_EPS, margin_qbx=margin_q, margin_fmm=margin_f,
+                                      q_ref=q_ref, p_ref=int(meta["p_ref"]), p_bound=pb)
+            sel_ms = 1e3 * (time.perf_counter() - ts)
+        import torch
+        dmu = torch.tensor(g["density"], dtype=torch.float64, device=dev)
+        out = torch.empty(nt, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            geo.eval(args.kernel, dmu, out)
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            _, st = geo.eval(args.kernel, dmu, out, stats=True)
+            ms.append(st.ms_total)
+        torch.cuda.synchronize()
+        vals = out.cpu().numpy()
+        sample[mode] = vals[mask.astype(bool)]
+        modes[mode] = {"p_fmm": int(p), "p_qbx_max": int(q), "eval_ms": statistics.median(ms),
+                       "eval_targets_per_s": nt / (statistics.median(ms) * 1e-3),
+                       "order_selection_ms": sel_ms, "precision": "MIXED" if prec else "FP64"}
+        geo.close()
+    geo0.close()
+    m.close()
+    rep = {"eps": LEARNED_EPS, "kernel": args.kernel, "training_curves": ntr, "held_out_curves": hold,
+           "training_centres": int(len(Xtr)), "labels": "oracle (tests/golden/order_labels.npz)",
+           "epochs": epochs, "final_loss": loss, "held_out_r2": {"qbx": r2[0], "fmm": r2[1]},
+           "margins": {"qbx": margin_q, "fmm": margin_f}, "features_s": t_feat, "train_s": t_train,
+           "inference": "BF16 mma.sync m16n8k16 (tensor cores), FP32 accumulation",
+           "modes": modes, "qbx_labels": "one-sided truncation error at the centre's base node",
+           "speedup_learned_vs_bound": modes["bound"]["eval_ms"] / modes["learned"]["eval_ms"],
+           "speedup_learned_mixed_vs_bound": modes["bound"]["eval_ms"] / modes["learned+mixed"]["eval_ms"]}
+    return rep, mask, sample
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, local):
     import torch
@@ -574,6 +698,10 @@ def run_gpu(args, rank, world, local):
         e2e = {"value": world * nt * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * tot / args.steps}
 
+    learned, l_mask, l_sample = None, None, None
+    if args.learned and rank == 0 and args.precision == 0 and os.path.exists(LABELS):
+        learned, l_mask, l_sample = run_learned(args, dev, g, flush)
+
     # ---- CPU oracle baseline (rank 0, N = 1): the whole workload on all host cores,
     # and a single-core figure on a sub-grid; the GPU result is compared with the
     # oracle at every target of the whole workload
@@ -592,6 +720,28 @@ def run_gpu(args, rank, world, local):
         gpu_vals[:] = d_out.cpu().numpy()
         L.gq_geometry_destroy(geo_full)
         rel_err = float(np.abs(gpu_vals - ref).max() / np.abs(ref).max())
+        if learned is not None:
+            # the acceleration error (the Theorem's quantity, Sec. 4.5) of the modes
+            # with one QBX order: their outputs against the oracle's unaccelerated QBX
+            # (O1) of that order at the sampled targets of every kind
+            import oracle
+            t0 = time.perf_counter()
+            qg = learned["modes"]["bound"]["p_qbx_max"]
+            oracle.set_threads(cores)
+            try:
+                o1 = oracle.Oracle(g, oracle.default_params(g, p_qbx=qg))
+                ref1 = o1.direct(args.kernel, g["density"], target_mask=l_mask)[l_mask.astype(bool)]
+            finally:
+                oracle.set_threads(1)
+            sc = np.abs(ref1).max()
+            for mode, v in l_sample.items():
+                if learned["modes"][mode]["p_qbx_max"] != qg or mode == "learned per-centre":
+                    continue
+                err = float(np.abs(v - ref1).max() / sc)
+                learned["modes"][mode]["err_vs_oracle_O1"] = err
+                learned["modes"][mode]["meets_eps"] = err <= LEARNED_EPS
+            learned["oracle_check"] = {"targets": int(l_mask.sum()), "s": time.perf_counter() - t0,
+                                       "reference": f"oracle O1 (unaccelerated QBX) at p_qbx {qg}"}
         gs, _, nts1, times1, _ = oracle_sample(args.kernel)
         cpu = {"value": nts / times[0], "unit": UNIT, "cores": used, "kind": "oracle",
                "nproc": os.cpu_count(), "cpu_model": cpu_model(),
@@ -714,6 +864,7 @@ def run_gpu(args, rank, world, local):
         "precision_sweep": sweep,
         "level_restricted": restricted,
         "batched": batched,
+        "learned_orders": learned,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

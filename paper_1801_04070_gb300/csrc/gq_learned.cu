@@ -28,8 +28,8 @@ constexpr int kNF = 32;                       // features per centre
 constexpr int kDims[5] = {32, 64, 32, 32, 2};
 constexpr int kLayers = 4;
 // parameter offsets: W_l [out][in] then b_l [out]
-constexpr int woff(int l) {
-    return l == 0 ? 0 : woff(l - 1) + kDims[l - 1] * kDims[l] + kDims[l];
+__host__ __device__ constexpr int woff(int l) {
+    return l == 0 ? 0 : woff(l - 1) + (l == 1 ? 32 * 64 + 64 : l == 2 ? 64 * 32 + 32 : l == 3 ? 32 * 32 + 32 : 32 * 2 + 2);
 }
 constexpr int kNParams = woff(kLayers);
 // the same layout for device code (runtime layer index)
@@ -190,30 +190,123 @@ __global__ void k_gather_rows(int B, int d, const int *__restrict__ perm, const 
     out[t] = (X[(size_t)perm[s] * d + c] - mu[c]) / sd[c];
 }
 
-// BF16 inference, thread per sample: weights and activations rounded to
-// BF16, products summed in FP32
-__global__ void k_mlp_infer_bf16(int n, const float *__restrict__ X, const __nv_bfloat16 *__restrict__ Wb,
-                                 const float *__restrict__ xmu, const float *__restrict__ xsd,
-                                 const float *__restrict__ ymu, const float *__restrict__ ysd, float *__restrict__ Y) {
-    __shared__ __nv_bfloat16 sw[kNParams];
+// BF16 inference on the tensor cores (mma.sync m16n8k16, BF16 inputs, FP32
+// accumulators): a warp takes 16 samples through all four layers.  Inputs
+// are normalised and rounded to BF16; each layer's accumulators start at its
+// BF16 bias, and after ReLU the accumulator fragments of output columns
+// 16k ... 16k+15 are, packed to BF16 pairs, exactly the A fragment of the
+// next layer's k-block k (row g = lane / 4 and g + 8, columns 2 (lane % 4)
+// and + 1, + 8), so activations never leave registers.  The last layer
+// (2 outputs) fills the first two columns of one 8-wide tile; its weight
+// rows 2 ... 7 read as zero.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// one dense layer for a warp's 16 rows: NIN inputs as NIN/16 A fragments,
+// NOUT outputs as NOUT/8 accumulator tiles; W [nout_real][NIN] BF16 in
+// shared memory, rows >= nout_real read as zero
+template <int NIN, int NOUT>
+__device__ __forceinline__ void mma_layer(const uint32_t (&A)[NIN / 16][4], const __nv_bfloat16 *W,
+                                          const __nv_bfloat16 *bias, int nout_real, float (&C)[NOUT / 8][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < NOUT / 8; ++j) {
+        const int c0 = 8 * j + 2 * t;
+        const float bl = c0 < nout_real ? __bfloat162float(bias[c0]) : 0.f;
+        const float bh = c0 + 1 < nout_real ? __bfloat162float(bias[c0 + 1]) : 0.f;
+        C[j][0] = bl; C[j][1] = bh; C[j][2] = bl; C[j][3] = bh;
+        const int n = 8 * j + g;
+#pragma unroll
+        for (int kb = 0; kb < NIN / 16; ++kb) {
+            uint32_t b0 = 0, b1 = 0;
+            if (n < nout_real) {
+                const __nv_bfloat16 *wr = W + n * NIN + 16 * kb + 2 * t;
+                b0 = *reinterpret_cast<const uint32_t *>(wr);
+                b1 = *reinterpret_cast<const uint32_t *>(wr + 8);
+            }
+            mma_bf16_16816(C[j], A[kb], b0, b1);
+        }
+    }
+}
+
+// accumulators of a hidden layer -> ReLU -> BF16 A fragments of the next layer
+template <int NOUT>
+__device__ __forceinline__ void relu_to_frags(const float (&C)[NOUT / 8][4], uint32_t (&A)[NOUT / 16][4]) {
+#pragma unroll
+    for (int kb = 0; kb < NOUT / 16; ++kb) {
+        A[kb][0] = pack_bf16x2(fmaxf(C[2 * kb][0], 0.f), fmaxf(C[2 * kb][1], 0.f));
+        A[kb][1] = pack_bf16x2(fmaxf(C[2 * kb][2], 0.f), fmaxf(C[2 * kb][3], 0.f));
+        A[kb][2] = pack_bf16x2(fmaxf(C[2 * kb + 1][0], 0.f), fmaxf(C[2 * kb + 1][1], 0.f));
+        A[kb][3] = pack_bf16x2(fmaxf(C[2 * kb + 1][2], 0.f), fmaxf(C[2 * kb + 1][3], 0.f));
+    }
+}
+
+static_assert(kDims[0] == 32 && kDims[1] == 64 && kDims[2] == 32 && kDims[3] == 32 && kDims[4] == 2,
+              "the tensor-core inference is written for 32-64-32-32-2");
+
+__global__ void __launch_bounds__(128) k_mlp_infer_mma(int n, const float *__restrict__ X,
+                                                       const __nv_bfloat16 *__restrict__ Wb,
+                                                       const float *__restrict__ xmu, const float *__restrict__ xsd,
+                                                       const float *__restrict__ ymu, const float *__restrict__ ysd,
+                                                       float *__restrict__ Y) {
+    __shared__ __align__(16) __nv_bfloat16 sw[kNParams + 8];
     for (int i = threadIdx.x; i < kNParams; i += blockDim.x) sw[i] = Wb[i];
     __syncthreads();
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    float a[64], z[64];
-    for (int i = 0; i < kNF; ++i) a[i] = __bfloat162float(__float2bfloat16((X[(size_t)s * kNF + i] - xmu[i]) / xsd[i]));
-    for (int l = 0; l < kLayers; ++l) {
-        int nin = ddim(l), nout = ddim(l + 1);
-        const __nv_bfloat16 *W = sw + dwoff(l), *bb = W + nin * nout;
-        for (int o = 0; o < nout; ++o) {
-            float acc = __bfloat162float(bb[o]);
-            for (int i = 0; i < nin; ++i) acc = fmaf(__bfloat162float(W[o * nin + i]), a[i], acc);
-            z[o] = l < kLayers - 1 ? fmaxf(acc, 0.f) : acc;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int s0 = 16 * (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); s0 < n; s0 += 16 * warps) {
+        // input fragments: rows s0 + g, s0 + g + 8; features 16 kb + 2t (+1), + 8
+        uint32_t A0[2][4];
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)        // column half: + 0 or + 8
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {  // row g or g + 8
+                    const int s = s0 + g + 8 * r, f = 16 * kb + 8 * h + 2 * t;
+                    float lo = 0.f, hi = 0.f;
+                    if (s < n) {
+                        lo = (X[(size_t)s * kNF + f] - xmu[f]) / xsd[f];
+                        hi = (X[(size_t)s * kNF + f + 1] - xmu[f + 1]) / xsd[f + 1];
+                    }
+                    A0[kb][2 * h + r] = pack_bf16x2(lo, hi);
+                }
+        float C1[8][4];
+        mma_layer<32, 64>(A0, sw + woff(0), sw + woff(0) + 32 * 64, 64, C1);
+        uint32_t A1[4][4];
+        relu_to_frags<64>(C1, A1);
+        float C2[4][4];
+        mma_layer<64, 32>(A1, sw + woff(1), sw + woff(1) + 64 * 32, 32, C2);
+        uint32_t A2[2][4];
+        relu_to_frags<32>(C2, A2);
+        float C3[4][4];
+        mma_layer<32, 32>(A2, sw + woff(2), sw + woff(2) + 32 * 32, 32, C3);
+        uint32_t A3[2][4];
+        relu_to_frags<32>(C3, A3);
+        float C4[1][4];
+        mma_layer<32, 8>(A3, sw + woff(3), sw + woff(3) + 32 * 2, 2, C4);
+        if (t == 0) {   // columns 0 and 1 of rows g and g + 8
+            const int sa = s0 + g, sb = s0 + g + 8;
+            if (sa < n) {
+                Y[(size_t)sa * 2] = C4[0][0] * ysd[0] + ymu[0];
+                Y[(size_t)sa * 2 + 1] = C4[0][1] * ysd[1] + ymu[1];
+            }
+            if (sb < n) {
+                Y[(size_t)sb * 2] = C4[0][2] * ysd[0] + ymu[0];
+                Y[(size_t)sb * 2 + 1] = C4[0][3] * ysd[1] + ymu[1];
+            }
         }
-        for (int o = 0; o < nout; ++o) a[o] = l < kLayers - 1 ? __bfloat162float(__float2bfloat16(z[o])) : z[o];
     }
-    Y[(size_t)s * 2] = a[0] * ysd[0] + ymu[0];
-    Y[(size_t)s * 2 + 1] = a[1] * ysd[1] + ymu[1];
 }
 
 __global__ void k_to_bf16(int n, const float *__restrict__ in, __nv_bfloat16 *__restrict__ out) {
@@ -435,9 +528,11 @@ void gq_mlp_predict_impl(gq_mlp *M, const float *X, int n, bool xdev, float *Y, 
         Yd = ty.p;
     }
     GQ_LAUNCH(ctx, k_to_bf16, gq_blocks(kNParams, kT), kT, 0, kNParams, (const float *)M->w.p, M->wb.p);
-    if (n > 0)
-        GQ_LAUNCH(ctx, k_mlp_infer_bf16, gq_blocks(n, 128), 128, 0, n, Xd, (const __nv_bfloat16 *)M->wb.p,
+    if (n > 0) {
+        const int blocks = std::min(gq_blocks(n, 64), 152 * 8);
+        GQ_LAUNCH(ctx, k_mlp_infer_mma, blocks, 128, 0, n, Xd, (const __nv_bfloat16 *)M->wb.p,
                   (const float *)M->xmu.p, (const float *)M->xsd.p, (const float *)M->ymu.p, (const float *)M->ysd.p, Yd);
+    }
     if (!ydev) GQ_CUDA(cudaMemcpyAsync(Y, Yd, sizeof(float) * n * 2, cudaMemcpyDeviceToHost, ctx->stream));
     GQ_CUDA(cudaStreamSynchronize(ctx->stream));
 }

@@ -14,4 +14,6 @@ from .starfish import (  # noqa: F401
     unit_circle,
     small_grid,
     random_fourier_curves,
+    order_training_curves,
+    order_training_problem,
 )

@@ -201,3 +201,20 @@ def random_fourier_curves(n_curves: int, seed: int = 5, n_panels: int = 32, kmax
                       for k in range(1, kmax + 1))
         out.append(Curve(modes=modes))
     return out
+
+
+def order_training_curves(n_curves: int = 2000, seed: int = 5):
+    """The curves of the order-selection training set: random star-shaped
+    curves (random_fourier_curves, 32 panels each)."""
+    return random_fourier_curves(n_curves, seed=seed)
+
+
+def order_training_problem(curve: Curve, index: int) -> dict:
+    """Curve `index` of the order-selection training set: 32 panels x 16
+    nodes (x4 upsampled), a random-Fourier density seeded by its index, the
+    base nodes as (on-surface, two-sided) targets."""
+    g = discretize([curve], 32)
+    g["density"] = fourier_density(g, np.random.default_rng(10_000 + index))
+    g["tgt_xy"] = g["base_xy"]
+    g["tgt_onsurf"] = np.arange(len(g["base_xy"]), dtype=np.int32)
+    return g
