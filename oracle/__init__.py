@@ -55,7 +55,7 @@ class _Params(C.Structure):
     _fields_ = [("p_qbx", C.c_int), ("p_fmm", C.c_int), ("n_max", C.c_int),
                 ("tf_num", C.c_int), ("tf_den", C.c_int), ("w3_demote", C.c_int),
                 ("max_level", C.c_int), ("radius_factor", C.c_double),
-                ("assoc_slack", C.c_double), ("level_restrict", C.c_int)]
+                ("assoc_slack", C.c_double), ("level_restrict", C.c_int), ("tcr_shape", C.c_int)]
 
 
 def lib():
@@ -87,6 +87,9 @@ def lib():
                 getattr(L, f).argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p]
                 getattr(L, f).restype = C.c_int
+            L.orc_sep_test.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64,
+                                       C.c_int, C.c_int64, C.c_int64]
+            L.orc_sep_test.restype = C.c_int
             L.orc_op_p2m.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_op_p2l.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_op_m2m.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -96,6 +99,14 @@ def lib():
             L.orc_op_eval_mpole.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
+
+
+def sep_test(shape, tn, td, which, a, b) -> bool:
+    """The oracle's adequate-separation relation (Sec. 4.3) for boxes a, b
+    given as (level, ix, iy): which 0 tests a |> TCR(b), 1 tests TCR(a) |> b;
+    shape 0 the square TCR, 1 the disk-shaped one."""
+    return bool(lib().orc_sep_test(int(shape), int(tn), int(td), int(which), int(a[0]), int(a[1]), int(a[2]),
+                                   int(b[0]), int(b[1]), int(b[2])))
 
 
 def set_threads(n: int) -> int:
@@ -116,7 +127,7 @@ def _p(a):
 
 def default_params(g: dict | None = None, **kw) -> dict:
     p = dict(p_qbx=5, p_fmm=10, n_max=32, tf_num=9, tf_den=10, w3_demote=15,
-             max_level=30, radius_factor=0.5, assoc_slack=1.2, level_restrict=0)
+             max_level=30, radius_factor=0.5, assoc_slack=1.2, level_restrict=0, tcr_shape=0)
     if g is not None:
         for k in ("p_qbx", "p_fmm", "n_max"):
             if k in g:
@@ -145,7 +156,7 @@ class Oracle:
         pr = self.params
         prm = _Params(pr["p_qbx"], pr["p_fmm"], pr["n_max"], pr["tf_num"], pr["tf_den"],
                       pr["w3_demote"], pr["max_level"], pr["radius_factor"], pr["assoc_slack"],
-                      int(pr.get("level_restrict", 0)))
+                      int(pr.get("level_restrict", 0)), int(pr.get("tcr_shape", 0)))
         self.h = self.L.orc_create(C.byref(geom), C.byref(prm))
         self.nt = len(a["tgt_xy"])
         self.nsrc = int(g["npanels"]) * int(g["nu"])

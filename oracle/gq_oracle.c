@@ -30,6 +30,11 @@
  *   M2M (eq. m2m), M2L (eq. m2l, with the a_0 term's sign as obtained by
  *   expanding log z about y: (-1)^(m+1) a_0 / (m y^m); the printed (-1)^m is
  *   a typo), L2L (eq. l2l).
+ *
+ * Target confinement region: the closed l-inf ball (square) of radius
+ * |b|(1 + t_f) (Sec. 4.3), or, with tcr_shape = 1, the closed l2 disk of that
+ * radius (the variant named in the appendix corrigendum; reading: every
+ * definition of Sec. 4.3 kept with the disk as the set).
  */
 #ifndef GQ_ORC_MUT
 #define GQ_ORC_MUT 0
@@ -287,8 +292,9 @@ static void root_and_keys(orc_state *s) {
 #undef KEY
 
     /* Centre level L_c (Sec. 4.3, TCR): the deepest level l such that the
-     * centre's disk lies in TCR(b_l) = B_inf(|b_l|(1 + t_f), centre(b_l)) for
-     * every box b_0..b_l on its key path (fitting is monotone in l). */
+     * centre's disk lies in TCR(b_l) = B_inf(|b_l|(1 + t_f), centre(b_l)) (or,
+     * with the disk-shaped TCR, the l2 disk of that radius) for every box
+     * b_0..b_l on its key path (fitting is monotone in l). */
     double tcr_scale = (double)(s->p.tf_den + s->p.tf_num) / (double)s->p.tf_den;
     for (int c = 0; c < s->nc; ++c) {
         int lc = -1;
@@ -297,7 +303,13 @@ static void root_and_keys(orc_state *s) {
             double hb = ldexp(s->H, -l);
             double bx = s->lo_x + (double)(2 * ix + 1) * hb;
             double by = s->lo_y + (double)(2 * iy + 1) * hb;
-            double d = fmax(fabs(s->c_xy[2 * c] - bx), fabs(s->c_xy[2 * c + 1] - by)) + (GQ_ORC_MUT == 16 ? 0.0 : s->c_r[c]);
+            double dx = s->c_xy[2 * c] - bx, dy = s->c_xy[2 * c + 1] - by;
+            /* the disk lies in the square TCR when its l-inf distance plus r fits the
+             * half-width, in the disk TCR when its l2 distance plus r fits the radius */
+            double d = s->p.tcr_shape == 1
+                           ? (GQ_ORC_MUT == 21 ? fmax(fabs(dx), fabs(dy)) : sqrt(dx * dx + dy * dy))
+                           : fmax(fabs(dx), fabs(dy));
+            d += (GQ_ORC_MUT == 16 ? 0.0 : s->c_r[c]);
             if (d <= hb * (GQ_ORC_MUT == 15 ? 1.0 : tcr_scale)) lc = l; else break;
         }
         s->c_lc[c] = lc < 0 ? 0 : lc;
@@ -420,15 +432,47 @@ static inline int adjacent(const obox *a, const obox *b) {
 }
 /* k-colleagues with k = 2: same level, inside B_inf(5|b|, c_b). */
 static inline int colleague2(const obox *a, const obox *b) { return a->level == b->level && dcen(a, b) <= 4 * bh(b); }
-/* a < TCR(b): dist >= 3|a| + |b|(1 + t_f) */
-static inline int sep_a_tcrb(const orc_state *s, const obox *a, const obox *b) {
-    int64_t tn = s->p.tf_num, td = s->p.tf_den;
+/* Disk-shaped TCR (appendix corrigendum), the definitions of Sec. 4.3 kept:
+ * the l-inf distance between a square S(c_s, h) and a disk D(c_d, rho) is at
+ * least s exactly when D misses the open square of half-width h + s around
+ * c_s, i.e. when the l2 distance from c_d to the closed square S(c_s, h + s)
+ * is at least rho:  max(X - T, 0)^2 + max(Y - T, 0)^2 >= rho^2  with X, Y the
+ * absolute centre differences and T = h + s.  Integer arithmetic (units of
+ * the level-30 half-width, scaled by td), squares in 128 bits. */
+static inline int disk_clear(int64_t X, int64_t Y, int64_t T, int64_t rho) {
+    __int128 ex = X > T ? (__int128)(X - T) : (GQ_ORC_MUT == 20 ? (__int128)(X - T) : 0);
+    __int128 ey = Y > T ? (__int128)(Y - T) : (GQ_ORC_MUT == 20 ? (__int128)(Y - T) : 0);
+    return ex * ex + ey * ey >= (__int128)rho * rho;
+}
+static inline void dxy(const obox *a, const obox *b, int64_t *X, int64_t *Y) {
+    *X = i64abs((2 * a->ix + 1) * bh(a) - (2 * b->ix + 1) * bh(b));
+    *Y = i64abs((2 * a->iy + 1) * bh(a) - (2 * b->iy + 1) * bh(b));
+}
+/* a < TCR(b): the l-inf distance between a and TCR(b) is at least 2|a|; for
+ * the square TCR, dist >= 3|a| + |b|(1 + t_f) */
+static inline int sep_a_tcrb_p(int shape, int64_t tn, int64_t td, const obox *a, const obox *b) {
+    if (shape == 1) {
+        int64_t X, Y;
+        dxy(a, b, &X, &Y);
+        return disk_clear(td * X, td * Y, 3 * td * bh(a), (td + tn) * bh(b));
+    }
     return td * dcen(a, b) >= 3 * td * bh(a) + (GQ_ORC_MUT == 14 ? td : td + tn) * bh(b);
 }
-/* TCR(a) < b: dist >= 3|a|(1 + t_f) + |b| */
-static inline int sep_tcra_b(const orc_state *s, const obox *a, const obox *b) {
-    int64_t tn = s->p.tf_num, td = s->p.tf_den;
+/* TCR(a) < b: the l-inf distance between TCR(a) and b is at least
+ * 2|a|(1 + t_f); for the square TCR, dist >= 3|a|(1 + t_f) + |b| */
+static inline int sep_tcra_b_p(int shape, int64_t tn, int64_t td, const obox *a, const obox *b) {
+    if (shape == 1) {
+        int64_t X, Y;
+        dxy(a, b, &X, &Y);
+        return disk_clear(td * X, td * Y, td * bh(b) + 2 * (td + tn) * bh(a), (td + tn) * bh(a));
+    }
     return td * dcen(a, b) >= 3 * (GQ_ORC_MUT == 13 ? td : td + tn) * bh(a) + td * bh(b);
+}
+static inline int sep_a_tcrb(const orc_state *s, const obox *a, const obox *b) {
+    return sep_a_tcrb_p(s->p.tcr_shape, s->p.tf_num, s->p.tf_den, a, b);
+}
+static inline int sep_tcra_b(const orc_state *s, const obox *a, const obox *b) {
+    return sep_tcra_b_p(s->p.tcr_shape, s->p.tf_num, s->p.tf_den, a, b);
 }
 static inline int is_leaf(const obox *b) { return b->child[0] < 0 && b->child[1] < 0 && b->child[2] < 0 && b->child[3] < 0; }
 static int is_strict_desc(const orc_state *s, int d, int a) {
@@ -719,6 +763,16 @@ int orc_build(orc_state *s) {
 }
 
 /* ------------------------------------------------------------------ accessors */
+int orc_sep_test(int shape, int tn, int td, int which, int la, int64_t ixa, int64_t iya, int lb, int64_t ixb,
+                 int64_t iyb) {
+    obox a, b;
+    memset(&a, 0, sizeof a);
+    memset(&b, 0, sizeof b);
+    a.level = la; a.ix = ixa; a.iy = iya;
+    b.level = lb; b.ix = ixb; b.iy = iyb;
+    return which == 0 ? sep_a_tcrb_p(shape, tn, td, &a, &b) : sep_tcra_b_p(shape, tn, td, &a, &b);
+}
+
 int orc_nbox(const orc_state *s) { return s->nbox; }
 int orc_ncentres(const orc_state *s) { return s->nc; }
 int orc_npoint_targets(const orc_state *s) { return s->npt; }

@@ -49,6 +49,9 @@ typedef struct {
     double radius_factor;         /* expansion radius = radius_factor * panel length */
     double assoc_slack;           /* off-surface target joins a centre if |t-c|/r <= slack */
     int level_restrict;           /* 1: balance the tree (Sec. 4.6, level-restriction remark) */
+    int tcr_shape;                /* TCR(b): 0 the closed l-inf ball (square) of radius |b|(1 + t_f)
+                                     (Sec. 4.3), 1 the closed l2 disk of that radius (the variant of
+                                     the appendix corrigendum) */
 } orc_params;
 
 enum { ORC_U = 0, ORC_V = 1, ORC_WC = 2, ORC_WF = 3, ORC_XC = 4, ORC_XF = 5, ORC_NLISTS = 6 };
@@ -60,6 +63,12 @@ orc_state *orc_create(const orc_geom *g, const orc_params *p);
 void orc_destroy(orc_state *s);
 /* Stages A2-A5: centres, target association, root, keys, tree, lists (O2). */
 int orc_build(orc_state *s);
+/* The adequate-separation relations of Sec. 4.3 (Def. "adequate separation")
+ * for two boxes given by level and index, with TCR shape `shape` (as
+ * orc_params.tcr_shape) and t_f = tn / td: which 0 tests a |> TCR(b), which 1
+ * tests TCR(a) |> b.  Exposed for tests of the relations themselves. */
+int orc_sep_test(int shape, int tn, int td, int which, int la, int64_t ixa, int64_t iya, int lb, int64_t ixb,
+                 int64_t iyb);
 /* O3: brute-force lists into a second list set. */
 int orc_lists_bruteforce(orc_state *s);
 

@@ -45,6 +45,10 @@ CASES = {
          "test_unit_circle_centres"),
     19: ("level restriction blind to boxes touching only at a corner (Sec. 4.6 remark)",
          "test_oracle_level_restrict.py", "test_balanced_tree_has_no_violation"),
+    20: ("disk-shaped TCR: separation without clamping the overlap along an axis to zero",
+         "test_oracle_tcr_disk.py", "test_disk_separation_is_the_geometric_relation"),
+    21: ("disk-shaped TCR: centre level from the l-inf distance, as for the square TCR",
+         "test_oracle_tcr_disk.py", "test_centre_disks_fit_their_disk_tcr"),
 }
 
 
