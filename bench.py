@@ -802,8 +802,10 @@ def run_gpu(args, rank, world, local):
 
         out_plain = d_out.clone()
         res = {}
-        for lr in (0, 1):
-            pr = params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"]), level_restrict=lr)
+        # 0: the plain tree, 1: level-restricted, 2: disk-shaped TCR (appendix corrigendum)
+        for lr in (0, 1, 2):
+            pr = params_default(p_qbx=Q, p_fmm=P, n_max=int(g["n_max"]), level_restrict=1 if lr == 1 else 0,
+                                tcr_shape=1 if lr == 2 else 0)
             sg = C.c_void_p()
             chk(L.gq_geometry_create(ctx, C.byref(desc), C.byref(pr), C.byref(sg)))
             chk(L.gq_targets_set(sg, nt, d_txy.data_ptr(), d_ton.data_ptr()))
@@ -832,11 +834,12 @@ def run_gpu(args, rank, world, local):
             res[lr] = {"build_ms": statistics.median(bms), "eval_ms": statistics.median(ems), "boxes": nb,
                        "list3_max_per_leaf": w3max, "list_entries": nlist,
                        "stages_ms": {STAGE_NAMES[i]: round(float(sst.ms_stage[i]), 3) for i in range(11)}}
-            if lr == 1:
+            if lr >= 1:
                 res[lr]["max_rel_diff_vs_plain_tree"] = float((d_out - out_plain).abs().max() / out_plain.abs().max())
             L.gq_geometry_destroy(sg)
         restricted = {"plain": res[0], "level_restricted": res[1],
-                      "eval_targets_per_s": nt / (res[1]["eval_ms"] * 1e-3)}
+                      "eval_targets_per_s": nt / (res[1]["eval_ms"] * 1e-3),
+                      "disk_tcr": res[2], "disk_tcr_eval_targets_per_s": nt / (res[2]["eval_ms"] * 1e-3)}
         d_out.copy_(out_plain)
 
     batched = run_batched(args, dev, stream) if args.batched else None
@@ -862,7 +865,7 @@ def run_gpu(args, rank, world, local):
         "stages_ms": stage_report,
         "rel_err_vs_oracle": rel_err,
         "precision_sweep": sweep,
-        "level_restricted": restricted,
+        "tree_variants": restricted,
         "batched": batched,
         "learned_orders": learned,
         "roofline": roof,

@@ -111,6 +111,7 @@ typedef struct {
     int precision;
     int m2l;
     int level_restrict;
+    int tcr_shape;
 } gq_params;
 
 enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1, GQ_PREC_MIXED_FMM = 2 };
@@ -136,6 +137,19 @@ enum { GQ_M2L_AUTO = 0, GQ_M2L_FP64 = 1 };
  * none is left.  A leaf with no particle eligible for children cannot be
  * refined and keeps its contact.  0 (default): the tree of Stage 1 alone.
  * Other values: GQ_ERR_INVALID. */
+
+/* tcr_shape: the target confinement region TCR(b) (Sec. 4.3) of a box b of
+ * half-width |b|
+ *   0 (default): the closed square (l-inf ball) of half-width |b|(1 + t_f),
+ *     the paper's definition;
+ *   1: the closed disk (l2 ball) of radius |b|(1 + t_f), the variant named in
+ *     the paper's appendix corrigendum.  Every definition of Sec. 4.3 is kept
+ *     with the disk as the set: a centre stays at the deepest level whose TCR
+ *     holds its whole disk (l2 distance of the centres plus the radius within
+ *     |b|(1 + t_f)); a |> TCR(b) when the l-inf distance between a and the
+ *     disk is at least 2|a|, TCR(a) |> b when the l-inf distance between the
+ *     disk and b is at least 2|a|(1 + t_f) (exact integer tests).
+ *   Other values: GQ_ERR_INVALID. */
 
 /* Discretised curve (Sec. 2.1, 2.2.1).  Panel k owns base nodes
  * [k*nb, (k+1)*nb) and quadrature (upsampled) nodes [k*nu, (k+1)*nu).

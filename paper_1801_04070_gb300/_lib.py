@@ -29,7 +29,7 @@ class Params(C.Structure):
                 ("tf_num", C.c_int), ("tf_den", C.c_int), ("w3_demote", C.c_int),
                 ("max_level", C.c_int), ("radius_factor", C.c_double),
                 ("assoc_slack", C.c_double), ("eps", C.c_double), ("precision", C.c_int), ("m2l", C.c_int),
-                ("level_restrict", C.c_int)]
+                ("level_restrict", C.c_int), ("tcr_shape", C.c_int)]
 
 
 class GeometryDesc(C.Structure):

@@ -98,6 +98,7 @@ void resolve_orders(gq_params &p) {
                GQ_ERR_INVALID, "unknown precision");
     GQ_REQUIRE(p.m2l == GQ_M2L_AUTO || p.m2l == GQ_M2L_FP64, GQ_ERR_INVALID, "unknown m2l mode");
     GQ_REQUIRE(p.level_restrict == 0 || p.level_restrict == 1, GQ_ERR_INVALID, "level_restrict must be 0 or 1");
+    GQ_REQUIRE(p.tcr_shape == 0 || p.tcr_shape == 1, GQ_ERR_INVALID, "tcr_shape must be 0 (square) or 1 (disk)");
 }
 
 }  // namespace
@@ -120,6 +121,7 @@ gq_status gq_params_default(gq_params *out) {
     out->precision = GQ_PREC_FP64;
     out->m2l = GQ_M2L_AUTO;
     out->level_restrict = 0;
+    out->tcr_shape = 0;
     return GQ_OK;
 }
 

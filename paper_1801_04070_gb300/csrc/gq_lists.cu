@@ -14,6 +14,10 @@
 //   a < TCR(b)        d >= 3 h_a + (1 + t_f) h_b
 //   TCR(a) < b        d >= 3 (1 + t_f) h_a + h_b
 // with t_f = tf_num / tf_den handled exactly by clearing the denominator.
+// With the disk-shaped TCR (tcr_shape 1, the appendix corrigendum's variant)
+// the two separations are l-inf distances between a square and a disk,
+// tested exactly as an l2 distance from the disk's centre to a grown square
+// (disk_clear below).
 //
 // Which boxes carry which list: List 1, 3 close/far and 4 close for boxes
 // owning targets (centres or point targets); List 2 and 4 far for boxes
@@ -37,6 +41,7 @@ struct TreeView {
     const int *sub_src, *sub_tgt, *own_tgt;
     const int *win;   // [nbox][25]: box at (ix + dx, iy + dy) of the same level, dx, dy in [-2, 2], or -1
     int64_t tn, td;
+    int shape;    // TCR: 0 square, 1 disk
     int demote;
 };
 
@@ -55,10 +60,29 @@ __device__ __forceinline__ int64_t dcen(IBox a, IBox b) {
     return dx > dy ? dx : dy;
 }
 __device__ __forceinline__ bool adjacent(IBox a, IBox b) { return dcen(a, b) <= ih(a.l) + ih(b.l); }
+// Disk-shaped TCR: the l-inf distance between a square S(c_s, h) and a disk
+// D(c_d, rho) is at least s exactly when the l2 distance from c_d to the
+// closed square S(c_s, h + s) is at least rho, i.e.
+//   max(X - T, 0)^2 + max(Y - T, 0)^2 >= rho^2,   T = h + s,
+// X, Y the absolute centre differences; exact with 128-bit squares.
+__device__ __forceinline__ bool disk_clear(int64_t X, int64_t Y, int64_t T, int64_t rho) {
+    const __int128 ex = X > T ? (__int128)(X - T) : (__int128)0;
+    const __int128 ey = Y > T ? (__int128)(Y - T) : (__int128)0;
+    return ex * ex + ey * ey >= (__int128)rho * rho;
+}
+__device__ __forceinline__ int64_t dax(IBox a, IBox b) { return i64abs((2 * a.x + 1) * ih(a.l) - (2 * b.x + 1) * ih(b.l)); }
+__device__ __forceinline__ int64_t day(IBox a, IBox b) { return i64abs((2 * a.y + 1) * ih(a.l) - (2 * b.y + 1) * ih(b.l)); }
+// a < TCR(b): l-inf distance between a and TCR(b) >= 2|a|
 __device__ __forceinline__ bool sep_a_tcrb(const TreeView &T, IBox a, IBox b) {
+    if (T.shape == 1)
+        return disk_clear(T.td * dax(a, b), T.td * day(a, b), 3 * T.td * ih(a.l), (T.td + T.tn) * ih(b.l));
     return T.td * dcen(a, b) >= 3 * T.td * ih(a.l) + (T.td + T.tn) * ih(b.l);
 }
+// TCR(a) < b: l-inf distance between TCR(a) and b >= 2|a|(1 + t_f)
 __device__ __forceinline__ bool sep_tcra_b(const TreeView &T, IBox a, IBox b) {
+    if (T.shape == 1)
+        return disk_clear(T.td * dax(a, b), T.td * day(a, b), T.td * ih(b.l) + 2 * (T.td + T.tn) * ih(a.l),
+                          (T.td + T.tn) * ih(a.l));
     return T.td * dcen(a, b) >= 3 * (T.td + T.tn) * ih(a.l) + T.td * ih(b.l);
 }
 __device__ __forceinline__ IBox ibox(const TreeView &T, int b) { return IBox{T.blev[b], T.bix[b], T.biy[b]}; }
@@ -364,6 +388,7 @@ void gq_build_lists(gq_geom *g) {
     T.own_tgt = g->own_tgt.p;
     T.tn = g->prm.tf_num;
     T.td = g->prm.tf_den;
+    T.shape = g->prm.tcr_shape;
     T.demote = g->prm.w3_demote;
     int nbox = g->nbox;
     dbuf<int> win;

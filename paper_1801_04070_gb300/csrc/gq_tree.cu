@@ -238,8 +238,8 @@ __device__ __forceinline__ uint64_t key1(double v, double lo, double inv_u) {
 // combined particle array: [0, nsrc) sources, [nsrc, nsrc+nc) centres, then point targets
 __global__ void k_keys(int nsrc, int nc, int npt, const double *__restrict__ up_xy, const double *__restrict__ c_xy,
                        const double *__restrict__ c_r, const int *__restrict__ pt_tgt, const double *__restrict__ tgt_xy,
-                       RootInfo R, double tcr_scale, int max_level, uint64_t *__restrict__ key, int *__restrict__ val,
-                       int *__restrict__ elig, int *__restrict__ c_lc) {
+                       RootInfo R, double tcr_scale, int tcr_shape, int max_level, uint64_t *__restrict__ key,
+                       int *__restrict__ val, int *__restrict__ elig, int *__restrict__ c_lc) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long n = (long long)nsrc + nc + npt;
     if (i >= n) return;
@@ -257,8 +257,8 @@ __global__ void k_keys(int nsrc, int nc, int npt, const double *__restrict__ up_
     const double inv_u = 1.0 / R.u;
     uint64_t kx = key1(x, R.lo_x, inv_u), ky = key1(y, R.lo_y, inv_u);
     if (i >= nsrc && i < nsrc + nc) {
-        // deepest level whose TCR (half-width |b|(1 + t_f)) holds the whole disk,
-        // for every box on the key path
+        // deepest level whose TCR (half-width, or with the disk-shaped TCR
+        // radius, |b|(1 + t_f)) holds the whole disk, for every box on the key path
         int c = (int)(i - nsrc);
         double r = c_r[c];
         int lc = -1;
@@ -267,7 +267,9 @@ __global__ void k_keys(int nsrc, int nc, int npt, const double *__restrict__ up_
             double hb = ldexp(R.H, -l);
             double bx = R.lo_x + (double)(2 * ix + 1) * hb;
             double by = R.lo_y + (double)(2 * iy + 1) * hb;
-            double d = fmax(fabs(x - bx), fabs(y - by)) + r;
+            double dx = x - bx, dy = y - by;
+            double d = tcr_shape == 1 ? sqrt(dx * dx + dy * dy) : fmax(fabs(dx), fabs(dy));
+            d += r;
             if (d <= hb * tcr_scale) lc = l; else break;
         }
         e = lc < 0 ? 0 : lc;
@@ -678,7 +680,7 @@ void gq_build_all(gq_geom *g) {
     double tcr_scale = (double)(g->prm.tf_den + g->prm.tf_num) / (double)g->prm.tf_den;
     GQ_LAUNCH(ctx, k_keys, gq_blocks(N, kT), kT, 0, g->nsrc, g->nc, g->npt, (const double *)g->up_xy,
               (const double *)g->c_xy, (const double *)g->c_r, (const int *)g->pt_tgt, (const double *)g->tgt_xy,
-              g->root, tcr_scale, g->prm.max_level, K.p, V.p, elig0.p, g->c_lc.p);
+              g->root, tcr_scale, g->prm.tcr_shape, g->prm.max_level, K.p, V.p, elig0.p, g->c_lc.p);
     gq_radix_sort_pairs(ctx, K.p, V.p, N, 2 * GQ_KEYBITS);
     GQ_LAUNCH(ctx, k_gather_int, gq_blocks(N, kT), kT, 0, N, (const int *)V.p, (const int *)elig0.p, elig.p);
 
