@@ -116,15 +116,22 @@ typedef struct {
 
 enum { GQ_PREC_FP64 = 0, GQ_PREC_MIXED = 1, GQ_PREC_MIXED_FMM = 2 };
 
-/* m2l: how the List 2 translations (Stage 4, Sec. 3.1 eq. m2l) run in FP64
- *   GQ_M2L_AUTO (default): on the BF16 tensor cores with FP64 accuracy when
- *     p_fmm <= 15 and the translations are FP64 (GQ_PREC_FP64, GQ_PREC_MIXED;
- *     GQ_PREC_MIXED_FMM keeps its FP32-pair M2L): every multipole and
- *     translation entry is split exactly into eleven 5-bit digits (54 bits) at
- *     a shared exponent, digit products accumulate exactly in FP32 tensor
- *     memory and are recombined in 64-bit integers (measured within a few
- *     units of 1e-15 of the FP64 M2L); otherwise FP64 FMAs.
- *   GQ_M2L_FP64: always the FP64 FMA kernel. */
+/* m2l: how the FP64 translations run
+ *   GQ_M2L_AUTO (default): on the BF16 tensor cores with FP64 accuracy
+ *     - the List 2 translations (Stage 4, Sec. 3.1 eq. m2l) when p_fmm <= 15
+ *       and they are FP64 (GQ_PREC_FP64, GQ_PREC_MIXED; GQ_PREC_MIXED_FMM keeps
+ *       its FP32-pair M2L): every multipole and translation entry is split
+ *       exactly into eleven 5-bit digits (54 bits) at a shared exponent, digit
+ *       products accumulate exactly in FP32 tensor memory and are recombined
+ *       in 64-bit integers (measured within a few units of 1e-15 of the FP64
+ *       M2L);
+ *     - the List 3 far multipoles to the QBX centres (Stage 5b) in the FP64
+ *       evaluation when p_fmm <= 16, p_qbx <= 15 and C(p_qbx + p_fmm - 1,
+ *       p_fmm - 1) < 2^24: the binomial sums of each (centre, box) pair as a
+ *       product of 64-bit fixed-point pair entries (eight 8-bit digits) and
+ *       the constant binomial matrix (three 8-bit digits);
+ *     otherwise FP64 FMAs.
+ *   GQ_M2L_FP64: always the FP64 FMA kernels. */
 enum { GQ_M2L_AUTO = 0, GQ_M2L_FP64 = 1 };
 
 /* level_restrict = 1: a level-restricted tree (Sec. 4.6, remark on

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgigaqbx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gq_api.cu", "gq_prims.cu", "gq_tree.cu", "gq_lists.cu", "gq_fmm.cu", "gq_probe.cu", "gq_gmres.cu", "gq_batch.cu", "gq_learned.cu", "gq_alloc.cu", "gq_m2l_tc.cu"]
+SOURCES = ["gq_api.cu", "gq_prims.cu", "gq_tree.cu", "gq_lists.cu", "gq_fmm.cu", "gq_probe.cu", "gq_gmres.cu", "gq_batch.cu", "gq_learned.cu", "gq_alloc.cu", "gq_m2l_tc.cu", "gq_w_tc.cu"]
 NO_FMA = {"gq_tree.cu"}
 
 

@@ -271,9 +271,11 @@ gq_status gq_build(gq_geom *g) {
         g->mixed_ready = false;
         g->split_ready = false;
         g->tc_ready = false;
+        g->wtc_ready = false;
         gq_form_centres(g);
         gq_build_all(g);
         if (gq_m2l_tc_supported(g)) gq_m2l_tc_build(g);   // tiles of the tensor-core M2L
+        if (gq_w_tc_supported(g)) gq_w_tc_build(g);       // pairs of the tensor-core M2QBXL
         GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
         g->built = true;
     });

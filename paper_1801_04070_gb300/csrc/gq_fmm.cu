@@ -2621,7 +2621,8 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     if (g->nc && split_w) {
         dispatch_w_centres_split(ctx, E, SX, g->nc, (const int *)g->ctr_owner, Qb);
     } else if (g->nc) {
-        dispatch_w_centres_q(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->M, Qb);
+        if (gq_w_tc_supported(g)) gq_w_centres_tc(g, E.R, (const double2 *)g->M, T.logt, Qb);
+        else dispatch_w_centres_q(ctx, E, g->nc, (const int *)g->ctr_owner, (const double2 *)g->M, Qb);
     }
     mark(S_WC, st);
     if (g->npt && !at_base) {

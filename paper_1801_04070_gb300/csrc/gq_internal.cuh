@@ -182,6 +182,11 @@ struct gq_geom {
     dbuf<float4> L2;      // local expansions
     dbuf<float4> lvl2;    // per level: (rho, 1/rho), (log rho, 1/rho^2)
     // tensor-core M2L (gq_m2l_tc.cu): tiles of the current build, multipole digits
+    // M2QBXL on the tensor cores: (centre, List 3 far box) pairs of the build
+    bool wtc_ready = false;
+    int wtc_npairs = 0;
+    dbuf<int> wtc_pstart, wtc_pc, wtc_pd;
+    dbuf<double2> wtc_contrib;
     bool tc_ready = false;
     dbuf<int> tc_tile_box, tc_slot_src, tc_tile_q, tc_err, tc_bexp, tc_lexp, tc_counter, tc_ntiles_dev, tc_cnt;
     dbuf<unsigned> tc_tile_mask;
@@ -240,6 +245,9 @@ bool gq_m2l_tc_supported(const gq_geom *g);                                     
 void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L);
 void gq_m2l_tc_build(gq_geom *g);
 int gq_m2l_tc_error(gq_geom *g);
+bool gq_w_tc_supported(const gq_geom *g);
+void gq_w_tc_build(gq_geom *g);
+void gq_w_centres_tc(gq_geom *g, const RootInfo &R, const double2 *M, const double *logt, double2 *Q);
 struct gq_mlp;
 int gq_mlp_param_count();                                                                   // gq_learned.cu
 gq_mlp *gq_mlp_new(gq_ctx *ctx, uint64_t seed);

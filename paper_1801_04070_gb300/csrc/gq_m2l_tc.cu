@@ -616,7 +616,7 @@ void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L) {
 // the device error flag of the tensor-core M2L (synchronises): 0 none, 1 a
 // bounded wait gave up, 2 a List 2 entry outside the offset window
 int gq_m2l_tc_error(gq_geom *g) {
-    if (!g->tc_ready || !g->tc_err.p) return 0;
+    if (!g->tc_err.p) return 0;
     int h = 0;
     GQ_CUDA(cudaMemcpyAsync(&h, g->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, g->ctx->stream));
     GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));

@@ -1,9 +1,10 @@
-"""The List 2 translations (Stage 4, Sec. 3.1 eq. m2l) on the BF16 tensor
-cores with FP64 accuracy (digit splitting, GQ_M2L_AUTO) against the FP64 FMA
-kernel (GQ_M2L_FP64) and the FP64 oracle: the potentials of the two modes
-agree to 1e-13 relative and both to the oracle within the 1e-12 parity bar;
-p_fmm > 15 falls back to the FP64 kernel; repeated evaluations give the same
-bits."""
+"""The List 2 translations (Stage 4, Sec. 3.1 eq. m2l) and the List 3 far
+multipole-to-QBX translations (Stage 5b) on the BF16 tensor cores with FP64
+accuracy (digit splitting, GQ_M2L_AUTO) against the FP64 FMA kernels
+(GQ_M2L_FP64) and the FP64 oracle: the potentials of the two modes agree to
+1e-13 relative and both to the oracle within the 1e-12 parity bar; p_fmm =
+16 isolates the second (the List 2 kernel takes p_fmm <= 15), p_fmm > 16
+falls back to the FP64 kernels; repeated evaluations give the same bits."""
 import numpy as np
 import pytest
 
@@ -51,6 +52,33 @@ def test_tensor_m2l_matches_fp64_and_oracle(case):
         assert _rel(a, b) <= 1e-13, (case, kern, _rel(a, b))
         ref = o.eval(kern, g["density"], target_mask=mask)
         assert _rel(a[sel], ref[sel]) <= 1e-12, (case, kern)
+        assert np.array_equal(a, tc.eval(kern, g["density"]))
+    tc.close()
+    f64.close()
+
+
+@pytest.mark.parametrize("p,q", [(16, 8), (12, 12), (10, 15)])
+def test_tensor_m2qbxl_alone(p, q):
+    """M2QBXL on the tensor cores with the FP64 List 2 kernel (p_fmm = 16) or
+    at QBX orders up to 15 (the binomial table's largest entry C(q+p-1, p-1)
+    stays below 2^24)."""
+    g = workloads.starfish_grid(4, 4, 64, n_off=1 << 16, on_surface="up", seed=3)
+    tc = _geo(g, p_qbx=q, p_fmm=p, n_max=32, m2l=0)
+    f64 = _geo(g, p_qbx=q, p_fmm=p, n_max=32, m2l=1)
+    o = oracle.Oracle(g, oracle.default_params(g, p_qbx=q, p_fmm=p))
+    kind, _ = o.association()
+    rng = np.random.default_rng(6)
+    mask = np.zeros(len(kind), np.int32)
+    for k in (0, 1, 2):
+        ids = np.nonzero(kind == k)[0]
+        mask[rng.choice(ids, min(300, len(ids)), replace=False)] = 1
+    sel = mask.astype(bool)
+    for kern in ("S", "D"):
+        a = tc.eval(kern, g["density"])
+        b = f64.eval(kern, g["density"])
+        assert _rel(a, b) <= 1e-13, (p, q, kern, _rel(a, b))
+        ref = o.eval(kern, g["density"], target_mask=mask)
+        assert _rel(a[sel], ref[sel]) <= 1e-12, (p, q, kern)
         assert np.array_equal(a, tc.eval(kern, g["density"]))
     tc.close()
     f64.close()
