@@ -68,6 +68,15 @@ __device__ __forceinline__ double w_pow2(int e) {
     return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
+// x 2^e by adding e to the exponent field (integer operations; a multiply
+// where the result would leave the normal range)
+__device__ __forceinline__ double w_scale2(double x, int e) {
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    if (ex == 0 || ex + e < 1 || ex + e > 2046) return x * w_pow2(e);
+    return __longlong_as_double(bits + ((long long)e << 52));
+}
+
 __device__ __forceinline__ double2 w_box_centre(const RootInfo &R, int l, int ix, int iy) {
     double h = R.H * w_pow2(-l);
     return make_double2(R.lo_x + (double)(2 * ix + 1) * h, R.lo_y + (double)(2 * iy + 1) * h);
@@ -83,16 +92,6 @@ __host__ __device__ inline uint16_t w_bf16_int(int v) {
 // 16-byte store of eight BF16 values to shared memory
 __device__ __forceinline__ void st_shared16(uint32_t dst, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-}
-
-// BF16 bit pattern of an integer in [-255, 255] (exact), by integer operations
-__device__ __forceinline__ uint32_t bf16_small(int v) {
-    if (v == 0) return 0u;
-    const uint32_t s = v < 0 ? 0x8000u : 0u;
-    const uint32_t a = (uint32_t)(v < 0 ? -v : v);        // 1 .. 255
-    const int msb = 31 - __clz(a);                          // 0 .. 7
-    // value = 2^msb * 1.f: exponent field 127 + msb, mantissa = the bits below the leading one
-    return s | ((uint32_t)(127 + msb) << 7) | ((a << (7 - msb)) & 0x7fu);
 }
 
 struct WArgs {
@@ -323,8 +322,8 @@ __global__ void __launch_bounds__(kWThreads, 1) k_w_centres_tc(WArgs a) {
 #pragma unroll
                 for (int m = 0; m < 16; ++m) {
                     if (m > q) break;
-                    double2 G = make_double2(emax ? (double)vcol[m] * w_pow2(E - 64 + sdrop[m]) : 0.0,
-                                             emax ? (double)vcol[16 + m] * w_pow2(E - 64 + sdrop[16 + m]) : 0.0);
+                    double2 G = make_double2(emax ? w_scale2((double)vcol[m], E - 64 + sdrop[m]) : 0.0,
+                                             emax ? w_scale2((double)vcol[16 + m], E - 64 + sdrop[16 + m]) : 0.0);
                     if (m == 0) {
                         dst[0] = make_double2(A0 * gq_log_half(n2, a.logt) + G.x, G.y);
                     } else {
@@ -343,32 +342,20 @@ __global__ void __launch_bounds__(kWThreads, 1) k_w_centres_tc(WArgs a) {
     if (warp == 0) gqtc::tmem_free(tmem, 512);
 }
 
-// each centre's contributions in list order, added to its QBX coefficients
-__global__ void k_w_centres_reduce(int nc, int q, const int *__restrict__ pstart, const double2 *__restrict__ contrib,
-                                   double2 *__restrict__ Q) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+// each centre's contributions in list order, added to its QBX coefficients:
+// one thread per (centre, real component), so that the threads of a centre
+// read each 16 (q + 1)-byte record together
+__global__ void k_w_centres_reduce(int nc, int q, const int *__restrict__ pstart, const double *__restrict__ contrib,
+                                   double *__restrict__ Q) {
+    const int ncomp = 2 * (q + 1);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nc * ncomp) return;
+    const int c = (int)(t / ncomp), comp = (int)(t - (long long)c * ncomp);
     const int p0 = pstart[c], p1 = pstart[c + 1];
     if (p0 == p1) return;
-    double2 acc[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) acc[m] = make_double2(0.0, 0.0);
-    for (int p = p0; p < p1; ++p) {
-        const double2 *src = contrib + (size_t)p * (q + 1);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            if (m > q) break;
-            const double2 v = src[m];
-            acc[m].x += v.x;
-            acc[m].y += v.y;
-        }
-    }
-    double2 *dst = Q + (size_t)c * (q + 1);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        if (m > q) break;
-        dst[m] = make_double2(dst[m].x + acc[m].x, dst[m].y + acc[m].y);
-    }
+    double acc = 0.0;
+    for (int p = p0; p < p1; ++p) acc += contrib[(size_t)p * ncomp + comp];
+    Q[(size_t)c * ncomp + comp] += acc;
 }
 
 // ---------------------------------------------------------------- pairs (per build)
@@ -531,6 +518,6 @@ void gq_w_centres_tc(gq_geom *g, const RootInfo &R, const double2 *M, const doub
     const int ntiles = (np + kWRows - 1) / kWRows;
     const int grid = ntiles < sms ? ntiles : sms;
     GQ_LAUNCH(ctx, k_w_centres_tc, grid, kWThreads, kWSmem, a);
-    GQ_LAUNCH(ctx, k_w_centres_reduce, gq_blocks(g->nc, 128), 128, 0, g->nc, q, (const int *)g->wtc_pstart.p,
-              (const double2 *)g->wtc_contrib.p, Q);
+    GQ_LAUNCH(ctx, k_w_centres_reduce, gq_blocks((long long)g->nc * 2 * (q + 1), 256), 256, 0, g->nc, q,
+              (const int *)g->wtc_pstart.p, (const double *)g->wtc_contrib.p, (double *)Q);
 }
