@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import ctypes as C
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -196,7 +197,9 @@ def work_model(geo, p, q, kernel="S"):
                 unit="(source, point) pair"),
         2: dict(name="k_m2l_tc" if p <= 15 else "k_m2l", units=v_pairs, flops_per_unit=8 * (p + 1) ** 2,
                 unit="List 2 pair (FP64-equivalent flops of the translation)"),
-        7: dict(name="k_w_centres", units=wf_ctr, flops_per_unit=8 * (p + 1) * (q + 1), unit="(List 3 far box, centre)"),
+        7: dict(name="k_w_centres_tc" if (p <= 16 and q <= 15 and math.comb(q + p - 1, p - 1) < 1 << 24)
+                else "k_w_centres_q", units=wf_ctr, flops_per_unit=8 * (p + 1) * (q + 1),
+                unit="(List 3 far box, centre) pair (FP64-equivalent flops of the translation)"),
     }
 
 
