@@ -277,6 +277,7 @@ gq_status gq_build(gq_geom *g) {
         if (gq_m2l_tc_supported(g)) gq_m2l_tc_build(g);   // tiles of the tensor-core M2L
         if (gq_w_tc_supported(g)) gq_w_tc_build(g);       // pairs of the tensor-core M2QBXL
         GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
+        GQ_REQUIRE(gq_scan_error_take() == 0, GQ_ERR_TIMEOUT, "gq_build: a prefix scan's bounded wait gave up");
         g->built = true;
     });
 }

@@ -203,6 +203,8 @@ inline int gq_blocks(long long n, int threads) {
 // Exclusive prefix sum of n ints: out[0..n] (out[n] = total).  tmp sized by scan_tmp_size.
 size_t gq_scan_tmp_size(long long n);
 void gq_exclusive_scan(gq_ctx *ctx, const int *in, int *out, long long n, int *tmp);
+// nonzero when a scan's bounded look-back wait gave up since the last call (cleared; synchronous)
+int gq_scan_error_take();
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  In/out may alias
 // the temporaries: results are returned in keys/vals.
 void gq_radix_sort_pairs(gq_ctx *ctx, uint64_t *keys, int *vals, long long n, int bits);

@@ -1,6 +1,7 @@
 // gq_prims.cu -- device-wide exclusive scan and stable LSD radix sort used by
 // the quadtree and list construction (tree build by sorting and scanning).
 #include "gq_internal.cuh"
+#include "gq_tc.cuh"
 
 namespace {
 
@@ -38,70 +39,111 @@ __device__ int block_exclusive_scan(int v, int &total) {
     return warp_excl + x - v;
 }
 
-__global__ void k_scan_reduce(const int *__restrict__ in, long long n, int *__restrict__ part) {
-    long long base = (long long)blockIdx.x * kScanTile;
-    int s = 0;
-    for (int i = 0; i < kScanItems; ++i) {
-        long long idx = base + (long long)i * kScanThreads + threadIdx.x;
-        if (idx < n) s += in[idx];
-    }
-    int tot;
-    block_exclusive_scan(s, tot);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+// Single-pass exclusive scan with decoupled look-back: a block takes the next
+// tile number from a counter, publishes its tile's sum, then walks back over
+// its predecessors' published words (32 at a time, one lane each) until it
+// meets one that carries an inclusive prefix; it publishes its own inclusive
+// prefix and writes its outputs.  A word is (flag << 32) | value, flag 1 = the
+// tile's sum, 2 = the inclusive prefix, written with one 64-bit atomic.  A
+// block waits only for tiles taken before its own, by blocks already running
+// that wait only for earlier tiles, so every wait ends; the spin is bounded
+// all the same (about 1 s), after which the error word is set and the block
+// goes on with what it has.
+__device__ int g_scan_err;
+
+__device__ __forceinline__ unsigned long long scan_word_load(const unsigned long long *p) {
+    return *(const volatile unsigned long long *)p;
 }
 
-// offs == nullptr: single tile, also writes out[n] = total
-__global__ void k_scan_tiles(const int *__restrict__ in, long long n, const int *__restrict__ offs,
-                             int *__restrict__ out) {
-    long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int *__restrict__ in, long long n,
+                                                               int *__restrict__ out, unsigned int *counter,
+                                                               unsigned long long *status) {
+    __shared__ int stile, sprefix;
+    if (threadIdx.x == 0) stile = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int tile = stile;
+    const long long nb = (n + kScanTile - 1) / kScanTile;
+    const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        long long idx = base + i;
+        const long long idx = base + i;
         v[i] = idx < n ? in[idx] : 0;
         s += v[i];
     }
     int tot;
-    int pre = block_exclusive_scan(s, tot);
-    int off = offs ? offs[blockIdx.x] : 0;
-    int run = off + pre;
+    const int pre = block_exclusive_scan(s, tot);
+    if (threadIdx.x < 32) {
+        int prefix = 0;
+        if (tile == 0) {
+            if (threadIdx.x == 0) atomicExch(&status[0], (2ull << 32) | (unsigned)tot);
+        } else {
+            if (threadIdx.x == 0) atomicExch(&status[tile], (1ull << 32) | (unsigned)tot);
+            const int lane = threadIdx.x;
+            const unsigned long long t0 = gqtc::globaltimer_ns();
+            int look = tile - 1;   // the newest predecessor not yet added
+            bool timed_out = false;
+            while (look >= 0) {
+                const int j = look - lane;
+                unsigned long long w = 0;
+                if (j >= 0) {
+                    for (;;) {   // bounded: waits for a tile taken earlier
+                        w = scan_word_load(&status[j]);
+                        if ((w >> 32) != 0ull || timed_out) break;
+                        if (gqtc::globaltimer_ns() - t0 > 1000000000ull) {
+                            timed_out = true;
+                            atomicExch(&g_scan_err, 1);
+                        }
+                    }
+                }
+                timed_out = __any_sync(0xffffffffu, timed_out);
+                const unsigned flag = (unsigned)(w >> 32);
+                // the nearest predecessor (lowest lane) with an inclusive prefix
+                const unsigned incl = __ballot_sync(0xffffffffu, j >= 0 && flag == 2u);
+                const int stop = incl ? __ffs(incl) - 1 : 31;
+                int val = (lane <= stop && j >= 0) ? (int)(unsigned)(w & 0xffffffffull) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                prefix += val;
+                if (incl || timed_out) break;
+                look -= 32;
+            }
+            if (lane == 0) atomicExch(&status[tile], (2ull << 32) | (unsigned)(prefix + tot));
+        }
+        if (threadIdx.x == 0) sprefix = prefix;
+    }
+    __syncthreads();
+    int run = sprefix + pre;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        long long idx = base + i;
+        const long long idx = base + i;
         if (idx < n) out[idx] = run;
         run += v[i];
     }
-    if (!offs && threadIdx.x == 0) out[n] = tot;
-}
-
-__global__ void k_set_total(const int *offs_scanned, long long nblk, int *out, long long n) {
-    out[n] = offs_scanned[nblk];
+    if (tile == nb - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;   // the total
+    if (nb == 0 && threadIdx.x == 0) out[0] = 0;
 }
 
 }  // namespace
 
 size_t gq_scan_tmp_size(long long n) {
-    size_t s = 0;
-    while (n > kScanTile) {
-        long long nb = (n + kScanTile - 1) / kScanTile;
-        s += 2 * nb + 1;
-        n = nb;
-    }
-    return s + 16;
+    const long long nb = (n + kScanTile - 1) / kScanTile;
+    return (size_t)(2 * (nb + 2) + 4);   // 8-byte aligned counter + status words, in ints
 }
 
 void gq_exclusive_scan(gq_ctx *ctx, const int *in, int *out, long long n, int *tmp) {
-    if (n <= kScanTile) {
-        GQ_LAUNCH(ctx, k_scan_tiles, 1, kScanThreads, 0, in, n, (const int *)nullptr, out);
-        return;
-    }
-    long long nb = (n + kScanTile - 1) / kScanTile;
-    int *part = tmp, *part_scan = tmp + nb;
-    GQ_LAUNCH(ctx, k_scan_reduce, (int)nb, kScanThreads, 0, in, n, part);
-    gq_exclusive_scan(ctx, part, part_scan, nb, tmp + 2 * nb + 1);
-    GQ_LAUNCH(ctx, k_scan_tiles, (int)nb, kScanThreads, 0, in, n, (const int *)part_scan, out);
-    GQ_LAUNCH(ctx, k_set_total, 1, 1, 0, (const int *)part_scan, nb, out, n);
+    const long long nb = (n + kScanTile - 1) / kScanTile;
+    unsigned long long *w = (unsigned long long *)(((uintptr_t)tmp + 7) & ~(uintptr_t)7);
+    GQ_CUDA(cudaMemsetAsync(w, 0, sizeof(unsigned long long) * (nb + 1), ctx->stream));
+    GQ_LAUNCH(ctx, k_scan_single, (int)(nb > 0 ? nb : 1), kScanThreads, 0, in, n, out, (unsigned int *)w, w + 1);
+}
+
+int gq_scan_error_take() {
+    int h = 0, z = 0;
+    GQ_CUDA(cudaMemcpyFromSymbol(&h, g_scan_err, sizeof(int)));
+    if (h) GQ_CUDA(cudaMemcpyToSymbol(g_scan_err, &z, sizeof(int)));
+    return h;
 }
 
 // ------------------------------------------------------------------ radix sort
