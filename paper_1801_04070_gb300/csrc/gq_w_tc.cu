@@ -29,12 +29,14 @@
 // the epilogue (q complex products and powers, one logarithm) -- about 250
 // FP64 instructions against about 580 for the direct FP64 kernel.
 //
-// CTA: warps 0-3 and 4-7 are two groups that stage, in turn, tiles of 128
-// pairs (thread = pair: FP64 At, integer digit split into shared memory) and
-// run their epilogue; warp 8 issues the 48 MMAs (128 x 32 x 16) of a tile
-// into ten tensor-memory accumulators and commits them.  One accumulator set:
-// a group reads it out (tcgen05.ld) and releases it before finishing its
-// epilogue from registers, while the other group's tile is multiplied.
+// CTA: warps 0-3, 4-7 and 8-11 are three groups that stage, in turn, tiles
+// of 128 pairs (thread = pair: FP64 At, integer digit split into shared
+// memory); the group's first thread then issues the tile's 48 MMAs
+// (128 x 32 x 16) into ten tensor-memory accumulators, once the previous
+// tile has been read out, and commits them.  One accumulator set: a group
+// reads it out (tcgen05.ld) and releases it before finishing its epilogue
+// from registers, while the next group's tile is multiplied.  Twelve warps
+// put three on each SM sub-partition, so a thread may hold 168 registers.
 // Per-pair contributions go to a buffer; a second kernel adds each centre's
 // contributions in list order (deterministic, no atomics).
 #include <math.h>
@@ -59,8 +61,9 @@ constexpr int kWLev = kWAD + kWBD - 1;                // accumulated digit level
 constexpr uint32_t kWTileA = kWRows * kWK * 2;        // bytes per pair digit tile (8 KiB)
 constexpr uint32_t kWTileB = kWN * kWK * 2;           // bytes per constant digit tile (2 KiB)
 constexpr uint32_t kWStageA = kWAD * kWTileA;         // 64 KiB per group
-constexpr uint32_t kWSmem = 2 * kWStageA + kWBD * kWTileB;   // 137,216 bytes
-constexpr int kWThreads = 288;                        // 2 x 4 staging/epilogue warps + 1 issuer warp
+constexpr int kWGroups = 3;                           // staging/epilogue warp groups (4 warps each)
+constexpr uint32_t kWSmem = kWGroups * kWStageA + kWBD * kWTileB;   // 202,752 bytes
+constexpr int kWThreads = 32 * 4 * kWGroups;
 constexpr uint64_t kWWaitNs = 2000000000ull;          // bounded waits: 2 s
 
 // 2^e from its bits (ldexp outside the normal range)
@@ -112,7 +115,7 @@ struct WArgs {
 
 __global__ void __launch_bounds__(kWThreads, 1) k_w_centres_tc(WArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint64_t full[2], accfull[2], tfree;
+    __shared__ uint64_t full[kWGroups], accfull[kWGroups], tfree[kWGroups];
     __shared__ uint32_t tslot;
     __shared__ int sdrop[kWN];
     __shared__ volatile int abort_flag;
@@ -120,15 +123,15 @@ __global__ void __launch_bounds__(kWThreads, 1) k_w_centres_tc(WArgs a) {
     if (warp == 0) gqtc::tmem_alloc(&tslot, 512);
     if (tid < kWN) sdrop[tid] = a.drop[tid];
     if (tid == 0) {
-        gqtc::mbar_init(&full[0], kWRows);
-        gqtc::mbar_init(&full[1], kWRows);
-        gqtc::mbar_init(&accfull[0], 1);
-        gqtc::mbar_init(&accfull[1], 1);
-        gqtc::mbar_init(&tfree, kWRows);
+        for (int g = 0; g < kWGroups; ++g) {
+            gqtc::mbar_init(&full[g], kWRows);
+            gqtc::mbar_init(&accfull[g], 1);
+            gqtc::mbar_init(&tfree[g], kWRows);   // group g's tile read out
+        }
         abort_flag = 0;
     }
     const uint32_t sbase = gqtc::smem_u32(sm);
-    const uint32_t sB = sbase + 2 * kWStageA;
+    const uint32_t sB = sbase + kWGroups * kWStageA;
     // the constant digit tiles, once per CTA
     for (int c = tid; c < (int)(kWBD * kWTileB / 16); c += blockDim.x) {
         const uint4 v = reinterpret_cast<const uint4 *>(a.bdig)[c];
@@ -141,49 +144,15 @@ __global__ void __launch_bounds__(kWThreads, 1) k_w_centres_tc(WArgs a) {
     const uint32_t tmem = tslot;
     const int npairs = *a.npairs;
     const int ntiles = (npairs + kWRows - 1) / kWRows;
-    if (warp == 8) {
-        // ---------------- MMA issue (one thread); tile k of this CTA uses group k & 1
-        if ((tid & 31) == 0) {
-            bool ok = true;
-            int k = 0, last = -1;   // last: the latest tile whose MMAs were committed
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++k) {
-                const int w = k & 1;
-                ok = gqtc::mbar_wait_abortable(&full[w], (uint32_t)((k >> 1) & 1), kWWaitNs, &abort_flag);
-                if (ok && k >= 1) ok = gqtc::mbar_wait_abortable(&tfree, (uint32_t)((k - 1) & 1), kWWaitNs, &abort_flag);
-                if (!ok) break;
-                gqtc::fence_smem_to_async();
-                gqtc::fence_after_sync();
-                const uint32_t sA = sbase + w * kWStageA;
-                // digit pair (i, j) lands in level i + j (32 columns each); the first
-                // product written to a level overwrites it
-#pragma unroll 1
-                for (int j = 0; j < kWBD; ++j)
-#pragma unroll 1
-                    for (int i = 0; i < kWAD; ++i)
-#pragma unroll 1
-                        for (int ks = 0; ks < 2; ++ks) {
-                            const bool first = ks == 0 && (j == 0 || i == kWAD - 1);
-                            const uint64_t ad = gqtc::smem_desc(sA + i * kWTileA + ks * 256, 128, 512);
-                            const uint64_t bd = gqtc::smem_desc(sB + j * kWTileB + ks * 256, 128, 512);
-                            gqtc::mma_bf16(tmem + (uint32_t)((i + j) * 32), ad, bd, gqtc::idesc_bf16_f32(128, 32),
-                                           first ? 0u : 1u);
-                        }
-                gqtc::mma_commit(&accfull[w]);
-                last = k;
-            }
-            // leave no MMA in flight (the accumulators are freed below): wait, boundedly,
-            // for the last commit, which covers every earlier MMA of this thread
-            if (last >= 0) gqtc::mbar_wait(&accfull[last & 1], (uint32_t)((last >> 1) & 1), kWWaitNs);
-        }
-    } else {
+    {
         // ---------------- staging and epilogue: group w, thread r = row of its tiles
         const int w = warp >> 2, r = tid & 127, wq = warp & 3;
         const uint32_t sA = sbase + w * kWStageA;
         const uint32_t rowoff = (uint32_t)(((r >> 3) * (kWK / 8)) << 7) + (uint32_t)((r & 7) << 4);
         const int P = a.P, q = a.q;
         bool ok = true;
-        int k = w;
-        for (int t = blockIdx.x + w * gridDim.x; t < ntiles; t += 2 * gridDim.x, k += 2) {
+        int k = w, pend = -1;   // pend: a tile this thread committed but has not seen complete
+        for (int t = blockIdx.x + w * gridDim.x; t < ntiles; t += kWGroups * gridDim.x, k += kWGroups) {
             const int p = t * kWRows + r;
             const bool valid = p < npairs;
             // ---- stage: At_k of this pair, the row exponent, eight digits per entry
@@ -277,8 +246,43 @@ __global__ void __launch_bounds__(kWThreads, 1) k_w_centres_tc(WArgs a) {
                 }
             gqtc::fence_smem_to_async();
             gqtc::mbar_arrive(&full[w]);
+            // ---- issue: the group's first thread, once the whole group has staged
+            // and the previous tile (another group's) has left the accumulators
+            if (r == 0) {
+                if (ok) ok = gqtc::mbar_wait_abortable(&full[w], (uint32_t)((k / kWGroups) & 1), kWWaitNs, &abort_flag);
+                // tile k - 1 belongs to group (k - 1) % G; its read-out is that barrier's
+                // completion number (k - 1) / G, and the one before (tile k - 1 - G) is
+                // complete (this group's tile k - G was issued after it), so the parity
+                // wait is never more than one phase behind
+                if (ok && k >= 1)
+                    ok = gqtc::mbar_wait_abortable(&tfree[(k - 1) % kWGroups], (uint32_t)(((k - 1) / kWGroups) & 1),
+                                                   kWWaitNs, &abort_flag);
+                if (ok) {
+                    gqtc::fence_smem_to_async();
+                    gqtc::fence_after_sync();
+                    // digit pair (i, j) lands in level i + j (32 columns each); the first
+                    // product written to a level overwrites it
+#pragma unroll 1
+                    for (int j = 0; j < kWBD; ++j)
+#pragma unroll 1
+                        for (int i = 0; i < kWAD; ++i)
+#pragma unroll 1
+                            for (int ks = 0; ks < 2; ++ks) {
+                                const bool first = ks == 0 && (j == 0 || i == kWAD - 1);
+                                const uint64_t ad = gqtc::smem_desc(sA + i * kWTileA + ks * 256, 128, 512);
+                                const uint64_t bd = gqtc::smem_desc(sB + j * kWTileB + ks * 256, 128, 512);
+                                gqtc::mma_bf16(tmem + (uint32_t)((i + j) * 32), ad, bd, gqtc::idesc_bf16_f32(128, 32),
+                                               first ? 0u : 1u);
+                            }
+                    gqtc::mma_commit(&accfull[w]);
+                    pend = k;
+                } else {
+                    abort_flag = 1;
+                }
+            }
             // ---- epilogue: the ten levels of this row, recombined per column
-            if (ok) ok = gqtc::mbar_wait_abortable(&accfull[w], (uint32_t)((k >> 1) & 1), kWWaitNs, &abort_flag);
+            if (ok) ok = gqtc::mbar_wait_abortable(&accfull[w], (uint32_t)((k / kWGroups) & 1), kWWaitNs, &abort_flag);
+            if (ok) pend = -1;
             if (!__all_sync(0xffffffffu, ok)) {   // tcgen05.ld is warp-collective
                 abort_flag = 1;
                 break;
@@ -314,7 +318,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_w_centres_tc(WArgs a) {
                 }
             }
             gqtc::fence_before_sync();
-            gqtc::mbar_arrive(&tfree);   // the accumulators may be overwritten now
+            gqtc::mbar_arrive(&tfree[w]);   // the accumulators may be overwritten now
             if (valid) {
                 const int E = (int)emax - 1022;
                 double2 *dst = a.contrib + (size_t)p * (q + 1);
@@ -335,6 +339,9 @@ __global__ void __launch_bounds__(kWThreads, 1) k_w_centres_tc(WArgs a) {
             }
         }
         if (!ok) abort_flag = 1;
+        // leave no MMA in flight (the accumulators are freed below): wait, boundedly,
+        // for a commit whose completion this thread has not seen
+        if (pend >= 0) gqtc::mbar_wait(&accfull[pend % kWGroups], (uint32_t)((pend / kWGroups) & 1), kWWaitNs);
     }
     if (abort_flag && tid == 0) atomicExch(a.err, 1);
     gqtc::fence_before_sync();
@@ -442,11 +449,31 @@ const WConst &w_const(int dev, int P, int q) {
     return tabs[dev][key] = T;
 }
 
+// Once per device: the shared-memory attribute, and whether one CTA fits an SM
+// (resident blocks per SM from the occupancy calculator).
+bool w_tc_launchable(int dev) {
+    static std::mutex mu;
+    static int state[64] = {};   // 0 unknown, 1 fits, 2 does not
+    if (dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (state[dev] == 0) {
+        int cur = 0;
+        GQ_CUDA(cudaGetDevice(&cur));
+        GQ_CUDA(cudaSetDevice(dev));
+        GQ_CUDA(cudaFuncSetAttribute(k_w_centres_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+        int nb = 0;
+        GQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_w_centres_tc, kWThreads, kWSmem));
+        GQ_CUDA(cudaSetDevice(cur));
+        state[dev] = nb >= 1 ? 1 : 2;
+    }
+    return state[dev] == 1;
+}
+
 }  // namespace
 
 bool gq_w_tc_supported(const gq_geom *g) {
     return g->prm.m2l == GQ_M2L_AUTO && g->prm.p_fmm <= 16 && g->prm.p_qbx <= 15 &&
-           w_binom_fits(g->prm.p_fmm, g->prm.p_qbx);
+           w_binom_fits(g->prm.p_fmm, g->prm.p_qbx) && w_tc_launchable(g->ctx->device);
 }
 
 // Pairs of the current build: every sorted centre with each box of its owner's
@@ -507,12 +534,8 @@ void gq_w_centres_tc(gq_geom *g, const RootInfo &R, const double2 *M, const doub
     a.logt = logt;
     a.contrib = g->wtc_contrib;
     a.err = g->tc_err;
-    static bool attr_set[64] = {};
     const int dev = ctx->device;
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        GQ_CUDA(cudaFuncSetAttribute(k_w_centres_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
-        attr_set[dev] = true;
-    }
+    GQ_REQUIRE(w_tc_launchable(dev), GQ_ERR_UNSUPPORTED, "M2QBXL on tensor cores: the kernel does not fit an SM");
     int sms = 0;
     GQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int ntiles = (np + kWRows - 1) / kWRows;
