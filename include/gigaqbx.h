@@ -489,6 +489,15 @@ gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y);
  * GQ_ERR_TIMEOUT if the bounded completion wait gave up. */
 gq_status gq_probe_umma(gq_ctx *ctx, int K, const uint16_t *a, const uint16_t *b, int swap, float *d);
 
+/* Which translations the next gq_eval of a built geometry runs on the BF16
+ * tensor cores with FP64 accuracy (see gq_params.m2l): *m2l_tc = 1 for the
+ * List 2 translations (Stage 4), *m2qbxl_tc = 1 for List 3 far to the QBX
+ * centres (Stage 5b); 0 where the FP64 FMA kernels (or, in the mixed tiers,
+ * their FP32-pair kernels) run instead -- orders or mode outside the
+ * tensor-core kernels' range, or a device on which the kernel cannot be
+ * resident.  GQ_ERR_STATE before gq_build. */
+gq_status gq_tensor_paths(gq_geom *g, int *m2l_tc, int *m2qbxl_tc);
+
 /* Check of the persistent batch launch's bounded waits: wait_ns bounds every
  * dependency wait (default 1 s); stall_geom >= 0 makes that geometry's final
  * items wait for one direct item more than exist (a count nothing reaches),

@@ -85,6 +85,7 @@ def lib():
             "gq_probe_fma_peak": (st, [vp, i32, C.POINTER(C.c_double)]),
             "gq_probe_math": (st, [vp, i32, i32, vp, vp]),
             "gq_probe_umma": (st, [vp, i32, vp, vp, i32, vp]),
+            "gq_tensor_paths": (st, [vp, C.POINTER(i32), C.POINTER(i32)]),
             "gq_memory_cached": (st, [C.POINTER(C.c_int64)]),
             "gq_memory_release": (st, []),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
@@ -264,6 +265,13 @@ class Geometry:
         res = C.c_double()
         self._check(self.L.gq_gmres(self._geom, _ptr(rhs), tol, maxit, restart, _ptr(mu), C.byref(it), C.byref(res)))
         return mu, it.value, res.value
+
+    def tensor_paths(self):
+        """(List 2 on the tensor cores, List 3 far to centres on the tensor
+        cores) for the next evaluation (gq_tensor_paths)."""
+        a, b = C.c_int(), C.c_int()
+        self._check(self.L.gq_tensor_paths(self._geom, C.byref(a), C.byref(b)))
+        return bool(a.value), bool(b.value)
 
     def features(self):
         """[ncentres, 32] FP32 per-centre features (gq_centre_features)."""

@@ -691,6 +691,15 @@ gq_status gq_probe_umma(gq_ctx *ctx, int K, const uint16_t *a, const uint16_t *b
     });
 }
 
+gq_status gq_tensor_paths(gq_geom *g, int *m2l_tc, int *m2qbxl_tc) {
+    if (!g || !m2l_tc || !m2qbxl_tc) return GQ_ERR_INVALID;
+    if (!g->built) return GQ_ERR_STATE;
+    return guarded(g->ctx, [&] {
+        GQ_CUDA(cudaSetDevice(g->ctx->device));
+        gq_tensor_paths_impl(g, m2l_tc, m2qbxl_tc);
+    });
+}
+
 gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y) {
     if (!ctx || fn < 0 || fn > 5 || n < 0 || (n > 0 && (!x || !y))) return GQ_ERR_INVALID;
     return guarded(ctx, [&] {

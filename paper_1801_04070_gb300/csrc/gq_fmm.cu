@@ -2701,6 +2701,18 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
     g->last_kernel = kernel;
 }
 
+// Which FP64 translations the next gq_eval of g runs on the tensor cores (the
+// conditions of the dispatch in gq_eval_all).
+void gq_tensor_paths_impl(gq_geom *g, int *m2l_tc, int *m2qbxl_tc) {
+    const bool mixed = g->prm.precision == GQ_PREC_MIXED || g->prm.precision == GQ_PREC_MIXED_FMM;
+    const bool f32 = mixed && g->prm.eps >= kF32TierEps;
+    const bool split = mixed && g->prm.eps >= 1e-12 && g->prm.eps < kF32TierEps;
+    const bool split_w = (split || f32) && g->nlev <= 24;
+    const bool m2l_split = g->prm.precision == GQ_PREC_MIXED_FMM && (split || f32) && g->prm.eps >= 1e-10;
+    *m2l_tc = !m2l_split && gq_m2l_tc_supported(g) ? 1 : 0;
+    *m2qbxl_tc = !split_w && g->nc > 0 && gq_w_tc_supported(g) ? 1 : 0;
+}
+
 // the evaluation views a batch item needs
 static void gq_batch_geom_view(gq_geom *g, int kernel, BatchGeomDev &out) {
     EvalTables &T = get_tables(g);

@@ -248,6 +248,7 @@ void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L);
 void gq_m2l_tc_build(gq_geom *g);
 int gq_m2l_tc_error(gq_geom *g);
 bool gq_w_tc_supported(const gq_geom *g);
+void gq_tensor_paths_impl(gq_geom *g, int *m2l_tc, int *m2qbxl_tc);
 void gq_w_tc_build(gq_geom *g);
 void gq_w_centres_tc(gq_geom *g, const RootInfo &R, const double2 *M, const double *logt, double2 *Q);
 struct gq_mlp;

@@ -100,3 +100,18 @@ def test_unknown_m2l_mode_rejected():
     g = workloads.starfish_c1()
     with pytest.raises(GigaQBXError):
         Geometry(g, params_default(m2l=2))
+
+
+def test_tensor_paths_are_taken():
+    """gq_tensor_paths: both translations run on the tensor cores at the
+    benchmark orders (the occupancy-checked launch did not fall back), the List
+    2 kernel stops at p_fmm 15, both stop past p_fmm 16 and with
+    GQ_M2L_FP64, and the mixed tier's pair kernel takes List 3 far."""
+    g = workloads.small_grid(2, 2, 16, 3000, seed=7)
+    cases = [(dict(p_qbx=8, p_fmm=15), (True, True)), (dict(p_qbx=8, p_fmm=16), (False, True)),
+             (dict(p_qbx=5, p_fmm=20), (False, False)), (dict(p_qbx=8, p_fmm=15, m2l=1), (False, False)),
+             (dict(p_qbx=8, p_fmm=15, eps=1e-8, precision=1), (True, False))]
+    for kw, want in cases:
+        geo = _geo(g, n_max=32, **kw)
+        assert geo.tensor_paths() == want, kw
+        geo.close()
