@@ -619,6 +619,9 @@ def run_gpu(args, rank, world, local):
     wrap.L, wrap._ctx, wrap._geom, wrap.nt = L, ctx, geom, nt
     info = TreeInfo()
     chk(L.gq_tree_info_get(geom, C.byref(info)))
+    tp = (C.c_int(), C.c_int())
+    chk(L.gq_tensor_paths(geom, C.byref(tp[0]), C.byref(tp[1])))
+    tensor_paths = {"m2l": bool(tp[0].value), "m2qbxl": bool(tp[1].value)}
     wrap.info, wrap.nbox, wrap.nc, wrap.npt, wrap.nsrc = info, info.nbox, info.ncentres, info.npoint_targets, info.nsources
     model = work_model(wrap, P, Q, args.kernel)
     wrap._geom = wrap._ctx = None     # borrowed handles: released below, not by the wrapper
@@ -871,6 +874,7 @@ def run_gpu(args, rank, world, local):
         "tree_variants": restricted,
         "batched": batched,
         "learned_orders": learned,
+        "tensor_core_translations": tensor_paths,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
