@@ -353,7 +353,7 @@ def run_batched(args, dev, stream):
     auto_pick = "persistent" if b.persistent_tile() > 0 else "graph"
     b.mode(0)
     res["persistent"] = timed3(lambda: b.eval(kern, dens, outs))
-    tile, streams = b.persistent_tile(), b.streams()
+    tile, streams, ctas = b.persistent_tile(), b.streams(), b.persistent_ctas()
     b.mode(1)
     res["graph"] = timed3(lambda: b.eval(kern, dens, outs))
     graph_streams = b.streams()
@@ -414,7 +414,8 @@ def run_batched(args, dev, stream):
             "persistent_targets_per_s": ntot / (res["persistent"] * 1e-3),
             "graph_targets_per_s": ntot / (res["graph"] * 1e-3),
             "sequential_targets_per_s": ntot / (res["sequential"] * 1e-3),
-            "persistent_tile": tile, "persistent_streams": streams, "graph_streams": graph_streams,
+            "persistent_tile": tile, "persistent_ctas": ctas, "persistent_streams": streams,
+            "graph_streams": graph_streams,
             "max_rel_diff_vs_sequential": diff, "gmres": gmres}
 
 

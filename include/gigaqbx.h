@@ -315,8 +315,8 @@ gq_status gq_batch_streams(const gq_batch *b, int *streams);
  *     targets.  Every direct item precedes every final item; a final item
  *     waits, boundedly, for its geometry's direct items (a counter in global
  *     memory); a wait that runs out makes the call return GQ_ERR_TIMEOUT.
- *     The autotuner picks the branch streams and then the target boxes per
- *     direct item (1, 2, 4).  The call synchronises the stream to read the
+ *     The autotuner picks the branch streams, then the target boxes per
+ *     direct item (1, 2, 4), then the CTAs (1, 3/4 or 1/2 per SM).  The call synchronises the stream to read the
  *     wait status.  Other configurations use the branches of mode 1.
  *   mode 1: every evaluation in the per-geometry branches (as described at
  *     gq_batch_eval).
@@ -326,6 +326,9 @@ gq_status gq_batch_mode(gq_batch *b, int mode);
 /* Target boxes per direct item of the persistent launch in use (0: the
  * captured graph does not use the persistent launch). */
 gq_status gq_batch_persistent(const gq_batch *b, int *tile);
+/* CTAs of the persistent launch in use (0: the captured graph does not use
+ * it): the autotuner picks one, three quarters or half of one per SM. */
+gq_status gq_batch_persistent_ctas(const gq_batch *b, int *ctas);
 
 /* Exterior Neumann solves (Sec. 1, as gq_gmres) for every geometry of the
  * batch at once: restarted GMRES(restart) from mu = 0 on each geometry in

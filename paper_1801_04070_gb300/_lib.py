@@ -106,6 +106,7 @@ def lib():
             "gq_batch_streams": (st, [vp, C.POINTER(i32)]),
             "gq_batch_mode": (st, [vp, i32]),
             "gq_batch_persistent": (st, [vp, C.POINTER(i32)]),
+            "gq_batch_persistent_ctas": (st, [vp, C.POINTER(i32)]),
             "gq_batch_wait_test": (st, [vp, C.c_int64, i32]),
             "gq_batch_gmres": (st, [vp, C.POINTER(vp), C.c_double, i32, i32, C.POINTER(vp), C.POINTER(i32),
                                     C.POINTER(C.c_double)]),
@@ -375,6 +376,12 @@ class Batch:
     def persistent_tile(self):
         t = C.c_int()
         self.L.gq_batch_persistent(self._b, C.byref(t))
+        return t.value
+
+    def persistent_ctas(self):
+        """CTAs of the persistent launch in use (0 when the graph branches run)."""
+        t = C.c_int()
+        self.L.gq_batch_persistent_ctas(self._b, C.byref(t))
         return t.value
 
     def wait_test(self, wait_ns, stall_geom):

@@ -443,6 +443,11 @@ gq_status gq_batch_persistent(const gq_batch *b, int *tile) {
     return GQ_OK;
 }
 
+gq_status gq_batch_persistent_ctas(const gq_batch *b, int *ctas) {
+    if (!b || !ctas) return GQ_ERR_INVALID;
+    return guarded(gq_batch_ctx(b), [&] { *ctas = gq_batch_persistent_ctas_impl(b); });
+}
+
 gq_status gq_batch_wait_test(gq_batch *b, int64_t wait_ns, int stall_geom) {
     if (!b || wait_ns <= 0 || stall_geom < -1 || stall_geom >= gq_batch_size(b)) return GQ_ERR_INVALID;
     return guarded(gq_batch_ctx(b), [&] { gq_batch_config_impl(b, 0, (long long)wait_ns, stall_geom); });

@@ -37,6 +37,7 @@ struct gq_batch {
     int mode = 2;                          // 0: persistent where supported, 1: graph branches, 2: the faster
     bool persistent = false;               // the captured graph uses the persistent launch
     int tile = 1;                          // target boxes per direct item (tuned)
+    int quarters = 4;                      // persistent CTAs: quarters of one per SM (tuned)
     unsigned long long wait_ns = 1000000000ull;   // bound of each dependency wait
     int stall_geom = -1;                   // test hook: that geometry's final items can never start
     gq_bplan *plan = nullptr;              // buffers and items of the persistent launch
@@ -168,8 +169,9 @@ cudaGraphExec_t capture(gq_batch *b, int kernel, int ndens, const double *const 
 
 // Persistent variant: branch i records geometry i's strengths and FMM passes
 // (gq_bplan_fmm); after the join, one persistent launch on the origin stream
-// does every direct part and final sum (gq_bplan_persistent).
-cudaGraphExec_t capture_persistent(gq_batch *b, gq_bplan *P, int S, int64_t *kernels) {
+// does every direct part and final sum (gq_bplan_persistent) with `quarters`
+// quarters of a CTA per SM.
+cudaGraphExec_t capture_persistent(gq_batch *b, gq_bplan *P, int S, int quarters, int64_t *kernels) {
     cudaStream_t origin;
     GQ_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
     std::vector<cudaStream_t> st(S);
@@ -215,7 +217,7 @@ cudaGraphExec_t capture_persistent(gq_batch *b, gq_bplan *P, int S, int64_t *ker
             GQ_CUDA(cudaEventRecord(joins[s], st[s]));
             GQ_CUDA(cudaStreamWaitEvent(origin, joins[s], 0));
         }
-        gq_bplan_persistent(P, &octx, sms, b->wait_ns);
+        gq_bplan_persistent(P, &octx, std::max(1, sms * quarters / 4), b->wait_ns);
         GQ_CUDA(cudaStreamEndCapture(origin, &graph));
     } catch (...) {
         for (size_t i = 0; i < b->geoms.size(); ++i)
@@ -292,6 +294,11 @@ void gq_batch_config_impl(gq_batch *b, int mode, long long wait_ns, int stall_ge
 }
 
 int gq_batch_persistent_tile(const gq_batch *b) { return b->persistent ? b->tile : 0; }
+int gq_batch_persistent_ctas_impl(const gq_batch *b) {
+    int sms = 0;
+    GQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx->device));
+    return b->persistent ? std::max(1, sms * b->quarters / 4) : 0;
+}
 
 void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const *dens, double *const *out) {
     gq_ctx *ctx = b->ctx;
@@ -315,7 +322,7 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
         const bool can_p = b->mode != 1 && gq_bplan_supported(b->geoms, kernel);
         const bool try_g = b->mode != 0 || !can_p;
         std::string key = std::string(b->mode == 2 ? "A" : (can_p ? "P" : "")) + shape_key(b, kernel, ndens);
-        int S = 0, tile = 1;
+        int S = 0, tile = 1, quarters = 4;
         bool pers = can_p && !try_g;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -324,12 +331,13 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
             if (it != g_tune.end()) {
                 S = it->second % 100;
                 tile = (it->second / 100) % 100;
-                pers = can_p && (!try_g || (it->second / 10000) == 1);
+                pers = can_p && (!try_g || (it->second / 10000) % 10 == 1);
+                quarters = it->second / 100000 ? it->second / 100000 : 4;
             }
         }
-        auto time_config = [&](bool p, int streams, int t) {
+        auto time_config = [&](bool p, int streams, int t, int qq) {
             int64_t kn = 0;
-            cudaGraphExec_t ex = p ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, t), streams, &kn)
+            cudaGraphExec_t ex = p ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, t), streams, qq, &kn)
                                    : capture(b, kernel, ndens, dens, out, streams, &kn);
             double ms = time_replays(b, ex);
             cudaGraphExecDestroy(ex);
@@ -338,43 +346,53 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
         if (S <= 0 || tile <= 0) {
             // per path: streams for the per-geometry branches first, then (the
             // persistent launch) the target boxes per direct item with those
-            // streams; the faster path wins
+            // streams, then its CTA count; the faster path wins
             double best = 1e300;
             for (int path = 0; path < 2; ++path) {
                 const bool p = path == 0;
                 if (p ? !can_p : !try_g) continue;
                 double pbest = 1e300;
-                int pS = 1, pt = 1;
+                int pS = 1, pt = 1, pq = 4;
                 for (int cand : {1, 2, 4, 8, 16}) {
                     if (cand > (int)n && cand != 1) break;
-                    double ms = time_config(p, cand, 1);
+                    double ms = time_config(p, cand, 1, 4);
                     if (ms < pbest) {
                         pbest = ms;
                         pS = cand;
                     }
                 }
-                if (p)
+                if (p) {
                     for (int t : {2, 4}) {
-                        double ms = time_config(p, pS, t);
+                        double ms = time_config(p, pS, t, 4);
                         if (ms < pbest) {
                             pbest = ms;
                             pt = t;
                         }
                     }
+                    for (int qq : {3, 2}) {
+                        double ms = time_config(p, pS, pt, qq);
+                        if (ms < pbest) {
+                            pbest = ms;
+                            pq = qq;
+                        }
+                    }
+                }
                 {   // each path's winner also serves a later call in mode 0 or 1
                     std::lock_guard<std::mutex> lk(g_tune_mu);
-                    g_tune[std::string(p ? "P" : "") + shape_key(b, kernel, ndens)] = (p ? 10000 : 0) + pt * 100 + pS;
+                    g_tune[std::string(p ? "P" : "") + shape_key(b, kernel, ndens)] =
+                        pq * 100000 + (p ? 10000 : 0) + pt * 100 + pS;
                 }
                 if (pbest < best) {
                     best = pbest;
                     S = pS;
                     tile = pt;
+                    quarters = pq;
                     pers = p;
                 }
             }
             b->tuned_ms = best;
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tune[key] = (pers ? 10000 : 0) + tile * 100 + S;
+            g_tune[key] = quarters * 100000 + (pers ? 10000 : 0) + tile * 100 + S;
             save_cache_file();
         }
         b->persistent = pers;
@@ -386,10 +404,11 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
             }
             GQ_REQUIRE(e == 0, GQ_ERR_TIMEOUT, "batched evaluation: a bounded dependency wait gave up");
         }
-        b->exec = b->persistent ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, tile), S,
+        b->exec = b->persistent ? capture_persistent(b, plan_for(b, kernel, ndens, dens, out, tile), S, quarters,
                                                      &b->kernels_per_replay)
                                 : capture(b, kernel, ndens, dens, out, S, &b->kernels_per_replay);
         b->tile = tile;
+        b->quarters = quarters;
         b->kernel = kernel;
         b->ndens = ndens;
         b->streams = S;

@@ -272,6 +272,7 @@ void gq_batch_eval_impl(gq_batch *b, int kernel, int ndens, const double *const 
 int gq_batch_streams(const gq_batch *b);
 void gq_batch_config_impl(gq_batch *b, int mode, long long wait_ns, int stall_geom);
 int gq_batch_persistent_tile(const gq_batch *b);
+int gq_batch_persistent_ctas_impl(const gq_batch *b);
 gq_ctx *gq_batch_ctx(const gq_batch *b);
 int gq_batch_size(const gq_batch *b);
 gq_geom *gq_batch_geom(const gq_batch *b, int i);

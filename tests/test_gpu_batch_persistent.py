@@ -48,12 +48,14 @@ def test_persistent_equals_graph_and_eval(q, nd):
         b.eval(kern, dens, outs)           # a replay
         torch.cuda.synchronize()
         assert b.persistent_tile() in (1, 2, 4)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert b.persistent_ctas() in (sms, sms * 3 // 4, sms // 2)
         assert all(torch.equal(a, c) for a, c in zip(first, outs)), kern
         pers = [o.clone() for o in outs]
         b.mode(1)
         b.eval(kern, dens, outs)
         torch.cuda.synchronize()
-        assert b.persistent_tile() == 0
+        assert b.persistent_tile() == 0 and b.persistent_ctas() == 0
         for a, c in zip(pers, outs):
             assert (a - c).abs().max().item() <= 1e-12 * c.abs().max().item(), kern
         for geo, d, o in zip(geos, dens, pers):
