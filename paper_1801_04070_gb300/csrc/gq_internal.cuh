@@ -182,6 +182,8 @@ struct gq_geom {
     dbuf<float4> L2;      // local expansions
     dbuf<float4> lvl2;    // per level: (rho, 1/rho), (log rho, 1/rho^2)
     // tensor-core M2L (gq_m2l_tc.cu): tiles of the current build, multipole digits
+    // scratch of compact_flags and of its callers' flags (kept between calls)
+    dbuf<int> cf_pos, cf_tmp, cf_flag;
     // M2QBXL on the tensor cores: (centre, List 3 far box) pairs of the build
     bool wtc_ready = false;
     int wtc_npairs = 0;
@@ -203,6 +205,8 @@ inline int gq_blocks(long long n, int threads) {
 // Exclusive prefix sum of n ints: out[0..n] (out[n] = total).  tmp sized by scan_tmp_size.
 size_t gq_scan_tmp_size(long long n);
 void gq_exclusive_scan(gq_ctx *ctx, const int *in, int *out, long long n, int *tmp);
+// the same for the flags vals[i] > thresh (computed on the fly)
+void gq_exclusive_scan_above(gq_ctx *ctx, const int *vals, int thresh, int *out, long long n, int *tmp);
 // nonzero when a scan's bounded look-back wait gave up since the last call (cleared; synchronous)
 int gq_scan_error_take();
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  In/out may alias

@@ -55,9 +55,20 @@ __device__ __forceinline__ unsigned long long scan_word_load(const unsigned long
     return *(const volatile unsigned long long *)p;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int *__restrict__ in, long long n,
-                                                               int *__restrict__ out, unsigned int *counter,
-                                                               unsigned long long *status) {
+// the scanned values: an array, or the flags vals[i] > thresh
+struct ScanArray {
+    const int *p;
+    __device__ __forceinline__ int operator()(long long i) const { return p[i]; }
+};
+struct ScanAbove {
+    const int *p;
+    int thresh;
+    __device__ __forceinline__ int operator()(long long i) const { return p[i] > thresh ? 1 : 0; }
+};
+
+template <class Ld>
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(Ld in, long long n, int *__restrict__ out,
+                                                               unsigned int *counter, unsigned long long *status) {
     __shared__ int stile, sprefix;
     if (threadIdx.x == 0) stile = (int)atomicAdd(counter, 1u);
     __syncthreads();
@@ -69,7 +80,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(const int *__restr
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const long long idx = base + i;
-        v[i] = idx < n ? in[idx] : 0;
+        v[i] = idx < n ? in(idx) : 0;
         s += v[i];
     }
     int tot;
@@ -132,11 +143,21 @@ size_t gq_scan_tmp_size(long long n) {
     return (size_t)(2 * (nb + 2) + 4);   // 8-byte aligned counter + status words, in ints
 }
 
-void gq_exclusive_scan(gq_ctx *ctx, const int *in, int *out, long long n, int *tmp) {
+template <class Ld>
+static void scan_launch(gq_ctx *ctx, Ld in, int *out, long long n, int *tmp) {
     const long long nb = (n + kScanTile - 1) / kScanTile;
     unsigned long long *w = (unsigned long long *)(((uintptr_t)tmp + 7) & ~(uintptr_t)7);
     GQ_CUDA(cudaMemsetAsync(w, 0, sizeof(unsigned long long) * (nb + 1), ctx->stream));
-    GQ_LAUNCH(ctx, k_scan_single, (int)(nb > 0 ? nb : 1), kScanThreads, 0, in, n, out, (unsigned int *)w, w + 1);
+    auto k = k_scan_single<Ld>;
+    GQ_LAUNCH(ctx, k, (int)(nb > 0 ? nb : 1), kScanThreads, 0, in, n, out, (unsigned int *)w, w + 1);
+}
+
+void gq_exclusive_scan(gq_ctx *ctx, const int *in, int *out, long long n, int *tmp) {
+    scan_launch(ctx, ScanArray{in}, out, n, tmp);
+}
+
+void gq_exclusive_scan_above(gq_ctx *ctx, const int *vals, int thresh, int *out, long long n, int *tmp) {
+    scan_launch(ctx, ScanAbove{vals, thresh}, out, n, tmp);
 }
 
 int gq_scan_error_take() {

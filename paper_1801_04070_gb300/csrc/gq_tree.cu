@@ -286,11 +286,6 @@ __global__ void k_gather_int(long long n, const int *__restrict__ idx, const int
 }
 
 // ------------------------------------------------------------------ A4: level-by-level subdivision
-__global__ void k_flags_level(long long n, const int *__restrict__ elig, int l, int *__restrict__ flag) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = elig[i] >= l + 1;
-}
-
 __device__ int lower_bound_prefix(const uint64_t *K, int lo, int hi, int shift, uint64_t target) {
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
@@ -515,18 +510,20 @@ __global__ void k_flag_nonempty(int n, const int *__restrict__ beg, const int *_
 
 }  // namespace
 
-// compact indices i in [0, n) with flag[i] != 0 into out (ascending); returns the count
+// compact indices i in [0, n) with flag[i] != 0 into out (ascending); returns the
+// count.  The scan's buffers belong to the geometry (grown, never freed during a
+// build), so nothing goes back to the shared pool while the kernels may still
+// read it and no second synchronisation is needed.
 static int compact_flags(gq_geom *g, const int *flag, long long n, dbuf<int> &out) {
-    dbuf<int> pos, tmp;
-    pos.alloc(n + 1);
-    tmp.alloc(gq_scan_tmp_size(n));
-    gq_exclusive_scan(g->ctx, flag, pos.p, n, tmp.p);
+    g->cf_pos.alloc(n + 1);
+    g->cf_tmp.alloc(gq_scan_tmp_size(n));
+    gq_exclusive_scan(g->ctx, flag, g->cf_pos.p, n, g->cf_tmp.p);
     int cnt = 0;
-    GQ_CUDA(cudaMemcpyAsync(&cnt, pos.p + n, sizeof(int), cudaMemcpyDeviceToHost, g->ctx->stream));
+    GQ_CUDA(cudaMemcpyAsync(&cnt, g->cf_pos.p + n, sizeof(int), cudaMemcpyDeviceToHost, g->ctx->stream));
     GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
     out.alloc(cnt);
-    if (n > 0) GQ_LAUNCH(g->ctx, k_compact_index, gq_blocks(n, kT), kT, 0, (int)n, flag, (const int *)pos.p, out.p);
-    GQ_CUDA(cudaStreamSynchronize(g->ctx->stream));
+    if (n > 0)
+        GQ_LAUNCH(g->ctx, k_compact_index, gq_blocks(n, kT), kT, 0, (int)n, flag, (const int *)g->cf_pos.p, out.p);
     return cnt;
 }
 
@@ -545,7 +542,7 @@ static void associate(gq_geom *g) {
     int nt = g->nt, nc = g->nc;
     g->t_kind.alloc(nt);
     g->t_ctr.alloc(nt);
-    dbuf<int> is_pt;
+    dbuf<int> &is_pt = g->cf_flag;   // read by the compaction after this function returns
     is_pt.alloc(nt);
     Ext ce = device_extent(g, 0);
     double slack = g->prm.assoc_slack;
@@ -718,8 +715,8 @@ void gq_build_all(gq_geom *g) {
         for (int l = 0;; ++l) {
             LevelBufs &cur = *lv[l];
             int nl = cur.n;
-            GQ_LAUNCH(ctx, k_flags_level, gq_blocks(N, kT), kT, 0, N, (const int *)elig.p, l, flag.p);
-            gq_exclusive_scan(ctx, flag.p, P.p, N, scan_tmp.p);
+            // prefix counts of the particles eligible at level l + 1 (elig > l)
+            gq_exclusive_scan_above(ctx, (const int *)elig.p, l, P.p, N, scan_tmp.p);
             nchild.alloc(nl);
             coff.alloc(nl + 1);
             cbeg.alloc(nl);
@@ -909,7 +906,7 @@ __global__ void k_flag_far(int nbox, const int *__restrict__ voff, const int *__
 }
 
 void gq_build_far_boxes(gq_geom *g) {
-    dbuf<int> bflag;
+    dbuf<int> &bflag = g->cf_flag;   // read by the compaction after this function returns
     bflag.alloc(g->nbox);
     GQ_LAUNCH(g->ctx, k_flag_far, gq_blocks(g->nbox, kT), kT, 0, g->nbox, (const int *)g->list_off[1].p,
               (const int *)g->list_off[5].p, bflag.p);
