@@ -190,7 +190,7 @@ struct gq_geom {
     dbuf<int> wtc_pstart, wtc_pc, wtc_pd;
     dbuf<double2> wtc_contrib;
     bool tc_ready = false;
-    dbuf<int> tc_tile_box, tc_slot_src, tc_tile_q, tc_err, tc_bexp, tc_lexp, tc_counter, tc_ntiles_dev, tc_cnt;
+    dbuf<int> tc_tile_box, tc_slot_src, tc_tile_q, tc_err, tc_lexp, tc_counter, tc_ntiles_dev, tc_cnt;
     dbuf<unsigned> tc_tile_mask;
     dbuf<uint16_t> tc_mdig;
 };

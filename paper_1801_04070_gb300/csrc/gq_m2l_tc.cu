@@ -83,8 +83,10 @@ __host__ __device__ inline uint16_t bf16_of_small_int(int v) {
 }
 
 // ---------------------------------------------------------------- per-eval: multipole digits
-// largest biased exponent of box b's 32 real multipole terms (a warp per box)
-__global__ void k_tc_boxexp(int nbox, int P, const double2 *__restrict__ M, int *__restrict__ bexp) {
+// largest biased exponent of the 32 real multipole terms of every box of a
+// level (a warp per box, then an atomic maximum per level; lexp zeroed first)
+__global__ void k_tc_levexp(int nbox, int P, const int *__restrict__ blev, const double2 *__restrict__ M,
+                            int *__restrict__ lexp) {
     int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, kk = threadIdx.x & 31;
     if (b >= nbox) return;
     int k = kk >> 1;
@@ -95,24 +97,7 @@ __global__ void k_tc_boxexp(int nbox, int P, const double2 *__restrict__ M, int 
     }
     unsigned e = (unsigned)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
     e = __reduce_max_sync(0xffffffffu, e);
-    if (kk == 0) bexp[b] = (int)e;
-}
-
-// largest exponent per level (one block per level)
-__global__ void k_tc_levexp(const int *__restrict__ level_start, const int *__restrict__ bexp, int *__restrict__ lexp) {
-    __shared__ int red[32];
-    int l = blockIdx.x;
-    int s = level_start[l], e = level_start[l + 1];
-    int m = 0;
-    for (int b = s + threadIdx.x; b < e; b += blockDim.x) m = max(m, bexp[b]);
-    m = __reduce_max_sync(0xffffffffu, (unsigned)m);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        int v = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0;
-        v = __reduce_max_sync(0xffffffffu, (unsigned)v);
-        if (threadIdx.x == 0) lexp[l] = v;
-    }
+    if (kk == 0 && e) atomicMax(&lexp[blev[b]], (int)e);
 }
 
 // 11 BF16 digits of every real multipole term at its level's exponent:
@@ -571,11 +556,10 @@ void gq_m2l_tc(gq_geom *g, const double2 *M, double2 *L) {
     if (!g->tc_ready) gq_m2l_tc_build(g);
     const TcConst &T = tc_const(ctx->device);
     const int nbox = g->nbox, P = g->prm.p_fmm;
-    g->tc_bexp.alloc(nbox);
     g->tc_lexp.alloc(g->nlev);
     g->tc_mdig.alloc((size_t)nbox * kTcND * kTcK);
-    GQ_LAUNCH(ctx, k_tc_boxexp, gq_blocks((long long)nbox * 32, 256), 256, 0, nbox, P, M, g->tc_bexp.p);
-    GQ_LAUNCH(ctx, k_tc_levexp, g->nlev, 256, 0, (const int *)g->level_start.p, (const int *)g->tc_bexp.p,
+    GQ_CUDA(cudaMemsetAsync(g->tc_lexp.p, 0, sizeof(int) * g->nlev, ctx->stream));
+    GQ_LAUNCH(ctx, k_tc_levexp, gq_blocks((long long)nbox * 32, 256), 256, 0, nbox, P, (const int *)g->blev.p, M,
               g->tc_lexp.p);
     GQ_LAUNCH(ctx, k_tc_digits, gq_blocks((long long)nbox * 32, 256), 256, 0, nbox, P, (const int *)g->blev.p,
               (const int *)g->tc_lexp.p, M, g->tc_mdig.p);
