@@ -193,11 +193,32 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
     return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
-__global__ void k_m2m_t(EvalView E, int lstart, int lend, const double2 *__restrict__ T, double2 *__restrict__ M) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int P1 = E.P + 1;
-    int b = lstart + (int)(t / P1), m = (int)(t % P1);
-    if (b >= lend) return;
+// M2M and L2L with the quadrant matrices, one level per launch: a block takes
+// 128 / (P + 1) boxes, thread (box, order m).  The block first stages the
+// boxes' children's multipoles (M2M) or parents' local expansions (L2L) in
+// shared memory with one round of independent loads; each output is then
+// summed over k in ascending order exactly as one thread per order would.
+__device__ __forceinline__ int tab_boxes(int P1) { return 128 / P1; }
+__device__ __forceinline__ int child_of(int4 c4, int q) { return q == 0 ? c4.x : q == 1 ? c4.y : q == 2 ? c4.z : c4.w; }
+
+__global__ void __launch_bounds__(128) k_m2m_t(EvalView E, int lstart, int lend, const double2 *__restrict__ T,
+                                               double2 *__restrict__ M) {
+    __shared__ double2 sA[4 * 128];
+    const int P1 = E.P + 1, bpb = tab_boxes(P1);
+    const int b0 = lstart + blockIdx.x * bpb;
+    for (int i = threadIdx.x; i < bpb * 4 * P1; i += blockDim.x) {
+        const int bb = i / (4 * P1), rest = i - bb * 4 * P1, q = rest / P1, k = rest - q * P1;
+        const int b = b0 + bb;
+        double2 v = make_double2(0.0, 0.0);
+        if (b < lend) {
+            const int c = child_of(E.bchild[b], q);
+            if (c >= 0) v = M[(size_t)c * P1 + k];
+        }
+        sA[i] = v;
+    }
+    __syncthreads();
+    const int bl = threadIdx.x / P1, m = threadIdx.x - bl * P1, b = b0 + bl;
+    if (bl >= bpb || b >= lend) return;
     int4 c4 = E.bchild[b];
     int ch[4] = {c4.x, c4.y, c4.z, c4.w};
     if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;  // leaf
@@ -206,7 +227,7 @@ __global__ void k_m2m_t(EvalView E, int lstart, int lend, const double2 *__restr
     for (int q = 0; q < 4; ++q) {
         int c = ch[q];
         if (c < 0 || E.sub_src[c] == 0) continue;
-        const double2 *A = M + (size_t)c * P1;
+        const double2 *A = sA + (bl * 4 + q) * P1;
         if (m == 0) {
             acc = cadd(acc, A[0]);
             continue;
@@ -219,14 +240,22 @@ __global__ void k_m2m_t(EvalView E, int lstart, int lend, const double2 *__restr
     M[(size_t)b * P1 + m] = acc;
 }
 
-__global__ void k_l2l_t(EvalView E, int lstart, int lend, const double2 *__restrict__ U, double2 *__restrict__ L) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int P1 = E.P + 1;
-    int c = lstart + (int)(t / P1), m = (int)(t % P1);
-    if (c >= lend || E.sub_tgt[c] == 0) return;
-    int p = E.bparent[c];
+__global__ void __launch_bounds__(128) k_l2l_t(EvalView E, int lstart, int lend, const double2 *__restrict__ U,
+                                               double2 *__restrict__ L) {
+    __shared__ double2 sB[128];
+    const int P1 = E.P + 1, bpb = tab_boxes(P1);
+    const int c0 = lstart + blockIdx.x * bpb;
+    for (int i = threadIdx.x; i < bpb * P1; i += blockDim.x) {
+        const int bb = i / P1, k = i - bb * P1, c = c0 + bb;
+        double2 v = make_double2(0.0, 0.0);
+        if (c < lend) v = L[(size_t)E.bparent[c] * P1 + k];   // levels >= 1: the parent exists
+        sB[i] = v;
+    }
+    __syncthreads();
+    const int bl = threadIdx.x / P1, m = threadIdx.x - bl * P1, c = c0 + bl;
+    if (bl >= bpb || c >= lend || E.sub_tgt[c] == 0) return;
     int q = (E.bix[c] & 1) | ((E.biy[c] & 1) << 1);
-    const double2 *B = L + (size_t)p * P1;
+    const double2 *B = sB + bl * P1;
     const double2 *Uq = U + ((size_t)q * kTN + m) * kTN;
     double2 acc = make_double2(0.0, 0.0);
     for (int k = m; k <= E.P; ++k) acc = cfma(__ldg(&Uq[k]), B[k], acc);
@@ -2560,7 +2589,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         if (m2l_split)
             GQ_LAUNCH(ctx, k_m2m_split, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, T.tm2m2, g->M2.p);
         else
-            GQ_LAUNCH(ctx, k_m2m_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e,
+            GQ_LAUNCH(ctx, k_m2m_t, gq_blocks(e - s, 128 / P1), (128 / P1) * P1, 0, E, s, e,
                       (const double2 *)T.tm2m, g->M.p);
     }
     mark(S_M2M, st);
@@ -2607,7 +2636,7 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         if (m2l_split)
             GQ_LAUNCH(ctx, k_l2l_split, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, T.tl2l2, g->L2.p);
         else
-            GQ_LAUNCH(ctx, k_l2l_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e,
+            GQ_LAUNCH(ctx, k_l2l_t, gq_blocks(e - s, 128 / P1), (128 / P1) * P1, 0, E, s, e,
                       (const double2 *)T.tl2l, g->L.p);
     }
     if (m2l_split)
@@ -3115,7 +3144,7 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
     }
     for (int l = g->nlev - 2; l >= 0; --l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_m2m_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, tm2m, M);
+        GQ_LAUNCH(ctx, k_m2m_t, gq_blocks(e - s, 128 / P1), (128 / P1) * P1, 0, E, s, e, tm2m, M);
     }
     if (g->n_far_boxes) {
         size_t sm = sizeof(double) * P1 * P1;
@@ -3129,7 +3158,7 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
     }
     for (int l = 1; l < g->nlev; ++l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_l2l_t, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, tl2l, L);
+        GQ_LAUNCH(ctx, k_l2l_t, gq_blocks(e - s, 128 / P1), (128 / P1) * P1, 0, E, s, e, tl2l, L);
     }
     // the direct part writes the coefficients, the List 3 far and local parts add to them
     if (g->n_ctr_boxes) dispatch_near_centres(ctx, E, g->n_ctr_boxes, g->ctr_boxes, Qc);
