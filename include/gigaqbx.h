@@ -304,7 +304,7 @@ gq_status gq_batch_streams(const gq_batch *b, int *streams);
 
 /* How gq_batch_eval evaluates (the next call recaptures):
  *   mode 2 (default): the autotuner times modes 0 and 1 (each with its own
- *     streams and tiles) and keeps the faster.
+ *     streams, and for mode 0 its tiles and CTA count) and keeps the faster.
  *   mode 0: when every geometry is FP64 with the same p_qbx (5 or
  *     8), the graph's per-geometry branches run only the strengths and the
  *     FMM passes (Stages 2, 4, 5b, 6b, 7, 8) of each density into buffers of
