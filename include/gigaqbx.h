@@ -501,6 +501,17 @@ gq_status gq_probe_umma(gq_ctx *ctx, int K, const uint16_t *a, const uint16_t *b
  * resident.  GQ_ERR_STATE before gq_build. */
 gq_status gq_tensor_paths(gq_geom *g, int *m2l_tc, int *m2qbxl_tc);
 
+/* Check of the one-pass list construction (no counterpart in the paper):
+ * gq_build enumerates each box's lists once into scratch rows of fixed
+ * capacity and copies them into the CSR arrays; a box whose list exceeds its
+ * row sends the build to a second enumeration that fills the CSR rows
+ * directly, with the same lists.  row_cap > 0 caps every row at row_cap
+ * entries for this geometry's next builds, 0 restores the default
+ * capacities, and a negative value leaves the setting as it is.  *passes
+ * (if not null) receives the enumeration passes of the geometry's last
+ * build (1 or 2; 0 before the first).  No device work. */
+gq_status gq_lists_check(gq_geom *g, int row_cap, int *passes);
+
 /* Check of the persistent batch launch's bounded waits: wait_ns bounds every
  * dependency wait (default 1 s); stall_geom >= 0 makes that geometry's final
  * items wait for one direct item more than exist (a count nothing reaches),

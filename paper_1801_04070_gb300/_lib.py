@@ -86,6 +86,7 @@ def lib():
             "gq_probe_math": (st, [vp, i32, i32, vp, vp]),
             "gq_probe_umma": (st, [vp, i32, vp, vp, i32, vp]),
             "gq_tensor_paths": (st, [vp, C.POINTER(i32), C.POINTER(i32)]),
+            "gq_lists_check": (st, [vp, i32, C.POINTER(i32)]),
             "gq_memory_cached": (st, [C.POINTER(C.c_int64)]),
             "gq_memory_release": (st, []),
             "gq_tree_info_get": (st, [vp, C.POINTER(TreeInfo)]),
@@ -273,6 +274,14 @@ class Geometry:
         a, b = C.c_int(), C.c_int()
         self._check(self.L.gq_tensor_paths(self._geom, C.byref(a), C.byref(b)))
         return bool(a.value), bool(b.value)
+
+    def lists_check(self, row_cap=-1):
+        """Enumeration passes of the last list construction (gq_lists_check);
+        row_cap >= 0 sets the scratch row capacity of the next builds (0: the
+        default capacities)."""
+        n = C.c_int()
+        self._check(self.L.gq_lists_check(self._geom, int(row_cap), C.byref(n)))
+        return n.value
 
     def features(self):
         """[ncentres, 32] FP32 per-centre features (gq_centre_features)."""

@@ -705,6 +705,13 @@ gq_status gq_tensor_paths(gq_geom *g, int *m2l_tc, int *m2qbxl_tc) {
     });
 }
 
+gq_status gq_lists_check(gq_geom *g, int row_cap, int *passes) {
+    if (!g) return GQ_ERR_INVALID;
+    if (row_cap >= 0) g->list_row_cap = row_cap;
+    if (passes) *passes = g->lists_fill_passes;
+    return GQ_OK;
+}
+
 gq_status gq_probe_math(gq_ctx *ctx, int fn, int n, const double *x, double *y) {
     if (!ctx || fn < 0 || fn > 5 || n < 0 || (n > 0 && (!x || !y))) return GQ_ERR_INVALID;
     return guarded(ctx, [&] {

@@ -138,6 +138,8 @@ struct gq_geom {
     // lists (CSR over boxes): 0 U, 1 V, 2 WC, 3 WF, 4 XC, 5 XF
     dbuf<int> list_off[6], list_idx[6];
     int64_t list_size[6] = {0, 0, 0, 0, 0, 0};
+    int list_row_cap = 0;            // scratch row capacity override of the list fill (0: per-list defaults)
+    int lists_fill_passes = 0;       // enumeration passes of the last list construction (1 or 2)
     // work lists for the evaluation
     dbuf<int> leaf_src_boxes;  int n_leaf_src = 0;   // leaves owning sources
     dbuf<int> ctr_boxes;       int n_ctr_boxes = 0;  // boxes owning centres

@@ -1,6 +1,8 @@
 // gq_lists.cu -- interaction lists of Sec. 4.3.2 (Definitions 1-8) for the
-// target-confinement quadtree, as CSR arrays over boxes, built by a count
-// pass, a prefix scan and a fill pass that share one enumeration routine.
+// target-confinement quadtree, as CSR arrays over boxes: one enumeration pass
+// writes each box's entries to fixed-capacity scratch rows and counts them, a
+// prefix scan gives the CSR offsets, and a compaction copies the rows; if a
+// row overflows, a second enumeration fills the CSR rows directly.
 //
 // Same-level neighbours come from a 5x5 window of box indices per box, built
 // level by level from the parent's window (no searches).
@@ -163,13 +165,28 @@ enum { LU = 0, LV = 1, LWC = 2, LWF = 3, LXC = 4, LXF = 5 };
 // stack modes
 enum { M_OWN = 0, M_COLL = 1, M_FARCLOSE = 2, M_LEAVES_WC = 3 };
 
+// Row capacities of the one-pass fill (entries per box and list): List 2 holds
+// at most 75 boxes, List 4 close 42 and List 4 far 63; Lists 1 and 3 have no
+// fixed bound, and a box that exceeds a capacity sends the build to the
+// second enumeration pass, which fills the exact CSR rows.
+constexpr int kRowCap[6] = {64, 80, 128, 96, 48, 64};
+
+enum { E_COUNT = 0, E_FILL = 1, E_ROWS = 2 };
+
+// scratch rows: list i's rows (cap[i] slots each) start at base[i]
+struct RowTable {
+    int cap[6];
+    long long base[6];
+};
+
 struct Emitter {
-    bool fill;
+    int mode;   // E_COUNT: count only; E_FILL: write the CSR rows; E_ROWS: write capped scratch rows
     int cnt[6];
+    int cap[6];
     int *dst[6];
     __device__ void emit(int which, int d) {
-        if (fill) dst[which][cnt[which]] = d;
-        cnt[which]++;
+        int c = cnt[which]++;
+        if (mode == E_FILL || (mode == E_ROWS && c < cap[which])) dst[which][c] = d;
     }
 };
 
@@ -319,25 +336,49 @@ __device__ void enumerate(const TreeView &T, int b, Emitter &E, int *err) {
     }
 }
 
-__global__ void k_lists(TreeView T, int nbox, int fill, const int *__restrict__ off0, const int *__restrict__ off1,
-                        const int *__restrict__ off2, const int *__restrict__ off3, const int *__restrict__ off4,
-                        const int *__restrict__ off5, int *idx0, int *idx1, int *idx2, int *idx3, int *idx4, int *idx5,
-                        int *cnt0, int *cnt1, int *cnt2, int *cnt3, int *cnt4, int *cnt5, int *err) {
+struct ListPtrs {
+    const int *off[6];
+    int *idx[6];
+    int *cnt[6];
+};
+
+// One enumeration per box.  E_ROWS (the default pass): entries go to row b of
+// the scratch table and the counts to cnt; a count above its row's capacity
+// raises *ovf.  E_COUNT counts only; E_FILL writes the CSR rows at off[i][b].
+__global__ void k_lists(TreeView T, int nbox, int mode, ListPtrs LP, RowTable R, int *__restrict__ rows, int *err,
+                        int *ovf) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox) return;
     Emitter E;
-    E.fill = fill != 0;
-    for (int i = 0; i < 6; ++i) E.cnt[i] = 0;
-    if (fill) {
-        E.dst[0] = idx0 + off0[b]; E.dst[1] = idx1 + off1[b]; E.dst[2] = idx2 + off2[b];
-        E.dst[3] = idx3 + off3[b]; E.dst[4] = idx4 + off4[b]; E.dst[5] = idx5 + off5[b];
+    E.mode = mode;
+    for (int i = 0; i < 6; ++i) {
+        E.cnt[i] = 0;
+        E.cap[i] = R.cap[i];
+        if (mode == E_FILL) E.dst[i] = LP.idx[i] + LP.off[i][b];
+        else if (mode == E_ROWS) E.dst[i] = rows + R.base[i] + (long long)b * R.cap[i];
     }
     int e = 0;
     enumerate(T, b, E, &e);
     if (e) atomicExch(err, 1);
-    if (!fill) {
-        cnt0[b] = E.cnt[0]; cnt1[b] = E.cnt[1]; cnt2[b] = E.cnt[2];
-        cnt3[b] = E.cnt[3]; cnt4[b] = E.cnt[4]; cnt5[b] = E.cnt[5];
+    if (mode != E_FILL) {
+        bool over = false;
+        for (int i = 0; i < 6; ++i) {
+            LP.cnt[i][b] = E.cnt[i];
+            over |= E.cnt[i] > R.cap[i];
+        }
+        if (over && mode == E_ROWS) atomicExch(ovf, 1);
+    }
+}
+
+// the scratch rows into the CSR arrays: one warp per box
+__global__ void k_lists_compact(int nbox, ListPtrs LP, RowTable R, const int *__restrict__ rows) {
+    int b = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (b >= nbox) return;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int o = LP.off[i][b], n = LP.off[i][b + 1] - o;
+        const int *src = rows + R.base[i] + (long long)b * R.cap[i];
+        for (int j = lane; j < n; j += 32) LP.idx[i][o + j] = src[j];
     }
 }
 
@@ -399,36 +440,51 @@ void gq_build_lists(gq_geom *g) {
                   (const int *)g->bix.p, (const int *)g->biy.p, (const int4 *)g->bchild.p, win.p);
     }
     T.win = win.p;
-    dbuf<int> cnt[6], err, tmp;
+    dbuf<int> cnt[6], err, tmp, rows;
+    ListPtrs LP;
     for (int i = 0; i < 6; ++i) {
         cnt[i].alloc(nbox);
         g->list_off[i].alloc(nbox + 1);
+        LP.off[i] = g->list_off[i].p;
+        LP.cnt[i] = cnt[i].p;
+        LP.idx[i] = nullptr;
     }
-    err.alloc(1);
-    GQ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    // err[0]: a traversal stack overflowed; err[1]: a scratch row overflowed
+    err.alloc(2);
+    GQ_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int), st));
     tmp.alloc(gq_scan_tmp_size(nbox));
-    GQ_LAUNCH(ctx, k_lists, gq_blocks(nbox, kT), kT, 0, T, nbox, 0, (const int *)nullptr, (const int *)nullptr,
-              (const int *)nullptr, (const int *)nullptr, (const int *)nullptr, (const int *)nullptr, (int *)nullptr,
-              (int *)nullptr, (int *)nullptr, (int *)nullptr, (int *)nullptr, (int *)nullptr, cnt[0].p, cnt[1].p,
-              cnt[2].p, cnt[3].p, cnt[4].p, cnt[5].p, err.p);
+    RowTable R;
+    long long rows_n = 0;
+    for (int i = 0; i < 6; ++i) {
+        R.cap[i] = g->list_row_cap > 0 ? g->list_row_cap : kRowCap[i];
+        R.base[i] = rows_n;
+        rows_n += (long long)nbox * R.cap[i];
+    }
+    rows.alloc((size_t)rows_n);
+    GQ_LAUNCH(ctx, k_lists, gq_blocks(nbox, kT), kT, 0, T, nbox, (int)E_ROWS, LP, R, rows.p, err.p, err.p + 1);
     int tot[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < 6; ++i) {
         gq_exclusive_scan(ctx, cnt[i].p, g->list_off[i].p, nbox, tmp.p);
         GQ_CUDA(cudaMemcpyAsync(&tot[i], g->list_off[i].p + nbox, sizeof(int), cudaMemcpyDeviceToHost, st));
     }
+    int herr[2] = {0, 0};
+    GQ_CUDA(cudaMemcpyAsync(herr, err.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     GQ_CUDA(cudaStreamSynchronize(st));
     for (int i = 0; i < 6; ++i) {
         g->list_size[i] = tot[i];
         g->list_idx[i].alloc(tot[i]);
+        LP.idx[i] = g->list_idx[i].p;
     }
-    GQ_LAUNCH(ctx, k_lists, gq_blocks(nbox, kT), kT, 0, T, nbox, 1, (const int *)g->list_off[0].p,
-              (const int *)g->list_off[1].p, (const int *)g->list_off[2].p, (const int *)g->list_off[3].p,
-              (const int *)g->list_off[4].p, (const int *)g->list_off[5].p, g->list_idx[0].p, g->list_idx[1].p,
-              g->list_idx[2].p, g->list_idx[3].p, g->list_idx[4].p, g->list_idx[5].p, (int *)nullptr, (int *)nullptr,
-              (int *)nullptr, (int *)nullptr, (int *)nullptr, (int *)nullptr, err.p);
-    int herr = 0;
-    GQ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GQ_CUDA(cudaStreamSynchronize(st));
-    GQ_REQUIRE(herr == 0, GQ_ERR_UNSUPPORTED, "list construction: traversal stack overflow");
+    if (herr[1] == 0) {
+        GQ_LAUNCH(ctx, k_lists_compact, gq_blocks((long long)nbox * 32, 256), 256, 0, nbox, LP, R, (const int *)rows.p);
+    } else {   // a row overflowed: enumerate again into the exact CSR rows
+        GQ_LAUNCH(ctx, k_lists, gq_blocks(nbox, kT), kT, 0, T, nbox, (int)E_FILL, LP, R, (int *)nullptr, err.p,
+                  err.p + 1);
+        GQ_CUDA(cudaMemcpyAsync(herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GQ_CUDA(cudaStreamSynchronize(st));
+    }
+    g->lists_fill_passes = herr[1] == 0 ? 1 : 2;
+    int herr0 = herr[0];
+    GQ_REQUIRE(herr0 == 0, GQ_ERR_UNSUPPORTED, "list construction: traversal stack overflow");
     gq_build_far_boxes(g);
 }

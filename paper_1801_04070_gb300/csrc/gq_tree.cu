@@ -361,23 +361,25 @@ __global__ void k_emit_children(int nl, int next_start, const uint64_t *__restri
     child[j] = make_int4(ch[0], ch[1], ch[2], ch[3]);
 }
 
-// particles owned by a subdividing level-l box move to the child holding
-// them when eligible for level l+1
-__global__ void k_own_update(long long n, int l, int lstart, int lend, const uint64_t *__restrict__ K,
-                             const int *__restrict__ elig, const int4 *__restrict__ child, int *__restrict__ owner) {
+// Ownership (Sec. 4.3): a particle descends from the root into the child
+// holding it while it is eligible for that child's level and the child
+// exists; the box where it stops owns it.  One walk per particle once the
+// box tree is final (the levels' child tables in bchild).
+__global__ void k_owner_walk(long long n, int nlev, const uint64_t *__restrict__ K, const int *__restrict__ elig,
+                             const int4 *__restrict__ bchild, int *__restrict__ owner) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int o = owner[i];
-    if (o < lstart || o >= lend || elig[i] < l + 1) return;
-    int4 c = child[o - lstart];
-    int q = (int)((K[i] >> (2 * (GQ_KEYBITS - (l + 1)))) & 3);
-    int nc = q == 0 ? c.x : q == 1 ? c.y : q == 2 ? c.z : c.w;
-    if (nc >= 0) owner[i] = nc;
-}
-
-__global__ void k_fill_int(long long n, int v, int *__restrict__ a) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = v;
+    const uint64_t k = K[i];
+    const int e = elig[i];
+    int o = 0;
+    for (int l = 0; l + 1 < nlev && e >= l + 1; ++l) {
+        int4 c = bchild[o];
+        int q = (int)((k >> (2 * (GQ_KEYBITS - (l + 1)))) & 3);
+        int nc = q == 0 ? c.x : q == 1 ? c.y : q == 2 ? c.z : c.w;
+        if (nc < 0) break;
+        o = nc;
+    }
+    owner[i] = o;
 }
 
 // de-interleave a Morton key into box coordinates
@@ -709,8 +711,6 @@ void gq_build_all(gq_geom *g) {
         flag.alloc(N);
         P.alloc(N + 1);
         scan_tmp.alloc(gq_scan_tmp_size(N));
-        owner.alloc(N);
-        GQ_LAUNCH(ctx, k_fill_int, gq_blocks(N, kT), kT, 0, N, 0, owner.p);
         lstart = {0, 1};
         for (int l = 0;; ++l) {
             LevelBufs &cur = *lv[l];
@@ -742,8 +742,6 @@ void gq_build_all(gq_geom *g) {
             GQ_LAUNCH(ctx, k_emit_children, gq_blocks(nl, kT), kT, 0, nl, next_start, (const uint64_t *)cur.key.p,
                       (const int *)coff.p, (const int4 *)cbeg.p, (const int4 *)cend.p, lstart[l], cur.child.p, nxt.key.p,
                       nxt.beg.p, nxt.end.p, nxt.par.p);
-            GQ_LAUNCH(ctx, k_own_update, gq_blocks(N, kT), kT, 0, N, l, lstart[l], lstart[l + 1], (const uint64_t *)K.p,
-                      (const int *)elig.p, (const int4 *)cur.child.p, owner.p);
             if (total == 0) {
                 lv.pop_back();
                 break;
@@ -774,6 +772,9 @@ void gq_build_all(gq_geom *g) {
                       g->bparent.p, g->bchild.p);
             GQ_CUDA(cudaMemcpyAsync(belig.p + lstart[l], B.elig.p, sizeof(int) * B.n, cudaMemcpyDeviceToDevice, st));
         }
+        owner.alloc(N);
+        GQ_LAUNCH(ctx, k_owner_walk, gq_blocks(N, kT), kT, 0, N, g->nlev, (const uint64_t *)K.p, (const int *)elig.p,
+                  (const int4 *)g->bchild.p, owner.p);
     };
     build_levels(nullptr, 0);
     if (g->prm.level_restrict) {
