@@ -109,11 +109,15 @@ Ext device_extent(gq_geom *g, int mode) {
 }
 
 // ------------------------------------------------------------------ A3: association
-__global__ void k_cell_of_centre(int nc, const double *__restrict__ c_xy, double x0, double y0, double cell, int ncx,
-                                 int ncy, uint32_t *__restrict__ key, int *__restrict__ val) {
+// Grid cells of the association search: cell index floor((x - x0) * inv_cell)
+// for centres and targets alike.  The map is monotone in x and within a few
+// ulps of (x - x0) / cell, so a centre within 0.8 cell widths of a target
+// (the search radius is below that) is in a cell adjacent to the target's.
+__global__ void k_cell_of_centre(int nc, const double *__restrict__ c_xy, double x0, double y0, double inv_cell,
+                                 int ncx, int ncy, uint32_t *__restrict__ key, int *__restrict__ val) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
-    int gx = (int)floor((c_xy[2 * c] - x0) / cell), gy = (int)floor((c_xy[2 * c + 1] - y0) / cell);
+    int gx = (int)floor((c_xy[2 * c] - x0) * inv_cell), gy = (int)floor((c_xy[2 * c + 1] - y0) * inv_cell);
     gx = min(max(gx, 0), ncx - 1);
     gy = min(max(gy, 0), ncy - 1);
     key[c] = (uint32_t)(gy * ncx + gx);
@@ -124,7 +128,7 @@ __global__ void k_cell_of_centre(int nc, const double *__restrict__ c_xy, double
 // cells and candidate lists: off-surface targets by cell (targets outside the
 // searched grid after them), on-surface targets last
 __global__ void k_cell_of_target(int nt, const double *__restrict__ tgt_xy, const int *__restrict__ tgt_on, double x0,
-                                 double y0, double cell, int ncx, int ncy, uint32_t *__restrict__ key,
+                                 double y0, double inv_cell, int ncx, int ncy, uint32_t *__restrict__ key,
                                  int *__restrict__ val) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
@@ -132,7 +136,7 @@ __global__ void k_cell_of_target(int nt, const double *__restrict__ tgt_xy, cons
     if (tgt_on[t] >= 0) {
         k = ncell + 1;
     } else {
-        double fgx = floor((tgt_xy[2 * t] - x0) / cell), fgy = floor((tgt_xy[2 * t + 1] - y0) / cell);
+        double fgx = floor((tgt_xy[2 * t] - x0) * inv_cell), fgy = floor((tgt_xy[2 * t + 1] - y0) * inv_cell);
         if (fgx >= -1 && fgx <= ncx && fgy >= -1 && fgy <= ncy) {
             int gx = min(max((int)fgx, 0), ncx - 1), gy = min(max((int)fgy, 0), ncy - 1);
             k = (uint32_t)gy * (uint32_t)ncx + (uint32_t)gx;
@@ -144,8 +148,8 @@ __global__ void k_cell_of_target(int nt, const double *__restrict__ tgt_xy, cons
     val[t] = t;
 }
 
-// centres in cell order as float (x, y, threshold): the threshold bounds the
-// squared distance of any centre the exact test could accept
+// centres in cell order as float (x, y, threshold, 1/r): the threshold bounds
+// the squared distance of any centre the exact test could accept
 __global__ void k_cell_floats(int n, const int *__restrict__ items, const double *__restrict__ c_xy,
                               const double *__restrict__ c_r, double slack, double delta, float4 *__restrict__ cf) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,7 +157,7 @@ __global__ void k_cell_floats(int n, const int *__restrict__ items, const double
     int c = items[k];
     double lim = slack * c_r[c] * 1.001 + delta;
     cf[k] = make_float4((float)c_xy[2 * c], (float)c_xy[2 * c + 1], __double2float_ru(lim * lim * 1.001),
-                        (float)c_r[c]);
+                        (float)(1.0 / c_r[c]));
 }
 
 __global__ void k_cell_bounds(int n, const uint32_t *__restrict__ key, int *__restrict__ start, int *__restrict__ end) {
@@ -167,12 +171,20 @@ __global__ void k_cell_bounds(int n, const uint32_t *__restrict__ key, int *__re
 // On-surface targets use the centre pair of their base node; an off-surface
 // target takes the centre minimising |t-c|^2/r^2 (lowest id on ties) if that
 // ratio is <= slack^2, else it is a point target.
+//
+// The candidates of the 3 x 3 cells around the target are scanned twice in
+// FP32.  With df the FP32 distance (|df - |t - c|| <= delta), every candidate
+// has rho = |t - c| / r in [lo, hi] = [(df - delta) / r, (df + delta) / r]
+// (each widened by 1e-5 for the FP32 roundings).  The first scan finds the
+// smallest hi; the exact minimiser, and every candidate tied with it, has
+// lo <= rho <= rho_min <= that bound, so the second scan evaluates the exact
+// FP64 key only for candidates with lo at or below it.
 __global__ void k_associate(int nt, const int *__restrict__ order, const double *__restrict__ tgt_xy,
                             const int *__restrict__ tgt_on,
                             const double *__restrict__ c_xy, const double *__restrict__ c_r,
                             const int *__restrict__ cell_items, const float4 *__restrict__ cell_f,
                             const int *__restrict__ cstart, const int *__restrict__ cend, double x0, double y0,
-                            double cell, int ncx, int ncy, double slack2, float delta, int have_grid,
+                            double inv_cell, int ncx, int ncy, double slack2, float delta, int have_grid,
                             int *__restrict__ kind, int *__restrict__ ctr, int *__restrict__ is_pt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nt) return;
@@ -185,36 +197,42 @@ __global__ void k_associate(int nt, const int *__restrict__ order, const double 
     float txf = (float)tx, tyf = (float)ty;
     int best = -1;
     double bestk = INFINITY;
-    double fgx = floor((tx - x0) / cell), fgy = floor((ty - y0) / cell);
+    double fgx = floor((tx - x0) * inv_cell), fgy = floor((ty - y0) * inv_cell);
     if (have_grid && fgx >= -1 && fgx <= ncx && fgy >= -1 && fgy <= ncy) {
-        int gx = (int)fgx, gy = (int)fgy;
-        float sbest = INFINITY;   // bounds sqrt(bestk) from above: candidates beyond cannot reach it
-        for (int yy = gy - 1; yy <= gy + 1; ++yy) {
-            if (yy < 0 || yy >= ncy) continue;
-            for (int xx = gx - 1; xx <= gx + 1; ++xx) {
-                if (xx < 0 || xx >= ncx) continue;
-                int cid = yy * ncx + xx;
+        const int gx = (int)fgx, gy = (int)fgy;
+        const int y_lo = max(gy - 1, 0), y_hi = min(gy + 1, ncy - 1);
+        const int x_lo = max(gx - 1, 0), x_hi = min(gx + 1, ncx - 1);
+        float hmin = INFINITY;   // smallest upper bound of rho over the candidates
+        for (int yy = y_lo; yy <= y_hi; ++yy)
+            for (int xx = x_lo; xx <= x_hi; ++xx) {
+                const int cid = yy * ncx + xx;
                 for (int k = cstart[cid]; k < cend[cid]; ++k) {
-                    float4 f = cell_f[k];
-                    float fx = txf - f.x, fy = tyf - f.y;
-                    float d2f = fx * fx + fy * fy;
+                    const float4 f = cell_f[k];
+                    const float fx = txf - f.x, fy = tyf - f.y;
+                    const float d2f = fx * fx + fy * fy;
                     if (d2f > f.z) continue;     // cannot pass the slack test
-                    // nor reach the best key so far: |t - c| <= sqrt(bestk) r must hold, and the
-                    // float distance exceeds the exact one by at most delta
-                    float lim = fmaf(sbest, f.w * 1.00002f, delta);
-                    if (d2f > lim * lim * 1.00002f) continue;
-                    int c = cell_items[k];
-                    double dx = tx - c_xy[2 * c], dy = ty - c_xy[2 * c + 1];
-                    double d2 = dx * dx + dy * dy;
-                    double key = d2 / (c_r[c] * c_r[c]);
+                    hmin = fminf(hmin, (sqrtf(d2f) + delta) * f.w * 1.00001f);
+                }
+            }
+        for (int yy = y_lo; yy <= y_hi; ++yy)
+            for (int xx = x_lo; xx <= x_hi; ++xx) {
+                const int cid = yy * ncx + xx;
+                for (int k = cstart[cid]; k < cend[cid]; ++k) {
+                    const float4 f = cell_f[k];
+                    const float fx = txf - f.x, fy = tyf - f.y;
+                    const float d2f = fx * fx + fy * fy;
+                    if (d2f > f.z) continue;
+                    if ((sqrtf(d2f) - delta) * f.w * 0.99999f > hmin) continue;   // lo above the bound
+                    const int c = cell_items[k];
+                    const double dx = tx - c_xy[2 * c], dy = ty - c_xy[2 * c + 1];
+                    const double d2 = dx * dx + dy * dy;
+                    const double key = d2 / (c_r[c] * c_r[c]);
                     if (key < bestk || (key == bestk && c < best)) {
                         bestk = key;
                         best = c;
-                        sbest = fminf(sbest, sqrtf(__double2float_ru(key)) * 1.00001f);
                     }
                 }
             }
-        }
     }
     if (best >= 0 && bestk <= slack2) { kind[t] = 1; ctr[t] = best; is_pt[t] = 0; }
     else { kind[t] = 0; ctr[t] = -1; is_pt[t] = 1; }
@@ -238,8 +256,9 @@ __device__ __forceinline__ uint64_t key1(double v, double lo, double inv_u) {
 // combined particle array: [0, nsrc) sources, [nsrc, nsrc+nc) centres, then point targets
 __global__ void k_keys(int nsrc, int nc, int npt, const double *__restrict__ up_xy, const double *__restrict__ c_xy,
                        const double *__restrict__ c_r, const int *__restrict__ pt_tgt, const double *__restrict__ tgt_xy,
-                       RootInfo R, double tcr_scale, int tcr_shape, int max_level, uint64_t *__restrict__ key,
-                       int *__restrict__ val, int *__restrict__ elig, int *__restrict__ c_lc) {
+                       RootInfo R, double inv_u, double tcr_scale, double kappa_H, int tcr_shape, int max_level,
+                       uint64_t *__restrict__ key, int *__restrict__ val, int *__restrict__ elig,
+                       int *__restrict__ c_lc) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long n = (long long)nsrc + nc + npt;
     if (i >= n) return;
@@ -254,15 +273,23 @@ __global__ void k_keys(int nsrc, int nc, int npt, const double *__restrict__ up_
         int t = pt_tgt[i - nsrc - nc];
         x = tgt_xy[2 * t]; y = tgt_xy[2 * t + 1];
     }
-    const double inv_u = 1.0 / R.u;
     uint64_t kx = key1(x, R.lo_x, inv_u), ky = key1(y, R.lo_y, inv_u);
     if (i >= nsrc && i < nsrc + nc) {
         // deepest level whose TCR (half-width, or with the disk-shaped TCR
         // radius, |b|(1 + t_f)) holds the whole disk, for every box on the key path
         int c = (int)(i - nsrc);
         double r = c_r[c];
-        int lc = -1;
-        for (int l = 0; l <= max_level; ++l) {
+        int lc = -1, l0 = 0;
+        // Levels l with r <= kappa H 2^-l (and at most 23, so that the key's
+        // rounding, one level-30 unit, is below 1/64 of the box) hold the disk
+        // with a margin of a tenth of the box whatever the rounding, so the
+        // scan below would pass them: it starts after them.
+        if (kappa_H > 0 && r > 0) {
+            l0 = min(ilogb(kappa_H / r), min(max_level, GQ_KEYBITS - 7));
+            l0 = max(l0, 0);
+            lc = l0 - 1;
+        }
+        for (int l = l0; l <= max_level; ++l) {
             int64_t ix = (int64_t)(kx >> (GQ_KEYBITS - l)), iy = (int64_t)(ky >> (GQ_KEYBITS - l));
             double hb = ldexp(R.H, -l);
             double bx = R.lo_x + (double)(2 * ix + 1) * hb;
@@ -550,6 +577,7 @@ static void associate(gq_geom *g) {
     double slack = g->prm.assoc_slack;
     double cell = 1.25 * slack * ce.rmax;
     int have_grid = (nc > 0 && cell > 0);
+    const double inv_cell = have_grid ? 1.0 / cell : 0.0;
     int ncx = 1, ncy = 1;
     if (have_grid) {
         double fx = floor((ce.x1 - ce.x0) / cell) + 1, fy = floor((ce.y1 - ce.y0) / cell) + 1;
@@ -570,8 +598,8 @@ static void associate(gq_geom *g) {
     GQ_CUDA(cudaMemsetAsync(cstart.p, 0, sizeof(int) * ncell, ctx->stream));
     GQ_CUDA(cudaMemsetAsync(cend.p, 0, sizeof(int) * ncell, ctx->stream));
     if (have_grid) {
-        GQ_LAUNCH(ctx, k_cell_of_centre, gq_blocks(nc, kT), kT, 0, nc, (const double *)g->c_xy, ce.x0, ce.y0, cell, ncx,
-                  ncy, ckey.p, cval.p);
+        GQ_LAUNCH(ctx, k_cell_of_centre, gq_blocks(nc, kT), kT, 0, nc, (const double *)g->c_xy, ce.x0, ce.y0, inv_cell,
+                  ncx, ncy, ckey.p, cval.p);
         int bits = 1;
         while ((1ll << bits) < ncell) ++bits;
         gq_radix_sort_pairs32(ctx, ckey.p, cval.p, nc, bits);
@@ -590,7 +618,7 @@ static void associate(gq_geom *g) {
         tkey.alloc(nt);
         torder.alloc(nt);
         GQ_LAUNCH(ctx, k_cell_of_target, gq_blocks(nt, kT), kT, 0, nt, (const double *)g->tgt_xy,
-                  (const int *)g->tgt_on, ce.x0, ce.y0, cell, ncx, ncy, tkey.p, torder.p);
+                  (const int *)g->tgt_on, ce.x0, ce.y0, inv_cell, ncx, ncy, tkey.p, torder.p);
         int bits = 1;
         while ((1ll << bits) < ncell + 2) ++bits;
         gq_radix_sort_pairs32(ctx, tkey.p, torder.p, nt, bits);
@@ -599,7 +627,7 @@ static void associate(gq_geom *g) {
         GQ_LAUNCH(ctx, k_associate, gq_blocks(nt, kT), kT, 0, nt, (const int *)torder.p, (const double *)g->tgt_xy,
                   (const int *)g->tgt_on,
                   (const double *)g->c_xy, (const double *)g->c_r, (const int *)cval.p, (const float4 *)cf.p,
-                  (const int *)cstart.p, (const int *)cend.p, ce.x0, ce.y0, cell, ncx, ncy, slack * slack,
+                  (const int *)cstart.p, (const int *)cend.p, ce.x0, ce.y0, inv_cell, ncx, ncy, slack * slack,
                   (float)(delta_assoc * 1.001), have_grid, g->t_kind.p,
                   g->t_ctr.p, is_pt.p);
     g->npt = compact_flags(g, is_pt.p, nt, g->pt_tgt);
@@ -677,9 +705,17 @@ void gq_build_all(gq_geom *g) {
     elig0.alloc(N);
     elig.alloc(N);
     double tcr_scale = (double)(g->prm.tf_den + g->prm.tf_num) / (double)g->prm.tf_den;
+    // A disk of radius r centred in a level-l box lies at distance at most
+    // c0 (h + u) from the box centre (c0 = 1 for the square TCR, sqrt 2 for
+    // the disk; h the half-width, u one level-30 unit <= h/64): with
+    // r <= kappa h, kappa = 0.8 (scale - c0 - 1/32), the fit holds with room.
+    const double c0 = g->prm.tcr_shape == 1 ? 1.4143 : 1.0;
+    const double kappa = 0.8 * (tcr_scale - c0 - 1.0 / 32.0);
+    const double kappa_H = kappa > 0 ? kappa * g->root.H : 0.0;
     GQ_LAUNCH(ctx, k_keys, gq_blocks(N, kT), kT, 0, g->nsrc, g->nc, g->npt, (const double *)g->up_xy,
               (const double *)g->c_xy, (const double *)g->c_r, (const int *)g->pt_tgt, (const double *)g->tgt_xy,
-              g->root, tcr_scale, g->prm.tcr_shape, g->prm.max_level, K.p, V.p, elig0.p, g->c_lc.p);
+              g->root, 1.0 / g->root.u, tcr_scale, kappa_H, g->prm.tcr_shape, g->prm.max_level, K.p, V.p, elig0.p,
+              g->c_lc.p);
     gq_radix_sort_pairs(ctx, K.p, V.p, N, 2 * GQ_KEYBITS);
     GQ_LAUNCH(ctx, k_gather_int, gq_blocks(N, kT), kT, 0, N, (const int *)V.p, (const int *)elig0.p, elig.p);
 
