@@ -320,10 +320,16 @@ __global__ void k_m2l(EvalView E, int nwork, const int *__restrict__ work, const
     }
 }
 
-// ------------------------------------------------------------------ Stage 6b: P2L over List 4 far (warp per box, lane = m)
+// ------------------------------------------------------------------ Stage 6b: P2L over List 4 far
+// Warp per box; a group of G lanes per source, lane m of the group = order m.
+// With p_fmm < 16 (G = 16) the two half-warps take alternate sources of each
+// List 4 far box, so the per-source reciprocal and powers are formed once per
+// 16 orders instead of once per 32 lanes, and add their sums at the end.
 __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, double2 *__restrict__ L) {
-    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, m = threadIdx.x & 31;
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (wid >= nwork) return;
+    const int G = E.P < 16 ? 16 : 32, NS = 32 / G;
+    const int m = lane & (G - 1), h = lane / G;
     int b = work[wid];
     int beg = E.loff[5][b], end = E.loff[5][b + 1];
     if (beg == end) return;
@@ -334,12 +340,15 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
     double2 acc = make_double2(0.0, 0.0);
     for (int i = beg; i < end; ++i) {
         int d = E.lidx[5][i];
-        for (int s = E.src_beg[d]; s < E.src_end[d]; ++s) {
-            double2 y = E.s_xy[s], st = E.str[s];
+        const int s0 = E.src_beg[d], s1 = E.src_end[d];
+        for (int sb = s0; sb < s1; sb += NS) {   // the same trip count in every lane
+            const int s = sb + h;
+            const bool valid = s < s1;
+            double2 y = E.s_xy[valid ? s : sb], st = valid ? E.str[s] : make_double2(0.0, 0.0);
             double2 w = make_double2(y.x - zc.x, y.y - zc.y);
             double n2 = w.x * w.x + w.y * w.y, inv = gq_rcp(n2);
             double2 winv = make_double2(w.x * inv, -w.y * inv);      // 1/w
-            double2 um = lane_powers(cscale(winv, rho), m, 32);      // (rho/w)^m
+            double2 um = lane_powers(cscale(winv, rho), m, G);       // (rho/w)^m
             if (E.kernel == GQ_D) {
                 acc = cfma(cmul(st, winv), um, acc);
             } else if (m == 0) {
@@ -349,7 +358,11 @@ __global__ void k_p2l(EvalView E, int nwork, const int *__restrict__ work, doubl
             }
         }
     }
-    if (m <= E.P) {
+    if (G == 16) {
+        acc.x += __shfl_down_sync(0xffffffffu, acc.x, 16);
+        acc.y += __shfl_down_sync(0xffffffffu, acc.y, 16);
+    }
+    if (h == 0 && m <= E.P) {
         double2 *dst = L + (size_t)b * (E.P + 1) + m;
         *dst = cadd(*dst, acc);
     }
