@@ -201,24 +201,27 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ int tab_boxes(int P1) { return 128 / P1; }
 __device__ __forceinline__ int child_of(int4 c4, int q) { return q == 0 ? c4.x : q == 1 ? c4.y : q == 2 ? c4.z : c4.w; }
 
-__global__ void __launch_bounds__(128) k_m2m_t(EvalView E, int lstart, int lend, const double2 *__restrict__ T,
-                                               double2 *__restrict__ M) {
+// The boxes are entries [lstart, lend) of `boxes` (one level's non-leaf boxes
+// with sources below), or box numbers [lstart, lend) when boxes is null.
+__global__ void __launch_bounds__(128) k_m2m_t(EvalView E, const int *__restrict__ boxes, int lstart, int lend,
+                                               const double2 *__restrict__ T, double2 *__restrict__ M) {
     __shared__ double2 sA[4 * 128];
     const int P1 = E.P + 1, bpb = tab_boxes(P1);
-    const int b0 = lstart + blockIdx.x * bpb;
+    const int i0 = lstart + blockIdx.x * bpb;
     for (int i = threadIdx.x; i < bpb * 4 * P1; i += blockDim.x) {
         const int bb = i / (4 * P1), rest = i - bb * 4 * P1, q = rest / P1, k = rest - q * P1;
-        const int b = b0 + bb;
+        const int ib = i0 + bb;
         double2 v = make_double2(0.0, 0.0);
-        if (b < lend) {
-            const int c = child_of(E.bchild[b], q);
+        if (ib < lend) {
+            const int c = child_of(E.bchild[boxes ? boxes[ib] : ib], q);
             if (c >= 0) v = M[(size_t)c * P1 + k];
         }
         sA[i] = v;
     }
     __syncthreads();
-    const int bl = threadIdx.x / P1, m = threadIdx.x - bl * P1, b = b0 + bl;
-    if (bl >= bpb || b >= lend) return;
+    const int bl = threadIdx.x / P1, m = threadIdx.x - bl * P1, ib = i0 + bl;
+    if (bl >= bpb || ib >= lend) return;
+    const int b = boxes ? boxes[ib] : ib;
     int4 c4 = E.bchild[b];
     int ch[4] = {c4.x, c4.y, c4.z, c4.w};
     if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;  // leaf
@@ -2601,9 +2604,10 @@ void gq_eval_all(gq_geom *g, int kernel, const double *dens_dev, double *out_dev
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
         if (m2l_split)
             GQ_LAUNCH(ctx, k_m2m_split, gq_blocks((long long)(e - s) * P1, 128), 128, 0, E, s, e, T.tm2m2, g->M2.p);
-        else
-            GQ_LAUNCH(ctx, k_m2m_t, gq_blocks(e - s, 128 / P1), (128 / P1) * P1, 0, E, s, e,
-                      (const double2 *)T.tm2m, g->M.p);
+        else if (g->m2m_level_start_h[l + 1] > g->m2m_level_start_h[l])
+            GQ_LAUNCH(ctx, k_m2m_t, gq_blocks(g->m2m_level_start_h[l + 1] - g->m2m_level_start_h[l], 128 / P1),
+                      (128 / P1) * P1, 0, E, (const int *)g->m2m_boxes, g->m2m_level_start_h[l],
+                      g->m2m_level_start_h[l + 1], (const double2 *)T.tm2m, g->M.p);
     }
     mark(S_M2M, st);
     if (m2l_split)
@@ -3157,7 +3161,8 @@ void gq_eval_noalloc_impl(gq_geom *g, int kernel, const double *dens_dev, double
     }
     for (int l = g->nlev - 2; l >= 0; --l) {
         int s = g->level_start_h[l], e = g->level_start_h[l + 1];
-        GQ_LAUNCH(ctx, k_m2m_t, gq_blocks(e - s, 128 / P1), (128 / P1) * P1, 0, E, s, e, tm2m, M);
+        GQ_LAUNCH(ctx, k_m2m_t, gq_blocks(e - s, 128 / P1), (128 / P1) * P1, 0, E, (const int *)nullptr, s, e, tm2m,
+                  M);
     }
     if (g->n_far_boxes) {
         size_t sm = sizeof(double) * P1 * P1;

@@ -145,6 +145,8 @@ struct gq_geom {
     dbuf<int> ctr_boxes;       int n_ctr_boxes = 0;  // boxes owning centres
     dbuf<int> pt_boxes;        int n_pt_boxes = 0;   // boxes owning point targets
     dbuf<int> far_boxes;       int n_far_boxes = 0;  // boxes with V or X far entries
+    dbuf<int> m2m_boxes;       int n_m2m_boxes = 0;  // non-leaf boxes with sources below, by level
+    std::vector<int> m2m_level_start_h;              // [nlev+1] level l's part of m2m_boxes
     // evaluation buffers
     dbuf<double2> strength;          // sorted sources: S -> (q, 0), D -> d
     dbuf<unsigned int> qexp;         // largest biased exponent of the strengths (one value)

@@ -537,6 +537,16 @@ __global__ void k_flag_nonempty(int n, const int *__restrict__ beg, const int *_
     if (b < n) flag[b] = end[b] > beg[b];
 }
 
+// boxes whose multipole the upward pass forms from their children's (M2M):
+// not a leaf, sources in the subtree
+__global__ void k_flag_parents(int n, const int4 *__restrict__ bchild, const int *__restrict__ sub_src,
+                               int *__restrict__ flag) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    int4 c = bchild[b];
+    flag[b] = (c.x >= 0 || c.y >= 0 || c.z >= 0 || c.w >= 0) && sub_src[b] > 0;
+}
+
 }  // namespace
 
 // compact indices i in [0, n) with flag[i] != 0 into out (ascending); returns the
@@ -929,6 +939,18 @@ void gq_build_all(gq_geom *g) {
     g->n_ctr_boxes = compact_flags(g, bflag.p, nbox, g->ctr_boxes);
     GQ_LAUNCH(ctx, k_flag_nonempty, gq_blocks(nbox, kT), kT, 0, nbox, (const int *)g->pt_beg.p, (const int *)g->pt_end.p, bflag.p);
     g->n_pt_boxes = compact_flags(g, bflag.p, nbox, g->pt_boxes);
+    // the M2M parents, kept in box order, so that level l's are the entries
+    // from the compaction offset of its first box to that of the next level's
+    GQ_LAUNCH(ctx, k_flag_parents, gq_blocks(nbox, kT), kT, 0, nbox, (const int4 *)g->bchild.p,
+              (const int *)g->sub_src.p, bflag.p);
+    g->n_m2m_boxes = compact_flags(g, bflag.p, nbox, g->m2m_boxes);
+    dbuf<int> m2m_ls;
+    m2m_ls.alloc(g->nlev + 1);
+    GQ_LAUNCH(ctx, k_gather_int, gq_blocks(g->nlev + 1, kT), kT, 0, (long long)(g->nlev + 1),
+              (const int *)g->level_start.p, (const int *)g->cf_pos.p, m2m_ls.p);
+    g->m2m_level_start_h.assign(g->nlev + 1, 0);
+    GQ_CUDA(cudaMemcpyAsync(g->m2m_level_start_h.data(), m2m_ls.p, sizeof(int) * (g->nlev + 1),
+                            cudaMemcpyDeviceToHost, st));
     GQ_CUDA(cudaStreamSynchronize(st));
     pt.mark("work_lists");
 
