@@ -45,6 +45,7 @@ def test_host_entry_points(libpath):
     assert L.gq_build(None) == -1
     assert L.gq_eval(None, 0, None, None, None) == -1
     assert L.gq_apply(None, 0, -0.5, None, None) == -1
+    assert L.gq_lists_check(None, 0, None) == -1
     assert L.gq_last_error(None) == b"null context"
     n = C.c_int64(-1)
     assert L.gq_memory_cached(C.byref(n)) == 0 and n.value >= 0
